@@ -1,0 +1,369 @@
+"""Benchmark: forward + backward Monte Carlo direct-illumination shading.
+
+A step is one pass of the hot path over one synthetic batch: probe sampling
+tables, LBVH over this iteration's mesh, G-buffer ray cast, forward MIS
+estimator with shadow rays, and the adjoint (Sec. 3-4 of the paper).  The
+workload is the 512 x 512, 16 spp (8 light / 4 cosine / 4 GGX) view of the
+~198k-triangle sphere-union mesh with 1024^2 textures and a 512 x 256
+three-lobe probe.  The metric is shaded samples per second (covered pixels x
+spp, forward + backward), with the dominant kernel's HBM roofline fraction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mcdi|reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (weak scaling; the
+path has no data exchange that this single-GPU build performs).  The
+``reference`` arm times the FP64 CPU oracle on a bounded pixel sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd MC shading Msamples/s & %HBM roofline at 512² 16spp"
+UNIT = "Msamples/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed harness
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(", ") for r in self.out.strip().splitlines() if r.strip()]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if r[5 + k].strip() == "Active"})
+        busy = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi, scenes
+    from paper_2206_03380_gb300.pipeline import ShadingPipeline
+
+    local = dist_env()[2]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scenes.sphere_union_scene(seed=scenes.BASE_SEED + 2 + 1000 * rank if world > 1 else scenes.BASE_SEED + 2)
+    pipe = ShadingPipeline(sc, device=dev)
+    N, H, W = pipe.N, pipe.H, pipe.W
+    rng = np.random.default_rng(3)
+    g_up = [torch.from_numpy(rng.normal(size=(N, H, W, 4)).astype(np.float32)).to(dev) for _ in range(3)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    stages = ["probe_cdf", "bvh_build", "primary_cast", "shade_fwd", "shade_bwd"]
+    n_launch = {"probe_cdf": 2, "bvh_build": 3 + 12 + 1 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 1,
+                "shade_fwd": 1, "shade_bwd": 1}
+
+    def one_step(ev=None):
+        calls = [pipe.build_probe, pipe.build_bvh, pipe.primary, pipe.forward,
+                 lambda: pipe.backward(*g_up)]
+        for k, f in enumerate(calls):
+            if ev is not None:
+                ev[k].record(stream)
+            f()
+        if ev is not None:
+            ev[len(calls)].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    covered = pipe.covered_pixels()
+    samples_per_step = covered * sc.spp
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            one_step(evs[s])
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+    stage_ms = {st: [evs[s][k].elapsed_time(evs[s][k + 1]) for s in range(args.steps)] for k, st in enumerate(stages)}
+    step_ms = [evs[s][0].elapsed_time(evs[s][-1]) for s in range(args.steps)]
+    dev_ms = float(np.mean(step_ms))
+    dev_ms_max = max_over_ranks(dev_ms, dev)
+    total_samples = sum_over_ranks(float(samples_per_step), dev)
+    value = total_samples / (dev_ms_max * 1e-3) / 1e6
+
+    # e2e: host inputs -> device -> the same step -> host outputs, per step
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
+               [("verts", sc.verts), ("vnrm", sc.vnrm), ("tris", sc.tris), ("env", sc.env)]}
+    host_g = [g.cpu().pin_memory() for g in g_up]
+    outs_dev = [pipe.c_d, pipe.kd_out, pipe.c_s, pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env]
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs_dev]
+    h2d = sum(t.numel() * t.element_size() for t in list(host_in.values()) + host_g)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def e2e_step():
+        pipe.verts.copy_(host_in["verts"], non_blocking=True)
+        pipe.vnrm.copy_(host_in["vnrm"], non_blocking=True)
+        pipe.tris.copy_(host_in["tris"], non_blocking=True)
+        pipe.env.copy_(host_in["env"], non_blocking=True)
+        for d, h in zip(g_up, host_g):
+            d.copy_(h, non_blocking=True)
+        one_step()
+        for h, d in zip(host_out, outs_dev):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    e2e_value = total_samples / (e2e_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / event time)
+    avg = {st: float(np.mean(v)) for st, v in stage_ms.items()}
+    P = N * H * W
+    words = (sc.spp + 31) // 32
+    bvh_bytes = sum(mcdi.bvh_sizes(sc.tris.shape[0])[:2])
+    probe_bytes = sc.env.nbytes + pipe.probe.cond.numel() * 4 + pipe.probe.marg.numel() * 4
+    algo = {
+        # G-buffer planes in (4 x 16 B), c_d / kd_out / c_s out (3 x 16 B), mask out; BVH, probe, tables once
+        "shade_fwd": P * (64 + 48 + 4 * words) + bvh_bytes + probe_bytes,
+        # G-buffer + upstream (3 x 16 B) + mask in, three gradient planes out; probe in, probe gradient in+out
+        "shade_bwd": P * (64 + 48 + 4 * words + 48) + probe_bytes + 2 * sc.env.nbytes,
+    }
+    dom = max(("shade_fwd", "shade_bwd"), key=lambda s: avg[s])
+    peak, peak_kind = peaks()
+    achieved = algo[dom] / (avg[dom] * 1e-3) / 1e9
+    clocks = clk.summary()
+    launches = args.steps * sum(n_launch.values())
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dev_ms_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded sphere-union SDF mesh, value-noise "
+                                                   "textures, log-normal probe with sun lobes)",
+        "config": {"workload": sc.name, "views": N, "width": W, "height": H, "spp": sc.spp,
+                   "split": [sc.n_light, sc.n_cos, sc.n_ggx], "triangles": int(sc.tris.shape[0]),
+                   "probe": [int(sc.env.shape[1]), int(sc.env.shape[0])], "texture": int(sc.tex_kd.shape[0]),
+                   "pixels_covered": covered, "samples_per_step": samples_per_step,
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "stage_ms": {k: round(v, 4) for k, v in avg.items()},
+        "wall_s": round(wall, 3),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 5), "traffic": None, "peak_source": peak_kind,
+                     "algorithmic_bytes": int(algo[dom])},
+        "clocks": clocks,
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": launches,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
+    return result
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+def oracle_step(orc, sc, pix, tables=None):
+    """One bounded oracle pass: probe tables, G-buffer rows, forward with records, adjoint."""
+    cond, marg, _, tot = orc.envmap_cdf(sc.env)
+    c32, m32 = cond.astype(np.float32), marg.astype(np.float32)
+    W, H = sc.width, sc.height
+    gb = orc.primary_cast(sc.verts, sc.vnrm, sc.tris, sc.cams[0], W, H, pix, sc.tex_kd, sc.tex_korm, sc.uvmap)
+    keep = gb[:, 3] > 0
+    rows = gb[keep].astype(np.float32)
+    p = pix[keep]
+    cam = np.tile(sc.cams[0, :3].astype(np.float64), (len(p), 1))
+    ctr = np.stack([p, np.zeros(len(p))], 1).astype(np.uint32)
+    out, vis, recs = orc.shade_fwd(sc.verts, sc.tris, sc.env, c32, m32, tot, rows, cam, ctr, n_light=sc.n_light,
+                                   n_cos=sc.n_cos, n_ggx=sc.n_ggx, seed=sc.seed)
+    g = np.ones((len(p), 9))
+    orc.frozen_adjoint(recs, orc.param_rows(rows), cam, out[:, 9].astype(np.int32),
+                       sc.env[..., :3].reshape(-1, 3).astype(np.float64), g)
+    return len(p) * sc.spp
+
+
+def oracle_pixel_sample(sc, n_pix, salt=0):
+    rng = np.random.default_rng(1234 + salt)
+    return np.sort(rng.choice(sc.width * sc.height, size=n_pix, replace=False)).astype(np.int32)
+
+
+def omp_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(sc, n_pix=1024):
+    import oracle
+
+    orc = oracle
+    orc.load()
+    pix = oracle_pixel_sample(sc, n_pix)
+    t0 = time.perf_counter()
+    samples = oracle_step(orc, sc, pix)
+    dt = time.perf_counter() - t0
+    return {"value": round(samples / dt / 1e6, 6), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+            "sample": f"{n_pix} seeded pixels ({samples} covered-pixel samples) of the same view: probe tables, "
+                      f"G-buffer rows, forward with brute-force visibility over all {sc.tris.shape[0]} triangles, "
+                      f"adjoint", "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+
+    from paper_2206_03380_gb300 import scenes
+
+    sc = scenes.sphere_union_scene()
+    oracle.load()
+    for k in range(args.warmup):
+        oracle_step(oracle, sc, oracle_pixel_sample(sc, 8, salt=100 + k))
+    times, samples = [], 0
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        pix = oracle_pixel_sample(sc, args.ref_pixels, salt=k)
+        t0 = time.perf_counter()
+        samples += oracle_step(oracle, sc, pix)
+        times.append(time.perf_counter() - t0)
+    total = time.perf_counter() - t_all
+    value = samples / sum(times) / 1e6
+    cb = {"value": round(value, 6), "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+          "sample": f"{args.ref_pixels} seeded pixels per step of the {sc.name} workload (brute-force visibility "
+                    f"over all triangles, FP64)"}
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": sc.name, "pixels_per_step": args.ref_pixels, "spp": sc.spp,
+                       "triangles": int(sc.tris.shape[0])},
+            "cpu_baseline": cb, "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}, "wall_s": round(total, 2)}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mcdi", choices=["mcdi", "reference"])
+    ap.add_argument("--cpu-pixels", type=int, default=1024)
+    ap.add_argument("--ref-pixels", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        rank, world = init_dist("gloo")
+        res = run_reference(args, rank, world)
+    else:
+        import torch
+
+        rank, world = init_dist("nccl" if torch.cuda.is_available() else "gloo")
+        res = run_gpu(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

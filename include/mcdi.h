@@ -1,0 +1,191 @@
+/*
+ * mcdi.h -- C ABI of the GB300 (sm_103a) differentiable Monte Carlo
+ * direct-illumination library: the shading hot path of Hasselgren, Hofmann and
+ * Munkberg, "Shape, Light, and Material Decomposition from Images using Monte
+ * Carlo Rendering and Denoising" (NeurIPS 2022).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an mcdi_status and never aborts, traps or prints.
+ *   On failure mcdi_last_error() (per calling thread) holds a one-line reason.
+ * - Every pointer argument named as a buffer is a DEVICE pointer on the
+ *   current CUDA device, owned by the caller; the library keeps no reference
+ *   after the call returns.  Host-side arguments are marked "host".
+ * - Work is enqueued asynchronously on the caller's stream (a cudaStream_t
+ *   passed as void*; NULL = the legacy default stream).  No entry point
+ *   synchronises the device or allocates device memory; scratch is passed in
+ *   by the caller, sized by the matching *_sizes query.
+ * - float4 / int arrays are 16-byte aligned (checked: MCDI_INVALID_ARG).
+ * - Images are N views x H rows x W columns, row-major, one float4 per pixel.
+ * - Bad shapes, NULL buffers, misalignment or an invalid sample split give
+ *   MCDI_INVALID_ARG before anything is enqueued; a failed launch gives
+ *   MCDI_DEVICE_ERROR.
+ */
+#ifndef MCDI_H
+#define MCDI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MCDI_API __attribute__((visibility("default")))
+#else
+#define MCDI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCDI_OK = 0,
+    MCDI_INVALID_ARG = 1,
+    MCDI_UNSUPPORTED = 2,
+    MCDI_OOM = 3,
+    MCDI_TIMEOUT = 4,
+    MCDI_DEVICE_ERROR = 5
+} mcdi_status;
+
+/* Reason for the last failure on the calling thread ("" if none). */
+MCDI_API const char* mcdi_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+MCDI_API int mcdi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Light probe sampling distribution.
+ * Sec. 4.1: light importance sampling with a piecewise-constant 2D
+ * distribution over the HDR probe, recomputed whenever the probe changes.
+ *
+ * env      [H][W] float4 lat-long probe (y up; row j spans polar angle
+ *          [pi j/H, pi (j+1)/H), column i azimuth [2 pi i/W, 2 pi (i+1)/W);
+ *          rgb radiance, w ignored).  1 <= W <= 8192, 1 <= H <= 4096.
+ * Texel weight w_ij = max((r+g+b)/3, 0) * sin(pi (j+0.5)/H); sums in FP64.
+ * cond_cdf [H][W+1] float out: cond[j][k] = sum_{i<k} w_ij / R_j, cond[j][W] = 1
+ *          (uniform k/W for a black row).
+ * marg_cdf [H+1]    float out: marg[k] = sum_{j<k} R_j / T, marg[H] = 1
+ *          (uniform k/H for a black probe).
+ * row_sum  [H]      double out: R_j.   total [1] double out: T.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_build_envmap_cdf(const float* env, int W, int H, float* cond_cdf, float* marg_cdf,
+                                  double* row_sum, double* total, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Shadow-ray acceleration structure: a linear BVH over the triangle mesh
+ * extracted in each iteration (Sec. 3; the paper traces shadow rays with
+ * hardware ray tracing, Sec. 6 "Compute resources").
+ *
+ * mcdi_bvh_sizes (host): bytes of the node array, the triangle-record array
+ * and the build scratch for n_tris triangles (1 <= n_tris <= 2^27).
+ * mcdi_build_bvh: verts [n_verts][3] float, tris [n_tris][3] int32 (vertex
+ * indices, checked in range on the device: a bad index yields a degenerate
+ * triangle, never an out-of-bounds read).  Writes `nodes` and `tri_records`
+ * (opaque layout, valid until the caller frees them); `scratch` is
+ * overwritten.  Build = Morton codes -> LSD radix sort -> Karras hierarchy ->
+ * bottom-up bounds.  Deterministic for a given input.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_bvh_sizes(int n_tris, size_t* node_bytes, size_t* tri_bytes, size_t* scratch_bytes);
+MCDI_API mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
+                           void* tri_records, void* scratch, size_t scratch_bytes, void* stream);
+
+/* A built BVH as the shading kernels read it (host struct, device pointers). */
+typedef struct {
+    const void* nodes;
+    const void* tri_records;
+    int n_tris;
+} mcdi_bvh_view;
+
+/* Pinhole camera (14 floats): origin, right, up, forward (orthonormal),
+ * tan(fovy/2), aspect = W/H.  Pixel (x, y), y down, looks along
+ * normalize(forward + sx right + sy up), sx = (2(x+.5)/W - 1) tan aspect,
+ * sy = (1 - 2(y+.5)/H) tan. */
+typedef struct {
+    float origin[3], right[3], up[3], forward[3];
+    float tan_half_fovy, aspect;
+} mcdi_camera;
+
+/* ------------------------------------------------------------------------
+ * Primary visibility -> G-buffer.  The paper rasterises it (nvdiffrast,
+ * Sec. 3.1); this closest-hit ray cast on the same BVH stands in.
+ * cams [N] mcdi_camera (device).  Hit: position and normal are barycentric
+ * interpolations of verts / vnrm ([n_verts][3] float); k_d and k_orm are
+ * bilinear, clamp-to-edge lookups of tex_kd / tex_korm ([S][S] float4) at the
+ * planar coordinate ((x - uvmap[0]) uvmap[2], (z - uvmap[1]) uvmap[2])
+ * (uvmap: host, 3 floats).  Outputs [N][H][W] float4:
+ *   gb_pos (x, y, z, coverage), gb_nrm (N, 0), gb_kd (r, g, b, 0),
+ *   gb_korm (o, r, m, 0); a miss writes zeros.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* verts, const float* vnrm, const int* tris,
+                              int n_verts, const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                              const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos,
+                              float* gb_nrm, float* gb_kd, float* gb_korm, void* stream);
+
+/* Sampling and shading parameters (host struct). */
+typedef struct {
+    int n_light;              /* samples of the probe distribution            */
+    int n_cos;                /* cosine-weighted samples (diffuse lobe)       */
+    int n_ggx;                /* GGX visible-normal samples (specular lobe)   */
+    int decorrelate_bwd;      /* 1: backward draws its own samples (App. D)   */
+    unsigned long long seed;  /* Philox4x32-10 key                            */
+    float tau;                /* shadow leakage, H = 1 - tau on a hit (App. A) */
+    float ray_eps;            /* shadow-ray origin offset along the normal    */
+} mcdi_shade_params;
+
+/* ------------------------------------------------------------------------
+ * Forward Monte Carlo direct illumination (Sec. 3.1 estimator, Sec. 4.1 MIS
+ * with the balance heuristic, Sec. 4.2 light separation).
+ *
+ * Per covered pixel, spp = n_light + n_cos + n_ggx samples (1 <= spp <= 1024;
+ * sample j < n_light is a probe sample, then n_cos cosine, then n_ggx GGX).
+ * Sample j draws two 24-bit uniforms from Philox4x32-10 with key = seed and
+ * counter = (pixel index y*W + x, view, j, 0).  Each sample contributes
+ *   g(w) / sum_k n_k p_k(w),   g = L(w) H(w) f(w, wo) (n.w)^+,
+ * split into c_d (L H (n.w)/pi, demodulated diffuse) and c_s (specular GGX,
+ * alpha = max(r^2, 1e-4), Smith height-correlated masking, Schlick Fresnel
+ * with F0 = 0.04 (1 - m) + k_d m); kd_out = k_d (1 - m).  Shadow rays start
+ * at p + ray_eps n and test every triangle (two-sided, t > 0); the probe is
+ * looked up at the nearest texel.
+ *
+ * Inputs: G-buffer planes [N][H][W] float4 as written by mcdi_primary_cast;
+ * env [Hp][Wp] float4; the three tables of mcdi_build_envmap_cdf (total is
+ * read on the device); cams [N] (origins give the view vectors).
+ * Outputs [N][H][W] float4 (w = 0): c_d, kd_out, c_s.
+ * vis_mask (nullable) [N][H][W][ceil(spp/32)] uint32: bit j = sample j's
+ * shadow ray was blocked; the backward pass can reuse it.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                              const float* marg_cdf, const double* total, const float* gb_pos,
+                              const float* gb_nrm, const float* gb_kd, const float* gb_korm,
+                              const mcdi_camera* cams, int N, int H, int W, const mcdi_shade_params* params,
+                              float* c_d, float* kd_out, float* c_s, uint32_t* vis_mask, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Hand-written adjoint of mcdi_shade_mc_fwd (Sec. 4.1: detached importance
+ * sampling, the forward seed reused in the backward pass; Sec. 3.1: shadow
+ * visibility detached).  Samples are regenerated from the same Philox
+ * counters (stream word 1 instead of 0 when decorrelate_bwd is set), sample
+ * directions, MIS denominators and visibility are held constant, and the
+ * gradient of  sum <g_cd, c_d> + <g_kdout, kd_out> + <g_cs, c_s>  is taken
+ * with respect to the G-buffer normal (before normalisation), k_d, k_orm and
+ * the probe texels.
+ *
+ * Same scene / G-buffer / table / camera inputs and params as the forward.
+ * g_cd, g_kdout, g_cs: [N][H][W] float4 upstream gradients.
+ * vis_mask: the forward's mask (reused when not decorrelating), or NULL to
+ *           re-trace the shadow rays.
+ * Outputs (overwritten) [N][H][W] float4: g_kd (rgb), g_korm (o = 0, r, m),
+ * g_nrm (xyz).  g_env [Hp][Wp] float4 is ACCUMULATED (rgb; zero it first).
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                              const float* marg_cdf, const double* total, const float* gb_pos,
+                              const float* gb_nrm, const float* gb_kd, const float* gb_korm,
+                              const mcdi_camera* cams, int N, int H, int W, const mcdi_shade_params* params,
+                              const float* g_cd, const float* g_kdout, const float* g_cs,
+                              const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm, float* g_env,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCDI_H */

@@ -93,7 +93,7 @@ def _declare(lib):
         "orc_primary_cast": (None, [P, P, P, i, P, i, i, P, i, P, P, i, P, P]),
         "orc_shade_fwd": (None, [P, P, i, P, i, i, P, P, d, P, P, P, i, _Params, P, P, P]),
         "orc_frozen_eval": (None, [P, i, i, P, P, P, P, P]),
-        "orc_frozen_adjoint": (None, [P, i, i, P, P, P, P, P, P, P]),
+        "orc_frozen_adjoint": (None, [P, i, i, P, P, P, P, P, P, P, P, P]),
         "orc_sample_rec_size": (i, []),
         "orc_pdf_light_n": (None, [P, P, i, i, d, P, i, P]),
         "orc_sample_light_n": (None, [P, P, i, i, d, P, i, P, P, P]),
@@ -335,16 +335,21 @@ def frozen_eval(recs, prow, cam_pos_rows, spec_on, env3):
     return out
 
 
-def frozen_adjoint(recs, prow, cam_pos_rows, spec_on, env3, g):
+def frozen_adjoint(recs, prow, cam_pos_rows, spec_on, env3, g, with_scale=False):
+    """Adjoint of frozen_eval.  Returns (grad (n, 9), genv (texels, 3)); with
+    with_scale also the per-component sums of |per-sample contribution|."""
     recs = np.ascontiguousarray(recs)
     n, spp = recs.shape
     prow = _f64(prow).reshape(n, 12)
     env3 = _f64(env3)
     grad = np.zeros((n, 9))
     genv = np.zeros_like(env3)
+    scale = np.zeros((n, 9)) if with_scale else None
+    genv_scale = np.zeros_like(env3) if with_scale else None
     load().orc_frozen_adjoint(_p(recs), spp, n, _p(prow), _p(_f64(cam_pos_rows)), _p(_i32(spec_on)), _p(env3),
-                              _p(_f64(g)), _p(grad), _p(genv))
-    return grad, genv
+                              _p(_f64(g)), _p(grad), _p(genv), _p(scale) if with_scale else None,
+                              _p(genv_scale) if with_scale else None)
+    return (grad, genv, scale, genv_scale) if with_scale else (grad, genv)
 
 
 # ---------------------------------------------------------------- batch forms (tests)

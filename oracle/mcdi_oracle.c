@@ -708,99 +708,154 @@ void orc_frozen_eval(const orc_sample_rec* recs, int spp, int n_pix, const doubl
     }
 }
 
+/* Per-pixel constants of the frozen estimator's adjoint. */
+typedef struct {
+    double n[3], wo[3], lN, co, alpha, a2, r, m, F0[3];
+    const double* kd;
+} adj_pixel;
+
+static int adj_setup(const double* P, const double* cam, adj_pixel* A) {
+    double N[3] = {P[0], P[1], P[2]};
+    A->lN = norm3(N);
+    if (!(A->lN > 0.0)) return 0;
+    for (int k = 0; k < 3; ++k) A->n[k] = N[k] / A->lN;
+    A->kd = P + 3;
+    A->r = P[7];
+    A->m = P[8];
+    A->alpha = orc_alpha(A->r);
+    A->a2 = A->alpha * A->alpha;
+    sub3(cam, P + 9, A->wo);
+    normalize3(A->wo);
+    A->co = dot3(A->n, A->wo);
+    for (int c = 0; c < 3; ++c) A->F0[c] = 0.04 * (1.0 - A->m) + A->kd[c] * A->m;
+    return 1;
+}
+
+/* Contribution of one frozen sample to the gradient: dL/dn (unprojected,
+ * including the view-cosine term along wo), dL/dalpha, dL/dF0 and dL/dtexel. */
+static void adj_sample(const adj_pixel* A, const orc_sample_rec* s, int spec_on, const double* L, const double* gd,
+                       const double* gs, double dn[3], double* dalpha, double dF0[3], double dL[3]) {
+    const double* n = A->n;
+    const double* wo = A->wo;
+    double a = s->vis * s->inv_denom;
+    double ci = dot3(n, s->wi);
+    double g_ci = 0.0, g_co = 0.0, g_nh = 0.0, h[3] = {0, 0, 0};
+    *dalpha = 0.0;
+    /* diffuse: c_d,c = a L_c ci / pi */
+    for (int c = 0; c < 3; ++c) {
+        dL[c] = a * gd[c] * ci / ORC_PI;
+        dF0[c] = 0.0;
+        g_ci += a * gd[c] * L[c] / ORC_PI;
+    }
+    if (spec_on) {
+        double alpha = A->alpha, a2 = A->a2, co = A->co;
+        for (int k = 0; k < 3; ++k) h[k] = s->wi[k] + wo[k];
+        normalize3(h);
+        double nh = dot3(n, h), vh = dot3(wo, h);
+        double D = orc_ggx_D(nh, alpha);
+        double li = orc_ggx_lambda(ci, alpha), lo = orc_ggx_lambda(co, alpha);
+        double G2 = 1.0 / (1.0 + li + lo);
+        double S = D * G2 / (4.0 * co); /* c_s,c = a L_c S F_c */
+        double x = 1.0 - (vh < 0.0 ? 0.0 : (vh > 1.0 ? 1.0 : vh));
+        double q5 = x * x * x * x * x;
+        double gS = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double F = A->F0[c] + (1.0 - A->F0[c]) * q5;
+            dL[c] += a * gs[c] * S * F;
+            gS += a * gs[c] * L[c] * F;
+            dF0[c] = a * gs[c] * L[c] * S * (1.0 - q5);
+        }
+        /* S = D(nh, alpha) G2(Lambda_i, Lambda_o) / (4 co) */
+        double dD_dnh = 0.0, dD_dalpha = 0.0;
+        if (nh > 0.0) {
+            double dd = nh * nh * (a2 - 1.0) + 1.0;
+            dD_dnh = -4.0 * D * nh * (a2 - 1.0) / dd;
+            dD_dalpha = D * (2.0 / alpha - 4.0 * alpha * nh * nh / dd);
+        }
+        /* Lambda(c) = (sqrt(1+z)-1)/2, z = alpha^2 (1/c^2 - 1) */
+        double zi = a2 * (1.0 / (ci * ci) - 1.0), zo = a2 * (1.0 / (co * co) - 1.0);
+        double si = sqrt(1.0 + zi), so = sqrt(1.0 + zo);
+        double dli_dci = (1.0 / (4.0 * si)) * (-2.0 * a2 / (ci * ci * ci));
+        double dlo_dco = (1.0 / (4.0 * so)) * (-2.0 * a2 / (co * co * co));
+        double dli_dalpha = (1.0 / (4.0 * si)) * 2.0 * alpha * (1.0 / (ci * ci) - 1.0);
+        double dlo_dalpha = (1.0 / (4.0 * so)) * 2.0 * alpha * (1.0 / (co * co) - 1.0);
+        double dS_dD = G2 / (4.0 * co);
+        double dS_dLam = -D * G2 * G2 / (4.0 * co); /* dG2/dLambda = -G2^2 */
+        g_nh = gS * dS_dD * dD_dnh;
+        *dalpha = gS * (dS_dD * dD_dalpha + dS_dLam * (dli_dalpha + dlo_dalpha));
+        g_ci += gS * dS_dLam * dli_dci;
+        g_co = gS * (dS_dLam * dlo_dco - S / co);
+    }
+    for (int k = 0; k < 3; ++k) dn[k] = g_ci * s->wi[k] + g_nh * h[k] + g_co * wo[k];
+}
+
+/* n = N / |N|:  dL/dN = (I - n n^T) dL/dn / |N| */
+static void adj_project(const adj_pixel* A, const double gn[3], double out[3]) {
+    double ng = dot3(A->n, gn);
+    for (int k = 0; k < 3; ++k) out[k] = (gn[k] - A->n[k] * ng) / A->lN;
+}
+
 /* Analytic adjoint of orc_frozen_eval for the scalar  sum_q <g_q, out_q>.
  * g: 9 per pixel (dL/dc_d, dL/dk_d,out, dL/dc_s).
  * Writes grad: 9 per pixel (dL/dN.xyz, dL/dk_d.rgb, dL/d(o,r,m)) and
- * accumulates dL/dtexel into genv3 (3 per texel; serial over pixels). */
+ * accumulates dL/dtexel into genv3 (3 per texel; serial over pixels).
+ * With scale != NULL it also writes, per pixel and component, the sum of the
+ * absolute values of the per-sample contributions (and accumulates the same
+ * for the texels into genv3_scale): the magnitude a floating-point summation
+ * error of the gradient is measured against. */
 void orc_frozen_adjoint(const orc_sample_rec* recs, int spp, int n_pix, const double* prow, const double* cam_pos,
-                        const int* spec_on, const double* env3, const double* g, double* grad, double* genv3) {
+                        const int* spec_on, const double* env3, const double* g, double* grad, double* genv3,
+                        double* scale, double* genv3_scale) {
     for (int q = 0; q < n_pix; ++q) {
-        const double* P = prow + 12 * (size_t)q;
         const double* gd = g + 9 * (size_t)q;
         const double* gk = gd + 3;
         const double* gs = gd + 6;
         double* G = grad + 9 * (size_t)q;
+        double* Sc = scale ? scale + 9 * (size_t)q : NULL;
         memset(G, 0, 9 * sizeof(double));
-        double N[3] = {P[0], P[1], P[2]};
-        double lN = norm3(N);
-        if (!(lN > 0.0)) continue;
-        double n[3] = {N[0] / lN, N[1] / lN, N[2] / lN};
-        const double* kd = P + 3;
-        double r = P[7], m = P[8];
-        double alpha = orc_alpha(r);
-        double a2 = alpha * alpha;
-        double wo[3];
-        sub3(cam_pos + 3 * (size_t)q, P + 9, wo);
-        normalize3(wo);
-        double co = dot3(n, wo);
-        double F0[3];
-        for (int c = 0; c < 3; ++c) F0[c] = 0.04 * (1.0 - m) + kd[c] * m;
-        double gn[3] = {0, 0, 0}, g_co = 0.0, g_alpha = 0.0, gF0[3] = {0, 0, 0};
+        if (Sc) memset(Sc, 0, 9 * sizeof(double));
+        adj_pixel A;
+        if (!adj_setup(prow + 12 * (size_t)q, cam_pos + 3 * (size_t)q, &A)) continue;
+        double gn[3] = {0, 0, 0}, g_alpha = 0.0, gF0[3] = {0, 0, 0};
+        const double* kd = A.kd;
+        double m = A.m, r = A.r;
+        int r_live = r * r > 1e-4;
         for (int j = 0; j < spp; ++j) {
             const orc_sample_rec* s = recs + (size_t)q * spp + j;
             if (!s->active) continue;
-            double a = s->vis * s->inv_denom;
-            double ci = dot3(n, s->wi);
-            const double* L = env3 + 3 * (size_t)s->texel;
+            double dn[3], da, dF0[3], dL[3];
+            adj_sample(&A, s, spec_on[q], env3 + 3 * (size_t)s->texel, gd, gs, dn, &da, dF0, dL);
             double* gL = genv3 + 3 * (size_t)s->texel;
-            double g_ci = 0.0;
-            /* diffuse: c_d,c = a L_c ci / pi */
-            for (int c = 0; c < 3; ++c) {
-                gL[c] += a * gd[c] * ci / ORC_PI;
-                g_ci += a * gd[c] * L[c] / ORC_PI;
+            for (int k = 0; k < 3; ++k) {
+                gn[k] += dn[k];
+                gF0[k] += dF0[k];
+                gL[k] += dL[k];
             }
-            if (spec_on[q]) {
-                double h[3] = {s->wi[0] + wo[0], s->wi[1] + wo[1], s->wi[2] + wo[2]};
-                normalize3(h);
-                double nh = dot3(n, h), vh = dot3(wo, h);
-                double D = orc_ggx_D(nh, alpha);
-                double li = orc_ggx_lambda(ci, alpha), lo = orc_ggx_lambda(co, alpha);
-                double G2 = 1.0 / (1.0 + li + lo);
-                double S = D * G2 / (4.0 * co); /* c_s,c = a L_c S F_c */
-                double x = 1.0 - (vh < 0.0 ? 0.0 : (vh > 1.0 ? 1.0 : vh));
-                double q5 = x * x * x * x * x;
-                double gS = 0.0;
-                for (int c = 0; c < 3; ++c) {
-                    double F = F0[c] + (1.0 - F0[c]) * q5;
-                    gL[c] += a * gs[c] * S * F;
-                    gS += a * gs[c] * L[c] * F;
-                    gF0[c] += a * gs[c] * L[c] * S * (1.0 - q5);
+            g_alpha += da;
+            if (Sc) {
+                double pn[3], dm = 0.0;
+                adj_project(&A, dn, pn);
+                for (int k = 0; k < 3; ++k) {
+                    Sc[k] += fabs(pn[k]);
+                    Sc[3 + k] += fabs(dF0[k] * m);
+                    dm += dF0[k] * (kd[k] - 0.04);
+                    genv3_scale[3 * (size_t)s->texel + k] += fabs(dL[k]);
                 }
-                /* S = D(nh, alpha) G2(Lambda_i, Lambda_o) / (4 co) */
-                double dD_dnh = 0.0, dD_dalpha = 0.0;
-                if (nh > 0.0) {
-                    double dd = nh * nh * (a2 - 1.0) + 1.0;
-                    dD_dnh = -4.0 * D * nh * (a2 - 1.0) / dd;
-                    dD_dalpha = D * (2.0 / alpha - 4.0 * alpha * nh * nh / dd);
-                }
-                /* Lambda(c) = (sqrt(1+z)-1)/2, z = alpha^2 (1/c^2 - 1) */
-                double zi = a2 * (1.0 / (ci * ci) - 1.0), zo = a2 * (1.0 / (co * co) - 1.0);
-                double si = sqrt(1.0 + zi), so = sqrt(1.0 + zo);
-                double dli_dci = (1.0 / (4.0 * si)) * (-2.0 * a2 / (ci * ci * ci));
-                double dlo_dco = (1.0 / (4.0 * so)) * (-2.0 * a2 / (co * co * co));
-                double dli_dalpha = (1.0 / (4.0 * si)) * 2.0 * alpha * (1.0 / (ci * ci) - 1.0);
-                double dlo_dalpha = (1.0 / (4.0 * so)) * 2.0 * alpha * (1.0 / (co * co) - 1.0);
-                double dS_dD = G2 / (4.0 * co);
-                double dS_dLam = -D * G2 * G2 / (4.0 * co); /* dG2/dLambda = -G2^2 */
-                double g_nh = gS * dS_dD * dD_dnh;
-                g_alpha += gS * (dS_dD * dD_dalpha + dS_dLam * (dli_dalpha + dlo_dalpha));
-                g_ci += gS * dS_dLam * dli_dci;
-                g_co += gS * (dS_dLam * dlo_dco - S / co);
-                for (int k = 0; k < 3; ++k) gn[k] += g_nh * h[k];
+                Sc[7] += r_live ? fabs(da * 2.0 * r) : 0.0;
+                Sc[8] += fabs(dm);
             }
-            for (int k = 0; k < 3; ++k) gn[k] += g_ci * s->wi[k];
         }
-        for (int k = 0; k < 3; ++k) gn[k] += g_co * wo[k];
-        /* n = N / |N|:  dL/dN = (I - n n^T) dL/dn / |N| */
-        double ng = dot3(n, gn);
-        for (int k = 0; k < 3; ++k) G[k] = (gn[k] - n[k] * ng) / lN;
-        double g_m = 0.0;
+        adj_project(&A, gn, G);
+        double g_m = 0.0, dmk = 0.0;
         for (int c = 0; c < 3; ++c) {
             G[3 + c] = gk[c] * (1.0 - m) + gF0[c] * m;
             g_m += -gk[c] * kd[c] + gF0[c] * (kd[c] - 0.04);
+            dmk += -gk[c] * kd[c];
+            if (Sc) Sc[3 + c] += fabs(gk[c] * (1.0 - m));
         }
+        if (Sc) Sc[8] += fabs(dmk);
         G[6] = 0.0;
-        G[7] = (r * r > 1e-4) ? g_alpha * 2.0 * r : 0.0;
+        G[7] = r_live ? g_alpha * 2.0 * r : 0.0;
         G[8] = g_m;
     }
 }

@@ -1,0 +1,223 @@
+// C-ABI entry points of libmcdi: argument checks, then kernel launches on the
+// caller's stream.  No entry point allocates device memory or synchronises.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+mcdi_status fail(mcdi_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mcdi_status ok() {
+    g_err[0] = '\0';
+    return MCDI_OK;
+}
+
+mcdi_status launched(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return fail(MCDI_DEVICE_ERROR, "%s: %s", what, cudaGetErrorString(e));
+    return ok();
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+#define REQUIRE(cond, ...)                                  \
+    do {                                                    \
+        if (!(cond)) return fail(MCDI_INVALID_ARG, __VA_ARGS__); \
+    } while (0)
+
+#define REQUIRE_BUF16(p) REQUIRE((p) != nullptr && aligned16(p), "%s must be a non-NULL 16-byte aligned device pointer", #p)
+
+mcdi_status check_params(const mcdi_shade_params* prm) {
+    REQUIRE(prm != nullptr, "params is NULL");
+    REQUIRE(prm->n_light >= 0 && prm->n_cos >= 0 && prm->n_ggx >= 0, "sample counts must be >= 0");
+    const long long spp = (long long)prm->n_light + prm->n_cos + prm->n_ggx;
+    REQUIRE(spp >= 1 && spp <= 1024, "spp = n_light + n_cos + n_ggx must be in [1, 1024], got %lld", spp);
+    REQUIRE(prm->tau >= 0.0f && prm->tau <= 1.0f, "tau must be in [0, 1]");
+    REQUIRE(prm->ray_eps >= 0.0f && prm->ray_eps < 1e30f, "ray_eps must be finite and >= 0");
+    return MCDI_OK;
+}
+
+mcdi_status shade_common(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond,
+                         const float* marg, const double* total, const float* gb_pos, const float* gb_nrm,
+                         const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                         const mcdi_shade_params* prm, mcdi::ShadeArgs* a) {
+    REQUIRE(bvh != nullptr, "bvh is NULL");
+    REQUIRE(bvh->n_tris >= 0, "bvh->n_tris must be >= 0");
+    if (bvh->n_tris > 0) {
+        REQUIRE_BUF16(bvh->nodes);
+        REQUIRE_BUF16(bvh->tri_records);
+    }
+    REQUIRE_BUF16(env);
+    REQUIRE(Wp >= 1 && Wp <= 8192 && Hp >= 1 && Hp <= 4096, "probe size %dx%d out of range", Wp, Hp);
+    REQUIRE(cond != nullptr && marg != nullptr && total != nullptr, "CDF tables must be non-NULL");
+    REQUIRE_BUF16(gb_pos);
+    REQUIRE_BUF16(gb_nrm);
+    REQUIRE_BUF16(gb_kd);
+    REQUIRE_BUF16(gb_korm);
+    REQUIRE(cams != nullptr && ((uintptr_t)cams & 3u) == 0, "cams must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE(N >= 1 && H >= 1 && W >= 1, "image shape must be positive");
+    REQUIRE((long long)N * H * W <= (1LL << 31) - 1, "too many pixels");
+    REQUIRE((long long)H * W <= 0xffffffffLL, "too many pixels per view");
+    mcdi_status s = check_params(prm);
+    if (s != MCDI_OK) return s;
+    a->nodes = bvh->nodes;
+    a->tris = bvh->tri_records;
+    a->n_tris = bvh->n_tris;
+    a->env = reinterpret_cast<const float4*>(env);
+    a->Wp = Wp;
+    a->Hp = Hp;
+    a->cond = cond;
+    a->marg = marg;
+    a->total = total;
+    a->gb_pos = reinterpret_cast<const float4*>(gb_pos);
+    a->gb_nrm = reinterpret_cast<const float4*>(gb_nrm);
+    a->gb_kd = reinterpret_cast<const float4*>(gb_kd);
+    a->gb_korm = reinterpret_cast<const float4*>(gb_korm);
+    a->cams = cams;
+    a->N = N;
+    a->H = H;
+    a->W = W;
+    a->n_light = prm->n_light;
+    a->n_cos = prm->n_cos;
+    a->n_ggx = prm->n_ggx;
+    a->seed = prm->seed;
+    a->tau = prm->tau;
+    a->ray_eps = prm->ray_eps;
+    a->stream_word = 0;
+    return MCDI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mcdi_last_error(void) { return g_err; }
+
+int mcdi_version(void) { return 100; }
+
+mcdi_status mcdi_build_envmap_cdf(const float* env, int W, int H, float* cond_cdf, float* marg_cdf, double* row_sum,
+                                  double* total, void* stream) {
+    REQUIRE_BUF16(env);
+    REQUIRE(W >= 1 && W <= 8192 && H >= 1 && H <= 4096, "probe size %dx%d out of range", W, H);
+    REQUIRE(cond_cdf != nullptr && marg_cdf != nullptr, "CDF outputs must be non-NULL");
+    REQUIRE(row_sum != nullptr && total != nullptr && ((uintptr_t)row_sum & 7u) == 0 && ((uintptr_t)total & 7u) == 0,
+            "row_sum / total must be non-NULL 8-byte aligned");
+    return launched(mcdi::launch_envmap_cdf(env, W, H, cond_cdf, marg_cdf, row_sum, total,
+                                            static_cast<cudaStream_t>(stream)),
+                    "build_envmap_cdf");
+}
+
+mcdi_status mcdi_bvh_sizes(int n_tris, size_t* node_bytes, size_t* tri_bytes, size_t* scratch_bytes) {
+    REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
+    REQUIRE(node_bytes && tri_bytes && scratch_bytes, "size outputs must be non-NULL");
+    *node_bytes = mcdi::bvh_node_bytes(n_tris);
+    *tri_bytes = mcdi::bvh_tri_bytes(n_tris);
+    *scratch_bytes = mcdi::bvh_scratch_layout(n_tris).total;
+    return ok();
+}
+
+mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
+                           void* tri_records, void* scratch, size_t scratch_bytes, void* stream) {
+    REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
+    REQUIRE(n_verts >= 1, "n_verts must be >= 1");
+    REQUIRE(verts != nullptr && tris != nullptr, "verts / tris must be non-NULL");
+    REQUIRE(((uintptr_t)verts & 3u) == 0 && ((uintptr_t)tris & 3u) == 0, "verts / tris must be 4-byte aligned");
+    REQUIRE_BUF16(nodes);
+    REQUIRE_BUF16(tri_records);
+    REQUIRE(scratch != nullptr && ((uintptr_t)scratch & 255u) == 0, "scratch must be non-NULL 256-byte aligned");
+    const mcdi::BvhScratch L = mcdi::bvh_scratch_layout(n_tris);
+    REQUIRE(scratch_bytes >= L.total, "scratch too small: %zu < %zu bytes", scratch_bytes, L.total);
+    return launched(mcdi::launch_build_bvh(verts, n_verts, tris, n_tris, nodes, tri_records, scratch, L,
+                                           static_cast<cudaStream_t>(stream)),
+                    "build_bvh");
+}
+
+mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* verts, const float* vnrm, const int* tris,
+                              int n_verts, const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                              const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos, float* gb_nrm,
+                              float* gb_kd, float* gb_korm, void* stream) {
+    REQUIRE(bvh != nullptr && bvh->n_tris >= 0, "bvh is NULL or invalid");
+    if (bvh->n_tris > 0) {
+        REQUIRE_BUF16(bvh->nodes);
+        REQUIRE_BUF16(bvh->tri_records);
+    }
+    REQUIRE(verts && vnrm && tris && n_verts >= 1, "mesh arrays must be non-NULL");
+    REQUIRE(cams != nullptr, "cams is NULL");
+    REQUIRE(N >= 1 && H >= 1 && W >= 1 && (long long)N * H * W <= (1LL << 31) - 1, "bad image shape");
+    REQUIRE(tex_size >= 1 && tex_size <= 16384, "tex_size out of range");
+    REQUIRE_BUF16(tex_kd);
+    REQUIRE_BUF16(tex_korm);
+    REQUIRE(uvmap != nullptr, "uvmap (host, 3 floats) is NULL");
+    REQUIRE_BUF16(gb_pos);
+    REQUIRE_BUF16(gb_nrm);
+    REQUIRE_BUF16(gb_kd);
+    REQUIRE_BUF16(gb_korm);
+    return launched(mcdi::launch_primary_cast(bvh->nodes, bvh->tri_records, bvh->n_tris, verts, vnrm, tris, n_verts,
+                                              cams, N, H, W, tex_kd, tex_korm, tex_size, uvmap[0], uvmap[1],
+                                              uvmap[2], gb_pos, gb_nrm, gb_kd, gb_korm,
+                                              static_cast<cudaStream_t>(stream)),
+                    "primary_cast");
+}
+
+mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                              const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
+                              const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                              const mcdi_shade_params* params, float* c_d, float* kd_out, float* c_s,
+                              uint32_t* vis_mask, void* stream) {
+    mcdi::ShadeArgs a;
+    mcdi_status s = shade_common(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N,
+                                 H, W, params, &a);
+    if (s != MCDI_OK) return s;
+    REQUIRE_BUF16(c_d);
+    REQUIRE_BUF16(kd_out);
+    REQUIRE_BUF16(c_s);
+    REQUIRE(vis_mask == nullptr || ((uintptr_t)vis_mask & 3u) == 0, "vis_mask must be 4-byte aligned");
+    return launched(mcdi::launch_shade_fwd(a, reinterpret_cast<float4*>(c_d), reinterpret_cast<float4*>(kd_out),
+                                           reinterpret_cast<float4*>(c_s), vis_mask,
+                                           static_cast<cudaStream_t>(stream)),
+                    "shade_mc_fwd");
+}
+
+mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                              const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
+                              const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                              const mcdi_shade_params* params, const float* g_cd, const float* g_kdout,
+                              const float* g_cs, const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm,
+                              float* g_env, void* stream) {
+    mcdi::ShadeArgs a;
+    mcdi_status s = shade_common(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N,
+                                 H, W, params, &a);
+    if (s != MCDI_OK) return s;
+    REQUIRE_BUF16(g_cd);
+    REQUIRE_BUF16(g_kdout);
+    REQUIRE_BUF16(g_cs);
+    REQUIRE_BUF16(g_kd);
+    REQUIRE_BUF16(g_korm);
+    REQUIRE_BUF16(g_nrm);
+    REQUIRE_BUF16(g_env);
+    REQUIRE(vis_mask == nullptr || ((uintptr_t)vis_mask & 3u) == 0, "vis_mask must be 4-byte aligned");
+    const uint32_t* mask = vis_mask;
+    if (params->decorrelate_bwd) {
+        a.stream_word = 1;  // fresh samples: the forward's visibility does not apply
+        mask = nullptr;
+    }
+    return launched(mcdi::launch_shade_bwd(a, reinterpret_cast<const float4*>(g_cd),
+                                           reinterpret_cast<const float4*>(g_kdout),
+                                           reinterpret_cast<const float4*>(g_cs), mask,
+                                           reinterpret_cast<float4*>(g_kd), reinterpret_cast<float4*>(g_korm),
+                                           reinterpret_cast<float4*>(g_nrm), reinterpret_cast<float4*>(g_env),
+                                           static_cast<cudaStream_t>(stream)),
+                    "shade_mc_bwd");
+}
+
+}  // extern "C"

@@ -1,0 +1,389 @@
+// Linear BVH over the triangle mesh extracted each iteration (the paper traces
+// shadow rays with hardware ray tracing, Sec. 3 and Sec. 6; GB300 has no RT
+// cores, so the acceleration structure is built and traversed in software).
+//
+// Build (Karras 2012, "Maximizing parallelism in the construction of BVHs,
+// octrees, and k-d trees"):
+//   1. centroid bounds (block min/max + one atomic per block and axis);
+//   2. 30-bit Morton code of each centroid;
+//   3. stable LSD radix sort, 4 passes of 8 bits (histogram / per-digit scan
+//      across tiles / scatter with warp match_any ranking);
+//   4. one thread per internal node finds its key range and split from the
+//      common-prefix lengths of the sorted keys (ties broken by position);
+//   5. bottom-up bounds: each leaf walks to the root, the second thread to
+//      reach a node (atomic arrival counter) writes its two child boxes.
+// Output: 64-byte two-child nodes (root = node 0) and 48-byte triangle records
+// in leaf (Morton) order.
+#include <float.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace mcdi {
+namespace {
+
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ void load_tri(const float* __restrict__ verts, int n_verts, const int* __restrict__ tris,
+                                         int k, f3& a, f3& b, f3& c) {
+    const int i0 = tris[3 * (size_t)k], i1 = tris[3 * (size_t)k + 1], i2 = tris[3 * (size_t)k + 2];
+    if ((unsigned)i0 >= (unsigned)n_verts || (unsigned)i1 >= (unsigned)n_verts || (unsigned)i2 >= (unsigned)n_verts) {
+        a = b = c = mk(0.f, 0.f, 0.f);  // bad index: degenerate triangle, never hit
+        return;
+    }
+    a = mk(verts[3 * (size_t)i0], verts[3 * (size_t)i0 + 1], verts[3 * (size_t)i0 + 2]);
+    b = mk(verts[3 * (size_t)i1], verts[3 * (size_t)i1 + 1], verts[3 * (size_t)i1 + 2]);
+    c = mk(verts[3 * (size_t)i2], verts[3 * (size_t)i2 + 1], verts[3 * (size_t)i2 + 2]);
+}
+
+__global__ void init_bounds_kernel(uint32_t* bounds) {
+    if (threadIdx.x < 3) bounds[threadIdx.x] = f2ord(FLT_MAX);
+    else if (threadIdx.x < 6) bounds[threadIdx.x] = f2ord(-FLT_MAX);
+}
+
+__global__ void __launch_bounds__(256) centroid_bounds_kernel(const float* __restrict__ verts, int n_verts,
+                                                              const int* __restrict__ tris, int n,
+                                                              uint32_t* __restrict__ bounds) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (k < n) {
+        f3 a, b, c;
+        load_tri(verts, n_verts, tris, k, a, b, c);
+        const f3 m = (a + b + c) * (1.0f / 3.0f);
+        lo[0] = hi[0] = m.x;
+        lo[1] = hi[1] = m.y;
+        lo[2] = hi[2] = m.z;
+    }
+    __shared__ float red[6][8];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[ax] = fminf(lo[ax], __shfl_xor_sync(0xffffffffu, lo[ax], off));
+            hi[ax] = fmaxf(hi[ax], __shfl_xor_sync(0xffffffffu, hi[ax], off));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int ax = 0; ax < 3; ++ax) {
+            red[ax][warp] = lo[ax];
+            red[3 + ax][warp] = hi[ax];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int r = threadIdx.x;
+        float v = red[r][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = r < 3 ? fminf(v, red[r][w]) : fmaxf(v, red[r][w]);
+        if (r < 3) atomicMin(bounds + r, f2ord(v));
+        else atomicMax(bounds + r, f2ord(v));
+    }
+}
+
+// spread the low 10 bits of v so that bit i lands at bit 3i
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) morton_kernel(const float* __restrict__ verts, int n_verts,
+                                                     const int* __restrict__ tris, int n,
+                                                     const uint32_t* __restrict__ bounds, uint32_t* __restrict__ keys,
+                                                     uint32_t* __restrict__ vals) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    f3 a, b, c;
+    load_tri(verts, n_verts, tris, k, a, b, c);
+    const f3 m = (a + b + c) * (1.0f / 3.0f);
+    const float lo[3] = {ord2f(bounds[0]), ord2f(bounds[1]), ord2f(bounds[2])};
+    const float hi[3] = {ord2f(bounds[3]), ord2f(bounds[4]), ord2f(bounds[5])};
+    const float p[3] = {m.x, m.y, m.z};
+    uint32_t code = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float ext = hi[ax] - lo[ax];
+        float t = ext > 0.f ? (p[ax] - lo[ax]) / ext : 0.5f;
+        t = fminf(fmaxf(t, 0.f), 1.f);
+        const uint32_t q = min(1023u, (uint32_t)(t * 1024.f));
+        code |= spread3(q) << (2 - ax);
+    }
+    keys[k] = code;
+    vals[k] = (uint32_t)k;
+}
+
+// ---- radix sort: one 8-bit digit per pass ----
+__global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift,
+                                                                  int nblocks, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const size_t i = base + (size_t)it * kSortThreads + threadIdx.x;
+        if (i < (size_t)n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// one block per digit: exclusive scan of that digit's counts across tiles
+__global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t* __restrict__ hist, int nblocks,
+                                                         uint32_t* __restrict__ digit_tot) {
+    uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
+    __shared__ uint32_t warp_tot[8];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < nblocks; base += 256) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nblocks ? row[i] : 0u;
+        uint32_t inc = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += t;
+        }
+        if (lane == 31) warp_tot[warp] = inc;
+        __syncthreads();
+        uint32_t woff = 0, all = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) woff += warp_tot[w];
+            all += warp_tot[w];
+        }
+        if (i < nblocks) row[i] = carry + woff + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) digit_tot[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int n, int shift, int nblocks,
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_tot, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t wc[kWarps][256];  // per-warp digit counters, then per-warp offsets
+    __shared__ uint32_t dbase[256];       // global start of each digit
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int w = 0; w < kWarps; ++w) wc[w][threadIdx.x] = 0;
+    {  // exclusive scan of the 256 digit totals
+        __shared__ uint32_t wt[kWarps];
+        const uint32_t v = digit_tot[threadIdx.x];
+        uint32_t inc = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += t;
+        }
+        if (lane == 31) wt[warp] = inc;
+        __syncthreads();
+        uint32_t woff = 0;
+        for (int w = 0; w < warp; ++w) woff += wt[w];
+        dbase[threadIdx.x] = woff + inc - v + hist[(size_t)threadIdx.x * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    // warp w ranks elements [base + w*256, base + (w+1)*256) in order, 32 at a time
+    const size_t base = (size_t)blockIdx.x * kSortTile + (size_t)warp * (32 * kSortItems);
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const size_t i = base + (size_t)it * 32 + lane;
+        const bool valid = i < (size_t)n;
+        key[it] = valid ? keys_in[i] : 0u;
+        val[it] = valid ? vals_in[i] : 0u;
+        const uint32_t d = valid ? ((key[it] >> shift) & 255u) : (256u + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (valid) before = wc[warp][d];
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wc[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[it] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {  // per digit: exclusive scan over warps (warp order = element order)
+        uint32_t run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = wc[w][threadIdx.x];
+            wc[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const size_t i = base + (size_t)it * 32 + lane;
+        if (i < (size_t)n) {
+            const uint32_t d = (key[it] >> shift) & 255u;
+            const uint32_t pos = dbase[d] + wc[warp][d] + rank[it];
+            keys_out[pos] = key[it];
+            vals_out[pos] = val[it];
+        }
+    }
+}
+
+// ---- hierarchy ----
+__device__ __forceinline__ int common_prefix(const uint32_t* __restrict__ keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    const uint32_t a = keys[i], b = keys[j];
+    if (a == b) return 32 + __clz((uint32_t)(i ^ j));
+    return __clz(a ^ b);
+}
+
+__global__ void __launch_bounds__(256) karras_kernel(const uint32_t* __restrict__ keys, int n,
+                                                     BvhNode* __restrict__ nodes, int* __restrict__ parent_int,
+                                                     int* __restrict__ parent_leaf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (common_prefix(keys, n, i, i + 1) - common_prefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = common_prefix(keys, n, i, i - d);
+    int lmax = 2;
+    while (common_prefix(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (common_prefix(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = common_prefix(keys, n, i, j);
+    int s = 0;
+    for (int div = 2;; div <<= 1) {
+        const int t = (l + div - 1) / div;
+        if (common_prefix(keys, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    const int g = i + s * d + min(d, 0);
+    const int left = (min(i, j) == g) ? ~g : g;
+    const int right = (max(i, j) == g + 1) ? ~(g + 1) : g + 1;
+    nodes[i].d = make_int4(left, right, 0, 0);
+    if (left < 0) parent_leaf[g] = i;
+    else parent_int[g] = i;
+    if (right < 0) parent_leaf[g + 1] = i;
+    else parent_int[g + 1] = i;
+    if (i == 0) parent_int[0] = -1;
+}
+
+// triangle records in leaf order + leaf boxes + cleared arrival counters
+__global__ void __launch_bounds__(256) leaf_kernel(const float* __restrict__ verts, int n_verts,
+                                                   const int* __restrict__ tris, int n,
+                                                   const uint32_t* __restrict__ order, TriRecord* __restrict__ recs,
+                                                   float4* __restrict__ box_leaf, uint32_t* __restrict__ flags) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (p < n - 1) flags[p] = 0u;
+    const int k = (int)order[p];
+    f3 a, b, c;
+    load_tri(verts, n_verts, tris, k, a, b, c);
+    TriRecord r;
+    r.v0 = make_float4(a.x, a.y, a.z, __int_as_float(k));
+    r.e1 = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, 0.f);
+    r.e2 = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, 0.f);
+    recs[p] = r;
+    // box of the triangle, widened by a few ulps so that it also holds the
+    // triangle v0 + u e1 + v e2 the intersection test actually sees
+    float lo[3] = {fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z))};
+    float hi[3] = {fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z))};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float pad = 4.0f * FLT_EPSILON * fmaxf(fabsf(lo[ax]), fabsf(hi[ax])) + 1e-30f;
+        lo[ax] -= pad;
+        hi[ax] += pad;
+    }
+    box_leaf[2 * (size_t)p] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    box_leaf[2 * (size_t)p + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+}
+
+__device__ __forceinline__ void child_box(int link, const float4* box_int, const float4* box_leaf, float4& lo,
+                                          float4& hi) {
+    const float4* b = link < 0 ? box_leaf + 2 * (size_t)(~link) : box_int + 2 * (size_t)link;
+    lo = __ldcg(b);
+    hi = __ldcg(b + 1);
+}
+
+__global__ void __launch_bounds__(256) refit_kernel(int n, BvhNode* __restrict__ nodes,
+                                                    const int* __restrict__ parent_int,
+                                                    const int* __restrict__ parent_leaf, uint32_t* __restrict__ flags,
+                                                    float4* __restrict__ box_int,
+                                                    const float4* __restrict__ box_leaf) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int node = parent_leaf[p];
+    // at most n - 1 steps: each internal node is completed by exactly one thread
+    for (int steps = 0; node >= 0 && steps < n; ++steps) {
+        __threadfence();
+        if (atomicAdd(flags + node, 1u) == 0u) return;  // first arrival: the sibling finishes this node
+        const int4 d = __ldcg(&nodes[node].d);
+        float4 l0, h0, l1, h1;
+        child_box(d.x, box_int, box_leaf, l0, h0);
+        child_box(d.y, box_int, box_leaf, l1, h1);
+        nodes[node].a = make_float4(l0.x, h0.x, l0.y, h0.y);
+        nodes[node].b = make_float4(l1.x, h1.x, l1.y, h1.y);
+        nodes[node].c = make_float4(l0.z, h0.z, l1.z, h1.z);
+        box_int[2 * (size_t)node] = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
+        box_int[2 * (size_t)node + 1] = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
+        node = parent_int[node];
+    }
+}
+
+// one triangle: a root whose two links both point at leaf 0
+__global__ void single_leaf_root_kernel(BvhNode* nodes, const float4* box_leaf) {
+    const float4 lo = box_leaf[0], hi = box_leaf[1];
+    nodes[0].a = make_float4(lo.x, hi.x, lo.y, hi.y);
+    nodes[0].b = nodes[0].a;
+    nodes[0].c = make_float4(lo.z, hi.z, lo.z, hi.z);
+    nodes[0].d = make_int4(~0, ~0, 0, 0);
+}
+
+}  // namespace
+
+cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, int n, void* nodes_v, void* recs_v,
+                             void* scratch, const BvhScratch& L, cudaStream_t stream) {
+    char* s = static_cast<char*>(scratch);
+    uint32_t* bounds = reinterpret_cast<uint32_t*>(s + L.bounds);
+    uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(s + L.keys0), reinterpret_cast<uint32_t*>(s + L.keys1)};
+    uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(s + L.vals0), reinterpret_cast<uint32_t*>(s + L.vals1)};
+    uint32_t* hist = reinterpret_cast<uint32_t*>(s + L.hist);
+    uint32_t* dtot = reinterpret_cast<uint32_t*>(s + L.digit_tot);
+    int* parent_int = reinterpret_cast<int*>(s + L.parent_int);
+    int* parent_leaf = reinterpret_cast<int*>(s + L.parent_leaf);
+    uint32_t* flags = reinterpret_cast<uint32_t*>(s + L.flags);
+    float4* box_int = reinterpret_cast<float4*>(s + L.box_int);
+    float4* box_leaf = reinterpret_cast<float4*>(s + L.box_leaf);
+    BvhNode* nodes = static_cast<BvhNode*>(nodes_v);
+    TriRecord* recs = static_cast<TriRecord*>(recs_v);
+
+    const int g256 = (n + 255) / 256;
+    init_bounds_kernel<<<1, 32, 0, stream>>>(bounds);
+    centroid_bounds_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, bounds);
+    morton_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, bounds, keys[0], vals[0]);
+    int cur = 0;
+    for (int shift = 0; shift < 32; shift += 8) {
+        digit_hist_kernel<<<L.nblocks, kSortThreads, 0, stream>>>(keys[cur], n, shift, L.nblocks, hist);
+        digit_scan_kernel<<<256, 256, 0, stream>>>(hist, L.nblocks, dtot);
+        digit_scatter_kernel<<<L.nblocks, kSortThreads, 0, stream>>>(keys[cur], vals[cur], n, shift, L.nblocks, hist,
+                                                                     dtot, keys[cur ^ 1], vals[cur ^ 1]);
+        cur ^= 1;
+    }
+    leaf_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, vals[cur], recs, box_leaf, flags);
+    if (n == 1) {
+        single_leaf_root_kernel<<<1, 1, 0, stream>>>(nodes, box_leaf);
+    } else {
+        karras_kernel<<<(n - 1 + 255) / 256, 256, 0, stream>>>(keys[cur], n, nodes, parent_int, parent_leaf);
+        refit_kernel<<<g256, 256, 0, stream>>>(n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mcdi

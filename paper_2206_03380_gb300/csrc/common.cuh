@@ -1,0 +1,74 @@
+// Device-side building blocks shared by the mcdi kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MCDI_PI 3.14159265358979323846f
+#define MCDI_INV_PI 0.318309886183790671538f
+
+namespace mcdi {
+
+// ---------------------------------------------------------------- float3 math
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator*(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ f3 operator*(float s, f3 a) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ f3 normalize(f3 a) { return a * rsqrtf(dot(a, a)); }
+__device__ __forceinline__ f3 xyz(float4 v) { return {v.x, v.y, v.z}; }
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC 2011).  Ten rounds of the 4x32 S-box with multipliers 0xD2511F53 and
+// 0xCD9E8D57 and the Weyl key schedule 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo_a = 0xD2511F53u * c.x, hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z, hi_b = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k.x, lo_b, hi_a ^ c.w ^ k.y, lo_a);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The two uniforms of sample `j` of `pixel` in `view`: 24-bit fractions
+// (x >> 8) * 2^-24, exact in float.
+__device__ __forceinline__ float2 sample_uniforms(unsigned long long seed, uint32_t pixel, uint32_t view, uint32_t j,
+                                                  uint32_t stream) {
+    const uint4 x = philox4x32_10(make_uint4(pixel, view, j, stream),
+                                  make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32)));
+    return make_float2((float)(x.x >> 8) * 5.9604644775390625e-8f, (float)(x.y >> 8) * 5.9604644775390625e-8f);
+}
+
+// ---------------------------------------------------------------- BVH layout
+// Internal node of a binary BVH, 64 bytes: the bounds of both children (so one
+// node fetch tests two boxes) and the two child links.  link >= 0: internal
+// node index; link < 0: leaf, ~link = index into the triangle records.
+struct __align__(16) BvhNode {
+    float4 a;  // child0 lo.x, hi.x, lo.y, hi.y
+    float4 b;  // child1 lo.x, hi.x, lo.y, hi.y
+    float4 c;  // child0 lo.z, hi.z, child1 lo.z, hi.z
+    int4 d;    // child0 link, child1 link, -, -
+};
+
+// Triangle in leaf order, 48 bytes: v0 (w = original triangle index as int
+// bits), e1 = v1 - v0, e2 = v2 - v0.
+struct __align__(16) TriRecord {
+    float4 v0;
+    float4 e1;
+    float4 e2;
+};
+
+constexpr int kTraversalStack = 64;  // >= depth of a tree over 62-bit unique keys
+
+}  // namespace mcdi

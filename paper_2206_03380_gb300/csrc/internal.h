@@ -1,0 +1,90 @@
+// Host-side declarations shared between the C-ABI layer and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/mcdi.h"
+
+namespace mcdi {
+
+// ---- BVH build scratch layout (offsets in bytes, 256-byte aligned) ----
+struct BvhScratch {
+    size_t bounds, keys0, keys1, vals0, vals1, hist, digit_tot, parent_int, parent_leaf, flags, box_int, box_leaf;
+    size_t total;
+    int nblocks;  // radix-sort tiles
+};
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline BvhScratch bvh_scratch_layout(int n) {
+    BvhScratch s{};
+    const size_t un = (size_t)(n > 0 ? n : 1);
+    const size_t ni = un > 1 ? un - 1 : 1;
+    s.nblocks = (int)((un + kSortTile - 1) / kSortTile);
+    size_t o = 0;
+    s.bounds = o; o = align256(o + 8 * sizeof(uint32_t));
+    s.keys0 = o; o = align256(o + un * sizeof(uint32_t));
+    s.keys1 = o; o = align256(o + un * sizeof(uint32_t));
+    s.vals0 = o; o = align256(o + un * sizeof(uint32_t));
+    s.vals1 = o; o = align256(o + un * sizeof(uint32_t));
+    s.hist = o; o = align256(o + (size_t)256 * s.nblocks * sizeof(uint32_t));
+    s.digit_tot = o; o = align256(o + 256 * sizeof(uint32_t));
+    s.parent_int = o; o = align256(o + ni * sizeof(int));
+    s.parent_leaf = o; o = align256(o + un * sizeof(int));
+    s.flags = o; o = align256(o + ni * sizeof(uint32_t));
+    s.box_int = o; o = align256(o + ni * 2 * sizeof(float4));
+    s.box_leaf = o; o = align256(o + un * 2 * sizeof(float4));
+    s.total = o;
+    return s;
+}
+
+inline size_t bvh_node_bytes(int n) { return (size_t)(n > 1 ? n - 1 : 1) * 64; }
+inline size_t bvh_tri_bytes(int n) { return (size_t)(n > 0 ? n : 1) * 48; }
+
+// ---- launchers (each enqueues kernels on `stream`, returns cudaGetLastError) ----
+cudaError_t launch_envmap_cdf(const float* env, int W, int H, float* cond, float* marg, double* row_sum,
+                              double* total, cudaStream_t stream);
+
+cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
+                             void* tri_records, void* scratch, const BvhScratch& layout, cudaStream_t stream);
+
+struct ShadeArgs {
+    const void* nodes;
+    const void* tris;
+    int n_tris;
+    const float4* env;
+    int Wp, Hp;
+    const float* cond;
+    const float* marg;
+    const double* total;
+    const float4* gb_pos;
+    const float4* gb_nrm;
+    const float4* gb_kd;
+    const float4* gb_korm;
+    const mcdi_camera* cams;
+    int N, H, W;
+    int n_light, n_cos, n_ggx;
+    unsigned long long seed;
+    float tau, ray_eps;
+    uint32_t stream_word;
+};
+
+cudaError_t launch_primary_cast(const void* nodes, const void* tris, int n_tris, const float* verts,
+                                const float* vnrm, const int* tri_idx, int n_verts, const mcdi_camera* cams, int N,
+                                int H, int W, const float* tex_kd, const float* tex_korm, int tex_size, float uv_ox,
+                                float uv_oz, float uv_s, float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm,
+                                cudaStream_t stream);
+
+cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
+                             cudaStream_t stream);
+
+cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float4* g_kdout, const float4* g_cs,
+                             const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,
+                             cudaStream_t stream);
+
+}  // namespace mcdi

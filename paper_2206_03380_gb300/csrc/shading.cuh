@@ -1,0 +1,344 @@
+// Device functions of the Monte Carlo direct-illumination estimator (Sec. 3.1,
+// Sec. 4.1): BVH traversal, probe / cosine / GGX sampling and densities, the
+// GGX lobe, and the per-sample MIS weight.  Everything is FP32.
+#pragma once
+
+#include <float.h>
+
+#include "common.cuh"
+
+namespace mcdi {
+
+// ---------------------------------------------------------------- traversal
+struct RayInv {
+    f3 o, d, inv;
+};
+
+__device__ __forceinline__ RayInv make_ray(f3 o, f3 d) {
+    // direction components are kept away from zero so that slab distances stay finite
+    auto safe = [](float x) { return fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x; };
+    RayInv r;
+    r.o = o;
+    r.d = d;
+    r.inv = mk(1.0f / safe(d.x), 1.0f / safe(d.y), 1.0f / safe(d.z));
+    return r;
+}
+
+// slab test of one box given as (lo.x, hi.x, lo.y, hi.y) + (lo.z, hi.z);
+// returns the entry distance or +inf on a miss.  The exit distance is scaled by
+// 1 + 2 gamma_3 so that rounding never drops a box the ray touches (Ize 2013).
+__device__ __forceinline__ float slab(const RayInv& r, float4 xy, float2 z, float tmax) {
+    const float tx0 = (xy.x - r.o.x) * r.inv.x, tx1 = (xy.y - r.o.x) * r.inv.x;
+    const float ty0 = (xy.z - r.o.y) * r.inv.y, ty1 = (xy.w - r.o.y) * r.inv.y;
+    const float tz0 = (z.x - r.o.z) * r.inv.z, tz1 = (z.y - r.o.z) * r.inv.z;
+    const float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax)) * 1.00000036f;
+    return t0 <= t1 ? t0 : FLT_MAX;
+}
+
+// Moller-Trumbore, two-sided, edges inclusive; returns t (> 0) or +inf
+__device__ __forceinline__ float tri_hit(const RayInv& r, const TriRecord* __restrict__ tris, int k, float* bu,
+                                         float* bv) {
+    const float4 v0 = __ldg(&tris[k].v0), e1v = __ldg(&tris[k].e1), e2v = __ldg(&tris[k].e2);
+    const f3 e1 = xyz(e1v), e2 = xyz(e2v);
+    const f3 p = cross(r.d, e2);
+    const float det = dot(e1, p);
+    if (det == 0.0f) return FLT_MAX;
+    const float inv = 1.0f / det;
+    const f3 s = r.o - xyz(v0);
+    const float u = dot(s, p) * inv;
+    if (u < 0.0f || u > 1.0f) return FLT_MAX;
+    const f3 q = cross(s, e1);
+    const float v = dot(r.d, q) * inv;
+    if (v < 0.0f || u + v > 1.0f) return FLT_MAX;
+    const float t = dot(e2, q) * inv;
+    if (!(t > 0.0f)) return FLT_MAX;
+    if (bu) {
+        *bu = u;
+        *bv = v;
+    }
+    return t;
+}
+
+// any hit with t > 0 (shadow ray, no far limit)
+__device__ __forceinline__ bool any_hit(const BvhNode* __restrict__ nodes, const TriRecord* __restrict__ tris,
+                                        int n_tris, const RayInv& r) {
+    if (n_tris <= 0) return false;
+    int stack[kTraversalStack];
+    int sp = 0;
+    int node = 0;
+    // a tree over n leaves has n - 1 internal nodes: each is visited at most once
+    for (int iter = 0; iter < n_tris + 1; ++iter) {
+        const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
+        const int4 d = __ldg(&nodes[node].d);
+        bool h0 = slab(r, a, make_float2(c.x, c.y), FLT_MAX) < FLT_MAX;
+        bool h1 = slab(r, b, make_float2(c.z, c.w), FLT_MAX) < FLT_MAX;
+        if (h0 && d.x < 0) {
+            if (tri_hit(r, tris, ~d.x, nullptr, nullptr) < FLT_MAX) return true;
+            h0 = false;
+        }
+        if (h1 && d.y < 0) {
+            if (tri_hit(r, tris, ~d.y, nullptr, nullptr) < FLT_MAX) return true;
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp < kTraversalStack) stack[sp++] = d.y;
+            node = d.x;
+        } else if (h0) {
+            node = d.x;
+        } else if (h1) {
+            node = d.y;
+        } else {
+            if (sp == 0) return false;
+            node = stack[--sp];
+        }
+    }
+    return false;
+}
+
+// closest hit; returns the leaf (triangle record) index or -1
+__device__ __forceinline__ int closest_hit(const BvhNode* __restrict__ nodes, const TriRecord* __restrict__ tris,
+                                           int n_tris, const RayInv& r, float* t_out, float* bu, float* bv) {
+    int best = -1;
+    float tbest = FLT_MAX;
+    if (n_tris <= 0) return -1;
+    int stack[kTraversalStack];
+    int sp = 0;
+    int node = 0;
+    for (int iter = 0; iter < n_tris + 1; ++iter) {
+        const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
+        const int4 d = __ldg(&nodes[node].d);
+        float t0 = slab(r, a, make_float2(c.x, c.y), tbest);
+        float t1 = slab(r, b, make_float2(c.z, c.w), tbest);
+        if (t0 < FLT_MAX && d.x < 0) {
+            float u, v;
+            const float t = tri_hit(r, tris, ~d.x, &u, &v);
+            if (t < tbest) tbest = t, best = ~d.x, *bu = u, *bv = v;
+            t0 = FLT_MAX;
+        }
+        if (t1 < FLT_MAX && d.y < 0) {
+            float u, v;
+            const float t = tri_hit(r, tris, ~d.y, &u, &v);
+            if (t < tbest) tbest = t, best = ~d.y, *bu = u, *bv = v;
+            t1 = FLT_MAX;
+        }
+        if (t0 < FLT_MAX && t1 < FLT_MAX) {
+            const bool first0 = t0 <= t1;
+            if (sp < kTraversalStack) stack[sp++] = first0 ? d.y : d.x;
+            node = first0 ? d.x : d.y;
+        } else if (t0 < FLT_MAX) {
+            node = d.x;
+        } else if (t1 < FLT_MAX) {
+            node = d.y;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    *t_out = tbest;
+    return best;
+}
+
+// ---------------------------------------------------------------- probe
+// largest k in [0, n-1] with cdf[k] <= u
+__device__ __forceinline__ int upper_index(const float* __restrict__ cdf, int n, float u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(cdf + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// (u, v) -> direction: phi = 2 pi u, theta = pi v, y up
+__device__ __forceinline__ f3 dir_from_uv(float u, float v, float* sin_theta) {
+    float sp, cp, st, ct;
+    sincospif(2.0f * u, &sp, &cp);
+    sincospif(v, &st, &ct);
+    *sin_theta = st;
+    return mk(st * cp, ct, st * sp);
+}
+
+struct Probe {
+    const float4* env;
+    const float* cond;
+    const float* marg;
+    int W, H;
+    bool on;  // total > 0
+};
+
+// probe texel of a direction and sin(theta) (accurate near the poles)
+__device__ __forceinline__ int texel_of_dir(const Probe& P, f3 d, float* sin_theta) {
+    const float st = sqrtf(d.x * d.x + d.z * d.z);
+    float u = atan2f(d.z, d.x) * (0.5f * MCDI_INV_PI);
+    if (u < 0.0f) u += 1.0f;
+    const float v = atan2f(st, d.y) * MCDI_INV_PI;
+    const int i = min(P.W - 1, (int)(u * (float)P.W));
+    const int j = min(P.H - 1, (int)(v * (float)P.H));
+    *sin_theta = st;
+    return j * P.W + i;
+}
+
+// density of the probe technique at texel t for a direction with sin(theta) st
+__device__ __forceinline__ float pdf_light_texel(const Probe& P, int t, float st) {
+    if (!P.on || !(st > 0.0f)) return 0.0f;
+    const int j = t / P.W, i = t - j * P.W;
+    const float* c = P.cond + (size_t)j * (P.W + 1);
+    const float wr = __ldg(P.marg + j + 1) - __ldg(P.marg + j);
+    const float wc = __ldg(c + i + 1) - __ldg(c + i);
+    return ((float)P.W * (float)P.H * wr * wc) / (2.0f * MCDI_PI * MCDI_PI * st);
+}
+
+// probe sample; returns false if the technique is off
+__device__ __forceinline__ bool sample_light(const Probe& P, float u0, float u1, f3* d, int* texel, float* pdf) {
+    if (!P.on) return false;
+    const int j = upper_index(P.marg, P.H, u0);
+    const float m0 = __ldg(P.marg + j), m1 = __ldg(P.marg + j + 1);
+    const float* c = P.cond + (size_t)j * (P.W + 1);
+    const int i = upper_index(c, P.W, u1);
+    const float c0 = __ldg(c + i), c1 = __ldg(c + i + 1);
+    const float dv = fminf((u0 - m0) / (m1 - m0), 0.99999994f);
+    const float du = fminf((u1 - c0) / (c1 - c0), 0.99999994f);
+    float st;
+    *d = dir_from_uv(((float)i + du) / (float)P.W, ((float)j + dv) / (float)P.H, &st);
+    *texel = j * P.W + i;
+    *pdf = st > 0.0f ? ((float)P.W * (float)P.H * (m1 - m0) * (c1 - c0)) / (2.0f * MCDI_PI * MCDI_PI * st) : 0.0f;
+    return true;
+}
+
+// ---------------------------------------------------------------- frame + lobes
+// orthonormal basis of Duff et al. 2017 (sign(0) = +1)
+__device__ __forceinline__ void frame(f3 n, f3* b1, f3* b2) {
+    const float s = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (s + n.z);
+    const float b = n.x * n.y * a;
+    *b1 = mk(1.0f + s * n.x * n.x * a, s * b, -s * n.x);
+    *b2 = mk(b, s + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ f3 sample_cosine(f3 n, f3 b1, f3 b2, float u0, float u1) {
+    float sp, cp;
+    sincospif(2.0f * u1, &sp, &cp);
+    const float r = sqrtf(u0);
+    const float z = sqrtf(1.0f - u0);
+    return b1 * (r * cp) + b2 * (r * sp) + n * z;
+}
+
+// GGX normal distribution with the denominator term nh^2 (a2 - 1) + 1 written as
+// sin^2 + nh^2 a2 (s2 = |n x h|^2): free of the cancellation of 1 - nh^2 near the
+// lobe peak, which in FP32 would cost ~1e-3 relative accuracy at alpha ~ 0.006.
+__device__ __forceinline__ float ggx_D_denom(float nh, float s2, float a2) { return s2 + nh * nh * a2; }
+__device__ __forceinline__ float ggx_D(float nh, float s2, float a2) {
+    if (!(nh > 0.0f)) return 0.0f;
+    const float d = ggx_D_denom(nh, s2, a2);
+    return a2 / (MCDI_PI * d * d);
+}
+__device__ __forceinline__ float sin2_between(f3 n, f3 h) {
+    const f3 c = cross(n, h);
+    return dot(c, c);
+}
+
+__device__ __forceinline__ float ggx_lambda(float c, float a2) {
+    const float z = a2 * (1.0f / (c * c) - 1.0f);
+    return 0.5f * (sqrtf(1.0f + z) - 1.0f);
+}
+
+// Heitz 2018 visible-normal sample, returns the reflected light direction
+__device__ __forceinline__ f3 sample_ggx(f3 n, f3 b1, f3 b2, f3 wo, float alpha, float u0, float u1) {
+    const f3 lo = mk(dot(wo, b1), dot(wo, b2), dot(wo, n));
+    const f3 vh = normalize(mk(alpha * lo.x, alpha * lo.y, lo.z));
+    const float lensq = vh.x * vh.x + vh.y * vh.y;
+    f3 t1v = lensq > 0.0f ? mk(-vh.y, vh.x, 0.0f) * rsqrtf(lensq) : mk(1.0f, 0.0f, 0.0f);
+    const f3 t2v = cross(vh, t1v);
+    float sp, cp;
+    sincospif(2.0f * u1, &sp, &cp);
+    const float r = sqrtf(u0);
+    const float t1 = r * cp;
+    float t2 = r * sp;
+    const float s = 0.5f * (1.0f + vh.z);
+    t2 = (1.0f - s) * sqrtf(1.0f - t1 * t1) + s * t2;
+    const float tz = sqrtf(fmaxf(0.0f, 1.0f - t1 * t1 - t2 * t2));
+    const f3 nh = t1v * t1 + t2v * t2 + vh * tz;
+    const f3 hl = normalize(mk(alpha * nh.x, alpha * nh.y, fmaxf(nh.z, 0.0f)));
+    const f3 h = b1 * hl.x + b2 * hl.y + n * hl.z;
+    const float voh = dot(wo, h);
+    return h * (2.0f * voh) - wo;
+}
+
+__device__ __forceinline__ float pdf_ggx(f3 n, f3 wo, float co, float a2, float g1o, f3 wi) {
+    f3 h = wi + wo;
+    const float l2 = dot(h, h);
+    if (!(l2 > 0.0f)) return 0.0f;
+    h = h * rsqrtf(l2);
+    if (!(dot(wo, h) > 0.0f)) return 0.0f;
+    return g1o * ggx_D(dot(n, h), sin2_between(n, h), a2) / (4.0f * co);
+}
+
+__device__ __forceinline__ float schlick_weight(float vh) {
+    const float x = 1.0f - fminf(fmaxf(vh, 0.0f), 1.0f);
+    const float x2 = x * x;
+    return x2 * x2 * x;
+}
+
+// ---------------------------------------------------------------- per pixel
+struct Pixel {
+    f3 p, n, wo, b1, b2;
+    float lN, co, alpha, a2, g1o, r, m;
+    f3 kd, F0;
+    bool spec_on;
+};
+
+__device__ __forceinline__ bool load_pixel(float4 pos, float4 nrm, float4 kd, float4 korm, f3 cam, Pixel* px) {
+    const f3 N = xyz(nrm);
+    const float l2 = dot(N, N);
+    if (!(pos.w > 0.0f) || !(l2 > 0.0f)) return false;
+    px->lN = sqrtf(l2);
+    px->n = N * (1.0f / px->lN);
+    px->p = xyz(pos);
+    px->wo = normalize(cam - px->p);
+    px->co = dot(px->n, px->wo);
+    px->spec_on = px->co >= 1e-4f;
+    px->r = korm.y;
+    px->m = korm.z;
+    px->alpha = fmaxf(px->r * px->r, 1e-4f);
+    px->a2 = px->alpha * px->alpha;
+    px->g1o = px->spec_on ? 1.0f / (1.0f + ggx_lambda(px->co, px->a2)) : 0.0f;
+    px->kd = xyz(kd);
+    px->F0 = mk(0.04f * (1.0f - px->m) + px->kd.x * px->m, 0.04f * (1.0f - px->m) + px->kd.y * px->m,
+                0.04f * (1.0f - px->m) + px->kd.z * px->m);
+    frame(px->n, &px->b1, &px->b2);
+    return true;
+}
+
+// One sample of the MIS estimator: direction, texel and 1/denominator.
+// Returns false when the sample does not contribute (technique off, below the
+// horizon, zero density).
+__device__ __forceinline__ bool draw_sample(const Probe& P, const Pixel& px, int n_light, int n_cos, int n_ggx,
+                                            int j, float2 u, f3* wi, int* texel, float* ci, float* inv_denom) {
+    float pl = 0.0f, st = 0.0f;
+    int t = -1;
+    if (j < n_light) {
+        if (!sample_light(P, u.x, u.y, wi, &t, &pl)) return false;
+    } else if (j < n_light + n_cos) {
+        *wi = sample_cosine(px.n, px.b1, px.b2, u.x, u.y);
+    } else {
+        if (!px.spec_on) return false;
+        *wi = sample_ggx(px.n, px.b1, px.b2, px.wo, px.alpha, u.x, u.y);
+    }
+    const float c = dot(px.n, *wi);
+    if (!(c > 0.0f)) return false;
+    if (t < 0) {
+        t = texel_of_dir(P, *wi, &st);
+        pl = pdf_light_texel(P, t, st);
+    }
+    float denom = (float)n_light * pl + (float)n_cos * (c * MCDI_INV_PI);
+    if (px.spec_on && n_ggx > 0) denom += (float)n_ggx * pdf_ggx(px.n, px.wo, px.co, px.a2, px.g1o, *wi);
+    if (!(denom > 0.0f)) return false;
+    *texel = t;
+    *ci = c;
+    *inv_denom = 1.0f / denom;
+    return true;
+}
+
+}  // namespace mcdi

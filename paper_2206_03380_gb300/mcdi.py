@@ -1,0 +1,248 @@
+"""Python binding of libmcdi (ctypes): argument marshalling only.
+
+Each function carries the C entry point's name without the ``mcdi_`` prefix
+and takes torch CUDA tensors (or raw device addresses as ints); all the work
+runs in the library's CUDA kernels on the current torch stream.  There is no
+CPU fallback: if the library is not built, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmcdi.so")
+_lib = None
+
+OK, INVALID_ARG, UNSUPPORTED, OOM, TIMEOUT, DEVICE_ERROR = range(6)
+
+
+class McdiError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} failed (status {status}): {msg}")
+        self.status = status
+
+
+class BvhView(C.Structure):
+    _fields_ = [("nodes", C.c_void_p), ("tri_records", C.c_void_p), ("n_tris", C.c_int)]
+
+
+class ShadeParams(C.Structure):
+    _fields_ = [("n_light", C.c_int), ("n_cos", C.c_int), ("n_ggx", C.c_int), ("decorrelate_bwd", C.c_int),
+                ("seed", C.c_ulonglong), ("tau", C.c_float), ("ray_eps", C.c_float)]
+
+
+EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh_sizes", "mcdi_build_bvh",
+           "mcdi_primary_cast", "mcdi_shade_mc_fwd", "mcdi_shade_mc_bwd"]
+
+
+def load(path: str = LIB_PATH):
+    """Load libmcdi.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmcdi.so not built at {path}: run paper_2206_03380_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, i, sz, st = C.c_void_p, C.c_int, C.c_size_t, C.c_int
+    lib.mcdi_last_error.restype = C.c_char_p
+    lib.mcdi_last_error.argtypes = []
+    lib.mcdi_version.restype = C.c_int
+    lib.mcdi_version.argtypes = []
+    lib.mcdi_build_envmap_cdf.restype = st
+    lib.mcdi_build_envmap_cdf.argtypes = [P, i, i, P, P, P, P, P]
+    lib.mcdi_bvh_sizes.restype = st
+    lib.mcdi_bvh_sizes.argtypes = [i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
+    lib.mcdi_build_bvh.restype = st
+    lib.mcdi_build_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
+    lib.mcdi_primary_cast.restype = st
+    lib.mcdi_primary_cast.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
+                                      P, P, P, P, P]
+    lib.mcdi_shade_mc_fwd.restype = st
+    lib.mcdi_shade_mc_fwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
+                                      C.POINTER(ShadeParams), P, P, P, P, P]
+    lib.mcdi_shade_mc_bwd.restype = st
+    lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
+                                      C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor arguments must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise McdiError(status, where, load().mcdi_last_error().decode())
+
+
+# ------------------------------------------------------------------ entry points
+def version() -> int:
+    return load().mcdi_version()
+
+
+def build_envmap_cdf(env, cond, marg, row_sum, total, stream=None):
+    H, W = env.shape[0], env.shape[1]
+    _check(load().mcdi_build_envmap_cdf(_ptr(env), W, H, _ptr(cond), _ptr(marg), _ptr(row_sum), _ptr(total),
+                                        _stream(stream)), "build_envmap_cdf")
+
+
+def bvh_sizes(n_tris: int):
+    a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    _check(load().mcdi_bvh_sizes(int(n_tris), C.byref(a), C.byref(b), C.byref(c)), "bvh_sizes")
+    return a.value, b.value, c.value
+
+
+def build_bvh(verts, tris, nodes, tri_records, scratch, stream=None):
+    _check(load().mcdi_build_bvh(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(nodes),
+                                 _ptr(tri_records), _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                 _stream(stream)), "build_bvh")
+
+
+def primary_cast(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, stream=None):
+    uv = (C.c_float * 3)(*[float(x) for x in uvmap])
+    _check(load().mcdi_primary_cast(C.byref(bvh.view), _ptr(verts), _ptr(vnrm), _ptr(tris), verts.shape[0],
+                                    _ptr(cams), cams.shape[0], H, W, _ptr(tex_kd), _ptr(tex_korm), tex_kd.shape[0],
+                                    uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm), _stream(stream)),
+           "primary_cast")
+
+
+def shade_mc_fwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, c_d, kd_out, c_s,
+                 vis_mask=None, stream=None):
+    N, H, W = gb.pos.shape[:3]
+    Hp, Wp = probe.env.shape[:2]
+    _check(load().mcdi_shade_mc_fwd(C.byref(bvh.view), _ptr(probe.env), Wp, Hp, _ptr(probe.cond), _ptr(probe.marg),
+                                    _ptr(probe.total), _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm),
+                                    _ptr(cams), N, H, W, C.byref(params), _ptr(c_d), _ptr(kd_out), _ptr(c_s),
+                                    _ptr(vis_mask), _stream(stream)), "shade_mc_fwd")
+
+
+def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, g_cd, g_kdout, g_cs,
+                 vis_mask, g_kd, g_korm, g_nrm, g_env, stream=None):
+    N, H, W = gb.pos.shape[:3]
+    Hp, Wp = probe.env.shape[:2]
+    _check(load().mcdi_shade_mc_bwd(C.byref(bvh.view), _ptr(probe.env), Wp, Hp, _ptr(probe.cond), _ptr(probe.marg),
+                                    _ptr(probe.total), _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm),
+                                    _ptr(cams), N, H, W, C.byref(params), _ptr(g_cd), _ptr(g_kdout), _ptr(g_cs),
+                                    _ptr(vis_mask), _ptr(g_kd), _ptr(g_korm), _ptr(g_nrm), _ptr(g_env),
+                                    _stream(stream)), "shade_mc_bwd")
+
+
+# ------------------------------------------------------------------ device-resident objects
+def _empty_bytes(n: int, device) -> torch.Tensor:
+    # 256-byte aligned raw buffer
+    return torch.empty((max(n, 1) + 255) // 256 * 256, dtype=torch.uint8, device=device)
+
+
+@dataclass
+class Bvh:
+    nodes: torch.Tensor
+    tri_records: torch.Tensor
+    scratch: torch.Tensor
+    n_tris: int
+
+    @property
+    def view(self) -> BvhView:
+        return BvhView(self.nodes.data_ptr(), self.tri_records.data_ptr(), self.n_tris)
+
+    @classmethod
+    def allocate(cls, n_tris: int, device="cuda") -> "Bvh":
+        nb, tb, sb = bvh_sizes(n_tris)
+        return cls(_empty_bytes(nb, device), _empty_bytes(tb, device), _empty_bytes(sb, device), n_tris)
+
+    def build(self, verts, tris, stream=None) -> "Bvh":
+        build_bvh(verts, tris, self.nodes, self.tri_records, self.scratch, stream)
+        return self
+
+
+@dataclass
+class Probe:
+    env: torch.Tensor    # (Hp, Wp, 4) float32
+    cond: torch.Tensor   # (Hp, Wp + 1) float32
+    marg: torch.Tensor   # (Hp + 1,) float32
+    row_sum: torch.Tensor
+    total: torch.Tensor  # (1,) float64
+
+    @classmethod
+    def allocate(cls, env: torch.Tensor) -> "Probe":
+        Hp, Wp = env.shape[:2]
+        dev = env.device
+        return cls(env, torch.empty(Hp, Wp + 1, device=dev), torch.empty(Hp + 1, device=dev),
+                   torch.empty(Hp, dtype=torch.float64, device=dev), torch.empty(1, dtype=torch.float64, device=dev))
+
+    def build(self, stream=None) -> "Probe":
+        build_envmap_cdf(self.env, self.cond, self.marg, self.row_sum, self.total, stream)
+        return self
+
+
+@dataclass
+class GBuffer:
+    pos: torch.Tensor   # (N, H, W, 4)
+    nrm: torch.Tensor
+    kd: torch.Tensor
+    korm: torch.Tensor
+
+    @classmethod
+    def allocate(cls, N, H, W, device="cuda") -> "GBuffer":
+        return cls(*[torch.empty(N, H, W, 4, device=device) for _ in range(4)])
+
+
+def make_params(n_light, n_cos, n_ggx, seed, tau=0.0, ray_eps=1e-4, decorrelate_bwd=False) -> ShadeParams:
+    return ShadeParams(int(n_light), int(n_cos), int(n_ggx), int(bool(decorrelate_bwd)), int(seed), float(tau),
+                       float(ray_eps))
+
+
+class ShadeMC(torch.autograd.Function):
+    """c_d, kd_out, c_s = ShadeMC.apply(kd, korm, nrm, env, ctx_objects...)
+
+    Differentiable with respect to the G-buffer k_d, k_orm and normal planes and
+    the probe texels; the sampling tables, positions and BVH are constants.
+    """
+
+    @staticmethod
+    def forward(ctx, kd, korm, nrm, env, pos, bvh, probe, cams, params, keep_mask=True):
+        gb = GBuffer(pos.contiguous(), nrm.contiguous(), kd.contiguous(), korm.contiguous())
+        pr = Probe(env.contiguous(), probe.cond, probe.marg, probe.row_sum, probe.total)
+        N, H, W = pos.shape[:3]
+        spp = params.n_light + params.n_cos + params.n_ggx
+        c_d, kd_out, c_s = (torch.empty_like(pos) for _ in range(3))
+        mask = torch.empty(N, H, W, (spp + 31) // 32, dtype=torch.int32, device=pos.device) if keep_mask else None
+        shade_mc_fwd(bvh, pr, gb, cams, params, c_d, kd_out, c_s, mask)
+        ctx.bvh, ctx.probe, ctx.params, ctx.gb = bvh, pr, params, gb
+        ctx.save_for_backward(cams, mask if mask is not None else torch.empty(0, device=pos.device))
+        ctx.has_mask = mask is not None
+        return c_d, kd_out, c_s
+
+    @staticmethod
+    def backward(ctx, g_cd, g_kdout, g_cs):
+        cams, mask = ctx.saved_tensors
+        gb = ctx.gb
+        zeros = None
+        if g_cd is None or g_kdout is None or g_cs is None:
+            zeros = torch.zeros_like(gb.pos)
+        g_cd = (g_cd if g_cd is not None else zeros).contiguous()
+        g_kdout = (g_kdout if g_kdout is not None else zeros).contiguous()
+        g_cs = (g_cs if g_cs is not None else zeros).contiguous()
+        g_kd, g_korm, g_nrm = (torch.empty_like(gb.pos) for _ in range(3))
+        g_env = torch.zeros_like(ctx.probe.env)
+        shade_mc_bwd(ctx.bvh, ctx.probe, gb, cams, ctx.params, g_cd, g_kdout, g_cs, mask if ctx.has_mask else None,
+                     g_kd, g_korm, g_nrm, g_env)
+        return g_kd, g_korm, g_nrm, g_env, None, None, None, None, None, None

@@ -1,0 +1,76 @@
+"""The C-ABI library loads and exports every entry point that include/*.h
+declares, and rejects bad arguments on the host (no GPU needed: argument checks
+run before anything is enqueued)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        names |= set(re.findall(r"MCDI_API\s+[\w\s\*]+?\b(mcdi_\w+)\s*\(", open(h).read()))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2206_03380_gb300 import build, mcdi
+
+    if not os.path.exists(mcdi.LIB_PATH):
+        build.build()
+    return mcdi.load()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ["mcdi_build_envmap_cdf", "mcdi_build_bvh", "mcdi_shade_mc_fwd", "mcdi_shade_mc_bwd",
+                 "mcdi_primary_cast", "mcdi_bvh_sizes", "mcdi_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(mcdi.EXPORTS) <= set(declared_symbols())
+
+
+def test_argument_checks_without_gpu(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    assert lib.mcdi_version() >= 100
+    # NULL / misaligned / out-of-range arguments fail on the host with INVALID_ARG
+    assert lib.mcdi_build_envmap_cdf(None, 32, 16, None, None, None, None, None) == mcdi.INVALID_ARG
+    assert b"env" in lib.mcdi_last_error()
+    assert lib.mcdi_build_envmap_cdf(C.c_void_p(16), 0, 16, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16),
+                                     C.c_void_p(16), None) == mcdi.INVALID_ARG
+    a, b, s = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    assert lib.mcdi_bvh_sizes(0, C.byref(a), C.byref(b), C.byref(s)) == mcdi.INVALID_ARG
+    assert lib.mcdi_bvh_sizes(1000, C.byref(a), C.byref(b), C.byref(s)) == mcdi.OK
+    assert a.value == 999 * 64 and b.value == 1000 * 48 and s.value > 0
+    # scratch smaller than the query -> rejected before any launch
+    assert lib.mcdi_build_bvh(C.c_void_p(256), 3, C.c_void_p(256), 1000, C.c_void_p(256), C.c_void_p(256),
+                              C.c_void_p(256), s.value - 1, None) == mcdi.INVALID_ARG
+    assert b"scratch" in lib.mcdi_last_error()
+    bvh = mcdi.BvhView(None, None, 0)
+    prm = mcdi.make_params(4, 2, 2, 1)
+    bad = mcdi.make_params(0, 0, 0, 1)
+    p16 = C.c_void_p(4096)
+    args = [C.byref(bvh), p16, 32, 16, p16, p16, p16, p16, p16, p16, p16, p16, 1, 8, 8]
+    outs = [p16, p16, p16, None, None]
+    assert lib.mcdi_shade_mc_fwd(*args, C.byref(bad), *outs) == mcdi.INVALID_ARG
+    assert b"spp" in lib.mcdi_last_error()
+    mis = C.c_void_p(4100)  # not 16-byte aligned
+    args_mis = list(args)
+    args_mis[7] = mis
+    assert lib.mcdi_shade_mc_fwd(*args_mis, C.byref(prm), *outs) == mcdi.INVALID_ARG
+    assert b"gb_pos" in lib.mcdi_last_error()
+    tau_bad = mcdi.make_params(4, 2, 2, 1, tau=1.5)
+    assert lib.mcdi_shade_mc_fwd(*args, C.byref(tau_bad), *outs) == mcdi.INVALID_ARG

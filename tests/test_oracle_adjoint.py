@@ -107,3 +107,19 @@ def test_adjoint_of_black_pixels_is_zero(orc, frozen_case):
     g[:5, 3:6] = 0.0  # no upstream on k_d,out either
     grad, _ = orc.frozen_adjoint(rec, c["prow"], c["cam"], c["spec_on"], c["env3"], g)
     assert np.all(grad[:5] == 0.0)
+
+
+def test_adjoint_scale_bounds_gradient(orc, frozen_case):
+    c = frozen_case
+    grad, genv, scale, gscale = orc.frozen_adjoint(c["rec"], c["prow"], c["cam"], c["spec_on"], c["env3"], c["g"],
+                                                   with_scale=True)
+    g0, e0 = orc.frozen_adjoint(c["rec"], c["prow"], c["cam"], c["spec_on"], c["env3"], c["g"])
+    np.testing.assert_array_equal(grad, g0)
+    np.testing.assert_array_equal(genv, e0)
+    assert np.all(scale >= np.abs(grad) * (1 - 1e-12)) and np.all(gscale >= np.abs(genv) * (1 - 1e-12))
+    # a single active sample per pixel: no cancellation, the scale is the magnitude itself
+    rec = c["rec"].copy()
+    rec["active"][:, 1:] = 0
+    g1, _, s1, _ = orc.frozen_adjoint(rec, c["prow"], c["cam"], c["spec_on"], c["env3"], c["g"], with_scale=True)
+    g1n = g1.copy()
+    np.testing.assert_allclose(s1[:, 7], np.abs(g1n[:, 7]), rtol=1e-12)

@@ -77,7 +77,8 @@ MUTANTS = [
      [lambda o: E.test_specular_albedo_matches_quadrature(o, 0.25, 0.5)]),
     ("adjoint: D slope sign", "dD_dnh = -4.0 * D * nh * (a2 - 1.0) / dd;", "dD_dnh = 4.0 * D * nh * (a2 - 1.0) / dd;",
      [_adjoint_fd]),
-    ("adjoint: no tangent projection of the normal grad", "G[k] = (gn[k] - n[k] * ng) / lN;", "G[k] = gn[k] / lN;",
+    ("adjoint: no tangent projection of the normal grad", "out[k] = (gn[k] - A->n[k] * ng) / A->lN;",
+     "out[k] = gn[k] / A->lN;",
      [_adjoint_fd]),
     ("adjoint: metallic through F0 with the wrong sign", "g_m += -gk[c] * kd[c] + gF0[c] * (kd[c] - 0.04);",
      "g_m += -gk[c] * kd[c] + gF0[c] * (0.04 - kd[c]);", [_adjoint_fd]),
