@@ -88,6 +88,27 @@ MCDI_API mcdi_status mcdi_bvh_sizes(int n_tris, size_t* node_bytes, size_t* tri_
 MCDI_API mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
                            void* tri_records, void* scratch, size_t scratch_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * mcdi_build_bvh_noalloc: the same build as mcdi_build_bvh (identical nodes
+ * and triangle records for the same mesh) with no scratch argument.  The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * allocate device memory themselves, for example a plugin running inside a
+ * host application that owns every device allocation, or a request loop
+ * whose memory budget is fixed at start-up and may not grow (cudaMalloc can
+ * also block on the device, which such loops cannot afford).
+ * Scratch lives in one fixed device array inside the library (about 6 MB,
+ * held on every GPU that loads the library until the process exits); the
+ * first call on a device looks up its address on that device, so make that
+ * first call before any stream capture.  The call allocates and frees
+ * nothing.  n_tris is limited to MCDI_NOALLOC_MAX_TRIS (larger meshes give
+ * MCDI_INVALID_ARG: use mcdi_build_bvh).  All calls share the array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Other arguments as mcdi_build_bvh.
+ * ------------------------------------------------------------------------ */
+#define MCDI_NOALLOC_MAX_TRIS 65536
+MCDI_API mcdi_status mcdi_build_bvh_noalloc(const float* verts, int n_verts, const int* tris, int n_tris,
+                                            void* nodes, void* tri_records, void* stream);
+
 /* A built BVH as the shading kernels read it (host struct, device pointers). */
 typedef struct {
     const void* nodes;

@@ -99,6 +99,10 @@ mcdi_status shade_common(const mcdi_bvh_view* bvh, const float* env, int Wp, int
 
 }  // namespace
 
+namespace mcdi {
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace mcdi
+
 extern "C" {
 
 const char* mcdi_last_error(void) { return g_err; }

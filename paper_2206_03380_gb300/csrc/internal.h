@@ -46,6 +46,9 @@ inline BvhScratch bvh_scratch_layout(int n) {
 inline size_t bvh_node_bytes(int n) { return (size_t)(n > 1 ? n - 1 : 1) * 64; }
 inline size_t bvh_tri_bytes(int n) { return (size_t)(n > 0 ? n : 1) * 48; }
 
+// Record the reason returned by mcdi_last_error() on this thread ("" clears it).
+void set_last_error(const char* msg);
+
 // ---- launchers (each enqueues kernels on `stream`, returns cudaGetLastError) ----
 cudaError_t launch_envmap_cdf(const float* env, int W, int H, float* cond, float* marg, double* row_sum,
                               double* total, cudaStream_t stream);

@@ -36,7 +36,8 @@ class ShadeParams(C.Structure):
 
 
 EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh_sizes", "mcdi_build_bvh",
-           "mcdi_primary_cast", "mcdi_shade_mc_fwd", "mcdi_shade_mc_bwd"]
+           "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_mc_fwd", "mcdi_shade_mc_bwd"]
+NOALLOC_MAX_TRIS = 65536
 
 
 def load(path: str = LIB_PATH):
@@ -58,6 +59,8 @@ def load(path: str = LIB_PATH):
     lib.mcdi_bvh_sizes.argtypes = [i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_build_bvh.restype = st
     lib.mcdi_build_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
+    lib.mcdi_build_bvh_noalloc.restype = st
+    lib.mcdi_build_bvh_noalloc.argtypes = [P, i, P, i, P, P, P]
     lib.mcdi_primary_cast.restype = st
     lib.mcdi_primary_cast.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
                                       P, P, P, P, P]
@@ -115,6 +118,13 @@ def build_bvh(verts, tris, nodes, tri_records, scratch, stream=None):
     _check(load().mcdi_build_bvh(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(nodes),
                                  _ptr(tri_records), _ptr(scratch), scratch.numel() * scratch.element_size(),
                                  _stream(stream)), "build_bvh")
+
+
+def build_bvh_noalloc(verts, tris, nodes, tri_records, stream=None):
+    """BVH build with the library's own fixed scratch (no caller scratch; at most
+    NOALLOC_MAX_TRIS triangles; calls that overlap on the GPU must be serialised)."""
+    _check(load().mcdi_build_bvh_noalloc(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(nodes),
+                                         _ptr(tri_records), _stream(stream)), "build_bvh_noalloc")
 
 
 def primary_cast(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, stream=None):
