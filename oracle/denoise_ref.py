@@ -1,0 +1,129 @@
+"""Denoiser oracle: the U-Net of 3x3 convolutions applied to c_d and c_s
+(Sec. 4.2 "Neural denoisers": a direct-prediction U-Net, fully convolutional
+and therefore differentiable; App. B: random (Xavier) initialisation for the
+live-trained variant), written with plain PyTorch CPU float64 library ops
+(conv2d, max_pool2d, nearest interpolate, cat) and autograd for the adjoint.
+
+TEST INFRASTRUCTURE: only the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import it.
+
+Reading of the network (the paper names a U-Net, not its exact layers): four
+levels of widths (32, 48, 64, 96); two 3x3 zero-padded convolutions per level,
+each followed by ReLU; 2x2 max-pool down; nearest 2x upsample, then
+concatenation of [upsampled, skip] along channels; a final linear 3x3
+convolution to 3 channels.  Input 9 channels per image: the noisy term (c_d or
+c_s), k_d and the normal; the two terms form a batch of two images.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+
+def unet_plan(cin: int = 9, cout: int = 3, widths=(32, 48, 64, 96)):
+    """Ordered list of (name, c_in, c_out, relu) for the 15 convolutions."""
+    w1, w2, w3, w4 = widths
+    return [
+        ("enc1a", cin, w1, True), ("enc1b", w1, w1, True),
+        ("enc2a", w1, w2, True), ("enc2b", w2, w2, True),
+        ("enc3a", w2, w3, True), ("enc3b", w3, w3, True),
+        ("bot_a", w3, w4, True), ("bot_b", w4, w4, True),
+        ("dec3a", w4 + w3, w3, True), ("dec3b", w3, w3, True),
+        ("dec2a", w3 + w2, w2, True), ("dec2b", w2, w2, True),
+        ("dec1a", w2 + w1, w1, True), ("dec1b", w1, w1, True),
+        ("out", w1, cout, False),
+    ]
+
+
+def xavier_weights(seed: int, plan=None):
+    """Xavier-uniform weights (fan_in = 9 c_in, fan_out = 9 c_out) and zero-mean
+    small biases, from numpy PCG64; returns {name: (W (co, ci, 3, 3), b (co,))} float32."""
+    plan = plan or unet_plan()
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, ci, co, _ in plan:
+        a = math.sqrt(6.0 / (9 * ci + 9 * co))
+        W = rng.uniform(-a, a, size=(co, ci, 3, 3)).astype(np.float32)
+        b = rng.uniform(-0.05, 0.05, size=co).astype(np.float32)
+        out[name] = (W, b)
+    return out
+
+
+def _t(a):
+    return torch.as_tensor(np.asarray(a), dtype=torch.float64)
+
+
+def conv3x3(x, W, b):
+    """3x3 convolution with zero padding 1 (cross-correlation, as the library defines it)."""
+    return F.conv2d(x, W, b, padding=1)
+
+
+def _unet(x, P):
+    """The network on float64 tensors; P = {name: (W, b)}."""
+    def conv(name, h, relu):
+        z = conv3x3(h, *P[name])
+        return F.relu(z) if relu else z
+
+    up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
+    e1 = conv("enc1b", conv("enc1a", x, True), True)
+    e2 = conv("enc2b", conv("enc2a", F.max_pool2d(e1, 2), True), True)
+    e3 = conv("enc3b", conv("enc3a", F.max_pool2d(e2, 2), True), True)
+    bt = conv("bot_b", conv("bot_a", F.max_pool2d(e3, 2), True), True)
+    d3 = conv("dec3b", conv("dec3a", torch.cat([up(bt), e3], 1), True), True)
+    d2 = conv("dec2b", conv("dec2a", torch.cat([up(d3), e2], 1), True), True)
+    d1 = conv("dec1b", conv("dec1a", torch.cat([up(d2), e1], 1), True), True)
+    return conv("out", d1, False)
+
+
+def unet_forward(x, weights):
+    """x: (N, 9, H, W) (H, W divisible by 8) -> y (N, 3, H, W), float64."""
+    with torch.no_grad():
+        return _unet(_t(x), {k: (_t(W), _t(b)) for k, (W, b) in weights.items()})
+
+
+def unet_forward_backward(x, weights, gy):
+    """Forward and the adjoint of the scalar <gy, y>: returns (y, gx, {name: (gW, gb)})."""
+    x = _t(x).clone().requires_grad_(True)
+    P = {k: (_t(W).clone().requires_grad_(True), _t(b).clone().requires_grad_(True)) for k, (W, b) in weights.items()}
+    y = _unet(x, P)
+    (y * _t(gy)).sum().backward()
+    return y.detach(), x.grad.detach(), {k: (v[0].grad.detach(), v[1].grad.detach()) for k, v in P.items()}
+
+
+def conv3x3_direct(x, W, b):
+    """Textbook 3x3 cross-correlation with zero padding, by explicit loops over taps
+    (numpy float64); used to pin the library convolution on tiny inputs."""
+    x = np.asarray(x, np.float64)
+    N, C, H, Wd = x.shape
+    co = W.shape[0]
+    xp = np.zeros((N, C, H + 2, Wd + 2))
+    xp[:, :, 1:-1, 1:-1] = x
+    y = np.zeros((N, co, H, Wd)) + np.asarray(b, np.float64)[None, :, None, None]
+    for dy in range(3):
+        for dx in range(3):
+            patch = xp[:, :, dy:dy + H, dx:dx + Wd]  # (N, C, H, W)
+            y += np.einsum("nchw,oc->nohw", patch, np.asarray(W[:, :, dy, dx], np.float64))
+    return y
+
+
+def denoiser_input(term, kd, nrm):
+    """(N, H, W, 3) planes -> (N, 9, H, W) float64 network input [term, k_d, normal]."""
+    x = np.concatenate([term, kd, nrm], axis=-1).astype(np.float64)
+    return torch.from_numpy(np.ascontiguousarray(x.transpose(0, 3, 1, 2)))
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def psnr(a, ref):
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    peak = np.abs(ref).max()
+    mse = np.mean((a - ref) ** 2)
+    return float("inf") if mse == 0 else float(10 * np.log10(peak * peak / mse))

@@ -732,20 +732,38 @@ static int adj_setup(const double* P, const double* cam, adj_pixel* A) {
 }
 
 /* Contribution of one frozen sample to the gradient: dL/dn (unprojected,
- * including the view-cosine term along wo), dL/dalpha, dL/dF0 and dL/dtexel. */
+ * including the view-cosine term along wo), dL/dalpha, dL/dF0 and dL/dtexel.
+ * With mag != NULL it also returns the same quantities evaluated with every
+ * sum replaced by the sum of its terms' absolute values (upstream gradients
+ * may have either sign): mag->dn_terms holds the four vector terms of dL/dn
+ * separately (cosine of the diffuse part, cosine of the specular part, half
+ * vector, view), so that the caller can bound them after projection. */
+static double dd_safe(double nh, double a2) { return nh * nh * (a2 - 1.0) + 1.0; }
+
+typedef struct {
+    double dn_terms[4][3];
+    double dalpha, dF0[3], dL[3];
+} adj_mag;
+
 static void adj_sample(const adj_pixel* A, const orc_sample_rec* s, int spec_on, const double* L, const double* gd,
-                       const double* gs, double dn[3], double* dalpha, double dF0[3], double dL[3]) {
+                       const double* gs, double dn[3], double* dalpha, double dF0[3], double dL[3], adj_mag* mag) {
     const double* n = A->n;
     const double* wo = A->wo;
     double a = s->vis * s->inv_denom;
     double ci = dot3(n, s->wi);
     double g_ci = 0.0, g_co = 0.0, g_nh = 0.0, h[3] = {0, 0, 0};
+    double m_ci_d = 0.0, m_ci_s = 0.0, m_co = 0.0, m_nh = 0.0;
     *dalpha = 0.0;
+    if (mag) memset(mag, 0, sizeof(*mag));
     /* diffuse: c_d,c = a L_c ci / pi */
     for (int c = 0; c < 3; ++c) {
         dL[c] = a * gd[c] * ci / ORC_PI;
         dF0[c] = 0.0;
         g_ci += a * gd[c] * L[c] / ORC_PI;
+        if (mag) {
+            mag->dL[c] = fabs(dL[c]);
+            m_ci_d += fabs(a * gd[c] * L[c] / ORC_PI);
+        }
     }
     if (spec_on) {
         double alpha = A->alpha, a2 = A->a2, co = A->co;
@@ -758,12 +776,17 @@ static void adj_sample(const adj_pixel* A, const orc_sample_rec* s, int spec_on,
         double S = D * G2 / (4.0 * co); /* c_s,c = a L_c S F_c */
         double x = 1.0 - (vh < 0.0 ? 0.0 : (vh > 1.0 ? 1.0 : vh));
         double q5 = x * x * x * x * x;
-        double gS = 0.0;
+        double gS = 0.0, mS = 0.0;
         for (int c = 0; c < 3; ++c) {
             double F = A->F0[c] + (1.0 - A->F0[c]) * q5;
             dL[c] += a * gs[c] * S * F;
             gS += a * gs[c] * L[c] * F;
             dF0[c] = a * gs[c] * L[c] * S * (1.0 - q5);
+            if (mag) {
+                mag->dL[c] += fabs(a * gs[c] * S * F);
+                mS += fabs(a * gs[c] * L[c] * F);
+                mag->dF0[c] = fabs(dF0[c]);
+            }
         }
         /* S = D(nh, alpha) G2(Lambda_i, Lambda_o) / (4 co) */
         double dD_dnh = 0.0, dD_dalpha = 0.0;
@@ -785,8 +808,23 @@ static void adj_sample(const adj_pixel* A, const orc_sample_rec* s, int spec_on,
         *dalpha = gS * (dS_dD * dD_dalpha + dS_dLam * (dli_dalpha + dlo_dalpha));
         g_ci += gS * dS_dLam * dli_dci;
         g_co = gS * (dS_dLam * dlo_dco - S / co);
+        if (mag) {
+            m_nh = fabs(mS * dS_dD * dD_dnh);
+            mag->dalpha = mS * (fabs(dS_dD * D * 2.0 / alpha) + fabs(dS_dD * D * 4.0 * alpha * nh * nh / dd_safe(nh, a2)) +
+                                fabs(dS_dLam * dli_dalpha) + fabs(dS_dLam * dlo_dalpha));
+            m_ci_s = fabs(mS * dS_dLam * dli_dci);
+            m_co = mS * (fabs(dS_dLam * dlo_dco) + fabs(S / co));
+        }
     }
     for (int k = 0; k < 3; ++k) dn[k] = g_ci * s->wi[k] + g_nh * h[k] + g_co * wo[k];
+    if (mag) {
+        for (int k = 0; k < 3; ++k) {
+            mag->dn_terms[0][k] = m_ci_d * s->wi[k];
+            mag->dn_terms[1][k] = m_ci_s * s->wi[k];
+            mag->dn_terms[2][k] = m_nh * h[k];
+            mag->dn_terms[3][k] = m_co * wo[k];
+        }
+    }
 }
 
 /* n = N / |N|:  dL/dN = (I - n n^T) dL/dn / |N| */
@@ -824,7 +862,8 @@ void orc_frozen_adjoint(const orc_sample_rec* recs, int spp, int n_pix, const do
             const orc_sample_rec* s = recs + (size_t)q * spp + j;
             if (!s->active) continue;
             double dn[3], da, dF0[3], dL[3];
-            adj_sample(&A, s, spec_on[q], env3 + 3 * (size_t)s->texel, gd, gs, dn, &da, dF0, dL);
+            adj_mag M;
+            adj_sample(&A, s, spec_on[q], env3 + 3 * (size_t)s->texel, gd, gs, dn, &da, dF0, dL, Sc ? &M : NULL);
             double* gL = genv3 + 3 * (size_t)s->texel;
             for (int k = 0; k < 3; ++k) {
                 gn[k] += dn[k];
@@ -833,16 +872,17 @@ void orc_frozen_adjoint(const orc_sample_rec* recs, int spp, int n_pix, const do
             }
             g_alpha += da;
             if (Sc) {
-                double pn[3], dm = 0.0;
-                adj_project(&A, dn, pn);
-                for (int k = 0; k < 3; ++k) {
-                    Sc[k] += fabs(pn[k]);
-                    Sc[3 + k] += fabs(dF0[k] * m);
-                    dm += dF0[k] * (kd[k] - 0.04);
-                    genv3_scale[3 * (size_t)s->texel + k] += fabs(dL[k]);
+                for (int t = 0; t < 4; ++t) {
+                    double pn[3];
+                    adj_project(&A, M.dn_terms[t], pn);
+                    for (int k = 0; k < 3; ++k) Sc[k] += fabs(pn[k]);
                 }
-                Sc[7] += r_live ? fabs(da * 2.0 * r) : 0.0;
-                Sc[8] += fabs(dm);
+                for (int k = 0; k < 3; ++k) {
+                    Sc[3 + k] += M.dF0[k] * fabs(m);
+                    Sc[8] += M.dF0[k] * fabs(kd[k] - 0.04);
+                    genv3_scale[3 * (size_t)s->texel + k] += M.dL[k];
+                }
+                Sc[7] += r_live ? M.dalpha * 2.0 * fabs(r) : 0.0;
             }
         }
         adj_project(&A, gn, G);
@@ -850,10 +890,10 @@ void orc_frozen_adjoint(const orc_sample_rec* recs, int spp, int n_pix, const do
         for (int c = 0; c < 3; ++c) {
             G[3 + c] = gk[c] * (1.0 - m) + gF0[c] * m;
             g_m += -gk[c] * kd[c] + gF0[c] * (kd[c] - 0.04);
-            dmk += -gk[c] * kd[c];
+            dmk += fabs(gk[c] * kd[c]);
             if (Sc) Sc[3 + c] += fabs(gk[c] * (1.0 - m));
         }
-        if (Sc) Sc[8] += fabs(dmk);
+        if (Sc) Sc[8] += dmk;
         G[6] = 0.0;
         G[7] = r_live ? g_alpha * 2.0 * r : 0.0;
         G[8] = g_m;

@@ -176,9 +176,10 @@ def test_shade_fwd_matches_oracle(cuda_lib, orc, scene, oracle_gb):
 def check_adjoint(orc, scene, pipe, gb_rows, recs, o_out, pix, view, g):
     """g: (n, 9) upstream; zero on marginal pixels so that the probe gradient is comparable.
 
-    A gradient is a sum of per-sample terms of either sign (the upstream
-    gradient is random); its FP32 error is bounded relative to the sum of the
-    terms' magnitudes, which the oracle reports beside the gradient."""
+    A gradient is a sum of terms of either sign (the upstream gradient is
+    random; inside one sample the diffuse and specular parts can also cancel);
+    its FP32 error is bounded relative to the sum of the terms' magnitudes,
+    which the oracle reports beside the gradient."""
     cam = np.tile(scene.cams[view, :3].astype(np.float64), (len(pix), 1))
     prow = orc.param_rows(gb_rows)
     env3 = scene.env[..., :3].reshape(-1, 3).astype(np.float64)
