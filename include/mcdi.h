@@ -173,12 +173,20 @@ typedef struct {
  * Outputs [N][H][W] float4 (w = 0): c_d, kd_out, c_s.
  * vis_mask (nullable) [N][H][W][ceil(spp/32)] uint32: bit j = sample j's
  * shadow ray was blocked; the backward pass can reuse it.
+ * workspace (nullable): scratch of mcdi_shade_workspace_size bytes (256-byte
+ * aligned, overwritten).  With it the forward runs as three kernels (sample
+ * generation, a persistent shadow-ray tracer, accumulation; N*H*W*spp must
+ * stay below 2^31); with NULL it runs as one fused kernel.  Both give the same
+ * samples and visibility; sums agree to FP32 rounding.
  * ------------------------------------------------------------------------ */
-MCDI_API mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
-                              const float* marg_cdf, const double* total, const float* gb_pos,
-                              const float* gb_nrm, const float* gb_kd, const float* gb_korm,
-                              const mcdi_camera* cams, int N, int H, int W, const mcdi_shade_params* params,
-                              float* c_d, float* kd_out, float* c_s, uint32_t* vis_mask, void* stream);
+MCDI_API mcdi_status mcdi_shade_workspace_size(int N, int H, int W, const mcdi_shade_params* params,
+                                               size_t* bytes);
+MCDI_API mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp,
+                                       const float* cond_cdf, const float* marg_cdf, const double* total,
+                                       const float* gb_pos, const float* gb_nrm, const float* gb_kd,
+                                       const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                                       const mcdi_shade_params* params, float* c_d, float* kd_out, float* c_s,
+                                       uint32_t* vis_mask, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * Hand-written adjoint of mcdi_shade_mc_fwd (Sec. 4.1: detached importance

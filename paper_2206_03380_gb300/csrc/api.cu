@@ -173,11 +173,22 @@ mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* verts, cons
                     "primary_cast");
 }
 
+mcdi_status mcdi_shade_workspace_size(int N, int H, int W, const mcdi_shade_params* params, size_t* bytes) {
+    REQUIRE(N >= 1 && H >= 1 && W >= 1, "image shape must be positive");
+    REQUIRE(bytes != nullptr, "bytes is NULL");
+    mcdi_status s = check_params(params);
+    if (s != MCDI_OK) return s;
+    const long long spp = (long long)params->n_light + params->n_cos + params->n_ggx;
+    REQUIRE((long long)N * H * W * spp <= (1LL << 31) - 1, "N*H*W*spp too large for the wavefront path");
+    *bytes = mcdi::shade_workspace_bytes((long long)N * H * W, (int)spp);
+    return ok();
+}
+
 mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
                               const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
                               const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
                               const mcdi_shade_params* params, float* c_d, float* kd_out, float* c_s,
-                              uint32_t* vis_mask, void* stream) {
+                              uint32_t* vis_mask, void* workspace, size_t workspace_bytes, void* stream) {
     mcdi::ShadeArgs a;
     mcdi_status s = shade_common(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N,
                                  H, W, params, &a);
@@ -186,6 +197,17 @@ mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp
     REQUIRE_BUF16(kd_out);
     REQUIRE_BUF16(c_s);
     REQUIRE(vis_mask == nullptr || ((uintptr_t)vis_mask & 3u) == 0, "vis_mask must be 4-byte aligned");
+    if (workspace != nullptr) {
+        size_t need = 0;
+        s = mcdi_shade_workspace_size(N, H, W, params, &need);
+        if (s != MCDI_OK) return s;
+        REQUIRE(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
+        REQUIRE(workspace_bytes >= need, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+        return launched(mcdi::launch_shade_fwd_wave(a, reinterpret_cast<float4*>(c_d),
+                                                    reinterpret_cast<float4*>(kd_out), reinterpret_cast<float4*>(c_s),
+                                                    vis_mask, workspace, static_cast<cudaStream_t>(stream)),
+                        "shade_mc_fwd");
+    }
     return launched(mcdi::launch_shade_fwd(a, reinterpret_cast<float4*>(c_d), reinterpret_cast<float4*>(kd_out),
                                            reinterpret_cast<float4*>(c_s), vis_mask,
                                            static_cast<cudaStream_t>(stream)),

@@ -19,7 +19,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 inline BvhScratch bvh_scratch_layout(int n) {
     BvhScratch s{};
@@ -85,6 +85,10 @@ cudaError_t launch_primary_cast(const void* nodes, const void* tris, int n_tris,
 
 cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
                              cudaStream_t stream);
+
+size_t shade_workspace_bytes(long long pixels, int spp);
+cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
+                                  void* ws, cudaStream_t stream);
 
 cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float4* g_kdout, const float4* g_cs,
                              const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,

@@ -1,0 +1,249 @@
+// Wavefront form of the forward estimator (Sec. 3.1, 4.1, 4.2): the same
+// samples, weights and shadow rays as shade_fwd_kernel, split so that the
+// incoherent shadow-ray traversal runs in a lean kernel of its own.
+//
+//   gen    one thread per pixel: draws every sample, writes its shadow ray and
+//          its unshadowed contribution (c_d and c_s parts) to slot j*P + pixel
+//          (sample-major, so a warp's 32 consecutive slots are neighbouring
+//          pixels drawing the same technique: nearby origins, similar
+//          directions);
+//   trace  persistent warps pull slots from a global counter; a lane whose ray
+//          has finished (or whose slot holds no ray) takes the next slot at the
+//          next refill, so lanes do not wait for the warp's longest ray;
+//   accum  one thread per pixel: sums contribution_j x H_j in sample order
+//          j = 0..S-1 (bitwise repeatable) and packs the visibility mask.
+#include "common.cuh"
+#include "internal.h"
+#include "shading.cuh"
+
+namespace mcdi {
+namespace {
+
+constexpr int kGenThreads = 128;
+constexpr int kTraceThreads = 128;
+constexpr int kTraceStepsPerRefill = 16;
+
+struct WaveBuffers {
+    float4* ray_o;      // [slots] origin, w = 1 active / 0 no ray
+    float4* ray_d;      // [slots] direction
+    float* contrib;     // [6][slots] c_d rgb, c_s rgb without visibility
+    uint8_t* hit;       // [slots]
+    unsigned* counter;  // trace work queue head
+};
+
+__device__ __forceinline__ WaveBuffers wave_buffers(void* ws, long long slots) {
+    char* p = static_cast<char*>(ws);
+    WaveBuffers b;
+    size_t o = 0;
+    b.ray_o = reinterpret_cast<float4*>(p + o);
+    o += align256((size_t)slots * 16);
+    b.ray_d = reinterpret_cast<float4*>(p + o);
+    o += align256((size_t)slots * 16);
+    b.contrib = reinterpret_cast<float*>(p + o);
+    o += align256((size_t)slots * 24);
+    b.hit = reinterpret_cast<uint8_t*>(p + o);
+    o += align256((size_t)slots);
+    b.counter = reinterpret_cast<unsigned*>(p + o);
+    return b;
+}
+
+__device__ __forceinline__ Probe wave_probe(const ShadeArgs& a) {
+    Probe P;
+    P.env = a.env;
+    P.cond = a.cond;
+    P.marg = a.marg;
+    P.W = a.Wp;
+    P.H = a.Hp;
+    P.on = *a.total > 0.0;
+    return P;
+}
+
+__global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void* ws, float4* __restrict__ kd_out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long P = (long long)a.N * a.H * a.W;
+    const int spp = a.n_light + a.n_cos + a.n_ggx;
+    const long long slots = P * spp;
+    WaveBuffers B = wave_buffers(ws, slots);
+    if (idx == 0) *B.counter = 0u;
+    if (idx >= P) return;
+    const int view = (int)(idx / ((long long)a.H * a.W));
+    const uint32_t pix = (uint32_t)(idx - (long long)view * a.H * a.W);
+    Pixel px;
+    const mcdi_camera& C = a.cams[view];
+    const bool covered = load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
+                                    mk(C.origin[0], C.origin[1], C.origin[2]), &px);
+    kd_out[idx] = covered ? make_float4(px.kd.x * (1.f - px.m), px.kd.y * (1.f - px.m), px.kd.z * (1.f - px.m), 0.f)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    const Probe Pr = wave_probe(a);
+    const f3 origin = covered ? px.p + px.n * a.ray_eps : mk(0.f, 0.f, 0.f);
+    for (int j = 0; j < spp; ++j) {
+        const long long s = (long long)j * P + idx;
+        f3 wi = mk(0.f, 0.f, 0.f), cd = wi, cs = wi;
+        bool active = false;
+        if (covered) {
+            int t;
+            float ci, inv_denom;
+            const float2 u = sample_uniforms(a.seed, pix, (uint32_t)view, (uint32_t)j, a.stream_word);
+            if (draw_sample(Pr, px, a.n_light, a.n_cos, a.n_ggx, j, u, &wi, &t, &ci, &inv_denom)) {
+                active = true;
+                const float4 L = __ldg(Pr.env + t);
+                cd = mk(L.x, L.y, L.z) * (ci * MCDI_INV_PI * inv_denom);
+                if (px.spec_on) {
+                    const f3 h = normalize(wi + px.wo);
+                    const float D = ggx_D(dot(px.n, h), sin2_between(px.n, h), px.a2);
+                    const float G2 = 1.0f / (1.0f + ggx_lambda(ci, px.a2) + ggx_lambda(px.co, px.a2));
+                    const float q = schlick_weight(dot(px.wo, h));
+                    const float ws = D * G2 / (4.0f * px.co) * inv_denom;
+                    cs = mk(L.x * (px.F0.x + (1.0f - px.F0.x) * q), L.y * (px.F0.y + (1.0f - px.F0.y) * q),
+                            L.z * (px.F0.z + (1.0f - px.F0.z) * q)) *
+                         ws;
+                }
+            }
+        }
+        B.ray_o[s] = make_float4(origin.x, origin.y, origin.z, active ? 1.0f : 0.0f);
+        B.ray_d[s] = make_float4(wi.x, wi.y, wi.z, 0.0f);
+        B.contrib[0 * slots + s] = cd.x;
+        B.contrib[1 * slots + s] = cd.y;
+        B.contrib[2 * slots + s] = cd.z;
+        B.contrib[3 * slots + s] = cs.x;
+        B.contrib[4 * slots + s] = cs.y;
+        B.contrib[5 * slots + s] = cs.z;
+    }
+}
+
+// Persistent any-hit tracer with per-lane refill.  A lane holds one ray with
+// its own traversal state; every kTraceStepsPerRefill node visits the warp
+// refills the lanes that are idle from the global slot counter.
+__global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode* __restrict__ nodes,
+                                                                   const TriRecord* __restrict__ tris, int n_tris,
+                                                                   void* ws, long long slots) {
+    WaveBuffers B = wave_buffers(ws, slots);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    long long slot = -1;  // -1 idle, -2 no work left, >= 0 tracing
+    RayInv r;
+    int node = 0, sp = 0, iters = 0;
+    int stack[kTraversalStack];
+    while (true) {
+        const unsigned need = __ballot_sync(full, slot == -1);
+        if (need) {
+            unsigned long long base = 0;
+            if (lane == __ffs(need) - 1) base = atomicAdd(B.counter, (unsigned)__popc(need));
+            base = __shfl_sync(full, base, __ffs(need) - 1);
+            if (slot == -1) {
+                const long long my = (long long)base + __popc(need & lt);
+                if (my >= slots) {
+                    slot = -2;
+                } else {
+                    const float4 o = __ldg(B.ray_o + my);
+                    if (o.w > 0.0f && n_tris > 0) {
+                        const float4 d = __ldg(B.ray_d + my);
+                        r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
+                        node = 0;
+                        sp = 0;
+                        iters = 0;
+                        slot = my;
+                    } else {
+                        B.hit[my] = 0;  // no ray in this slot: stays idle, refilled next round
+                    }
+                }
+            }
+        }
+        if (__all_sync(full, slot == -2)) break;
+        if (slot < 0) continue;
+        // up to kTraceStepsPerRefill node visits of this lane's ray
+        for (int step = 0; step < kTraceStepsPerRefill; ++step) {
+            const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
+            const int4 d = __ldg(&nodes[node].d);
+            bool h0 = slab(r, a, make_float2(c.x, c.y), FLT_MAX) < FLT_MAX;
+            bool h1 = slab(r, b, make_float2(c.z, c.w), FLT_MAX) < FLT_MAX;
+            int result = -1;  // -1 continue, 0 miss, 1 hit
+            if (h0 && d.x < 0) {
+                if (tri_hit(r, tris, ~d.x, nullptr, nullptr) < FLT_MAX) result = 1;
+                h0 = false;
+            }
+            if (result < 0 && h1 && d.y < 0) {
+                if (tri_hit(r, tris, ~d.y, nullptr, nullptr) < FLT_MAX) result = 1;
+                h1 = false;
+            }
+            if (result < 0) {
+                if (h0 && h1) {
+                    if (sp < kTraversalStack) stack[sp++] = d.y;
+                    node = d.x;
+                } else if (h0) {
+                    node = d.x;
+                } else if (h1) {
+                    node = d.y;
+                } else if (sp == 0) {
+                    result = 0;
+                } else {
+                    node = stack[--sp];
+                }
+                // a tree over n leaves has n - 1 internal nodes, each visited at most once
+                if (result < 0 && ++iters > n_tris) result = 0;
+            }
+            if (result >= 0) {
+                B.hit[slot] = (uint8_t)result;
+                slot = -1;
+                break;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, const void* ws,
+                                                                 float4* __restrict__ c_d, float4* __restrict__ c_s,
+                                                                 uint32_t* __restrict__ vis_mask) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long P = (long long)a.N * a.H * a.W;
+    if (idx >= P) return;
+    const int spp = a.n_light + a.n_cos + a.n_ggx;
+    const int nwords = (spp + 31) >> 5;
+    const long long slots = P * spp;
+    WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
+    const float hv = 1.0f - a.tau;
+    f3 cd = mk(0.f, 0.f, 0.f), cs = cd;
+    uint32_t word = 0;
+    for (int j = 0; j < spp; ++j) {
+        const long long s = (long long)j * P + idx;
+        const bool hit = B.hit[s] != 0;
+        const float Hv = hit ? hv : 1.0f;
+        if (hit) word |= 1u << (j & 31);
+        cd = cd + mk(B.contrib[0 * slots + s], B.contrib[1 * slots + s], B.contrib[2 * slots + s]) * Hv;
+        cs = cs + mk(B.contrib[3 * slots + s], B.contrib[4 * slots + s], B.contrib[5 * slots + s]) * Hv;
+        if (vis_mask && ((j & 31) == 31 || j == spp - 1)) {
+            vis_mask[(size_t)idx * nwords + (j >> 5)] = word;
+            word = 0;
+        }
+    }
+    c_d[idx] = make_float4(cd.x, cd.y, cd.z, 0.f);
+    c_s[idx] = make_float4(cs.x, cs.y, cs.z, 0.f);
+}
+
+}  // namespace
+
+size_t shade_workspace_bytes(long long P, int spp) {
+    const long long slots = P * spp;
+    return align256((size_t)slots * 16) * 2 + align256((size_t)slots * 24) + align256((size_t)slots) + 256;
+}
+
+cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
+                                  void* ws, cudaStream_t stream) {
+    const long long P = (long long)a.N * a.H * a.W;
+    const int spp = a.n_light + a.n_cos + a.n_ggx;
+    const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
+    wave_gen_kernel<<<gblocks, kGenThreads, 0, stream>>>(a, ws, kd_out);
+    int dev = 0, sms = 152, per_sm = 8;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    wave_trace_kernel<<<sms * per_sm, kTraceThreads, 0, stream>>>(static_cast<const BvhNode*>(a.nodes),
+                                                                  static_cast<const TriRecord*>(a.tris), a.n_tris, ws,
+                                                                  P * spp);
+    wave_accum_kernel<<<gblocks, kGenThreads, 0, stream>>>(a, ws, c_d, c_s, vis_mask);
+    return cudaGetLastError();
+}
+
+}  // namespace mcdi

@@ -36,7 +36,8 @@ class ShadeParams(C.Structure):
 
 
 EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh_sizes", "mcdi_build_bvh",
-           "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_mc_fwd", "mcdi_shade_mc_bwd"]
+           "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_workspace_size", "mcdi_shade_mc_fwd",
+           "mcdi_shade_mc_bwd"]
 NOALLOC_MAX_TRIS = 65536
 
 
@@ -64,9 +65,11 @@ def load(path: str = LIB_PATH):
     lib.mcdi_primary_cast.restype = st
     lib.mcdi_primary_cast.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
                                       P, P, P, P, P]
+    lib.mcdi_shade_workspace_size.restype = st
+    lib.mcdi_shade_workspace_size.argtypes = [i, i, i, C.POINTER(ShadeParams), C.POINTER(sz)]
     lib.mcdi_shade_mc_fwd.restype = st
     lib.mcdi_shade_mc_fwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
-                                      C.POINTER(ShadeParams), P, P, P, P, P]
+                                      C.POINTER(ShadeParams), P, P, P, P, P, sz, P]
     lib.mcdi_shade_mc_bwd.restype = st
     lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
@@ -135,14 +138,22 @@ def primary_cast(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uv
            "primary_cast")
 
 
+def shade_workspace_size(N: int, H: int, W: int, params: ShadeParams) -> int:
+    b = C.c_size_t()
+    _check(load().mcdi_shade_workspace_size(int(N), int(H), int(W), C.byref(params), C.byref(b)),
+           "shade_workspace_size")
+    return b.value
+
+
 def shade_mc_fwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, c_d, kd_out, c_s,
-                 vis_mask=None, stream=None):
+                 vis_mask=None, workspace=None, stream=None):
     N, H, W = gb.pos.shape[:3]
     Hp, Wp = probe.env.shape[:2]
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().mcdi_shade_mc_fwd(C.byref(bvh.view), _ptr(probe.env), Wp, Hp, _ptr(probe.cond), _ptr(probe.marg),
                                     _ptr(probe.total), _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm),
                                     _ptr(cams), N, H, W, C.byref(params), _ptr(c_d), _ptr(kd_out), _ptr(c_s),
-                                    _ptr(vis_mask), _stream(stream)), "shade_mc_fwd")
+                                    _ptr(vis_mask), _ptr(workspace), ws_bytes, _stream(stream)), "shade_mc_fwd")
 
 
 def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, g_cd, g_kdout, g_cs,
@@ -228,14 +239,14 @@ class ShadeMC(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, kd, korm, nrm, env, pos, bvh, probe, cams, params, keep_mask=True):
+    def forward(ctx, kd, korm, nrm, env, pos, bvh, probe, cams, params, keep_mask=True, workspace=None):
         gb = GBuffer(pos.contiguous(), nrm.contiguous(), kd.contiguous(), korm.contiguous())
         pr = Probe(env.contiguous(), probe.cond, probe.marg, probe.row_sum, probe.total)
         N, H, W = pos.shape[:3]
         spp = params.n_light + params.n_cos + params.n_ggx
         c_d, kd_out, c_s = (torch.empty_like(pos) for _ in range(3))
         mask = torch.empty(N, H, W, (spp + 31) // 32, dtype=torch.int32, device=pos.device) if keep_mask else None
-        shade_mc_fwd(bvh, pr, gb, cams, params, c_d, kd_out, c_s, mask)
+        shade_mc_fwd(bvh, pr, gb, cams, params, c_d, kd_out, c_s, mask, workspace)
         ctx.bvh, ctx.probe, ctx.params, ctx.gb = bvh, pr, params, gb
         ctx.save_for_backward(cams, mask if mask is not None else torch.empty(0, device=pos.device))
         ctx.has_mask = mask is not None
@@ -255,4 +266,4 @@ class ShadeMC(torch.autograd.Function):
         g_env = torch.zeros_like(ctx.probe.env)
         shade_mc_bwd(ctx.bvh, ctx.probe, gb, cams, ctx.params, g_cd, g_kdout, g_cs, mask if ctx.has_mask else None,
                      g_kd, g_korm, g_nrm, g_env)
-        return g_kd, g_korm, g_nrm, g_env, None, None, None, None, None, None
+        return g_kd, g_korm, g_nrm, g_env, None, None, None, None, None, None, None

@@ -18,7 +18,7 @@ from .scenes import Scene
 
 class ShadingPipeline:
     def __init__(self, scene: Scene, device="cuda", tau: float = 0.0, ray_eps: float = 1e-4,
-                 decorrelate_bwd: bool = False, keep_mask: bool = True):
+                 decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True):
         mcdi.load()
         self.scene = scene
         self.device = torch.device(device)
@@ -45,6 +45,10 @@ class ShadingPipeline:
                      if keep_mask else None)
         self.g_kd, self.g_korm, self.g_nrm = (torch.zeros(shape, device=dev) for _ in range(3))
         self.g_env = torch.zeros_like(self.env)
+        self.workspace = None
+        if wavefront:
+            nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
+            self.workspace = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
 
     # ---- the steps
     def build_probe(self, stream=None):
@@ -59,7 +63,7 @@ class ShadingPipeline:
 
     def forward(self, stream=None):
         mcdi.shade_mc_fwd(self.bvh, self.probe, self.gb, self.cams, self.params, self.c_d, self.kd_out, self.c_s,
-                          self.mask, stream)
+                          self.mask, self.workspace, stream)
 
     def backward(self, g_cd, g_kdout, g_cs, stream=None, zero_env_grad=True):
         if zero_env_grad:

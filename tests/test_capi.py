@@ -64,7 +64,7 @@ def test_argument_checks_without_gpu(lib):
     bad = mcdi.make_params(0, 0, 0, 1)
     p16 = C.c_void_p(4096)
     args = [C.byref(bvh), p16, 32, 16, p16, p16, p16, p16, p16, p16, p16, p16, 1, 8, 8]
-    outs = [p16, p16, p16, None, None]
+    outs = [p16, p16, p16, None, None, 0, None]
     assert lib.mcdi_shade_mc_fwd(*args, C.byref(bad), *outs) == mcdi.INVALID_ARG
     assert b"spp" in lib.mcdi_last_error()
     mis = C.c_void_p(4100)  # not 16-byte aligned

@@ -165,8 +165,9 @@ def check_forward(orc, scene, gpu_out, gpu_mask, gb_rows, pix, view, tau=0.0):
     return o_out, recs
 
 
-def test_shade_fwd_matches_oracle(cuda_lib, orc, scene, oracle_gb):
-    pipe = make_pipe(scene)
+@pytest.mark.parametrize("wavefront", [True, False])
+def test_shade_fwd_matches_oracle(cuda_lib, orc, scene, oracle_gb, wavefront):
+    pipe = make_pipe(scene, wavefront=wavefront)
     out, mask = run_fwd(pipe, oracle_gb)
     o_out, recs = check_forward(orc, scene, out, mask, oracle_gb.astype(np.float32), np.arange(64 * 64), 0)
     assert recs["occluded"].sum() > 500  # the sphere shadows the ground
@@ -280,8 +281,9 @@ def test_small_meshes_leakage_and_decorrelated_backward(cuda_lib, orc, with_occl
         check_adjoint(orc, sc, pipe, og.astype(np.float32), recs_b, o_out_b, np.arange(4096), 0, g)
 
 
-def test_forward_is_repeatable(cuda_lib, scene):
-    pipe = make_pipe(scene)
+@pytest.mark.parametrize("wavefront", [True, False])
+def test_forward_is_repeatable(cuda_lib, scene, wavefront):
+    pipe = make_pipe(scene, wavefront=wavefront)
     pipe.build_probe()
     pipe.build_bvh()
     pipe.primary()
@@ -290,3 +292,11 @@ def test_forward_is_repeatable(cuda_lib, scene):
     pipe.forward()
     np.testing.assert_array_equal(a[0], to_np(pipe.c_s))
     np.testing.assert_array_equal(a[1], to_np(pipe.c_d))
+
+
+def test_wavefront_and_fused_forward_agree(cuda_lib, scene, oracle_gb):
+    a, b = make_pipe(scene, wavefront=True), make_pipe(scene, wavefront=False)
+    oa, ma = run_fwd(a, oracle_gb)
+    ob, mb = run_fwd(b, oracle_gb)
+    np.testing.assert_array_equal(ma, mb)  # same samples, same shadow rays
+    np.testing.assert_allclose(oa, ob, rtol=2e-6, atol=1e-7 * np.abs(ob).max())
