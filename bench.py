@@ -148,7 +148,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     stages = ["probe_cdf", "bvh_build", "primary_cast", "shade_fwd", "shade_bwd"]
     n_launch = {"probe_cdf": 2, "bvh_build": 3 + 12 + 1 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 1,
-                "shade_fwd": 3, "shade_bwd": 1}
+                "shade_fwd": 4, "shade_bwd": 1}
 
     def one_step(ev=None):
         calls = [pipe.build_probe, pipe.build_bvh, pipe.primary, pipe.forward,

@@ -2,14 +2,14 @@
 // samples, weights and shadow rays as shade_fwd_kernel, split so that the
 // incoherent shadow-ray traversal runs in a lean kernel of its own.
 //
-//   gen    one thread per pixel: draws every sample, writes its shadow ray and
-//          its unshadowed contribution (c_d and c_s parts) to slot j*P + pixel
-//          (sample-major, so a warp's 32 consecutive slots are neighbouring
-//          pixels drawing the same technique: nearby origins, similar
-//          directions);
-//   trace  persistent warps pull slots from a global counter; a lane whose ray
-//          has finished (or whose slot holds no ray) takes the next slot at the
-//          next refill, so lanes do not wait for the warp's longest ray;
+//   gen    one thread per pixel: draws every sample, writes its unshadowed
+//          contribution (c_d and c_s parts) to slot j*P + pixel and appends its
+//          shadow ray, if any, to a dense ray list (a warp's rays for one sample
+//          index stay together: neighbouring pixels, same technique, nearby
+//          origins and similar directions);
+//   trace  persistent warps pull rays from a global counter; a lane whose ray
+//          has finished takes the next ray at the next refill, so lanes do not
+//          wait for the warp's longest ray;
 //   accum  one thread per pixel: sums contribution_j x H_j in sample order
 //          j = 0..S-1 (bitwise repeatable) and packs the visibility mask.
 #include "common.cuh"
@@ -24,11 +24,11 @@ constexpr int kTraceThreads = 128;
 constexpr int kTraceStepsPerRefill = 16;
 
 struct WaveBuffers {
-    float4* ray_o;      // [slots] origin, w = 1 active / 0 no ray
-    float4* ray_d;      // [slots] direction
+    float4* ray_o;      // [rays] origin, w = slot index (int bits) of the sample
+    float4* ray_d;      // [rays] direction
     float* contrib;     // [6][slots] c_d rgb, c_s rgb without visibility
-    uint8_t* hit;       // [slots]
-    unsigned* counter;  // trace work queue head
+    uint8_t* hit;       // [slots] 1 = shadow ray blocked
+    unsigned* counter;  // [0] rays appended by gen, [1] trace work queue head
 };
 
 __device__ __forceinline__ WaveBuffers wave_buffers(void* ws, long long slots) {
@@ -58,22 +58,34 @@ __device__ __forceinline__ Probe wave_probe(const ShadeArgs& a) {
     return P;
 }
 
+__global__ void wave_reset_kernel(void* ws, long long slots) {
+    WaveBuffers B = wave_buffers(ws, slots);
+    B.counter[0] = 0u;
+    B.counter[1] = 0u;
+}
+
+// Active shadow rays are appended densely (one atomic per warp and sample):
+// a warp's rays for sample j stay together, so the tracer sees coherent
+// batches and no empty slots.
 __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void* ws, float4* __restrict__ kd_out) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const long long slots = P * spp;
     WaveBuffers B = wave_buffers(ws, slots);
-    if (idx == 0) *B.counter = 0u;
-    if (idx >= P) return;
+    const int lane = threadIdx.x & 31;
+    const bool in_range = idx0 < P;
+    const long long idx = in_range ? idx0 : P - 1;  // out-of-range lanes idle but join the warp votes
     const int view = (int)(idx / ((long long)a.H * a.W));
     const uint32_t pix = (uint32_t)(idx - (long long)view * a.H * a.W);
     Pixel px;
     const mcdi_camera& C = a.cams[view];
-    const bool covered = load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
-                                    mk(C.origin[0], C.origin[1], C.origin[2]), &px);
-    kd_out[idx] = covered ? make_float4(px.kd.x * (1.f - px.m), px.kd.y * (1.f - px.m), px.kd.z * (1.f - px.m), 0.f)
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool covered = in_range && load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
+                                                mk(C.origin[0], C.origin[1], C.origin[2]), &px);
+    if (in_range)
+        kd_out[idx] = covered ? make_float4(px.kd.x * (1.f - px.m), px.kd.y * (1.f - px.m),
+                                            px.kd.z * (1.f - px.m), 0.f)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
     const Probe Pr = wave_probe(a);
     const f3 origin = covered ? px.p + px.n * a.ray_eps : mk(0.f, 0.f, 0.f);
     for (int j = 0; j < spp; ++j) {
@@ -100,8 +112,20 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
                 }
             }
         }
-        B.ray_o[s] = make_float4(origin.x, origin.y, origin.z, active ? 1.0f : 0.0f);
-        B.ray_d[s] = make_float4(wi.x, wi.y, wi.z, 0.0f);
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        if (act) {
+            const int leader = __ffs(act) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(B.counter, (unsigned)__popc(act));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (active) {
+                const unsigned r = base + __popc(act & ((1u << lane) - 1u));
+                B.ray_o[r] = make_float4(origin.x, origin.y, origin.z, __int_as_float((int)s));
+                B.ray_d[r] = make_float4(wi.x, wi.y, wi.z, 0.0f);
+            }
+        }
+        if (!in_range) continue;
+        B.hit[s] = 0;
         B.contrib[0 * slots + s] = cd.x;
         B.contrib[1 * slots + s] = cd.y;
         B.contrib[2 * slots + s] = cd.z;
@@ -118,40 +142,41 @@ __global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode
                                                                    const TriRecord* __restrict__ tris, int n_tris,
                                                                    void* ws, long long slots) {
     WaveBuffers B = wave_buffers(ws, slots);
+    const long long n_rays = (long long)*((volatile unsigned*)B.counter);
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    long long slot = -1;  // -1 idle, -2 no work left, >= 0 tracing
+    long long ray = -1;  // -1 idle, -2 no work left, >= 0 tracing
+    int slot = 0;
     RayInv r;
     int node = 0, sp = 0, iters = 0;
     int stack[kTraversalStack];
+    if (n_tris <= 0) return;  // nothing can block a ray; gen already wrote misses
     while (true) {
-        const unsigned need = __ballot_sync(full, slot == -1);
+        const unsigned need = __ballot_sync(full, ray == -1);
         if (need) {
-            unsigned long long base = 0;
-            if (lane == __ffs(need) - 1) base = atomicAdd(B.counter, (unsigned)__popc(need));
-            base = __shfl_sync(full, base, __ffs(need) - 1);
-            if (slot == -1) {
+            const int leader = __ffs(need) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(B.counter + 1, (unsigned)__popc(need));
+            base = __shfl_sync(full, base, leader);
+            if (ray == -1) {
                 const long long my = (long long)base + __popc(need & lt);
-                if (my >= slots) {
-                    slot = -2;
+                if (my >= n_rays) {
+                    ray = -2;
                 } else {
                     const float4 o = __ldg(B.ray_o + my);
-                    if (o.w > 0.0f && n_tris > 0) {
-                        const float4 d = __ldg(B.ray_d + my);
-                        r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
-                        node = 0;
-                        sp = 0;
-                        iters = 0;
-                        slot = my;
-                    } else {
-                        B.hit[my] = 0;  // no ray in this slot: stays idle, refilled next round
-                    }
+                    const float4 d = __ldg(B.ray_d + my);
+                    r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
+                    slot = __float_as_int(o.w);
+                    node = 0;
+                    sp = 0;
+                    iters = 0;
+                    ray = my;
                 }
             }
         }
-        if (__all_sync(full, slot == -2)) break;
-        if (slot < 0) continue;
+        if (__all_sync(full, ray == -2)) break;
+        if (ray < 0) continue;
         // up to kTraceStepsPerRefill node visits of this lane's ray
         for (int step = 0; step < kTraceStepsPerRefill; ++step) {
             const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
@@ -184,8 +209,8 @@ __global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode
                 if (result < 0 && ++iters > n_tris) result = 0;
             }
             if (result >= 0) {
-                B.hit[slot] = (uint8_t)result;
-                slot = -1;
+                if (result) B.hit[slot] = 1;
+                ray = -1;
                 break;
             }
         }
@@ -233,6 +258,7 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
+    wave_reset_kernel<<<1, 1, 0, stream>>>(ws, P * spp);
     wave_gen_kernel<<<gblocks, kGenThreads, 0, stream>>>(a, ws, kd_out);
     int dev = 0, sms = 152, per_sm = 8;
     cudaGetDevice(&dev);
