@@ -2,7 +2,8 @@
 
 A step is one pass of the hot path over one synthetic batch: probe sampling
 tables, LBVH over this iteration's mesh, G-buffer ray cast, forward MIS
-estimator with shadow rays, and the adjoint (Sec. 3-4 of the paper).  The
+estimator with shadow rays, the U-Net denoiser on c_d and c_s, its input
+gradient, and the shading adjoint (Sec. 3-4 of the paper).  The
 workload is the 512 x 512, 16 spp (8 light / 4 cosine / 4 GGX) view of the
 ~198k-triangle sphere-union mesh with 1024^2 textures and a 512 x 256
 three-lobe probe.  The metric is shaded samples per second (covered pixels x
@@ -41,6 +42,18 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def tensor_peak():
+    """BF16 dense peak for a kernel timed inside a long step: the sustained figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops_sustained" in d:
+            return d["bf16_tflops_sustained"], "measured (sustained)"
+        if "bf16_tflops" in d:
+            return d["bf16_tflops"], "measured (burst)"
+    return 1700.0, "fallback (sustained)"
 
 
 # ------------------------------------------------------------------ distributed harness
@@ -140,19 +153,24 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc = scenes.sphere_union_scene(seed=scenes.BASE_SEED + 2 + 1000 * rank if world > 1 else scenes.BASE_SEED + 2)
-    pipe = ShadingPipeline(sc, device=dev)
+    den_params = mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
+    pipe = ShadingPipeline(sc, device=dev, denoiser_params=den_params)
     N, H, W = pipe.N, pipe.H, pipe.W
     rng = np.random.default_rng(3)
-    g_up = [torch.from_numpy(rng.normal(size=(N, H, W, 4)).astype(np.float32)).to(dev) for _ in range(3)]
+    # synthetic upstream gradients: of the loss w.r.t. the denoised terms and k_d,out
+    g_den = torch.from_numpy(rng.normal(size=(2 * N, H, W, 4)).astype(np.float32)).to(dev)
+    g_kdout = torch.from_numpy(rng.normal(size=(N, H, W, 4)).astype(np.float32)).to(dev)
+    g_up = [g_den, g_kdout]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    stages = ["probe_cdf", "bvh_build", "primary_cast", "shade_fwd", "shade_bwd"]
+    stages = ["probe_cdf", "bvh_build", "primary_cast", "shade_fwd", "denoise_fwd", "denoise_bwd", "shade_bwd"]
     n_launch = {"probe_cdf": 2, "bvh_build": 3 + 12 + 1 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 1,
-                "shade_fwd": 4, "shade_bwd": 1}
+                "shade_fwd": 4, "denoise_fwd": 1 + 15 + 3, "denoise_bwd": 1 + 15 + 3 + 3 + 1, "shade_bwd": 1}
 
     def one_step(ev=None):
-        calls = [pipe.build_probe, pipe.build_bvh, pipe.primary, pipe.forward,
-                 lambda: pipe.backward(*g_up)]
+        calls = [pipe.build_probe, pipe.build_bvh, pipe.primary, pipe.forward, pipe.denoise,
+                 lambda: pipe.denoise_backward(g_den),
+                 lambda: pipe.backward(pipe.g_terms[:N], g_kdout, pipe.g_terms[N:])]
         for k, f in enumerate(calls):
             if ev is not None:
                 ev[k].record(stream)
@@ -160,24 +178,31 @@ def run_gpu(args, rank, world):
         if ev is not None:
             ev[len(calls)].record(stream)
 
-    for _ in range(args.warmup):
+    clk = ClockSampler(local)
+    clk.__enter__()  # samples clocks from the warm-up (at least 1 s of load) through the timed region
+    t_w = time.perf_counter()
+    k = 0
+    while k < args.warmup or time.perf_counter() - t_w < 1.0:
         flush.zero_()
         one_step()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        k += 1
     covered = pipe.covered_pixels()
     samples_per_step = covered * sc.spp
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for s in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the events)
-            one_step(evs[s])
-        torch.cuda.synchronize()
-        barrier()
-        wall = time.perf_counter() - t0
+    for _ in range(4):
+        flush.zero_()  # a queue of device work so that the first timed launch does not wait for the host
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        one_step(evs[s])
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk.__exit__(None, None, None)
     stage_ms = {st: [evs[s][k].elapsed_time(evs[s][k + 1]) for s in range(args.steps)] for k, st in enumerate(stages)}
     step_ms = [evs[s][0].elapsed_time(evs[s][-1]) for s in range(args.steps)]
     dev_ms = float(np.mean(step_ms))
@@ -189,7 +214,7 @@ def run_gpu(args, rank, world):
     host_in = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
                [("verts", sc.verts), ("vnrm", sc.vnrm), ("tris", sc.tris), ("env", sc.env)]}
     host_g = [g.cpu().pin_memory() for g in g_up]
-    outs_dev = [pipe.c_d, pipe.kd_out, pipe.c_s, pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env]
+    outs_dev = [pipe.denoised, pipe.kd_out, pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env]
     host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs_dev]
     h2d = sum(t.numel() * t.element_size() for t in list(host_in.values()) + host_g)
     d2h = sum(t.numel() * t.element_size() for t in host_out)
@@ -230,9 +255,26 @@ def run_gpu(args, rank, world):
         # G-buffer + upstream (3 x 16 B) + mask in, three gradient planes out; probe in, probe gradient in+out
         "shade_bwd": P * (64 + 48 + 4 * words + 48) + probe_bytes + 2 * sc.env.nbytes,
     }
-    dom = max(("shade_fwd", "shade_bwd"), key=lambda s: avg[s])
+    # denoiser: algorithmic tensor FLOPs (2 * 9 * c_in * c_out per output pixel and conv, unpadded)
+    conv_flops = 0
+    for name, ci, co in scenes.UNET_SHAPES:
+        lvl = {"enc1": 0, "enc2": 1, "enc3": 2, "bot_": 3, "dec3": 2, "dec2": 1, "dec1": 0, "out": 0}[name[:4]]
+        conv_flops += 2 * 9 * ci * co * (2 * N) * (H >> lvl) * (W >> lvl)
+    flops = {"denoise_fwd": conv_flops, "denoise_bwd": conv_flops}  # input-gradient convs: same shapes
+    dom = max(("shade_fwd", "shade_bwd", "denoise_fwd", "denoise_bwd"), key=lambda s: avg[s])
     peak, peak_kind = peaks()
-    achieved = algo[dom] / (avg[dom] * 1e-3) / 1e9
+    if dom in flops:
+        tpeak, tkind = tensor_peak()
+        achieved = flops[dom] / (avg[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": round(achieved, 2), "peak": tpeak, "unit": "TFLOP/s",
+                "frac": round(achieved / tpeak, 5), "traffic": None, "peak_source": tkind,
+                "algorithmic_flops": int(flops[dom])}
+    else:
+        achieved = algo[dom] / (avg[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 5), "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes": int(algo[dom])}
+    den_tf = {k: round(flops[k] / (avg[k] * 1e-3) / 1e12, 2) for k in flops}
     clocks = clk.summary()
     launches = args.steps * sum(n_launch.values())
     result = {
@@ -248,9 +290,10 @@ def run_gpu(args, rank, world):
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "stage_ms": {k: round(v, 4) for k, v in avg.items()},
         "wall_s": round(wall, 3),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "traffic": None, "peak_source": peak_kind,
-                     "algorithmic_bytes": int(algo[dom])},
+        "roofline": roof,
+        "shade_fwd_hbm": {"achieved": round(algo["shade_fwd"] / (avg["shade_fwd"] * 1e-3) / 1e9, 2), "peak": peak,
+                          "unit": "GB/s", "frac": round(algo["shade_fwd"] / (avg["shade_fwd"] * 1e-3) / 1e9 / peak, 5)},
+        "denoiser_tflops": den_tf,
         "clocks": clocks,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
@@ -258,7 +301,36 @@ def run_gpu(args, rank, world):
     }
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
+    if args.serving_requests > 0:
+        del pipe, flush
+        torch.cuda.empty_cache()
+        result["serving"] = run_serving(args.serving_requests, args.serving_rate, dev, rank)
     return result
+
+
+def run_serving(n_requests, rate, dev, rank):
+    """Poisson stream of render requests (resolution side uniform over multiples of
+    32 in [128, 1024], spp uniform in {4, 8, 16, 32, 64}, 16 resident scenes and 16
+    probes) served with continuous batching and one at a time; p50/p99 latency."""
+    from paper_2206_03380_gb300 import mcdi, scenes
+    from paper_2206_03380_gb300.serving import ServingEngine
+
+    sc = scenes.serving_scenes(n_scenes=16)
+    pr = scenes.serving_probes(n_probes=16)
+    den = mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
+    eng = ServingEngine(sc, pr, den, n_slots=4, hbm_budget=24 << 30, device=dev)
+    reqs = scenes.poisson_requests(n_requests, rate, len(sc), len(pr), seed=scenes.BASE_SEED + 7 + rank)
+    eng.run(scenes.poisson_requests(32, 1e4, len(sc), len(pr), seed=1), mode="continuous")  # warm-up
+    out = {"requests": n_requests, "rate_per_s": rate,
+           "triangles": [int(s["tris"].shape[0]) for s in sc[:4]],
+           "offered_msamples_per_s": round(rate * float(np.mean([q.res * q.res * q.spp for q in reqs])) / 1e6, 1)}
+    for mode in ("continuous", "serial"):
+        r = eng.run(reqs, mode=mode)
+        out[mode] = {k: round(r[k], 3) for k in ("p50_ms", "p99_ms", "mean_ms", "req_per_s", "msamples_per_s",
+                                                  "wall_s")}
+        out[mode]["admission_waits"] = r["admission_waits"]
+    out["slots"] = eng.n_slots
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle arm
@@ -346,6 +418,8 @@ def main(argv=None):
     ap.add_argument("--cpu-pixels", type=int, default=1024)
     ap.add_argument("--ref-pixels", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

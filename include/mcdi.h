@@ -213,6 +213,54 @@ MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* en
                               const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm, float* g_env,
                               void* stream);
 
+/* ------------------------------------------------------------------------
+ * Differentiable denoiser (Sec. 4.2 "Neural denoisers": a U-Net applied to
+ * the demodulated diffuse and the specular terms separately; App. B).
+ * The network: widths 32/48/64/96 over four levels, two 3x3 zero-padded
+ * convolutions with ReLU per level, 2x2 max-pool down, nearest 2x upsample
+ * and [upsampled, skip] concatenation up, a final linear 3x3 convolution to
+ * 3 channels.  Input per image: 9 channels = term rgb, k_d rgb, normal xyz.
+ * Convolutions run on the tcgen05 tensor cores with BF16 operands and FP32
+ * accumulation; activations are stored as BF16.
+ *
+ * mcdi_denoise_sizes (host): bytes of the packed weights, of the forward's
+ * saved activations and of the backward's gradient scratch for n_img images
+ * of H x W (H, W multiples of 8), and the number of FP32 parameters.
+ * mcdi_denoise_pack_weights: params (device, FP32, for each of the 15
+ * convolutions in order enc1a enc1b enc2a enc2b enc3a enc3b bot_a bot_b dec3a
+ * dec3b dec2a dec2b dec1a dec1b out: W[co][ci][3][3] then b[co]) -> weights.
+ * mcdi_denoise_fwd: term [n_img][H][W] float4, kd and nrm [n_aux][H][W]
+ * float4 (image i uses guide i % n_aux) -> y [n_img][H][W] float4 (rgb, w=0);
+ * acts (act_bytes) receives the activations the backward needs.
+ * mcdi_denoise_bwd: gy [n_img][H][W] float4 -> gx [n_img][H][W] float4, the
+ * gradient with respect to the term channels (the weights are locked: no
+ * weight gradient).  err: device uint32 the kernels set to 1 if a pipeline
+ * wait timed out (zero it before the call; outputs are then invalid).
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, size_t* weight_bytes, size_t* act_bytes,
+                                        size_t* grad_bytes, size_t* n_params);
+MCDI_API mcdi_status mcdi_denoise_pack_weights(const float* params, void* weights, void* stream);
+MCDI_API mcdi_status mcdi_denoise_fwd(const void* weights, int n_img, int H, int W, const float* term,
+                                      const float* kd, const float* nrm, int n_aux, float* y, void* acts,
+                                      size_t act_bytes, unsigned* err, void* stream);
+MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int n_img, int H, int W, const void* acts,
+                                      size_t act_bytes, const float* gy, float* gx, void* grad_ws,
+                                      size_t grad_bytes, unsigned* err, void* stream);
+
+/* Final colour (Sec. 4.2): c = kd_out * D(c_d) + D(c_s), n pixels of float4
+ * planes (w of c = 0). */
+MCDI_API mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float* den_cs, long long n,
+                                    float* c, void* stream);
+
+/* One 3x3 convolution layer of the denoiser on its own (same kernel):
+ * x [n_img][H][W][cin_pad] BF16 NHWC, w [cout_pad][9][cin_pad] BF16 (tap =
+ * 3 ky + kx, cross-correlation, zero padding 1), bias [cout_pad] FP32
+ * (nullable), y [n_img][H][W][cout_pad] BF16 = act(conv + bias), act = ReLU
+ * if relu else identity.  cin_pad, cout_pad multiples of 16, cout_pad <= 256. */
+MCDI_API mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pad, const void* w,
+                                       const float* bias, int cout_pad, int relu, void* y, unsigned* err,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,18 +38,11 @@ def unet_plan(cin: int = 9, cout: int = 3, widths=(32, 48, 64, 96)):
     ]
 
 
-def xavier_weights(seed: int, plan=None):
-    """Xavier-uniform weights (fan_in = 9 c_in, fan_out = 9 c_out) and zero-mean
-    small biases, from numpy PCG64; returns {name: (W (co, ci, 3, 3), b (co,))} float32."""
-    plan = plan or unet_plan()
-    rng = np.random.default_rng(seed)
-    out = {}
-    for name, ci, co, _ in plan:
-        a = math.sqrt(6.0 / (9 * ci + 9 * co))
-        W = rng.uniform(-a, a, size=(co, ci, 3, 3)).astype(np.float32)
-        b = rng.uniform(-0.05, 0.05, size=co).astype(np.float32)
-        out[name] = (W, b)
-    return out
+def xavier_weights(seed: int):
+    """The seeded denoiser weights both sides receive (from the shared input generator)."""
+    from paper_2206_03380_gb300 import scenes
+
+    return scenes.unet_xavier_weights(seed)
 
 
 def _t(a):
@@ -61,35 +54,72 @@ def conv3x3(x, W, b):
     return F.conv2d(x, W, b, padding=1)
 
 
-def _unet(x, P):
-    """The network on float64 tensors; P = {name: (W, b)}."""
+class _RoundBF16(torch.autograd.Function):
+    """Identity up to rounding to bfloat16, in the forward value and in the
+    backward gradient: marks a tensor that is stored in bfloat16."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return x.to(torch.bfloat16).to(x.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g.to(torch.bfloat16).to(g.dtype)
+
+
+def _unet(x, P, storage=None):
+    """The network on float64 tensors; P = {name: (W, b)}.  storage="bf16" rounds
+    every stored tensor (input, each activation after its ReLU, pooled and
+    concatenated tensors) and every gradient of those to bfloat16, which is
+    where a bfloat16 implementation takes its discrete decisions (ReLU masks,
+    max-pool winners); arithmetic stays float64."""
+    r = _RoundBF16.apply if storage == "bf16" else (lambda t: t)
+
     def conv(name, h, relu):
         z = conv3x3(h, *P[name])
-        return F.relu(z) if relu else z
+        return r(F.relu(z)) if relu else z
 
     up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
+    pool = lambda t: r(F.max_pool2d(t, 2))
+    cat = lambda a, b: r(torch.cat([a, b], 1))
+    x = r(x)
     e1 = conv("enc1b", conv("enc1a", x, True), True)
-    e2 = conv("enc2b", conv("enc2a", F.max_pool2d(e1, 2), True), True)
-    e3 = conv("enc3b", conv("enc3a", F.max_pool2d(e2, 2), True), True)
-    bt = conv("bot_b", conv("bot_a", F.max_pool2d(e3, 2), True), True)
-    d3 = conv("dec3b", conv("dec3a", torch.cat([up(bt), e3], 1), True), True)
-    d2 = conv("dec2b", conv("dec2a", torch.cat([up(d3), e2], 1), True), True)
-    d1 = conv("dec1b", conv("dec1a", torch.cat([up(d2), e1], 1), True), True)
+    e2 = conv("enc2b", conv("enc2a", pool(e1), True), True)
+    e3 = conv("enc3b", conv("enc3a", pool(e2), True), True)
+    bt = conv("bot_b", conv("bot_a", pool(e3), True), True)
+    d3 = conv("dec3b", conv("dec3a", cat(up(bt), e3), True), True)
+    d2 = conv("dec2b", conv("dec2a", cat(up(d3), e2), True), True)
+    d1 = conv("dec1b", conv("dec1a", cat(up(d2), e1), True), True)
     return conv("out", d1, False)
 
 
-def unet_forward(x, weights):
-    """x: (N, 9, H, W) (H, W divisible by 8) -> y (N, 3, H, W), float64."""
+def _params(weights, storage, grad=False):
+    def w(a):
+        t = _t(a)
+        if storage == "bf16":
+            t = t.to(torch.bfloat16).to(torch.float64)
+        return t.clone().requires_grad_(grad)
+
+    return {k: (w(W), _t(b).clone().requires_grad_(grad)) for k, (W, b) in weights.items()}
+
+
+def unet_forward(x, weights, storage=None):
+    """x: (N, 9, H, W) (H, W divisible by 8) -> y (N, 3, H, W), float64.
+    storage="bf16" also rounds the weights to bfloat16."""
     with torch.no_grad():
-        return _unet(_t(x), {k: (_t(W), _t(b)) for k, (W, b) in weights.items()})
+        return _unet(_t(x), _params(weights, storage), storage)
 
 
-def unet_forward_backward(x, weights, gy):
-    """Forward and the adjoint of the scalar <gy, y>: returns (y, gx, {name: (gW, gb)})."""
+def unet_forward_backward(x, weights, gy, storage=None):
+    """Forward and the adjoint of the scalar <gy, y>: returns (y, gx, {name: (gW, gb)}).
+    With storage="bf16" the upstream gradient is rounded too."""
     x = _t(x).clone().requires_grad_(True)
-    P = {k: (_t(W).clone().requires_grad_(True), _t(b).clone().requires_grad_(True)) for k, (W, b) in weights.items()}
-    y = _unet(x, P)
-    (y * _t(gy)).sum().backward()
+    P = _params(weights, storage, grad=True)
+    y = _unet(x, P, storage)
+    g = _t(gy)
+    if storage == "bf16":
+        g = g.to(torch.bfloat16).to(torch.float64)
+    (y * g).sum().backward()
     return y.detach(), x.grad.detach(), {k: (v[0].grad.detach(), v[1].grad.detach()) for k, v in P.items()}
 
 

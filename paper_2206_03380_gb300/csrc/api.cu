@@ -246,4 +246,94 @@ mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp
                     "shade_mc_bwd");
 }
 
+mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, size_t* weight_bytes, size_t* act_bytes,
+                               size_t* grad_bytes, size_t* n_params) {
+    REQUIRE(n_img >= 1 && H >= 8 && W >= 8 && H % 8 == 0 && W % 8 == 0,
+            "denoiser needs n_img >= 1 and H, W positive multiples of 8 (got %d x %d)", H, W);
+    REQUIRE((long long)n_img * H * W <= (1LL << 28), "denoiser image batch too large");
+    const mcdi::UnetWeightLayout L = mcdi::unet_weight_layout();
+    if (weight_bytes) *weight_bytes = L.total;
+    if (act_bytes) *act_bytes = mcdi::unet_act_bytes(n_img, H, W);
+    if (grad_bytes) *grad_bytes = mcdi::unet_grad_bytes(n_img, H, W);
+    if (n_params) *n_params = L.n_params;
+    return ok();
+}
+
+mcdi_status mcdi_denoise_pack_weights(const float* params, void* weights, void* stream) {
+    REQUIRE(params != nullptr && ((uintptr_t)params & 3u) == 0, "params must be a non-NULL device pointer");
+    REQUIRE(weights != nullptr && ((uintptr_t)weights & 255u) == 0, "weights must be 256-byte aligned");
+    return launched(mcdi::launch_unet_pack_weights(params, weights, static_cast<cudaStream_t>(stream)),
+                    "denoise_pack_weights");
+}
+
+mcdi_status mcdi_denoise_fwd(const void* weights, int n_img, int H, int W, const float* term, const float* kd,
+                             const float* nrm, int n_aux, float* y, void* acts, size_t act_bytes, unsigned* err,
+                             void* stream) {
+    size_t need = 0;
+    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, nullptr, &need, nullptr, nullptr);
+    if (s != MCDI_OK) return s;
+    REQUIRE(weights != nullptr && ((uintptr_t)weights & 255u) == 0, "weights must be 256-byte aligned");
+    REQUIRE_BUF16(term);
+    REQUIRE_BUF16(kd);
+    REQUIRE_BUF16(nrm);
+    REQUIRE_BUF16(y);
+    REQUIRE(n_aux >= 1 && n_aux <= n_img, "n_aux must be in [1, n_img]");
+    REQUIRE(acts != nullptr && ((uintptr_t)acts & 255u) == 0, "acts must be 256-byte aligned");
+    REQUIRE(act_bytes >= need, "acts too small: %zu < %zu bytes", act_bytes, need);
+    REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
+    const char* why = "";
+    cudaError_t e = mcdi::launch_unet_fwd(weights, n_img, H, W, term, kd, nrm, n_aux, y, acts, err,
+                                          static_cast<cudaStream_t>(stream), &why);
+    if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "denoise_fwd: %s", why);
+    return launched(e, "denoise_fwd");
+}
+
+mcdi_status mcdi_denoise_bwd(const void* weights, int n_img, int H, int W, const void* acts, size_t act_bytes,
+                             const float* gy, float* gx, void* grad_ws, size_t grad_bytes, unsigned* err,
+                             void* stream) {
+    size_t need_a = 0, need_g = 0;
+    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, nullptr, &need_a, &need_g, nullptr);
+    if (s != MCDI_OK) return s;
+    REQUIRE(weights != nullptr && ((uintptr_t)weights & 255u) == 0, "weights must be 256-byte aligned");
+    REQUIRE(acts != nullptr && act_bytes >= need_a, "acts too small");
+    REQUIRE_BUF16(gy);
+    REQUIRE_BUF16(gx);
+    REQUIRE(grad_ws != nullptr && ((uintptr_t)grad_ws & 255u) == 0, "grad_ws must be 256-byte aligned");
+    REQUIRE(grad_bytes >= need_g, "grad_ws too small: %zu < %zu bytes", grad_bytes, need_g);
+    REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
+    const char* why = "";
+    cudaError_t e = mcdi::launch_unet_bwd(weights, n_img, H, W, acts, gy, gx, grad_ws, err,
+                                          static_cast<cudaStream_t>(stream), &why);
+    if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "denoise_bwd: %s", why);
+    return launched(e, "denoise_bwd");
+}
+
+mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float* den_cs, long long n, float* c,
+                           void* stream) {
+    REQUIRE(n >= 1, "n must be >= 1");
+    REQUIRE_BUF16(kd_out);
+    REQUIRE_BUF16(den_cd);
+    REQUIRE_BUF16(den_cs);
+    REQUIRE_BUF16(c);
+    return launched(mcdi::launch_composite(kd_out, den_cd, den_cs, n, c, static_cast<cudaStream_t>(stream)),
+                    "composite");
+}
+
+mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pad, const void* w, const float* bias,
+                              int cout_pad, int relu, void* y, unsigned* err, void* stream) {
+    REQUIRE(n_img >= 1 && H >= 1 && W >= 1 && (long long)n_img * H * W <= (1LL << 28), "bad image shape");
+    REQUIRE(cin_pad >= 16 && cin_pad % 16 == 0 && cin_pad <= 1024, "cin_pad must be a multiple of 16 in [16, 1024]");
+    REQUIRE(cout_pad >= 16 && cout_pad % 16 == 0 && cout_pad <= 256, "cout_pad must be a multiple of 16 in [16, 256]");
+    REQUIRE(x != nullptr && ((uintptr_t)x & 15u) == 0, "x must be 16-byte aligned");
+    REQUIRE(w != nullptr && ((uintptr_t)w & 15u) == 0, "w must be 16-byte aligned");
+    REQUIRE(y != nullptr && ((uintptr_t)y & 15u) == 0, "y must be 16-byte aligned");
+    REQUIRE(bias == nullptr || ((uintptr_t)bias & 3u) == 0, "bias must be 4-byte aligned");
+    REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
+    const char* why = "";
+    cudaError_t e = mcdi::launch_conv3x3(x, n_img, H, W, cin_pad, w, bias, cout_pad, relu, y, err,
+                                         static_cast<cudaStream_t>(stream), &why);
+    if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "conv3x3_bf16: %s", why);
+    return launched(e, "conv3x3_bf16");
+}
+
 }  // extern "C"

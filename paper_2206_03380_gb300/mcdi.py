@@ -37,7 +37,8 @@ class ShadeParams(C.Structure):
 
 EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh_sizes", "mcdi_build_bvh",
            "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_workspace_size", "mcdi_shade_mc_fwd",
-           "mcdi_shade_mc_bwd"]
+           "mcdi_shade_mc_bwd", "mcdi_denoise_sizes", "mcdi_denoise_pack_weights", "mcdi_denoise_fwd",
+           "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_composite"]
 NOALLOC_MAX_TRIS = 65536
 
 
@@ -73,6 +74,18 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shade_mc_bwd.restype = st
     lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
+    lib.mcdi_denoise_sizes.restype = st
+    lib.mcdi_denoise_sizes.argtypes = [i, i, i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
+    lib.mcdi_denoise_pack_weights.restype = st
+    lib.mcdi_denoise_pack_weights.argtypes = [P, P, P]
+    lib.mcdi_denoise_fwd.restype = st
+    lib.mcdi_denoise_fwd.argtypes = [P, i, i, i, P, P, P, i, P, P, sz, P, P]
+    lib.mcdi_denoise_bwd.restype = st
+    lib.mcdi_denoise_bwd.argtypes = [P, i, i, i, P, sz, P, P, P, sz, P, P]
+    lib.mcdi_composite.restype = st
+    lib.mcdi_composite.argtypes = [P, P, P, C.c_longlong, P, P]
+    lib.mcdi_conv3x3_bf16.restype = st
+    lib.mcdi_conv3x3_bf16.argtypes = [P, i, i, i, i, P, P, i, i, P, P, P]
     _lib = lib
     return lib
 
@@ -165,6 +178,82 @@ def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeP
                                     _ptr(cams), N, H, W, C.byref(params), _ptr(g_cd), _ptr(g_kdout), _ptr(g_cs),
                                     _ptr(vis_mask), _ptr(g_kd), _ptr(g_korm), _ptr(g_nrm), _ptr(g_env),
                                     _stream(stream)), "shade_mc_bwd")
+
+
+def denoise_sizes(n_img: int, H: int, W: int):
+    a, b, c, d = C.c_size_t(), C.c_size_t(), C.c_size_t(), C.c_size_t()
+    _check(load().mcdi_denoise_sizes(int(n_img), int(H), int(W), C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+           "denoise_sizes")
+    return a.value, b.value, c.value, d.value
+
+
+def denoise_pack_weights(params, weights, stream=None):
+    _check(load().mcdi_denoise_pack_weights(_ptr(params), _ptr(weights), _stream(stream)), "denoise_pack_weights")
+
+
+def denoise_fwd(weights, term, kd, nrm, y, acts, err, stream=None):
+    n, H, W = term.shape[:3]
+    _check(load().mcdi_denoise_fwd(_ptr(weights), n, H, W, _ptr(term), _ptr(kd), _ptr(nrm), kd.shape[0], _ptr(y),
+                                   _ptr(acts), acts.numel() * acts.element_size(), _ptr(err), _stream(stream)),
+           "denoise_fwd")
+
+
+def denoise_bwd(weights, acts, gy, gx, grad_ws, err, stream=None):
+    n, H, W = gy.shape[:3]
+    _check(load().mcdi_denoise_bwd(_ptr(weights), n, H, W, _ptr(acts), acts.numel() * acts.element_size(), _ptr(gy),
+                                   _ptr(gx), _ptr(grad_ws), grad_ws.numel() * grad_ws.element_size(), _ptr(err),
+                                   _stream(stream)), "denoise_bwd")
+
+
+def composite(kd_out, den_cd, den_cs, c, stream=None):
+    n = kd_out.numel() // 4
+    _check(load().mcdi_composite(_ptr(kd_out), _ptr(den_cd), _ptr(den_cs), n, _ptr(c), _stream(stream)), "composite")
+
+
+def conv3x3_bf16(x, w, bias, y, relu, err, stream=None):
+    n, H, W, cin = x.shape
+    _check(load().mcdi_conv3x3_bf16(_ptr(x), n, H, W, cin, _ptr(w), _ptr(bias), w.shape[0], int(bool(relu)), _ptr(y),
+                                    _ptr(err), _stream(stream)), "conv3x3_bf16")
+
+
+UNET_PLAN = [("enc1a", 9, 32), ("enc1b", 32, 32), ("enc2a", 32, 48), ("enc2b", 48, 48), ("enc3a", 48, 64),
+             ("enc3b", 64, 64), ("bot_a", 64, 96), ("bot_b", 96, 96), ("dec3a", 160, 64), ("dec3b", 64, 64),
+             ("dec2a", 112, 48), ("dec2b", 48, 48), ("dec1a", 80, 32), ("dec1b", 32, 32), ("out", 32, 3)]
+
+
+def flatten_unet_params(weights: dict):
+    """{name: (W (co, ci, 3, 3), b (co,))} -> one float32 vector in the library's order."""
+    import numpy as np
+
+    parts = []
+    for name, ci, co in UNET_PLAN:
+        W, b = weights[name]
+        assert tuple(W.shape) == (co, ci, 3, 3) and tuple(b.shape) == (co,)
+        parts += [np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32).ravel()]
+    return np.concatenate(parts)
+
+
+class Denoiser:
+    """Device-resident denoiser for n_img images of H x W: packed weights, saved
+    activations, gradient scratch and the error word."""
+
+    def __init__(self, params_flat, n_img: int, H: int, W: int, device="cuda"):
+        wb, ab, gb, n_params = denoise_sizes(n_img, H, W)
+        p = torch.as_tensor(params_flat, dtype=torch.float32, device=device).contiguous()
+        assert p.numel() == n_params, (p.numel(), n_params)
+        self.n_img, self.H, self.W = n_img, H, W
+        self.weights = _empty_bytes(wb, device)
+        self.acts = _empty_bytes(ab, device)
+        self.grad_ws = _empty_bytes(gb, device)
+        self.err = torch.zeros(1, dtype=torch.int32, device=device)
+        denoise_pack_weights(p, self.weights)
+        self._params = p
+
+    def forward(self, term, kd, nrm, y, stream=None):
+        denoise_fwd(self.weights, term, kd, nrm, y, self.acts, self.err, stream)
+
+    def backward(self, gy, gx, stream=None):
+        denoise_bwd(self.weights, self.acts, gy, gx, self.grad_ws, self.err, stream)
 
 
 # ------------------------------------------------------------------ device-resident objects

@@ -4,8 +4,9 @@ One object holds a scene on the GPU (mesh, BVH, probe tables, textures,
 cameras, G-buffer, outputs and gradients) and runs the hot path of one
 optimisation step as the paper describes it (Sec. 3, Fig. "System"):
 probe distribution -> BVH over this iteration's mesh -> primary visibility
-(G-buffer) -> Monte Carlo direct illumination forward -> adjoint.  Every step
-is a libmcdi kernel launch on the current torch stream.
+(G-buffer) -> Monte Carlo direct illumination forward -> denoiser on c_d and
+c_s (Sec. 4.2) -> denoiser input gradient -> shading adjoint.  Every step is
+a libmcdi kernel launch on the current torch stream.
 """
 from __future__ import annotations
 
@@ -18,7 +19,8 @@ from .scenes import Scene
 
 class ShadingPipeline:
     def __init__(self, scene: Scene, device="cuda", tau: float = 0.0, ray_eps: float = 1e-4,
-                 decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True):
+                 decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True,
+                 denoiser_params=None):
         mcdi.load()
         self.scene = scene
         self.device = torch.device(device)
@@ -40,7 +42,15 @@ class ShadingPipeline:
         self.probe = mcdi.Probe.allocate(self.env)
         self.gb = mcdi.GBuffer.allocate(self.N, self.H, self.W, dev)
         shape = (self.N, self.H, self.W, 4)
-        self.c_d, self.kd_out, self.c_s = (torch.zeros(shape, device=dev) for _ in range(3))
+        # c_d and c_s share one buffer so that the denoiser sees them as a batch of 2N images
+        self.terms = torch.zeros((2 * self.N, self.H, self.W, 4), device=dev)
+        self.c_d, self.c_s = self.terms[: self.N], self.terms[self.N:]
+        self.kd_out = torch.zeros(shape, device=dev)
+        self.denoiser = None
+        if denoiser_params is not None:
+            self.denoiser = mcdi.Denoiser(denoiser_params, 2 * self.N, self.H, self.W, device=dev)
+            self.denoised = torch.zeros_like(self.terms)
+            self.g_terms = torch.zeros_like(self.terms)
         self.mask = (torch.zeros(self.N, self.H, self.W, (self.spp + 31) // 32, dtype=torch.int32, device=dev)
                      if keep_mask else None)
         self.g_kd, self.g_korm, self.g_nrm = (torch.zeros(shape, device=dev) for _ in range(3))
@@ -71,12 +81,26 @@ class ShadingPipeline:
         mcdi.shade_mc_bwd(self.bvh, self.probe, self.gb, self.cams, self.params, g_cd, g_kdout, g_cs, self.mask,
                           self.g_kd, self.g_korm, self.g_nrm, self.g_env, stream)
 
+    def denoise(self, stream=None):
+        """D(c_d), D(c_s) with k_d,out and the normal as guides (Sec. 4.2)."""
+        self.denoiser.forward(self.terms, self.kd_out, self.gb.nrm, self.denoised, stream)
+
+    def denoise_backward(self, g_denoised, stream=None):
+        self.denoiser.backward(g_denoised, self.g_terms, stream)
+
     def step(self, g_cd, g_kdout, g_cs, stream=None):
-        """One pass of the hot path: tables, BVH, G-buffer, forward, adjoint."""
+        """One pass of the hot path: tables, BVH, G-buffer, forward, adjoint.
+        With a denoiser, g_cd / g_cs are gradients of the denoised terms and pass
+        through the denoiser's input gradient first."""
         self.build_probe(stream)
         self.build_bvh(stream)
         self.primary(stream)
         self.forward(stream)
+        if self.denoiser is not None:
+            self.denoise(stream)
+            g = torch.cat([g_cd, g_cs], 0) if g_cd.shape[0] == self.N else g_cd
+            self.denoise_backward(g, stream)
+            g_cd, g_cs = self.g_terms[: self.N], self.g_terms[self.N:]
         self.backward(g_cd, g_kdout, g_cs, stream)
 
     def covered_pixels(self) -> int:

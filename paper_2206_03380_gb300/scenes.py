@@ -343,6 +343,26 @@ def orbit_cameras(n_total: int, pick, radius: float, fovy_deg: float, aspect: fl
     return np.stack([look_at(eyes[k], (0, 0, 0), (0, 1, 0), fovy_deg, aspect) for k in pick])
 
 
+# ------------------------------------------------------------------ denoiser weights
+UNET_SHAPES = [("enc1a", 9, 32), ("enc1b", 32, 32), ("enc2a", 32, 48), ("enc2b", 48, 48), ("enc3a", 48, 64),
+               ("enc3b", 64, 64), ("bot_a", 64, 96), ("bot_b", 96, 96), ("dec3a", 160, 64), ("dec3b", 64, 64),
+               ("dec2a", 112, 48), ("dec2b", 48, 48), ("dec1a", 80, 32), ("dec1b", 32, 32), ("out", 32, 3)]
+
+
+def unet_xavier_weights(seed: int):
+    """Random denoiser weights (the live-trained denoiser of App. B starts from
+    Xavier initialisation): W ~ U(-a, a), a = sqrt(6 / (9 c_in + 9 c_out)), and
+    small uniform biases; {name: (W (co, ci, 3, 3), b (co,))} float32."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, ci, co in UNET_SHAPES:
+        a = np.sqrt(6.0 / (9 * ci + 9 * co))
+        W = rng.uniform(-a, a, size=(co, ci, 3, 3)).astype(np.float32)
+        b = rng.uniform(-0.05, 0.05, size=co).astype(np.float32)
+        out[name] = (W, b)
+    return out
+
+
 # ------------------------------------------------------------------ workloads
 def parity_scene(seed: int = BASE_SEED + 1) -> Scene:
     """64 x 64, one view, 8 spp (4 light, 2 cosine, 2 GGX); icosphere (1,280 tris, r = 1)
@@ -374,3 +394,61 @@ def sphere_union_scene(seed: int = BASE_SEED + 2, res: int = 512, spp=(8, 4, 4),
     return Scene(f"sphere-union-{tris.shape[0]}tris-{res}x{res}-{sum(spp)}spp", verts, vnrm, tris, env, kd, korm,
                  np.array([-1.0, -1.0, 0.5], np.float32), cams, res, res, spp[0], spp[1], spp[2], seed,
                  {"lobes": lobes})
+
+
+# ------------------------------------------------------------------ serving stream
+@dataclass
+class RenderRequest:
+    rid: int
+    arrival: float  # seconds after the start of the stream
+    scene: int
+    probe: int
+    res: int        # square image side
+    spp: int
+    view: int       # index into the scene's orbit cameras
+    seed: int
+
+
+def split_spp(spp: int):
+    """Light / cosine / GGX sample counts: half probe samples, a quarter each lobe."""
+    n_l = spp // 2
+    n_c = (spp - n_l) // 2
+    return n_l, n_c, spp - n_l - n_c
+
+
+def poisson_requests(n: int, rate: float, n_scenes: int, n_probes: int, seed: int, res_range=(128, 1024),
+                     spp_choices=(4, 8, 16, 32, 64), n_views: int = 200):
+    """Poisson arrivals at ``rate`` per second; side uniform over multiples of 32
+    in ``res_range``; spp uniform over ``spp_choices``; scene, probe and view uniform."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    sides = np.arange(res_range[0], res_range[1] + 1, 32)
+    out = []
+    for k in range(n):
+        out.append(RenderRequest(k, float(t[k]), int(rng.integers(n_scenes)), int(rng.integers(n_probes)),
+                                 int(rng.choice(sides)), int(rng.choice(spp_choices)), int(rng.integers(n_views)),
+                                 int(rng.integers(1, 2 ** 62))))
+    return out
+
+
+def serving_scenes(n_scenes: int = 16, grids=(64, 96, 128, 160), seed: int = BASE_SEED + 5, tex: int = 512):
+    """Resident scene set: meshes of the sphere-union family on several grid sizes
+    (tens of thousands to ~450k triangles), each scene with its own textures and
+    200 orbit cameras."""
+    rng = np.random.default_rng(seed)
+    meshes = [sdf_spheres_mesh(g, 32, np.random.default_rng(seed + g)) for g in grids]
+    out = []
+    for k in range(n_scenes):
+        v, n, t = meshes[k % len(meshes)]
+        kd, korm = pbr_textures(tex, rng)
+        cams = orbit_cameras(200, list(range(200)), 2.4, 45.0, 1.0, rng)
+        out.append(dict(verts=v, vnrm=n, tris=t, tex_kd=kd, tex_korm=korm, cams=cams,
+                        uvmap=np.array([-1.0, -1.0, 0.5], np.float32)))
+    return out
+
+
+def serving_probes(n_probes: int = 16, seed: int = BASE_SEED + 6):
+    """Probes from 256 x 128 to 1024 x 512 with sun lobes."""
+    rng = np.random.default_rng(seed)
+    sizes = [(256, 128), (512, 256), (1024, 512)]
+    return [env_with_lobes(*sizes[k % len(sizes)], rng)[0] for k in range(n_probes)]

@@ -1,0 +1,128 @@
+"""GPU parity of the denoiser (Sec. 4.2 neural denoiser, App. B) through the C ABI.
+
+* one convolution layer (tcgen05, BF16 operands, FP32 accumulation, BF16
+  output) against the library FP64 convolution of the same BF16-rounded
+  inputs, rounded to BF16: at least 99.5% of outputs bitwise equal, none more
+  than 2 units in the last place apart;
+* the whole U-Net forward and its input gradient against the oracle
+  (PyTorch CPU float64) run with bfloat16 storage at the points where the
+  kernels store bfloat16, so that ReLU masks and max-pool winners are decided
+  in the same precision: forward rel-L2 <= 1e-2, input gradient <= 6e-2 (rare
+  1-ulp differences from FP32 accumulation order compound through the layers);
+* and, as the precision statement, against the pure float64 network:
+  forward rel-L2 <= 2e-2 (PSNR reported), input gradient <= 0.2.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import denoise_ref as D
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+@pytest.mark.parametrize("cin,cout,H,W,relu", [(16, 32, 16, 8, True), (32, 48, 24, 40, False), (160, 64, 16, 16, True),
+                                                (80, 96, 8, 64, True), (16, 16, 4, 256, False), (48, 160, 12, 20, True)])
+def test_conv3x3_layer_matches_library(cuda_lib, cin, cout, H, W, relu):
+    mcdi = cuda_lib
+    rng = np.random.default_rng(cin * 1000 + cout)
+    n = 2
+    x = bf16_round(rng.normal(size=(n, H, W, cin)))
+    w = bf16_round(rng.normal(size=(cout, 3, 3, cin)) / np.sqrt(9 * cin))
+    b = torch.from_numpy(rng.normal(size=cout).astype(np.float32))
+    dev = "cuda"
+    xg = x.to(torch.bfloat16).to(dev).contiguous()
+    wg = w.reshape(cout, 9, cin).to(torch.bfloat16).to(dev).contiguous()
+    yg = torch.full((n, H, W, cout), float("nan"), dtype=torch.bfloat16, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    mcdi.conv3x3_bf16(xg, wg, b.to(dev), yg, relu, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = D.conv3x3(x.permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b.double())
+    if relu:
+        ref = torch.relu(ref)
+    ref = ref.permute(0, 2, 3, 1)
+    # the kernel stores BF16(FP32 accumulation): compare with BF16(FP64 reference) in units in the last place
+    ref_b = ref.to(torch.bfloat16)
+    got_b = yg.cpu()
+    assert torch.isfinite(got_b.float()).all()
+    ulp = (got_b.view(torch.int16).int() - ref_b.view(torch.int16).int()).abs()
+    assert (ulp == 0).float().mean().item() >= 0.995
+    assert ulp.max().item() <= 2
+
+
+def make_inputs(rng, n_views, H, W):
+    term = np.abs(rng.lognormal(0.0, 0.8, size=(2 * n_views, H, W, 4))).astype(np.float32)
+    kd = rng.uniform(0, 1, size=(n_views, H, W, 4)).astype(np.float32)
+    nrm = rng.normal(size=(n_views, H, W, 4)).astype(np.float32)
+    nrm[..., :3] /= np.linalg.norm(nrm[..., :3], axis=-1, keepdims=True)
+    for a in (term, kd, nrm):
+        a[..., 3] = 0
+    return term, kd, nrm
+
+
+def oracle_input(term, kd, nrm):
+    n = term.shape[0]
+    nv = kd.shape[0]
+    idx = np.arange(n) % nv
+    return D.denoiser_input(term[..., :3], kd[idx, ..., :3], nrm[idx, ..., :3])
+
+
+@pytest.mark.parametrize("H,W", [(64, 64), (48, 40)])
+def test_unet_forward_and_input_gradient_match_oracle(cuda_lib, H, W):
+    mcdi = cuda_lib
+    rng = np.random.default_rng(H * W)
+    term, kd, nrm = make_inputs(rng, 1, H, W)
+    weights = D.xavier_weights(5)
+    den = mcdi.Denoiser(mcdi.flatten_unet_params(weights), term.shape[0], H, W)
+    t = lambda a: torch.from_numpy(a).cuda().contiguous()
+    y = torch.zeros(term.shape, device="cuda")
+    den.forward(t(term), t(kd), t(nrm), y)
+    gy = rng.normal(size=term.shape).astype(np.float32)
+    gy[..., 3] = 0
+    gx = torch.zeros(term.shape, device="cuda")
+    den.backward(t(gy), gx)
+    torch.cuda.synchronize()
+    assert den.err.item() == 0
+    x = oracle_input(term, kd, nrm)
+    gyo = torch.from_numpy(gy[..., :3]).permute(0, 3, 1, 2)
+    yg = y.cpu().numpy()[..., :3]
+    gg = gx.cpu().numpy()[..., :3]
+    assert np.isfinite(yg).all() and np.isfinite(gg).all()
+    assert np.all(y.cpu().numpy()[..., 3] == 0)
+    res = {}
+    for storage in ("bf16", None):
+        yo, gxo, _ = D.unet_forward_backward(x, weights, gyo, storage=storage)
+        yo = yo.permute(0, 2, 3, 1).numpy()
+        go = gxo[:, 0:3].permute(0, 2, 3, 1).numpy()
+        res[storage] = (D.rel_l2(yg, yo), D.psnr(yg, yo), D.rel_l2(gg, go))
+    (bf_f, bf_p, bf_b), (f64_f, f64_p, f64_b) = res["bf16"], res[None]
+    print(f"denoiser {H}x{W}: vs BF16-storage oracle fwd rel-L2 {bf_f:.2e} ({bf_p:.1f} dB), input-grad rel-L2 "
+          f"{bf_b:.2e}; vs float64 network fwd rel-L2 {f64_f:.2e} ({f64_p:.1f} dB), input-grad rel-L2 {f64_b:.2e}")
+    # same precision for storage and decisions: only accumulation order differs, and the rare
+    # 1-ulp differences it causes compound through the 15 layers
+    assert bf_f <= 1e-2 and bf_b <= 6e-2
+    # the precision statement: BF16 storage against the float64 network
+    assert f64_f <= 2e-2 and f64_b <= 0.2
+
+
+def test_unet_forward_at_headline_size(cuda_lib):
+    """512 x 512, the two terms of one view (the benchmark's denoiser launch), forward only."""
+    mcdi = cuda_lib
+    rng = np.random.default_rng(512)
+    term, kd, nrm = make_inputs(rng, 1, 512, 512)
+    weights = D.xavier_weights(6)
+    den = mcdi.Denoiser(mcdi.flatten_unet_params(weights), 2, 512, 512)
+    t = lambda a: torch.from_numpy(a).cuda().contiguous()
+    y = torch.zeros(term.shape, device="cuda")
+    den.forward(t(term), t(kd), t(nrm), y)
+    torch.cuda.synchronize()
+    assert den.err.item() == 0
+    yo = D.unet_forward(oracle_input(term, kd, nrm), weights, storage="bf16").permute(0, 2, 3, 1).numpy()
+    e = D.rel_l2(y.cpu().numpy()[..., :3], yo)
+    print(f"denoiser 512x512 forward vs BF16-storage oracle rel-L2 {e:.2e}")
+    assert e <= 1e-2

@@ -105,3 +105,17 @@ def test_xavier_initialisation():
         if W.size > 2000:
             assert abs(W.var() / (a * a / 3) - 1) < 0.1
     assert D.rel_l2([1.0, 2.0], [1.0, 2.0]) == 0.0 and D.psnr([1.0, 2.0], [1.0, 2.0]) == float("inf")
+
+
+def test_bf16_storage_rounds_and_stays_close():
+    rng = np.random.default_rng(4)
+    w = D.xavier_weights(3)
+    x = np.abs(rng.normal(size=(1, 9, 16, 16)))
+    gy = rng.normal(size=(1, 3, 16, 16))
+    y64, g64, _ = D.unet_forward_backward(x, w, gy)
+    y16, g16, _ = D.unet_forward_backward(x, w, gy, storage="bf16")
+    assert 1e-4 < D.rel_l2(y16, y64) < 5e-2  # rounding happened, and stays bounded
+    # the routing network is exact in either precision when values are representable
+    xr = np.round(np.abs(rng.normal(size=(1, 9, 16, 24))) * 8) / 8
+    yr = D.unet_forward(xr, routing_weights(False), storage="bf16").numpy()
+    np.testing.assert_array_equal(yr[:, 0], xr[:, 0])
