@@ -324,11 +324,15 @@ def run_serving(n_requests, rate, dev, rank):
     out = {"requests": n_requests, "rate_per_s": rate,
            "triangles": [int(s["tris"].shape[0]) for s in sc[:4]],
            "offered_msamples_per_s": round(rate * float(np.mean([q.res * q.res * q.spp for q in reqs])) / 1e6, 1)}
+    keys = ("p50_ms", "p99_ms", "mean_ms", "req_per_s", "msamples_per_s", "wall_s")
     for mode in ("continuous", "serial"):
         r = eng.run(reqs, mode=mode)
-        out[mode] = {k: round(r[k], 3) for k in ("p50_ms", "p99_ms", "mean_ms", "req_per_s", "msamples_per_s",
-                                                  "wall_s")}
+        out[mode] = {k: round(r[k], 3) for k in keys}
         out[mode]["admission_waits"] = r["admission_waits"]
+    # the same stream arriving twice as fast: past what one request at a time sustains
+    fast = scenes.poisson_requests(n_requests, 2 * rate, len(sc), len(pr), seed=scenes.BASE_SEED + 7 + rank)
+    out["at_2x_rate"] = {mode: {k: round(v, 3) for k, v in eng.run(fast, mode=mode).items() if k in keys}
+                         for mode in ("continuous", "serial")}
     out["slots"] = eng.n_slots
     return out
 

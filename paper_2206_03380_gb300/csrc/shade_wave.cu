@@ -181,8 +181,9 @@ __global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode
         for (int step = 0; step < kTraceStepsPerRefill; ++step) {
             const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
             const int4 d = __ldg(&nodes[node].d);
-            bool h0 = slab(r, a, make_float2(c.x, c.y), FLT_MAX) < FLT_MAX;
-            bool h1 = slab(r, b, make_float2(c.z, c.w), FLT_MAX) < FLT_MAX;
+            const float t0 = slab(r, a, make_float2(c.x, c.y), FLT_MAX);
+            const float t1 = slab(r, b, make_float2(c.z, c.w), FLT_MAX);
+            bool h0 = t0 < FLT_MAX, h1 = t1 < FLT_MAX;
             int result = -1;  // -1 continue, 0 miss, 1 hit
             if (h0 && d.x < 0) {
                 if (tri_hit(r, tris, ~d.x, nullptr, nullptr) < FLT_MAX) result = 1;
@@ -193,9 +194,10 @@ __global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode
                 h1 = false;
             }
             if (result < 0) {
-                if (h0 && h1) {
-                    if (sp < kTraversalStack) stack[sp++] = d.y;
-                    node = d.x;
+                if (h0 && h1) {  // nearer child first: nearby occluders end the ray sooner
+                    const bool first0 = t0 <= t1;
+                    if (sp < kTraversalStack) stack[sp++] = first0 ? d.y : d.x;
+                    node = first0 ? d.x : d.y;
                 } else if (h0) {
                     node = d.x;
                 } else if (h1) {
