@@ -302,6 +302,225 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-tile form, for images at least 65 pixels wide (128-pixel row tiles).
+// A persistent CTA keeps a slice of Nc output channels of the layer's weights
+// resident in shared memory for its whole life ([chunk][tap][Nc][16 ch],
+// 32-byte swizzle, loaded once) and loops over tiles of R output rows x 128
+// pixels.  Per 16-channel input chunk, TMA brings the tile's halo once: R + 2
+// rows x 130 pixels, as two planes of 8 channels with 16-byte rows and no
+// swizzle.  With 16-byte rows any row starts a valid 8-row core matrix, so the
+// A operand of output row r and tap (dy, dx) is the window starting at halo
+// row (r + dy) * 130 + dx: 9 R MMAs (M = 128, N = Nc, K = 16) per chunk read
+// (R + 2) / R input rows per output row instead of 9.
+//   warp 0 lane 0   TMA producer (weights once, then halo chunks),
+//   warp 1 lane 0   MMA issuer; accumulators of tile i in TMEM buffer i & 1,
+//   warps 2..5      epilogue (TMEM lane quarter = warp % 4).
+constexpr int kRowThreads = 192;
+constexpr int kRowMaxStages = 6;
+constexpr int kHaloW = 130;
+constexpr int kMaxRows = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// K-major operand without swizzle: core matrices of 8 rows x 16 bytes with
+// rows 16 bytes apart, 8-row groups 128 bytes apart (stride byte offset) and
+// the second 8-channel half of K one plane further (leading byte offset).
+__device__ __forceinline__ uint64_t noswz_desc(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(128u >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; swizzle mode 0 (none)
+    return d;
+}
+
+__global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_xh,
+                                                                   const __grid_constant__ CUtensorMap tmap_wh,
+                                                                   const ConvParams p, const RowPlan rp) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kRowMaxStages], empty_bar[kRowMaxStages], accf_bar[2], acce_bar[2],
+        w_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t wbase = base + (uint32_t)rp.stages * rp.stage_bytes;
+    const int S = rp.stages, R = rp.rows, Nc = rp.nc;
+    const int n_chunks = p.cin_pad >> 4;
+    const uint32_t w_chunk = 9u * (uint32_t)Nc * 32u;  // bytes of one chunk's weights, all taps
+    const int slice = blockIdx.x % rp.n_slices;
+    const int n0 = slice * Nc;
+    const int first = blockIdx.x / rp.n_slices, step = gridDim.x / rp.n_slices;
+    const bool has_work = first < rp.n_tiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), 4);
+        }
+        mbar_init(smem_u32(&w_bar), 1);
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(rp.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    auto tile_origin = [&](int t, int* img, int* x0, int* y0) {
+        const int tx = t % p.tiles_x;
+        t /= p.tiles_x;
+        *y0 = (t % p.tiles_y) * R;
+        *img = t / p.tiles_y;
+        *x0 = tx * 128;
+    };
+
+    int issued = 0;
+    bool w_issued = false;
+    if (warp == 0) {
+        if (lane == 0 && has_work) {
+            const uint32_t wb = smem_u32(&w_bar);
+            mbar_expect_tx(wb, (uint32_t)n_chunks * w_chunk);
+            for (int c = 0; c < n_chunks; ++c) tma_load_4d(wbase + (uint32_t)c * w_chunk, &tmap_wh, 0, n0, 0, c, wb);
+            w_issued = true;
+            int g = 0;
+            for (int t = first; t < rp.n_tiles && !failed; t += step) {
+                int img, x0, y0;
+                tile_origin(t, &img, &x0, &y0);
+                for (int c = 0; c < n_chunks; ++c, ++g) {
+                    const int s = g % S;
+                    if (!mbar_wait(smem_u32(&empty_bar[s]), ((uint32_t)(g / S) & 1u) ^ 1u)) {
+                        failed = 1;
+                        break;
+                    }
+                    const uint32_t st = base + (uint32_t)s * rp.stage_bytes;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    mbar_expect_tx(fb, 2u * rp.plane_load);
+                    tma_load_4d(st, &tmap_xh, c * 16, x0 - 1, y0 - 1, img, fb);
+                    tma_load_4d(st + rp.plane_bytes, &tmap_xh, c * 16 + 8, x0 - 1, y0 - 1, img, fb);
+                    issued = g + 1;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && has_work) {
+            const uint32_t idesc = bf16_idesc(128, Nc);
+            bool ok = mbar_wait(smem_u32(&w_bar), 0u);
+            if (!ok) failed = 1;
+            int g = 0, i = 0;
+            for (int t = first; ok && t < rp.n_tiles && !failed; t += step, ++i) {
+                const int b = i & 1;
+                if (!mbar_wait(smem_u32(&acce_bar[b]), ((uint32_t)(i >> 1) & 1u) ^ 1u)) {
+                    failed = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d0 = tmem + (uint32_t)(b * R) * rp.acc_stride;
+                int c = 0;
+                for (; c < n_chunks; ++c, ++g) {
+                    const int s = g % S;
+                    if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(g / S) & 1u)) {
+                        failed = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = base + (uint32_t)s * rp.stage_bytes;
+                    const uint32_t wc = wbase + (uint32_t)c * w_chunk;
+#pragma unroll 1
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+                        const uint64_t bdesc = sw32_desc(wc + (uint32_t)tap * (uint32_t)Nc * 32u);
+                        const uint32_t accum = (c > 0 || tap > 0) ? 1u : 0u;
+#pragma unroll 1
+                        for (int r = 0; r < R; ++r) {
+                            const uint64_t adesc =
+                                noswz_desc(st + (uint32_t)((r + dy) * kHaloW + dx) * 16u, rp.plane_bytes);
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                    d0 + (uint32_t)r * rp.acc_stride),
+                                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+                                : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty_bar[s]))
+                                 : "memory");
+                }
+                if (c < n_chunks) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&accf_bar[b]))
+                             : "memory");
+            }
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        int i = 0;
+        for (int t = first; t < rp.n_tiles; t += step, ++i) {
+            const int b = i & 1;
+            const bool ok = mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)(i >> 1) & 1u);
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = 1;
+                break;
+            }
+            tc_fence_after();
+            int img, x0, y0;
+            tile_origin(t, &img, &x0, &y0);
+            const int x = x0 + m;
+            for (int r = 0; r < R; ++r) {
+                const int y = y0 + r;
+                const bool valid = x < p.W && y < p.H;
+                const size_t pix = ((size_t)img * p.H + y) * p.W + x;
+                const uint32_t tr = tmem + (uint32_t)(b * R + r) * rp.acc_stride + ((uint32_t)(q * 32) << 16);
+                for (int c0 = 0; c0 < Nc; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tr + (uint32_t)c0, v);
+                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, pix);
+                    __syncwarp();
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (failed) {
+        if (threadIdx.x == 0) atomicExch(p.err, 1u);
+        if (warp == 0 && lane == 0) {  // let this CTA's copies in flight land before it exits
+            if (w_issued) mbar_wait(smem_u32(&w_bar), 0u);
+            for (int g = 0; g < issued; ++g)
+                if (!mbar_wait(smem_u32(&full_bar[g % S]), (uint32_t)(g / S) & 1u)) break;
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(rp.tmem_cols)
+                     : "memory");
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn(const char** why) {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -315,6 +534,80 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn(const char** why) {
     });
     if (!fn) *why = "cuTensorMapEncodeTiled is not available from the driver";
     return fn;
+}
+
+struct DeviceLimits {
+    int sms = 0;
+    uint32_t rows_smem_max = 0;  // dynamic shared memory the row-tile kernel may request
+};
+
+const DeviceLimits& device_limits() {
+    static std::once_flag once;
+    static DeviceLimits L;
+    std::call_once(once, [] {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel) != cudaSuccess || optin <= (int)fa.sharedSizeBytes) {
+            L.sms = 0;
+            return;
+        }
+        L.rows_smem_max = (uint32_t)(optin - (int)fa.sharedSizeBytes);
+    });
+    return L;
+}
+
+uint32_t pow2_at_least(uint32_t v) {
+    uint32_t c = 32;
+    while (c < v) c <<= 1;
+    return c;
+}
+
+// Row-tile plan: the fewest channel slices whose resident weights leave room
+// for two halo stages; per slice the most rows per tile (up to kMaxRows) that
+// fit tensor memory (two buffers of R accumulators) and still give 1.5 tiles
+// per SM; two CTAs per SM where both fit in shared memory and tensor memory.
+bool plan_rows(const ConvParams& p, RowPlan* out) {
+    if (p.tw != 128 || p.th != 1) return false;
+    const DeviceLimits& lim = device_limits();
+    const int sms = lim.sms;
+    if (sms <= 0) return false;
+    const uint32_t kSmemMax = lim.rows_smem_max, kAlign = 1024u;
+    const int n_chunks = p.cin_pad / 16;
+    for (int n_slices = 1; 16 * n_slices <= p.cout_pad; ++n_slices) {
+        if (p.cout_pad % (16 * n_slices) != 0) continue;
+        const int nc = p.cout_pad / n_slices;
+        const uint32_t acc_stride = pow2_at_least((uint32_t)nc);
+        const uint32_t w_bytes = (uint32_t)n_chunks * 9u * (uint32_t)nc * 32u;
+        for (int R = kMaxRows; R >= 1; R >>= 1) {
+            const uint32_t tmem_cols = pow2_at_least(2u * (uint32_t)R * acc_stride);
+            if (tmem_cols > 512u) continue;
+            RowPlan rp{};
+            rp.rows = R;
+            rp.nc = nc;
+            rp.n_slices = n_slices;
+            rp.plane_load = (uint32_t)(R + 2) * kHaloW * 16u;
+            rp.plane_bytes = (rp.plane_load + 127u) & ~127u;
+            rp.stage_bytes = (2u * rp.plane_bytes + 1023u) & ~1023u;
+            rp.acc_stride = acc_stride;
+            rp.tmem_cols = tmem_cols;
+            if (w_bytes + 2u * rp.stage_bytes + kAlign > kSmemMax) continue;
+            rp.n_tiles = p.n_img * ((p.H + R - 1) / R) * p.tiles_x;
+            if (R > 1 && 2 * n_slices * rp.n_tiles < 3 * sms) continue;
+            const bool two = w_bytes + 3u * rp.stage_bytes + kAlign <= kSmemMax / 2 - 1024u && 2u * tmem_cols <= 512u;
+            const uint32_t budget = two ? kSmemMax / 2 - 1024u : kSmemMax;
+            int S = (int)((budget - kAlign - w_bytes) / rp.stage_bytes);
+            rp.stages = S > kRowMaxStages ? kRowMaxStages : S;
+            rp.smem_bytes = (uint32_t)rp.stages * rp.stage_bytes + w_bytes + kAlign;
+            const int per_slice = (two ? 2 : 1) * sms / n_slices;
+            rp.grid = n_slices * (per_slice < rp.n_tiles ? per_slice : rp.n_tiles);
+            *out = rp;
+            return true;
+        }
+    }
+    return false;
 }
 
 size_t conv_smem_bytes(int cout_pad) {
@@ -356,20 +649,52 @@ bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w,
         *why = "weight tensor map rejected by the driver";
         return false;
     }
+    d->rows_form = plan_rows(d->p, &d->rp);
+    if (d->rows_form) {
+        const RowPlan& rp = d->rp;
+        d->p.tiles_y = (p.H + rp.rows - 1) / rp.rows;
+        const cuuint32_t hbox[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)(rp.rows + 2), 1};
+        r = enc(&d->tmap_xh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(x), xdims, xstr, hbox,
+                ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "halo activation tensor map rejected by the driver";
+            return false;
+        }
+        // The same K-major weights [cout][tap][cin] viewed as (16 channels,
+        // cout, tap, chunk): one box lands in shared memory as [tap][nc][16].
+        const cuuint64_t hdims[4] = {16, (cuuint64_t)p.cout_pad, 9, (cuuint64_t)(p.cin_pad / 16)};
+        const cuuint64_t hstr[3] = {(cuuint64_t)9 * p.cin_pad * 2, (cuuint64_t)p.cin_pad * 2, 32};
+        const cuuint32_t hwbox[4] = {16, (cuuint32_t)rp.nc, 9, 1};
+        r = enc(&d->tmap_wh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w), hdims, hstr, hwbox,
+                ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "halo weight tensor map rejected by the driver";
+            return false;
+        }
+    }
     return true;
 }
 
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
-    const size_t smem = conv_smem_bytes(d.p.cout_pad);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)conv_smem_bytes(256));
+        if (attr_err == cudaSuccess && device_limits().rows_smem_max > 0)
+            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)device_limits().rows_smem_max);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    const int grid = d.p.n_img * d.p.tiles_y * d.p.tiles_x;
-    conv_tc_kernel<<<grid, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
+    if (d.rows_form) {
+        conv_tc_rows_kernel<<<d.rp.grid, kRowThreads, d.rp.smem_bytes, stream>>>(d.tmap_xh, d.tmap_wh, d.p, d.rp);
+        return cudaGetLastError();
+    }
+    const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;
+    const size_t smem = conv_smem_bytes(d.p.cout_pad);
+    conv_tc_kernel<<<n_tiles, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
     return cudaGetLastError();
 }
 

@@ -36,18 +36,42 @@ struct ConvParams {
     unsigned* err;             // device error word (set on a wait timeout)
 };
 
+// Launch plan of the row-tile form (tiles of `rows` x 128 pixels, weights of
+// `nc` output channels resident per CTA).
+struct RowPlan {
+    int rows;                // output rows per tile (R)
+    int nc;                  // output channels per CTA (MMA N); n_slices * nc = cout_pad
+    int n_slices;
+    int stages;              // halo ring depth
+    int n_tiles;             // tiles per channel slice
+    int grid;                // CTAs (a multiple of n_slices)
+    uint32_t plane_load;     // bytes one 8-channel halo plane load writes: (R + 2) * 130 * 16
+    uint32_t plane_bytes;    // plane stride in shared memory (128-byte aligned)
+    uint32_t stage_bytes;    // two planes, 1024-byte aligned
+    uint32_t acc_stride;     // TMEM columns between the accumulators of two rows
+    uint32_t tmem_cols;      // TMEM columns allocated (two buffers of R accumulators)
+    uint32_t smem_bytes;     // dynamic shared memory
+};
+
 // Host helpers (tc_conv.cu).
 struct ConvDesc {
     CUtensorMap tmap_x;
     CUtensorMap tmap_w;
+    CUtensorMap tmap_xh;  // row-tile form: 8-channel halo planes of R + 2 rows x 130 pixels, no swizzle
+    CUtensorMap tmap_wh;  // row-tile form: one 16-channel chunk of all 9 taps' weights, [tap][nc][16]
+    bool rows_form;
+    RowPlan rp;
     ConvParams p;
 };
 
 // Encodes the tensor maps of an NHWC BF16 input (n_img, H, W, cin_pad) and a
-// K-major BF16 weight matrix [cout_pad][9 * cin_pad]; returns false (with a
-// message) when the driver rejects them.
+// K-major BF16 weight matrix [cout_pad][9 * cin_pad]; for 128-pixel-wide row
+// tiles whose weights fit in shared memory it also plans the row-tile form and
+// encodes its maps.  Returns false (with a message) when the driver rejects a
+// map.
 bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w, const char** why);
 
+// Runs the persistent row-tile kernel when planned, else one CTA per tile.
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream);
 
 int conv_pick_tile_w(int W);

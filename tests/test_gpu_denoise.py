@@ -3,7 +3,8 @@
 * one convolution layer (tcgen05, BF16 operands, FP32 accumulation, BF16
   output) against the library FP64 convolution of the same BF16-rounded
   inputs, rounded to BF16: at least 99.5% of outputs bitwise equal, none more
-  than 2 units in the last place apart;
+  than 2 units in the last place apart except where the taps cancel, where
+  the error stays within 1e-5 of the summed magnitudes conv(|x|, |w|);
 * the whole U-Net forward and its input gradient against the oracle
   (PyTorch CPU float64) run with bfloat16 storage at the points where the
   kernels store bfloat16, so that ReLU masks and max-pool winners are decided
@@ -26,7 +27,18 @@ def bf16_round(a):
 
 
 @pytest.mark.parametrize("cin,cout,H,W,relu", [(16, 32, 16, 8, True), (32, 48, 24, 40, False), (160, 64, 16, 16, True),
-                                                (80, 96, 8, 64, True), (16, 16, 4, 256, False), (48, 160, 12, 20, True)])
+                                                (80, 96, 8, 64, True), (16, 16, 4, 256, False), (48, 160, 12, 20, True),
+                                                # many tiles: the persistent launch form
+                                                (32, 32, 96, 256, True), (112, 48, 64, 200, False),
+                                                # 128-pixel row tiles: the row-tile form, one row per tile,
+                                                # ragged last tile
+                                                (16, 32, 5, 129, True), (160, 64, 6, 130, True),
+                                                (96, 96, 10, 384, True), (64, 160, 3, 200, False),
+                                                # enough tiles for 4 rows (ragged in x and y) and 2 rows per tile
+                                                (32, 48, 238, 200, True), (32, 80, 240, 256, False),
+                                                (48, 112, 120, 256, True),
+                                                # weights too large for one CTA: 5 slices of 32 output channels
+                                                (256, 160, 8, 256, True)])
 def test_conv3x3_layer_matches_library(cuda_lib, cin, cout, H, W, relu):
     mcdi = cuda_lib
     rng = np.random.default_rng(cin * 1000 + cout)
@@ -46,13 +58,18 @@ def test_conv3x3_layer_matches_library(cuda_lib, cin, cout, H, W, relu):
     if relu:
         ref = torch.relu(ref)
     ref = ref.permute(0, 2, 3, 1)
-    # the kernel stores BF16(FP32 accumulation): compare with BF16(FP64 reference) in units in the last place
+    # the kernel stores BF16(FP32 accumulation): compare with BF16(FP64 reference) in units in the last place;
+    # where the taps cancel (outputs near zero) the FP32 accumulation error is bounded by the magnitude
+    # of the summed terms, conv(|x|, |w|), instead
     ref_b = ref.to(torch.bfloat16)
     got_b = yg.cpu()
     assert torch.isfinite(got_b.float()).all()
     ulp = (got_b.view(torch.int16).int() - ref_b.view(torch.int16).int()).abs()
     assert (ulp == 0).float().mean().item() >= 0.995
-    assert ulp.max().item() <= 2
+    mag = D.conv3x3(x.abs().permute(0, 3, 1, 2), w.abs().permute(0, 3, 1, 2), b.double().abs()).permute(0, 2, 3, 1)
+    r = ref_b.double().abs().clamp_min(1e-30)
+    ulp_size = torch.exp2(torch.floor(torch.log2(r)) - 7)
+    assert ((got_b.double() - ref_b.double()).abs() <= 2 * ulp_size + 1e-5 * mag).all()
 
 
 def make_inputs(rng, n_views, H, W):
