@@ -82,7 +82,8 @@ MCDI_API mcdi_status mcdi_build_envmap_cdf(const float* env, int W, int H, float
  * triangle, never an out-of-bounds read).  Writes `nodes` and `tri_records`
  * (opaque layout, valid until the caller frees them); `scratch` is
  * overwritten.  Build = Morton codes -> LSD radix sort -> Karras hierarchy ->
- * bottom-up bounds.  Deterministic for a given input.
+ * bottom-up bounds -> a depth-first copy with escape links, which shadow rays
+ * traverse without a stack.  Deterministic for a given input.
  * ------------------------------------------------------------------------ */
 MCDI_API mcdi_status mcdi_bvh_sizes(int n_tris, size_t* node_bytes, size_t* tri_bytes, size_t* scratch_bytes);
 MCDI_API mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
@@ -252,11 +253,14 @@ MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int n_img, int H, int
 MCDI_API mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float* den_cs, long long n,
                                     float* c, void* stream);
 
-/* One 3x3 convolution layer of the denoiser on its own (same kernel):
- * x [n_img][H][W][cin_pad] BF16 NHWC, w [cout_pad][9][cin_pad] BF16 (tap =
- * 3 ky + kx, cross-correlation, zero padding 1), bias [cout_pad] FP32
- * (nullable), y [n_img][H][W][cout_pad] BF16 = act(conv + bias), act = ReLU
- * if relu else identity.  cin_pad, cout_pad multiples of 16, cout_pad <= 256. */
+/* One 3x3 convolution layer of the denoiser on its own (same kernels):
+ * activations are BF16 in 8-channel planes, the layout the denoiser keeps
+ * them in: channel c of pixel (x, y) of image i is element
+ * (((i * C/8 + c/8) * H + y) * W + x) * 8 + c % 8 of a C-channel tensor.
+ * x: cin_pad channels, w [cout_pad][9][cin_pad] BF16 (tap = 3 ky + kx,
+ * cross-correlation, zero padding 1), bias [cout_pad] FP32 (nullable),
+ * y: cout_pad channels = act(conv + bias), act = ReLU if relu else identity.
+ * cin_pad, cout_pad multiples of 16, cout_pad <= 256. */
 MCDI_API mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pad, const void* w,
                                        const float* bias, int cout_pad, int relu, void* y, unsigned* err,
                                        void* stream);

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) karras_kernel(const uint32_t* __restrict_
     const int g = i + s * d + min(d, 0);
     const int left = (min(i, j) == g) ? ~g : g;
     const int right = (max(i, j) == g + 1) ? ~(g + 1) : g + 1;
-    nodes[i].d = make_int4(left, right, 0, 0);
+    nodes[i].d = make_int4(left, right, min(i, j), max(i, j));  // links, leaf range [first, last]
     if (left < 0) parent_leaf[g] = i;
     else parent_int[g] = i;
     if (right < 0) parent_leaf[g + 1] = i;
@@ -346,6 +346,51 @@ __global__ void single_leaf_root_kernel(BvhNode* nodes, const float4* box_leaf) 
     nodes[0].d = make_int4(~0, ~0, 0, 0);
 }
 
+// Depth-first (pre-order) copy of the tree with escape links.  For a node
+// whose subtree holds leaves [f, l], the nodes before it in pre-order are its
+// ancestors plus the subtrees hanging to the left of its root path, which
+// hold exactly the leaves [0, f): 2 f minus one per right turn of the path.
+// Hence dfs = 2 f + (left turns on the path from the root), and the subtree
+// of 2 (l - f) + 1 nodes ends just before skip = dfs + 2 (l - f) + 1.
+__global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __restrict__ nodes,
+                                                       const int* __restrict__ parent_int,
+                                                       const int* __restrict__ parent_leaf,
+                                                       const float4* __restrict__ box_int,
+                                                       const float4* __restrict__ box_leaf, float4* gap,
+                                                       int gap_vec4, ThreadedNode* __restrict__ out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    // zero the alignment gap before this array, so that equal meshes give equal bytes
+    if (v < gap_vec4) gap[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v >= 2 * n - 1) return;
+    const bool leaf = v >= n - 1;
+    const int k = leaf ? v - (n - 1) : v;  // leaf position or internal node index
+    int f = k, l = k, link = leaf ? ~k : k, par = -1;
+    float4 lo, hi;
+    if (leaf) {
+        lo = box_leaf[2 * (size_t)k];
+        hi = box_leaf[2 * (size_t)k + 1];
+        if (n > 1) par = parent_leaf[k];
+    } else {
+        const int4 d = nodes[k].d;
+        f = d.z;
+        l = d.w;
+        lo = box_int[2 * (size_t)k];
+        hi = box_int[2 * (size_t)k + 1];
+        par = parent_int[k];
+    }
+    int lefts = 0;
+    for (int steps = 0; par >= 0 && steps < n; ++steps) {  // the path to the root is shorter than n
+        if (nodes[par].d.x == link) ++lefts;
+        link = par;
+        par = parent_int[par];
+    }
+    const int dfs = 2 * f + lefts;
+    const int skip = dfs + 2 * (l - f) + 1;
+    if (dfs < 0 || dfs >= 2 * n - 1) return;  // unreachable for a well-formed tree
+    out[dfs].lo = make_float4(lo.x, lo.y, lo.z, __int_as_float(skip));
+    out[dfs].hi = make_float4(hi.x, hi.y, hi.z, __int_as_float(leaf ? k : -1));
+}
+
 }  // namespace
 
 cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, int n, void* nodes_v, void* recs_v,
@@ -383,6 +428,12 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
         karras_kernel<<<(n - 1 + 255) / 256, 256, 0, stream>>>(keys[cur], n, nodes, parent_int, parent_leaf);
         refit_kernel<<<g256, 256, 0, stream>>>(n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
     }
+    char* nb = static_cast<char*>(nodes_v);
+    ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
+    const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
+    const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
+    threaded_kernel<<<(2 * n - 1 + 255) / 256, 256, 0, stream>>>(
+        n, nodes, parent_int, parent_leaf, box_int, box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
     return cudaGetLastError();
 }
 

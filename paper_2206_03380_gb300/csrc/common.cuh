@@ -69,6 +69,25 @@ struct __align__(16) TriRecord {
     float4 e2;
 };
 
+// Node of the same tree in depth-first (pre-order) layout with escape links,
+// 32 bytes, for stackless traversal: the first child of an internal node is
+// the next node; `skip` is the node that follows the subtree (the escape link
+// taken when the box is missed or a leaf is done).  The array follows the
+// two-child nodes in the same allocation.
+struct __align__(32) ThreadedNode {
+    float4 lo;  // xyz: box minimum, w: skip index (int bits)
+    float4 hi;  // xyz: box maximum, w: triangle-record index (int bits) of a leaf, -1 for an internal node
+};
+
+__host__ __device__ inline size_t threaded_offset(int n_tris) {
+    const size_t n_int = (size_t)(n_tris > 1 ? n_tris - 1 : 1);
+    return (n_int * sizeof(BvhNode) + 255) & ~(size_t)255;
+}
+
+__host__ __device__ inline const ThreadedNode* threaded_nodes(const void* nodes, int n_tris) {
+    return reinterpret_cast<const ThreadedNode*>(static_cast<const char*>(nodes) + threaded_offset(n_tris));
+}
+
 constexpr int kTraversalStack = 64;  // >= depth of a tree over 62-bit unique keys
 
 }  // namespace mcdi

@@ -90,44 +90,12 @@ typedef __nv_bfloat16 bf16;
 __device__ __forceinline__ int pad16_dev(int c) { return (c + 15) & ~15; }
 
 // ---------------------------------------------------------------- small kernels
-// network input: [term.rgb, k_d.rgb, normal.xyz, 0 x 7] per pixel (BF16);
-// image i uses guide planes of image i % n_aux
-__global__ void pack_input_kernel(const float4* __restrict__ term, const float4* __restrict__ kd,
-                                  const float4* __restrict__ nrm, int n_img, int n_aux, int HW, bf16* __restrict__ x) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n_img * HW) return;
-    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
-    const long long g = (long long)(img % n_aux) * HW + p;
-    const float4 t = term[i], k = kd[g], n = nrm[g];
-    const float f[16] = {t.x, t.y, t.z, k.x, k.y, k.z, n.x, n.y, n.z, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t w[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
-        w[c] = *reinterpret_cast<uint32_t*>(&h);
-    }
-    uint4* d = reinterpret_cast<uint4*>(x + i * 16);
-    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-}
-
-// upstream gradient (rgb of float4) -> 16-channel BF16 (channels 3..15 zero)
-__global__ void pack_grad_kernel(const float4* __restrict__ gy, long long n, bf16* __restrict__ g) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float4 v = gy[i];
-    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, 0.0f);
-    uint4* d = reinterpret_cast<uint4*>(g + i * 16);
-    d[0] = make_uint4(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b), 0u, 0u);
-    d[1] = make_uint4(0u, 0u, 0u, 0u);
-}
-
-// input gradient of the network (channels 0..2 = the term) -> float4
-__global__ void unpack_grad_kernel(const bf16* __restrict__ g, long long n, float4* __restrict__ gx) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const bf16* s = g + i * 16;
-    gx[i] = make_float4(__bfloat162float(s[0]), __bfloat162float(s[1]), __bfloat162float(s[2]), 0.0f);
+// Activations and gradients are BF16 in 8-channel planes: a C-channel tensor
+// at H x W is [img][C / 8][H][W][8], so a warp's 32 pixels of one group are
+// 512 contiguous bytes and a tensor-map box of one group is a run of 16-byte
+// rows.
+__device__ __forceinline__ size_t poff(int img, int G, int g, int H, int W, int y, int x) {
+    return ((((size_t)img * G + g) * H + y) * W + x) * 8;
 }
 
 __device__ __forceinline__ void ld8(const bf16* p, float* f) {
@@ -151,55 +119,89 @@ __device__ __forceinline__ void st8(bf16* p, const float* f) {
     *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// network input: [term.rgb, k_d.rgb, normal.xyz, 0 x 7] per pixel (16
+// channels, two planes); image i uses guide planes of image i % n_aux
+__global__ void pack_input_kernel(const float4* __restrict__ term, const float4* __restrict__ kd,
+                                  const float4* __restrict__ nrm, int n_img, int n_aux, int HW, bf16* __restrict__ x) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n_img * HW) return;
+    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
+    const long long g = (long long)(img % n_aux) * HW + p;
+    const float4 t = term[i], k = kd[g], n = nrm[g];
+    const float f0[8] = {t.x, t.y, t.z, k.x, k.y, k.z, n.x, n.y}, f1[8] = {n.z, 0, 0, 0, 0, 0, 0, 0};
+    st8(x + (((size_t)img * 2 + 0) * HW + p) * 8, f0);
+    st8(x + (((size_t)img * 2 + 1) * HW + p) * 8, f1);
+}
+
+// upstream gradient (rgb of float4) -> 16-channel BF16 (channels 3..15 zero)
+__global__ void pack_grad_kernel(const float4* __restrict__ gy, int n_img, int HW, bf16* __restrict__ g) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n_img * HW) return;
+    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
+    const float4 v = gy[i];
+    const float f0[8] = {v.x, v.y, v.z, 0, 0, 0, 0, 0}, f1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    st8(g + (((size_t)img * 2 + 0) * HW + p) * 8, f0);
+    st8(g + (((size_t)img * 2 + 1) * HW + p) * 8, f1);
+}
+
+// input gradient of the network (channels 0..2 = the term) -> float4
+__global__ void unpack_grad_kernel(const bf16* __restrict__ g, int n_img, int HW, float4* __restrict__ gx) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n_img * HW) return;
+    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
+    float f[8];
+    ld8(g + ((size_t)img * 2 * HW + p) * 8, f);
+    gx[i] = make_float4(f[0], f[1], f[2], 0.0f);
+}
+
+// thread index -> (img, group, y, x) with x fastest
+__device__ __forceinline__ bool split_index(long long i, int groups, int H, int W, int* img, int* g, int* y, int* x,
+                                            int n) {
+    if (i >= (long long)n * groups * H * W) return false;
+    *x = (int)(i % W);
+    i /= W;
+    *y = (int)(i % H);
+    i /= H;
+    *g = (int)(i % groups);
+    *img = (int)(i / groups);
+    return true;
+}
+
 // 2x2 max-pool of channels [coff, coff + C) of src (Ctot channels, H x W) into dst (C channels)
 __global__ void maxpool2_kernel(const bf16* __restrict__ src, int Ctot, int coff, int C, int n, int H, int W,
                                 bf16* __restrict__ dst) {
-    const int groups = C >> 3;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int Ho = H >> 1, Wo = W >> 1;
-    if (i >= (long long)n * Ho * Wo * groups) return;
-    const int g = (int)(i % groups);
-    long long q = i / groups;
-    const int xo = (int)(q % Wo);
-    q /= Wo;
-    const int yo = (int)(q % Ho);
-    const int img = (int)(q / Ho);
+    int img, g, yo, xo;
+    if (!split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Ho, Wo, &img, &g, &yo, &xo, n)) return;
     float m[8], v[8];
+    const bf16* s = src + poff(img, Ctot >> 3, (coff >> 3) + g, H, W, 2 * yo, 2 * xo);
     for (int k = 0; k < 4; ++k) {
-        const int x = 2 * xo + (k & 1), y = 2 * yo + (k >> 1);
-        ld8(src + (((size_t)img * H + y) * W + x) * Ctot + coff + 8 * g, v);
+        ld8(s + ((size_t)(k >> 1) * W + (k & 1)) * 8, v);
 #pragma unroll
         for (int c = 0; c < 8; ++c) m[c] = k == 0 ? v[c] : fmaxf(m[c], v[c]);
     }
-    st8(dst + (((size_t)img * Ho + yo) * Wo + xo) * C + 8 * g, m);
+    st8(dst + poff(img, C >> 3, g, Ho, Wo, yo, xo), m);
 }
 
 // gradient through "nearest 2x upsample then ReLU output": g_low = sum of the
-// 2x2 block of g_cat[ucoff : ucoff + C] times [activation > 0], the activation
-// read from the upsampled copy in cat (top-left of the block)
+// 2x2 block of g_cat[0 : C] times [activation > 0], the activation read from
+// the upsampled copy in cat (top-left of the block)
 __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int C, int n,
                                int Hl, int Wl, bf16* __restrict__ glow) {
-    const int groups = C >> 3;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n * Hl * Wl * groups) return;
-    const int g = (int)(i % groups);
-    long long q = i / groups;
-    const int x = (int)(q % Wl);
-    q /= Wl;
-    const int y = (int)(q % Hl);
-    const int img = (int)(q / Hl);
+    int img, g, y, x;
+    if (!split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Hl, Wl, &img, &g, &y, &x, n)) return;
     const int H2 = 2 * Hl, W2 = 2 * Wl;
+    const size_t o = poff(img, Ctot >> 3, g, H2, W2, 2 * y, 2 * x);
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, v[8], a[8];
     for (int k = 0; k < 4; ++k) {
-        const size_t p = ((size_t)img * H2 + 2 * y + (k >> 1)) * W2 + 2 * x + (k & 1);
-        ld8(gcat + p * Ctot + 8 * g, v);
+        ld8(gcat + o + ((size_t)(k >> 1) * W2 + (k & 1)) * 8, v);
 #pragma unroll
         for (int c = 0; c < 8; ++c) s[c] += v[c];
     }
-    ld8(cat + (((size_t)img * H2 + 2 * y) * W2 + 2 * x) * Ctot + 8 * g, a);
+    ld8(cat + o, a);
 #pragma unroll
     for (int c = 0; c < 8; ++c) s[c] = a[c] > 0.0f ? s[c] : 0.0f;
-    st8(glow + (((size_t)img * Hl + y) * Wl + x) * C + 8 * g, s);
+    st8(glow + poff(img, C >> 3, g, Hl, Wl, y, x), s);
 }
 
 // gradient of an encoder output E (stored in cat at channel offset ecoff) that
@@ -207,25 +209,16 @@ __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __rest
 // pool gradient routed to the window's first maximum) * [E > 0]
 __global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int ecoff,
                                 int C, const bf16* __restrict__ gpool, int n, int H, int W, bf16* __restrict__ gE) {
-    const int groups = C >> 3;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n * H * W * groups) return;
-    const int g = (int)(i % groups);
-    long long q = i / groups;
-    const int x = (int)(q % W);
-    q /= W;
-    const int y = (int)(q % H);
-    const int img = (int)(q / H);
+    int img, g, y, x;
+    if (!split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, H, W, &img, &g, &y, &x, n)) return;
     const int xo = x >> 1, yo = y >> 1, me = (x & 1) + 2 * (y & 1);
+    const int G = Ctot >> 3, ge = (ecoff >> 3) + g;
+    const size_t w0 = poff(img, G, ge, H, W, 2 * yo, 2 * xo);
     float win[4][8];
-    for (int k = 0; k < 4; ++k) {
-        const size_t p = ((size_t)img * H + 2 * yo + (k >> 1)) * W + 2 * xo + (k & 1);
-        ld8(cat + p * Ctot + ecoff + 8 * g, win[k]);
-    }
+    for (int k = 0; k < 4; ++k) ld8(cat + w0 + ((size_t)(k >> 1) * W + (k & 1)) * 8, win[k]);
     float gs[8], gp[8];
-    const size_t pix = ((size_t)img * H + y) * W + x;
-    ld8(gcat + pix * Ctot + ecoff + 8 * g, gs);
-    ld8(gpool + (((size_t)img * (H >> 1) + yo) * (W >> 1) + xo) * C + 8 * g, gp);
+    ld8(gcat + poff(img, G, ge, H, W, y, x), gs);
+    ld8(gpool + poff(img, C >> 3, g, H >> 1, W >> 1, yo, xo), gp);
     float out[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -235,7 +228,7 @@ __global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __res
         const float v = gs[c] + (arg == me ? gp[c] : 0.0f);
         out[c] = win[me][c] > 0.0f ? v : 0.0f;
     }
-    st8(gE + pix * C + 8 * g, out);
+    st8(gE + poff(img, C >> 3, g, H, W, y, x), out);
 }
 
 // fp32 [co][ci][3][3] + [co] (the plan's parameters, concatenated) -> packed
@@ -398,7 +391,7 @@ cudaError_t launch_unet_bwd(const void* weights, int n, int H, int W, const void
     auto A = [&](int k) { return reinterpret_cast<const bf16*>(a + aoff[k]); };
     auto G = [&](int k) { return reinterpret_cast<bf16*>(g + goff[k]); };
     const long long P0 = (long long)n * H * W;
-    pack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(gy), P0, G(GY));
+    pack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(gy), n, H * W, G(GY));
     CHECK(cudaGetLastError());
     auto up_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int C, int low_level, bf16* glow) {
         const int Hl = H >> low_level, Wl = W >> low_level;
@@ -450,7 +443,7 @@ cudaError_t launch_unet_bwd(const void* weights, int n, int H, int W, const void
                    0, s, why));
     CHECK(run_conv(u, 0, G(GA1), 32, wf_of(u, 0), nullptr, 16, 16, kDgradPlain, 0, G(GX0), 16, 0, nullptr, nullptr, 0,
                    0, s, why));
-    unpack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(G(GX0), P0, reinterpret_cast<float4*>(gx_term));
+    unpack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(G(GX0), n, H * W, reinterpret_cast<float4*>(gx_term));
     return cudaGetLastError();
 }
 

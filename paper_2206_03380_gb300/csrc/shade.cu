@@ -231,7 +231,19 @@ __global__ void __launch_bounds__(kShadeThreads) shade_bwd_kernel(ShadeArgs a, c
             gn = gn + h * g_nh;
         }
         gn = gn + wi * g_ci;
-        atomicAdd(g_env + t, make_float4(ge.x, ge.y, ge.z, 0.f));
+        // Warp-aggregated scatter: lanes whose samples landed on the same texel
+        // (light samples crowd onto the bright lobes) sum their contributions
+        // in lane order and the lowest lane issues one atomic for the group.
+        const unsigned peers = __match_any_sync(__activemask(), t);
+        if (__popc(peers) > 1) {
+            f3 sum = mk(0.f, 0.f, 0.f);
+            for (unsigned rest = peers; rest; rest &= rest - 1u) {
+                const int q = __ffs(rest) - 1;
+                sum = sum + mk(__shfl_sync(peers, ge.x, q), __shfl_sync(peers, ge.y, q), __shfl_sync(peers, ge.z, q));
+            }
+            ge = sum;
+        }
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(g_env + t, make_float4(ge.x, ge.y, ge.z, 0.f));
     }
     gn = gn + px.wo * g_co;
     const float ng = dot(px.n, gn);

@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kGenThreads = 128;
 constexpr int kTraceThreads = 128;
-constexpr int kTraceStepsPerRefill = 16;
+constexpr int kTraceStepsPerRefill = 32;
 
 struct WaveBuffers {
     float4* ray_o;      // [rays] origin, w = slot index (int bits) of the sample
@@ -135,10 +135,12 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
     }
 }
 
-// Persistent any-hit tracer with per-lane refill.  A lane holds one ray with
-// its own traversal state; every kTraceStepsPerRefill node visits the warp
-// refills the lanes that are idle from the global slot counter.
-__global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode* __restrict__ nodes,
+// Persistent any-hit tracer with per-lane refill.  A lane holds one ray and
+// its position in the depth-first node array (stackless traversal along
+// escape links: the whole traversal state is one index); every
+// kTraceStepsPerRefill node visits the warp refills the lanes that are idle
+// from the global slot counter.
+__global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const void* __restrict__ nodes,
                                                                    const TriRecord* __restrict__ tris, int n_tris,
                                                                    void* ws, long long slots) {
     WaveBuffers B = wave_buffers(ws, slots);
@@ -149,9 +151,10 @@ __global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode
     long long ray = -1;  // -1 idle, -2 no work left, >= 0 tracing
     int slot = 0;
     RayInv r;
-    int node = 0, sp = 0, iters = 0;
-    int stack[kTraversalStack];
+    int node = 0;
     if (n_tris <= 0) return;  // nothing can block a ray; gen already wrote misses
+    const ThreadedNode* tn = threaded_nodes(nodes, n_tris);
+    const int end = 2 * n_tris - 1;
     while (true) {
         const unsigned need = __ballot_sync(full, ray == -1);
         if (need) {
@@ -169,49 +172,18 @@ __global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const BvhNode
                     r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
                     slot = __float_as_int(o.w);
                     node = 0;
-                    sp = 0;
-                    iters = 0;
                     ray = my;
                 }
             }
         }
         if (__all_sync(full, ray == -2)) break;
         if (ray < 0) continue;
-        // up to kTraceStepsPerRefill node visits of this lane's ray
+        // up to kTraceStepsPerRefill node visits of this lane's ray; the node
+        // index strictly increases, so a ray ends within 2 n - 1 visits
         for (int step = 0; step < kTraceStepsPerRefill; ++step) {
-            const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
-            const int4 d = __ldg(&nodes[node].d);
-            const float t0 = slab(r, a, make_float2(c.x, c.y), FLT_MAX);
-            const float t1 = slab(r, b, make_float2(c.z, c.w), FLT_MAX);
-            bool h0 = t0 < FLT_MAX, h1 = t1 < FLT_MAX;
-            int result = -1;  // -1 continue, 0 miss, 1 hit
-            if (h0 && d.x < 0) {
-                if (tri_hit(r, tris, ~d.x, nullptr, nullptr) < FLT_MAX) result = 1;
-                h0 = false;
-            }
-            if (result < 0 && h1 && d.y < 0) {
-                if (tri_hit(r, tris, ~d.y, nullptr, nullptr) < FLT_MAX) result = 1;
-                h1 = false;
-            }
-            if (result < 0) {
-                if (h0 && h1) {  // nearer child first: nearby occluders end the ray sooner
-                    const bool first0 = t0 <= t1;
-                    if (sp < kTraversalStack) stack[sp++] = first0 ? d.y : d.x;
-                    node = first0 ? d.x : d.y;
-                } else if (h0) {
-                    node = d.x;
-                } else if (h1) {
-                    node = d.y;
-                } else if (sp == 0) {
-                    result = 0;
-                } else {
-                    node = stack[--sp];
-                }
-                // a tree over n leaves has n - 1 internal nodes, each visited at most once
-                if (result < 0 && ++iters > n_tris) result = 0;
-            }
-            if (result >= 0) {
-                if (result) B.hit[slot] = 1;
+            node = threaded_step(tn, tris, r, node);
+            if (node < 0 || node >= end) {
+                if (node < 0) B.hit[slot] = 1;
                 ray = -1;
                 break;
             }
@@ -267,9 +239,8 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
     if (per_sm < 1) per_sm = 1;
-    wave_trace_kernel<<<sms * per_sm, kTraceThreads, 0, stream>>>(static_cast<const BvhNode*>(a.nodes),
-                                                                  static_cast<const TriRecord*>(a.tris), a.n_tris, ws,
-                                                                  P * spp);
+    wave_trace_kernel<<<sms * per_sm, kTraceThreads, 0, stream>>>(a.nodes, static_cast<const TriRecord*>(a.tris),
+                                                                  a.n_tris, ws, P * spp);
     wave_accum_kernel<<<gblocks, kGenThreads, 0, stream>>>(a, ws, c_d, c_s, vis_mask);
     return cudaGetLastError();
 }

@@ -60,38 +60,41 @@ __device__ __forceinline__ float tri_hit(const RayInv& r, const TriRecord* __res
     return t;
 }
 
-// any hit with t > 0 (shadow ray, no far limit)
-__device__ __forceinline__ bool any_hit(const BvhNode* __restrict__ nodes, const TriRecord* __restrict__ tris,
-                                        int n_tris, const RayInv& r) {
+// slab test of a box given by its corners (xyz of lo and hi); same rounding
+// rule as slab()
+__device__ __forceinline__ bool slab_hit(const RayInv& r, float4 lo, float4 hi) {
+    const float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
+    const float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
+    const float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+    const float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1)) * 1.00000036f;
+    return t0 <= t1;
+}
+
+// One step of stackless any-hit traversal at node i of the depth-first
+// layout: returns the next node index (> i), or -1 when the ray is blocked.
+__device__ __forceinline__ int threaded_step(const ThreadedNode* __restrict__ tn, const TriRecord* __restrict__ tris,
+                                             const RayInv& r, int i) {
+    const float4 lo = __ldg(&tn[i].lo), hi = __ldg(&tn[i].hi);
+    const int skip = __float_as_int(lo.w), tri = __float_as_int(hi.w);
+    int next = skip;
+    if (slab_hit(r, lo, hi)) {
+        if (tri < 0) next = i + 1;
+        else if (tri_hit(r, tris, tri, nullptr, nullptr) < FLT_MAX) return -1;
+    }
+    return next > i ? next : i + 1;  // strictly increasing: at most 2 n - 1 steps
+}
+
+// any hit with t > 0 (shadow ray, no far limit): stackless traversal of the
+// depth-first layout, no ordering needed since any blocker ends the ray
+__device__ __forceinline__ bool any_hit(const void* nodes, const TriRecord* __restrict__ tris, int n_tris,
+                                        const RayInv& r) {
     if (n_tris <= 0) return false;
-    int stack[kTraversalStack];
-    int sp = 0;
-    int node = 0;
-    // a tree over n leaves has n - 1 internal nodes: each is visited at most once
-    for (int iter = 0; iter < n_tris + 1; ++iter) {
-        const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
-        const int4 d = __ldg(&nodes[node].d);
-        bool h0 = slab(r, a, make_float2(c.x, c.y), FLT_MAX) < FLT_MAX;
-        bool h1 = slab(r, b, make_float2(c.z, c.w), FLT_MAX) < FLT_MAX;
-        if (h0 && d.x < 0) {
-            if (tri_hit(r, tris, ~d.x, nullptr, nullptr) < FLT_MAX) return true;
-            h0 = false;
-        }
-        if (h1 && d.y < 0) {
-            if (tri_hit(r, tris, ~d.y, nullptr, nullptr) < FLT_MAX) return true;
-            h1 = false;
-        }
-        if (h0 && h1) {
-            if (sp < kTraversalStack) stack[sp++] = d.y;
-            node = d.x;
-        } else if (h0) {
-            node = d.x;
-        } else if (h1) {
-            node = d.y;
-        } else {
-            if (sp == 0) return false;
-            node = stack[--sp];
-        }
+    const ThreadedNode* tn = threaded_nodes(nodes, n_tris);
+    const int end = 2 * n_tris - 1;
+    for (int i = 0; i < end;) {
+        i = threaded_step(tn, tris, r, i);
+        if (i < 0) return true;
     }
     return false;
 }

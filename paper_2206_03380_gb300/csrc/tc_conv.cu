@@ -6,8 +6,11 @@
 //   A[128 pixels x 16 ch] (the input shifted by the tap, zero outside the
 //   image: TMA out-of-bounds fill) x B[cout_pad x 16 ch]^T (weights).
 // Every chunk is one tcgen05.mma (M = 128, N = cout_pad, K = 16, BF16 inputs,
-// FP32 accumulation).  Operands are staged by TMA into 32-byte-swizzled shared
-// memory through a ring of kStages buffers guarded by mbarriers:
+// FP32 accumulation).  Operands are staged by TMA through a ring of kStages
+// shared-memory buffers guarded by mbarriers: the A tile as two 8-channel
+// planes of 16-byte rows (no swizzle; activations live in 8-channel planes in
+// global memory, so each plane's box is a run of contiguous rows), the weight
+// slice with the 32-byte swizzle:
 //   warp 0 lane 0  issues the TMA loads      (waits "empty", arms "full"),
 //   warp 1 lane 0  issues the MMAs           (waits "full", commits to "empty"),
 //   all 4 warps    run the epilogue: tcgen05.ld of their 32 TMEM lanes, bias,
@@ -100,10 +103,33 @@ __device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
     return d;
 }
 
+// K-major operand without swizzle: core matrices of 8 rows x 16 bytes with
+// rows 16 bytes apart, 8-row groups 128 bytes apart (stride byte offset) and
+// the second 8-channel half of K one plane further (leading byte offset).
+__device__ __forceinline__ uint64_t noswz_desc(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(128u >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; swizzle mode 0 (none)
+    return d;
+}
+
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
 __host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
     asm volatile(
@@ -115,28 +141,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void store16_bf16(__nv_bfloat16* dst, const float* f) {
-    uint32_t w[8];
+__device__ __forceinline__ void store8_bf16(__nv_bfloat16* dst, const float* f) {
+    uint32_t w[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 4; ++i) {
         __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
         w[i] = *reinterpret_cast<uint32_t*>(&h);
     }
-    uint4* d = reinterpret_cast<uint4*>(dst);
-    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// bias / activation / mask and store of 16 output channels of one pixel
+// Element offset of pixel (x, y) of image img in 8-channel group g of a
+// tensor with G groups at H x W (layout [img][g][y][x][8]).
+__device__ __forceinline__ size_t plane_off(int img, int G, int g, int H, int W, int y, int x) {
+    return ((((size_t)img * G + g) * H + y) * W + x) * 8;
+}
+
+// bias / activation / mask and store of 16 output channels (two 8-channel
+// groups) of one pixel
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
-                                           size_t pix) {
+                                           const float* bias16) {
     float f[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+    const size_t hw = (size_t)p.H * p.W;
     if (p.mode == kDgradMask || p.mode == kDgradPlain) {
         if (p.mode == kDgradMask) {
-            const uint4* mk4 = reinterpret_cast<const uint4*>(p.mask + pix * p.mask_ctotal + p.mask_coff + c0);
-            const uint4 m0 = mk4[0], m1 = mk4[1];
+            const __nv_bfloat16* mk =
+                p.mask + plane_off(img, p.mask_ctotal >> 3, (p.mask_coff + c0) >> 3, p.H, p.W, y, x);
+            const uint4 m0 = *reinterpret_cast<const uint4*>(mk), m1 = *reinterpret_cast<const uint4*>(mk + hw * 8);
             const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -145,27 +178,34 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
                 if (!(__bfloat162float(h.y) > 0.0f)) f[2 * i + 1] = 0.0f;
             }
         }
-        store16_bf16(p.out + pix * p.out_ctotal + p.out_coff + c0, f);
+        __nv_bfloat16* o = p.out + plane_off(img, p.out_ctotal >> 3, (p.out_coff + c0) >> 3, p.H, p.W, y, x);
+        store8_bf16(o, f);
+        store8_bf16(o + hw * 8, f + 8);
         return;
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        f[i] += p.bias ? __ldg(p.bias + c0 + i) : 0.0f;
+        f[i] += bias16 ? bias16[i] : 0.0f;
         if (p.relu) f[i] = fmaxf(f[i], 0.0f);
     }
     if (p.mode == kStoreF32) {
-        p.out_f32[pix] = make_float4(f[0], f[1], f[2], 0.0f);
+        p.out_f32[((size_t)img * p.H + y) * p.W + x] = make_float4(f[0], f[1], f[2], 0.0f);
     } else if (p.mode == kStoreUp2) {
         const int W2 = 2 * p.W, H2 = 2 * p.H;
+        __nv_bfloat16* o = p.out + plane_off(img, p.out_ctotal >> 3, (p.out_coff + c0) >> 3, H2, W2, 2 * y, 2 * x);
+        const size_t hw2 = (size_t)H2 * W2 * 8;
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const size_t q = ((size_t)img * H2 + 2 * y + j) * W2 + 2 * x + i;
-                store16_bf16(p.out + q * p.out_ctotal + p.out_coff + c0, f);
+                __nv_bfloat16* q = o + ((size_t)j * W2 + i) * 8;
+                store8_bf16(q, f);
+                store8_bf16(q + hw2, f + 8);
             }
     } else {
-        store16_bf16(p.out + pix * p.out_ctotal + p.out_coff + c0, f);
+        __nv_bfloat16* o = p.out + plane_off(img, p.out_ctotal >> 3, (p.out_coff + c0) >> 3, p.H, p.W, y, x);
+        store8_bf16(o, f);
+        store8_bf16(o + hw * 8, f + 8);
     }
 }
 
@@ -229,7 +269,9 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
             mbar_expect_tx(fb, a_bytes + b_bytes);
             const int tap = k / cpt, cc = k - tap * cpt;
             const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-            tma_load_4d(a_dst, &tmap_x, cc * 16, x0 + dx - 1, y0 + dy - 1, img, fb);
+            const int plane = img * (p.cin_pad >> 3) + 2 * cc;
+            tma_load_4d(a_dst, &tmap_x, 0, x0 + dx - 1, y0 + dy - 1, plane, fb);
+            tma_load_4d(a_dst + a_bytes / 2, &tmap_x, 0, x0 + dx - 1, y0 + dy - 1, plane + 1, fb);
             tma_load_2d(a_dst + a_bytes, &tmap_w, tap * p.cin_pad + cc * 16, 0, fb);
             issued = k + 1;
         }
@@ -246,7 +288,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
             }
             tc_fence_after();
             const uint32_t a_src = base + (uint32_t)s * stage_bytes;
-            const uint64_t adesc = sw32_desc(a_src), bdesc = sw32_desc(a_src + a_bytes);
+            const uint64_t adesc = noswz_desc(a_src, a_bytes / 2), bdesc = sw32_desc(a_src + a_bytes);
             const uint32_t accum = k > 0 ? 1u : 0u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -273,12 +315,11 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
     const int xx = m % p.tw, yy = m / p.tw;
     const int x = x0 + xx, y = y0 + yy;
     const bool valid = acc_ok && x < p.W && y < p.H;
-    const size_t pix = ((size_t)img * p.H + y) * p.W + x;
     for (int c0 = 0; c0 < p.cout_pad; c0 += 16) {
         uint32_t v[16];
         // collective load of 16 accumulator columns of this warp's 32 lanes
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, pix);
+        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr);
         __syncwarp();
     }
 
@@ -306,14 +347,17 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
 // Row-tile form, for images at least 65 pixels wide (128-pixel row tiles).
 // A persistent CTA keeps a slice of Nc output channels of the layer's weights
 // resident in shared memory for its whole life ([chunk][tap][Nc][16 ch],
-// 32-byte swizzle, loaded once) and loops over tiles of R output rows x 128
-// pixels.  Per 16-channel input chunk, TMA brings the tile's halo once: R + 2
-// rows x 130 pixels, as two planes of 8 channels with 16-byte rows and no
-// swizzle.  With 16-byte rows any row starts a valid 8-row core matrix, so the
-// A operand of output row r and tap (dy, dx) is the window starting at halo
-// row (r + dy) * 130 + dx: 9 R MMAs (M = 128, N = Nc, K = 16) per chunk read
-// (R + 2) / R input rows per output row instead of 9.
-//   warp 0 lane 0   TMA producer (weights once, then halo chunks),
+// 32-byte swizzle, one TMA load per chunk) and loops over tiles of R output
+// rows x 128 pixels.  Per 16-channel input chunk the tile's halo, R + 2 rows x
+// 130 pixels of two 8-channel planes, arrives once: each halo row is one
+// contiguous run in the planar activation layout, copied with one bulk copy
+// (large requests instead of one per 16-byte pixel), the part outside the
+// image zero-filled.  Rows are 16 bytes per pixel and unswizzled, so any row
+// starts a valid 8-row core matrix: the A operand of output row r and tap
+// (dy, dx) is the window starting at halo row (r + dy) * 130 + dx, and 9 R
+// MMAs (M = 128, N = Nc, K = 16) per chunk read (R + 2) / R input rows per
+// output row instead of 9.
+//   warp 0          weight TMA (lane 0), halo row copies (one lane per row),
 //   warp 1 lane 0   MMA issuer; accumulators of tile i in TMEM buffer i & 1,
 //   warps 2..5      epilogue (TMEM lane quarter = warp % 4).
 constexpr int kRowThreads = 192;
@@ -325,22 +369,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// K-major operand without swizzle: core matrices of 8 rows x 16 bytes with
-// rows 16 bytes apart, 8-row groups 128 bytes apart (stride byte offset) and
-// the second 8-channel half of K one plane further (leading byte offset).
-__device__ __forceinline__ uint64_t noswz_desc(uint32_t saddr, uint32_t lbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)(128u >> 4) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version; swizzle mode 0 (none)
-    return d;
-}
-
-__global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_xh,
-                                                                   const __grid_constant__ CUtensorMap tmap_wh,
+template <int R>
+__global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
     extern __shared__ uint8_t smem_raw[];
+    __shared__ float s_bias[256];
     __shared__ __align__(8) uint64_t full_bar[kRowMaxStages], empty_bar[kRowMaxStages], accf_bar[2], acce_bar[2],
         w_bar;
     __shared__ uint32_t tmem_slot;
@@ -349,7 +382,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t wbase = base + (uint32_t)rp.stages * rp.stage_bytes;
-    const int S = rp.stages, R = rp.rows, Nc = rp.nc;
+    const int S = rp.stages, Nc = rp.nc;
     const int n_chunks = p.cin_pad >> 4;
     const uint32_t w_chunk = 9u * (uint32_t)Nc * 32u;  // bytes of one chunk's weights, all taps
     const int slice = blockIdx.x % rp.n_slices;
@@ -370,6 +403,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
         failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int c = threadIdx.x; c < Nc; c += blockDim.x) s_bias[c] = p.bias ? p.bias[n0 + c] : 0.0f;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(rp.tmem_cols)
@@ -392,28 +426,70 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
     int issued = 0;
     bool w_issued = false;
     if (warp == 0) {
-        if (lane == 0 && has_work) {
-            const uint32_t wb = smem_u32(&w_bar);
-            mbar_expect_tx(wb, (uint32_t)n_chunks * w_chunk);
-            for (int c = 0; c < n_chunks; ++c) tma_load_4d(wbase + (uint32_t)c * w_chunk, &tmap_wh, 0, n0, 0, c, wb);
-            w_issued = true;
+        if (has_work) {
+            if (lane == 0) {
+                const uint32_t wb = smem_u32(&w_bar);
+                mbar_expect_tx(wb, (uint32_t)n_chunks * w_chunk);
+                for (int c = 0; c < n_chunks; ++c)
+                    tma_load_4d(wbase + (uint32_t)c * w_chunk, &tmap_wh, 0, n0, 0, c, wb);
+                w_issued = true;
+            }
+            // Halo rows by plain bulk copies: lane l < 2 (R + 2) owns row l % (R + 2)
+            // of plane l / (R + 2); the part of the row outside the image is
+            // zero-filled with shared-memory stores made visible to the async
+            // proxy before the stage's barrier is armed.
+            const int rows = R + 2;
+            const bool mine = lane < 2 * rows;
+            const int q = lane / rows, hr = lane - q * rows;
+            const size_t plane_elems = (size_t)p.H * p.W * 8;
             int g = 0;
-            for (int t = first; t < rp.n_tiles && !failed; t += step) {
+            for (int t = first; t < rp.n_tiles; t += step) {
                 int img, x0, y0;
                 tile_origin(t, &img, &x0, &y0);
-                for (int c = 0; c < n_chunks; ++c, ++g) {
+                const int y = y0 - 1 + hr;
+                const int xa = x0 - 1 < 0 ? 0 : x0 - 1, xb = x0 + 129 > p.W ? p.W : x0 + 129;
+                const bool row_in = mine && y >= 0 && y < p.H && xb > xa;
+                const uint32_t n_bytes = row_in ? (uint32_t)(xb - xa) * 16u : 0u;
+                const int lead = row_in ? xa - (x0 - 1) : kHaloW;  // zero pixels [0, lead)
+                const int tail = row_in ? xb - (x0 - 1) : kHaloW;  // zero pixels [tail, 130)
+                const uint32_t total = __reduce_add_sync(0xffffffffu, n_bytes);
+                int c = 0;
+                for (; c < n_chunks; ++c, ++g) {
                     const int s = g % S;
-                    if (!mbar_wait(smem_u32(&empty_bar[s]), ((uint32_t)(g / S) & 1u) ^ 1u)) {
-                        failed = 1;
+                    int ok = 1;
+                    if (lane == 0) ok = mbar_wait(smem_u32(&empty_bar[s]), ((uint32_t)(g / S) & 1u) ^ 1u) ? 1 : 0;
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) {
+                        if (lane == 0) failed = 1;
                         break;
                     }
-                    const uint32_t st = base + (uint32_t)s * rp.stage_bytes;
+                    const uint32_t row_smem = base + (uint32_t)s * rp.stage_bytes + (uint32_t)q * rp.plane_bytes +
+                                              (uint32_t)hr * (uint32_t)kHaloW * 16u;
+                    if (mine) {
+                        for (int x = 0; x < lead; ++x)
+                            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(row_smem + 16u * x), "r"(0)
+                                         : "memory");
+                        for (int x = tail; x < kHaloW; ++x)
+                            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(row_smem + 16u * x), "r"(0)
+                                         : "memory");
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
                     const uint32_t fb = smem_u32(&full_bar[s]);
-                    mbar_expect_tx(fb, 2u * rp.plane_load);
-                    tma_load_4d(st, &tmap_xh, c * 16, x0 - 1, y0 - 1, img, fb);
-                    tma_load_4d(st + rp.plane_bytes, &tmap_xh, c * 16 + 8, x0 - 1, y0 - 1, img, fb);
+                    if (lane == 0) mbar_expect_tx(fb, total);
+                    __syncwarp();
+                    if (n_bytes > 0) {
+                        const __nv_bfloat16* src =
+                            p.x + (size_t)(img * (p.cin_pad >> 3) + 2 * c + q) * plane_elems + ((size_t)y * p.W + xa) * 8;
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                row_smem + 16u * (uint32_t)lead),
+                            "l"(src), "r"(n_bytes), "r"(fb)
+                            : "memory");
+                    }
                     issued = g + 1;
                 }
+                if (c < n_chunks || failed) break;
             }
         }
         __syncwarp();
@@ -439,22 +515,25 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = base + (uint32_t)s * rp.stage_bytes;
-                    const uint32_t wc = wbase + (uint32_t)c * w_chunk;
-#pragma unroll 1
+                    // descriptors of the stage's halo and the chunk's weights; each MMA adds a
+                    // compile-time offset (in 16-byte units) to the start-address field, which
+                    // stays below 2^14 for any shared-memory address
+                    const uint64_t a0 = noswz_desc(base + (uint32_t)s * rp.stage_bytes, rp.plane_bytes);
+                    const uint64_t b0 = sw32_desc(wbase + (uint32_t)c * w_chunk);
+                    const uint64_t b_step = (uint64_t)((uint32_t)Nc * 2u);  // Nc x 32 bytes per tap, in 16-byte units
+                    const uint32_t acc0 = c > 0 ? 1u : 0u;
+#pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-                        const uint64_t bdesc = sw32_desc(wc + (uint32_t)tap * (uint32_t)Nc * 32u);
-                        const uint32_t accum = (c > 0 || tap > 0) ? 1u : 0u;
-#pragma unroll 1
+                        const int dy = tap / 3, dx = tap % 3;
+                        const uint64_t bdesc = b0 + (uint64_t)tap * b_step;
+#pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            const uint64_t adesc =
-                                noswz_desc(st + (uint32_t)((r + dy) * kHaloW + dx) * 16u, rp.plane_bytes);
+                            const uint64_t adesc = a0 + (uint64_t)(((r + dy) * kHaloW + dx));
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
                                     d0 + (uint32_t)r * rp.acc_stride),
-                                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+                                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(tap > 0 ? 1u : acc0)
                                 : "memory");
                         }
                     }
@@ -485,15 +564,21 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
             int img, x0, y0;
             tile_origin(t, &img, &x0, &y0);
             const int x = x0 + m;
+#pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int y = y0 + r;
                 const bool valid = x < p.W && y < p.H;
-                const size_t pix = ((size_t)img * p.H + y) * p.W + x;
                 const uint32_t tr = tmem + (uint32_t)(b * R + r) * rp.acc_stride + ((uint32_t)(q * 32) << 16);
-                for (int c0 = 0; c0 < Nc; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(tr + (uint32_t)c0, v);
-                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, pix);
+                // two 16-column loads in flight per wait
+                for (int c0 = 0; c0 < Nc; c0 += 32) {
+                    uint32_t v[32];
+                    const bool two = c0 + 16 < Nc;
+                    tmem_ld16_async(tr + (uint32_t)c0, v);
+                    if (two) tmem_ld16_async(tr + (uint32_t)c0 + 16u, v + 16);
+                    tmem_wait_ld();
+                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0);
+                    if (two && valid && n0 + c0 + 16 < p.cout_valid)
+                        epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16);
                     __syncwarp();
                 }
             }
@@ -538,23 +623,28 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn(const char** why) {
 
 struct DeviceLimits {
     int sms = 0;
-    uint32_t rows_smem_max = 0;  // dynamic shared memory the row-tile kernel may request
+    uint32_t rows_smem_max = 0;  // dynamic shared memory one row-tile CTA may request
+    uint32_t rows_smem_two = 0;  // dynamic shared memory per CTA with two CTAs on an SM
 };
 
 const DeviceLimits& device_limits() {
     static std::once_flag once;
     static DeviceLimits L;
     std::call_once(once, [] {
-        int dev = 0, optin = 0;
+        int dev = 0, optin = 0, per_sm = 0, reserved = 0;
         cudaFuncAttributes fa{};
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel) != cudaSuccess || optin <= (int)fa.sharedSizeBytes) {
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4>) != cudaSuccess || optin <= (int)fa.sharedSizeBytes) {
             L.sms = 0;
             return;
         }
         L.rows_smem_max = (uint32_t)(optin - (int)fa.sharedSizeBytes);
+        const int two = per_sm / 2 - (int)fa.sharedSizeBytes - reserved;
+        L.rows_smem_two = two > 0 ? (uint32_t)two : 0u;
     });
     return L;
 }
@@ -588,16 +678,15 @@ bool plan_rows(const ConvParams& p, RowPlan* out) {
             rp.rows = R;
             rp.nc = nc;
             rp.n_slices = n_slices;
-            rp.plane_load = (uint32_t)(R + 2) * kHaloW * 16u;
-            rp.plane_bytes = (rp.plane_load + 127u) & ~127u;
+            rp.plane_bytes = ((uint32_t)(R + 2) * kHaloW * 16u + 127u) & ~127u;
             rp.stage_bytes = (2u * rp.plane_bytes + 1023u) & ~1023u;
             rp.acc_stride = acc_stride;
             rp.tmem_cols = tmem_cols;
             if (w_bytes + 2u * rp.stage_bytes + kAlign > kSmemMax) continue;
             rp.n_tiles = p.n_img * ((p.H + R - 1) / R) * p.tiles_x;
             if (R > 1 && 2 * n_slices * rp.n_tiles < 3 * sms) continue;
-            const bool two = w_bytes + 3u * rp.stage_bytes + kAlign <= kSmemMax / 2 - 1024u && 2u * tmem_cols <= 512u;
-            const uint32_t budget = two ? kSmemMax / 2 - 1024u : kSmemMax;
+            const bool two = w_bytes + 3u * rp.stage_bytes + kAlign <= lim.rows_smem_two && 2u * tmem_cols <= 512u;
+            const uint32_t budget = two ? lim.rows_smem_two : kSmemMax;
             int S = (int)((budget - kAlign - w_bytes) / rp.stage_bytes);
             rp.stages = S > kRowMaxStages ? kRowMaxStages : S;
             rp.smem_bytes = (uint32_t)rp.stages * rp.stage_bytes + w_bytes + kAlign;
@@ -627,13 +716,13 @@ bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w,
     auto enc = encode_fn(why);
     if (!enc) return false;
     const ConvParams& p = d->p;
-    const cuuint64_t xdims[4] = {(cuuint64_t)p.cin_pad, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.n_img};
-    const cuuint64_t xstr[3] = {(cuuint64_t)p.cin_pad * 2, (cuuint64_t)p.W * p.cin_pad * 2,
-                                (cuuint64_t)p.H * p.W * p.cin_pad * 2};
-    const cuuint32_t xbox[4] = {16, (cuuint32_t)p.tw, (cuuint32_t)p.th, 1};
+    // activations: 8-channel planes [img * cin_pad / 8 + g][H][W][8]
+    const cuuint64_t xdims[4] = {8, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.n_img * (p.cin_pad / 8)};
+    const cuuint64_t xstr[3] = {16, (cuuint64_t)p.W * 16, (cuuint64_t)p.H * p.W * 16};
+    const cuuint32_t xbox[4] = {8, (cuuint32_t)p.tw, (cuuint32_t)p.th, 1};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
     CUresult r = enc(&d->tmap_x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(x), xdims, xstr,
-                     xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                     xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *why = "activation tensor map rejected by the driver";
@@ -649,18 +738,11 @@ bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w,
         *why = "weight tensor map rejected by the driver";
         return false;
     }
+    d->p.x = x;
     d->rows_form = plan_rows(d->p, &d->rp);
     if (d->rows_form) {
         const RowPlan& rp = d->rp;
         d->p.tiles_y = (p.H + rp.rows - 1) / rp.rows;
-        const cuuint32_t hbox[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)(rp.rows + 2), 1};
-        r = enc(&d->tmap_xh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(x), xdims, xstr, hbox,
-                ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            *why = "halo activation tensor map rejected by the driver";
-            return false;
-        }
         // The same K-major weights [cout][tap][cin] viewed as (16 channels,
         // cout, tap, chunk): one box lands in shared memory as [tap][nc][16].
         const cuuint64_t hdims[4] = {16, (cuuint64_t)p.cout_pad, 9, (cuuint64_t)(p.cin_pad / 16)};
@@ -683,13 +765,20 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)conv_smem_bytes(256));
-        if (attr_err == cudaSuccess && device_limits().rows_smem_max > 0)
-            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)device_limits().rows_smem_max);
+        const int lim = (int)device_limits().rows_smem_max;
+        if (attr_err == cudaSuccess && lim > 0)
+            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (attr_err == cudaSuccess && lim > 0)
+            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (attr_err == cudaSuccess && lim > 0)
+            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (d.rows_form) {
-        conv_tc_rows_kernel<<<d.rp.grid, kRowThreads, d.rp.smem_bytes, stream>>>(d.tmap_xh, d.tmap_wh, d.p, d.rp);
+        const dim3 g(d.rp.grid), t(kRowThreads);
+        if (d.rp.rows == 4) conv_tc_rows_kernel<4><<<g, t, d.rp.smem_bytes, stream>>>(d.tmap_wh, d.p, d.rp);
+        else if (d.rp.rows == 2) conv_tc_rows_kernel<2><<<g, t, d.rp.smem_bytes, stream>>>(d.tmap_wh, d.p, d.rp);
+        else conv_tc_rows_kernel<1><<<g, t, d.rp.smem_bytes, stream>>>(d.tmap_wh, d.p, d.rp);
         return cudaGetLastError();
     }
     const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;

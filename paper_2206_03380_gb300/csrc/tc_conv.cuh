@@ -1,6 +1,7 @@
 // 3x3 convolution as an implicit GEMM on the 5th-generation tensor cores
 // (tcgen05, sm_103a): the denoiser's building block (Sec. 4.2 neural denoiser,
-// App. B).  Activations are NHWC BF16 with channels padded to multiples of 16.
+// App. B).  Activations are BF16 in 8-channel planes, [img][C / 8][H][W][8],
+// with C padded to a multiple of 16.
 #pragma once
 
 #include <cuda.h>
@@ -27,11 +28,12 @@ struct ConvParams {
     int cout_valid;            // channels written
     int mode;
     int relu;
+    const __nv_bfloat16* x;    // input activations (the row-tile form copies halo rows directly)
     const float* bias;         // [cout_pad] or null
-    __nv_bfloat16* out;        // NHWC
+    __nv_bfloat16* out;        // 8-channel planes, out_ctotal channels
     int out_ctotal, out_coff;
     float4* out_f32;           // [n_img][H][W] (kStoreF32)
-    const __nv_bfloat16* mask; // NHWC, same spatial size as the output
+    const __nv_bfloat16* mask; // 8-channel planes, same spatial size as the output
     int mask_ctotal, mask_coff;
     unsigned* err;             // device error word (set on a wait timeout)
 };
@@ -45,8 +47,7 @@ struct RowPlan {
     int stages;              // halo ring depth
     int n_tiles;             // tiles per channel slice
     int grid;                // CTAs (a multiple of n_slices)
-    uint32_t plane_load;     // bytes one 8-channel halo plane load writes: (R + 2) * 130 * 16
-    uint32_t plane_bytes;    // plane stride in shared memory (128-byte aligned)
+    uint32_t plane_bytes;    // halo plane stride in shared memory: (R + 2) rows x 130 pixels x 16 bytes, 128-aligned
     uint32_t stage_bytes;    // two planes, 1024-byte aligned
     uint32_t acc_stride;     // TMEM columns between the accumulators of two rows
     uint32_t tmem_cols;      // TMEM columns allocated (two buffers of R accumulators)
@@ -57,14 +58,13 @@ struct RowPlan {
 struct ConvDesc {
     CUtensorMap tmap_x;
     CUtensorMap tmap_w;
-    CUtensorMap tmap_xh;  // row-tile form: 8-channel halo planes of R + 2 rows x 130 pixels, no swizzle
     CUtensorMap tmap_wh;  // row-tile form: one 16-channel chunk of all 9 taps' weights, [tap][nc][16]
     bool rows_form;
     RowPlan rp;
     ConvParams p;
 };
 
-// Encodes the tensor maps of an NHWC BF16 input (n_img, H, W, cin_pad) and a
+// Encodes the tensor maps of a BF16 input (n_img, H, W, cin_pad; 8-channel planes) and a
 // K-major BF16 weight matrix [cout_pad][9 * cin_pad]; for 128-pixel-wide row
 // tiles whose weights fit in shared memory it also plans the row-tile form and
 // encodes its maps.  Returns false (with a message) when the driver rejects a

@@ -211,7 +211,9 @@ def composite(kd_out, den_cd, den_cs, c, stream=None):
 
 
 def conv3x3_bf16(x, w, bias, y, relu, err, stream=None):
-    n, H, W, cin = x.shape
+    """x: BF16 [n][cin/8][H][W][8] (8-channel planes), w: [cout][9][cin], y: [n][cout/8][H][W][8]."""
+    n, g, H, W, _ = x.shape
+    cin = 8 * g
     _check(load().mcdi_conv3x3_bf16(_ptr(x), n, H, W, cin, _ptr(w), _ptr(bias), w.shape[0], int(bool(relu)), _ptr(y),
                                     _ptr(err), _stream(stream)), "conv3x3_bf16")
 

@@ -47,13 +47,16 @@ def test_conv3x3_layer_matches_library(cuda_lib, cin, cout, H, W, relu):
     w = bf16_round(rng.normal(size=(cout, 3, 3, cin)) / np.sqrt(9 * cin))
     b = torch.from_numpy(rng.normal(size=cout).astype(np.float32))
     dev = "cuda"
-    xg = x.to(torch.bfloat16).to(dev).contiguous()
+    # 8-channel planes [n][C/8][H][W][8]
+    planar = lambda t: t.reshape(t.shape[0], t.shape[1], t.shape[2], -1, 8).permute(0, 3, 1, 2, 4).contiguous()
+    xg = planar(x.to(torch.bfloat16)).to(dev)
     wg = w.reshape(cout, 9, cin).to(torch.bfloat16).to(dev).contiguous()
-    yg = torch.full((n, H, W, cout), float("nan"), dtype=torch.bfloat16, device=dev)
+    yg = torch.full((n, cout // 8, H, W, 8), float("nan"), dtype=torch.bfloat16, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     mcdi.conv3x3_bf16(xg, wg, b.to(dev), yg, relu, err)
     torch.cuda.synchronize()
     assert err.item() == 0
+    yg = yg.permute(0, 2, 3, 1, 4).reshape(n, H, W, cout)
     ref = D.conv3x3(x.permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b.double())
     if relu:
         ref = torch.relu(ref)

@@ -112,6 +112,47 @@ def test_bvh_structure_and_determinism(cuda_lib, scene):
     np.testing.assert_array_equal(a, to_np(pipe.bvh.nodes))
 
 
+def test_bvh_depth_first_escape_links(cuda_lib, scene):
+    """The stackless layout is the pre-order copy of the two-child tree: first
+    child next, escape link past the subtree, the same boxes, every triangle
+    in one leaf."""
+    pipe = make_pipe(scene)
+    pipe.build_bvh()
+    n = scene.tris.shape[0]
+    raw = to_np(pipe.bvh.nodes)
+    nodes = raw.view(np.float32)[: (n - 1) * 16].reshape(-1, 16)
+    links = nodes[:, 12:14].view(np.int32)
+    off = ((max(n - 1, 1) * 64 + 255) // 256) * 256
+    tn = raw[off: off + (2 * n - 1) * 32].view(np.float32).reshape(-1, 8)
+    skip, tri = tn[:, 3].view(np.int32), tn[:, 7].view(np.int32)
+    # child boxes as stored in the parent: (lo, hi) per link
+    child_box = {}
+    for k in range(n - 1):
+        a, b, c = nodes[k, 0:4], nodes[k, 4:8], nodes[k, 8:12]
+        child_box[int(links[k, 0])] = (np.array([a[0], a[2], c[0]]), np.array([a[1], a[3], c[1]]))
+        child_box[int(links[k, 1])] = (np.array([b[0], b[2], c[2]]), np.array([b[1], b[3], c[3]]))
+
+    def walk(link, i):
+        if link < 0:
+            assert tri[i] == ~link and skip[i] == i + 1
+        else:
+            assert tri[i] == -1
+            j = walk(int(links[link, 0]), i + 1)
+            j = walk(int(links[link, 1]), j)
+            assert skip[i] == j
+            lo = np.minimum(child_box[int(links[link, 0])][0], child_box[int(links[link, 1])][0])
+            hi = np.maximum(child_box[int(links[link, 0])][1], child_box[int(links[link, 1])][1])
+            np.testing.assert_array_equal(tn[i, 0:3], lo)
+            np.testing.assert_array_equal(tn[i, 4:7], hi)
+        if link in child_box:
+            np.testing.assert_array_equal(tn[i, 0:3], child_box[link][0])
+            np.testing.assert_array_equal(tn[i, 4:7], child_box[link][1])
+        return int(skip[i])
+
+    assert walk(0, 0) == 2 * n - 1
+    np.testing.assert_array_equal(np.sort(tri[tri >= 0]), np.arange(n))
+
+
 # ------------------------------------------------------------------ G-buffer
 def test_primary_cast_matches_oracle(cuda_lib, orc, scene, oracle_gb):
     pipe = make_pipe(scene)
