@@ -299,6 +299,7 @@ def run_gpu(args, rank, world):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
         "gpu_launches": launches,
     }
+    result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
     if args.serving_requests > 0:
@@ -306,6 +307,39 @@ def run_gpu(args, rank, world):
         torch.cuda.empty_cache()
         result["serving"] = run_serving(args.serving_requests, args.serving_rate, dev, rank)
     return result
+
+
+def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):
+    """The FP8 (E4M3, per-tensor scaling) denoiser on the same two 512^2 terms:
+    forward and input-gradient times (CUDA events, L2 flushed before each pass);
+    its error against the float64 network is a test result, not timed here."""
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi
+
+    den = mcdi.Denoiser(den_params, 2 * pipe.N, pipe.H, pipe.W, device=pipe.device, precision=mcdi.E4M3)
+    y = torch.empty_like(pipe.denoised)
+    gx = torch.empty_like(pipe.denoised)
+    g = torch.ones_like(pipe.denoised)
+    fwd, bwd = [], []
+    for k in range(steps + 3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        flush.zero_()
+        ev[0].record(stream)
+        den.forward(pipe.terms, pipe.kd_out, pipe.gb.nrm, y, stream)
+        ev[1].record(stream)
+        den.backward(g, gx, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+    if den.err.item() != 0:
+        raise RuntimeError("E4M3 denoiser pipeline wait timed out")
+    f, b = float(np.mean(fwd)), float(np.mean(bwd))
+    return {"fwd_ms": round(f, 4), "bwd_ms": round(b, 4), "fwd_tflops": round(conv_flops / (f * 1e-3) / 1e12, 2),
+            "bwd_tflops": round(conv_flops / (b * 1e-3) / 1e12, 2),
+            "note": "E4M3 operands with per-tensor scaling (amax pass + quantised copy before each convolution)"}
 
 
 def run_serving(n_requests, rate, dev, rank):

@@ -221,12 +221,17 @@ MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* en
  * convolutions with ReLU per level, 2x2 max-pool down, nearest 2x upsample
  * and [upsampled, skip] concatenation up, a final linear 3x3 convolution to
  * 3 channels.  Input per image: 9 channels = term rgb, k_d rgb, normal xyz.
- * Convolutions run on the tcgen05 tensor cores with BF16 operands and FP32
- * accumulation; activations are stored as BF16.
+ * Convolutions run on the tcgen05 tensor cores with FP32 accumulation and
+ * operands of the chosen precision: MCDI_DENOISE_BF16, or MCDI_DENOISE_E4M3
+ * (FP8 E4M3 with per-tensor scaling: each convolution's input and weights are
+ * quantised as round-to-nearest-even, saturating, of v * 448 / amax, and the
+ * accumulator is rescaled by (amax_x / 448) (amax_w / 448)).  Activations
+ * and gradients are stored as BF16 in both modes.
  *
- * mcdi_denoise_sizes (host): bytes of the packed weights, of the forward's
- * saved activations and of the backward's gradient scratch for n_img images
- * of H x W (H, W multiples of 8), and the number of FP32 parameters.
+ * mcdi_denoise_sizes (host): bytes of the packed weights (both precisions),
+ * of the forward's saved activations and of the backward's gradient scratch
+ * for n_img images of H x W (H, W multiples of 8) in `precision`, and the
+ * number of FP32 parameters.
  * mcdi_denoise_pack_weights: params (device, FP32, for each of the 15
  * convolutions in order enc1a enc1b enc2a enc2b enc3a enc3b bot_a bot_b dec3a
  * dec3b dec2a dec2b dec1a dec1b out: W[co][ci][3][3] then b[co]) -> weights.
@@ -235,16 +240,19 @@ MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* en
  * acts (act_bytes) receives the activations the backward needs.
  * mcdi_denoise_bwd: gy [n_img][H][W] float4 -> gx [n_img][H][W] float4, the
  * gradient with respect to the term channels (the weights are locked: no
- * weight gradient).  err: device uint32 the kernels set to 1 if a pipeline
- * wait timed out (zero it before the call; outputs are then invalid).
+ * weight gradient); acts from a forward of the same precision.  err: device
+ * uint32 the kernels set to 1 if a pipeline wait timed out (zero it before
+ * the call; outputs are then invalid).
  * ------------------------------------------------------------------------ */
-MCDI_API mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, size_t* weight_bytes, size_t* act_bytes,
-                                        size_t* grad_bytes, size_t* n_params);
+#define MCDI_DENOISE_BF16 0
+#define MCDI_DENOISE_E4M3 1
+MCDI_API mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, int precision, size_t* weight_bytes,
+                                        size_t* act_bytes, size_t* grad_bytes, size_t* n_params);
 MCDI_API mcdi_status mcdi_denoise_pack_weights(const float* params, void* weights, void* stream);
-MCDI_API mcdi_status mcdi_denoise_fwd(const void* weights, int n_img, int H, int W, const float* term,
+MCDI_API mcdi_status mcdi_denoise_fwd(const void* weights, int precision, int n_img, int H, int W, const float* term,
                                       const float* kd, const float* nrm, int n_aux, float* y, void* acts,
                                       size_t act_bytes, unsigned* err, void* stream);
-MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int n_img, int H, int W, const void* acts,
+MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_img, int H, int W, const void* acts,
                                       size_t act_bytes, const float* gy, float* gx, void* grad_ws,
                                       size_t grad_bytes, unsigned* err, void* stream);
 
@@ -264,6 +272,16 @@ MCDI_API mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, co
 MCDI_API mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pad, const void* w,
                                        const float* bias, int cout_pad, int relu, void* y, unsigned* err,
                                        void* stream);
+
+/* The same layer with E4M3 operands (the denoiser's FP8 path): x holds E4M3
+ * codes in 16-channel planes (element (((i * C/16 + c/16) * H + y) * W + x)
+ * * 16 + c % 16, one byte each), w [cout_pad][9][cin_pad] E4M3 codes;
+ * x_amax, w_amax (device float) give the scales: y = act(conv(x) *
+ * (x_amax / 448) * (w_amax / 448) + bias) as BF16 8-channel planes.
+ * cin_pad a multiple of 32, cout_pad a multiple of 16, <= 256. */
+MCDI_API mcdi_status mcdi_conv3x3_e4m3(const void* x, int n_img, int H, int W, int cin_pad, const void* w,
+                                       const float* x_amax, const float* w_amax, const float* bias, int cout_pad,
+                                       int relu, void* y, unsigned* err, void* stream);
 
 #ifdef __cplusplus
 }

@@ -54,6 +54,51 @@ def conv3x3(x, W, b):
     return F.conv2d(x, W, b, padding=1)
 
 
+E4M3_MAX = 448.0
+
+
+def e4m3_quantize(t, amax):
+    """Per-tensor E4M3 quantisation as the FP8 path defines it: scale s = 448 / amax
+    (float32), codes = round-to-nearest-even of v * s in float32, saturated to
+    +-448 (the OCP FP8 E4M3 format: 4 exponent bits, bias 7, 3 mantissa bits, no
+    infinities); returns the dequantised float64 values codes * amax / 448."""
+    amax = float(amax)
+    if not amax > 0:
+        return torch.zeros_like(t, dtype=torch.float64)
+    s = torch.tensor(E4M3_MAX, dtype=torch.float32) / torch.tensor(amax, dtype=torch.float32)
+    v = (t.to(torch.float32) * s).clamp(-E4M3_MAX, E4M3_MAX)
+    return v.to(torch.float8_e4m3fn).to(torch.float64) * (amax / E4M3_MAX)
+
+
+class _QuantX(torch.autograd.Function):
+    """Forward: per-tensor E4M3 quantisation of a convolution input; backward:
+    the gradient passes unchanged (the input gradient is computed from the
+    quantised operands, not through the rounding)."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return e4m3_quantize(x, x.abs().max())
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+class _QuantG(torch.autograd.Function):
+    """Forward: identity on a convolution output; backward: the gradient
+    arriving there (stored in bfloat16) is quantised per tensor to E4M3 before
+    the input-gradient convolution uses it."""
+
+    @staticmethod
+    def forward(ctx, z):
+        return z.view_as(z)
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.to(torch.bfloat16).to(torch.float64)
+        return e4m3_quantize(g, g.abs().max())
+
+
 class _RoundBF16(torch.autograd.Function):
     """Identity up to rounding to bfloat16, in the forward value and in the
     backward gradient: marks a tensor that is stored in bfloat16."""
@@ -72,11 +117,17 @@ def _unet(x, P, storage=None):
     every stored tensor (input, each activation after its ReLU, pooled and
     concatenated tensors) and every gradient of those to bfloat16, which is
     where a bfloat16 implementation takes its discrete decisions (ReLU masks,
-    max-pool winners); arithmetic stays float64."""
-    r = _RoundBF16.apply if storage == "bf16" else (lambda t: t)
+    max-pool winners); arithmetic stays float64.  storage="e4m3" stores the
+    same way and in addition quantises each convolution's input (per tensor,
+    forward) and the gradient entering each input-gradient convolution (per
+    tensor, backward) to E4M3; the weights arrive quantised in P."""
+    r = _RoundBF16.apply if storage in ("bf16", "e4m3") else (lambda t: t)
+    fp8 = storage == "e4m3"
 
     def conv(name, h, relu):
-        z = conv3x3(h, *P[name])
+        z = conv3x3(_QuantX.apply(h) if fp8 else h, *P[name])
+        if fp8:
+            z = _QuantG.apply(z)
         return r(F.relu(z)) if relu else z
 
     up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
@@ -98,6 +149,9 @@ def _params(weights, storage, grad=False):
         t = _t(a)
         if storage == "bf16":
             t = t.to(torch.bfloat16).to(torch.float64)
+        elif storage == "e4m3":  # per weight tensor, from the float32 parameters
+            t32 = t.to(torch.float32)
+            t = e4m3_quantize(t32, t32.abs().max())
         return t.clone().requires_grad_(grad)
 
     return {k: (w(W), _t(b).clone().requires_grad_(grad)) for k, (W, b) in weights.items()}
@@ -112,12 +166,12 @@ def unet_forward(x, weights, storage=None):
 
 def unet_forward_backward(x, weights, gy, storage=None):
     """Forward and the adjoint of the scalar <gy, y>: returns (y, gx, {name: (gW, gb)}).
-    With storage="bf16" the upstream gradient is rounded too."""
+    With storage="bf16" or "e4m3" the upstream gradient is rounded to bfloat16 too."""
     x = _t(x).clone().requires_grad_(True)
     P = _params(weights, storage, grad=True)
     y = _unet(x, P, storage)
     g = _t(gy)
-    if storage == "bf16":
+    if storage in ("bf16", "e4m3"):
         g = g.to(torch.bfloat16).to(torch.float64)
     (y * g).sum().backward()
     return y.detach(), x.grad.detach(), {k: (v[0].grad.detach(), v[1].grad.detach()) for k, v in P.items()}

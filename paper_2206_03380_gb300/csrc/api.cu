@@ -246,15 +246,17 @@ mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp
                     "shade_mc_bwd");
 }
 
-mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, size_t* weight_bytes, size_t* act_bytes,
+mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, int precision, size_t* weight_bytes, size_t* act_bytes,
                                size_t* grad_bytes, size_t* n_params) {
+    REQUIRE(precision == MCDI_DENOISE_BF16 || precision == MCDI_DENOISE_E4M3,
+            "precision must be MCDI_DENOISE_BF16 or MCDI_DENOISE_E4M3 (got %d)", precision);
     REQUIRE(n_img >= 1 && H >= 8 && W >= 8 && H % 8 == 0 && W % 8 == 0,
             "denoiser needs n_img >= 1 and H, W positive multiples of 8 (got %d x %d)", H, W);
     REQUIRE((long long)n_img * H * W <= (1LL << 28), "denoiser image batch too large");
     const mcdi::UnetWeightLayout L = mcdi::unet_weight_layout();
     if (weight_bytes) *weight_bytes = L.total;
-    if (act_bytes) *act_bytes = mcdi::unet_act_bytes(n_img, H, W);
-    if (grad_bytes) *grad_bytes = mcdi::unet_grad_bytes(n_img, H, W);
+    if (act_bytes) *act_bytes = mcdi::unet_act_bytes(n_img, H, W, precision);
+    if (grad_bytes) *grad_bytes = mcdi::unet_grad_bytes(n_img, H, W, precision);
     if (n_params) *n_params = L.n_params;
     return ok();
 }
@@ -266,11 +268,11 @@ mcdi_status mcdi_denoise_pack_weights(const float* params, void* weights, void* 
                     "denoise_pack_weights");
 }
 
-mcdi_status mcdi_denoise_fwd(const void* weights, int n_img, int H, int W, const float* term, const float* kd,
-                             const float* nrm, int n_aux, float* y, void* acts, size_t act_bytes, unsigned* err,
-                             void* stream) {
+mcdi_status mcdi_denoise_fwd(const void* weights, int precision, int n_img, int H, int W, const float* term,
+                             const float* kd, const float* nrm, int n_aux, float* y, void* acts, size_t act_bytes,
+                             unsigned* err, void* stream) {
     size_t need = 0;
-    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, nullptr, &need, nullptr, nullptr);
+    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, precision, nullptr, &need, nullptr, nullptr);
     if (s != MCDI_OK) return s;
     REQUIRE(weights != nullptr && ((uintptr_t)weights & 255u) == 0, "weights must be 256-byte aligned");
     REQUIRE_BUF16(term);
@@ -282,17 +284,17 @@ mcdi_status mcdi_denoise_fwd(const void* weights, int n_img, int H, int W, const
     REQUIRE(act_bytes >= need, "acts too small: %zu < %zu bytes", act_bytes, need);
     REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
     const char* why = "";
-    cudaError_t e = mcdi::launch_unet_fwd(weights, n_img, H, W, term, kd, nrm, n_aux, y, acts, err,
+    cudaError_t e = mcdi::launch_unet_fwd(weights, precision, n_img, H, W, term, kd, nrm, n_aux, y, acts, err,
                                           static_cast<cudaStream_t>(stream), &why);
     if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "denoise_fwd: %s", why);
     return launched(e, "denoise_fwd");
 }
 
-mcdi_status mcdi_denoise_bwd(const void* weights, int n_img, int H, int W, const void* acts, size_t act_bytes,
-                             const float* gy, float* gx, void* grad_ws, size_t grad_bytes, unsigned* err,
-                             void* stream) {
+mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_img, int H, int W, const void* acts,
+                             size_t act_bytes, const float* gy, float* gx, void* grad_ws, size_t grad_bytes,
+                             unsigned* err, void* stream) {
     size_t need_a = 0, need_g = 0;
-    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, nullptr, &need_a, &need_g, nullptr);
+    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, precision, nullptr, &need_a, &need_g, nullptr);
     if (s != MCDI_OK) return s;
     REQUIRE(weights != nullptr && ((uintptr_t)weights & 255u) == 0, "weights must be 256-byte aligned");
     REQUIRE(acts != nullptr && act_bytes >= need_a, "acts too small");
@@ -302,7 +304,7 @@ mcdi_status mcdi_denoise_bwd(const void* weights, int n_img, int H, int W, const
     REQUIRE(grad_bytes >= need_g, "grad_ws too small: %zu < %zu bytes", grad_bytes, need_g);
     REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
     const char* why = "";
-    cudaError_t e = mcdi::launch_unet_bwd(weights, n_img, H, W, acts, gy, gx, grad_ws, err,
+    cudaError_t e = mcdi::launch_unet_bwd(weights, precision, n_img, H, W, acts, gy, gx, grad_ws, err,
                                           static_cast<cudaStream_t>(stream), &why);
     if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "denoise_bwd: %s", why);
     return launched(e, "denoise_bwd");
@@ -334,6 +336,25 @@ mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pa
                                          static_cast<cudaStream_t>(stream), &why);
     if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "conv3x3_bf16: %s", why);
     return launched(e, "conv3x3_bf16");
+}
+
+mcdi_status mcdi_conv3x3_e4m3(const void* x, int n_img, int H, int W, int cin_pad, const void* w, const float* x_amax,
+                              const float* w_amax, const float* bias, int cout_pad, int relu, void* y, unsigned* err,
+                              void* stream) {
+    REQUIRE(n_img >= 1 && H >= 1 && W >= 1 && (long long)n_img * H * W <= (1LL << 28), "bad image shape");
+    REQUIRE(cin_pad >= 32 && cin_pad % 32 == 0 && cin_pad <= 2048, "cin_pad must be a multiple of 32 in [32, 2048]");
+    REQUIRE(cout_pad >= 16 && cout_pad % 16 == 0 && cout_pad <= 256, "cout_pad must be a multiple of 16 in [16, 256]");
+    REQUIRE(x != nullptr && ((uintptr_t)x & 15u) == 0, "x must be 16-byte aligned");
+    REQUIRE(w != nullptr && ((uintptr_t)w & 15u) == 0, "w must be 16-byte aligned");
+    REQUIRE(y != nullptr && ((uintptr_t)y & 15u) == 0, "y must be 16-byte aligned");
+    REQUIRE(x_amax != nullptr && w_amax != nullptr, "x_amax and w_amax must be device floats");
+    REQUIRE(bias == nullptr || ((uintptr_t)bias & 3u) == 0, "bias must be 4-byte aligned");
+    REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
+    const char* why = "";
+    cudaError_t e = mcdi::launch_conv3x3_e4m3(x, n_img, H, W, cin_pad, w, x_amax, w_amax, bias, cout_pad, relu, y, err,
+                                              static_cast<cudaStream_t>(stream), &why);
+    if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "conv3x3_e4m3: %s", why);
+    return launched(e, "conv3x3_e4m3");
 }
 
 }  // extern "C"

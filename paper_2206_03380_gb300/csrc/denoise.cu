@@ -5,13 +5,21 @@
 // weights, so no weight gradient is formed; Sec. 4.2's gradient-sharing
 // identity dL/dX = dL/dO conv F^T is what the backward convolutions compute).
 //
-// Layout: NHWC BF16 activations, channels padded to multiples of 16.  Skip
+// Precision: BF16 operands, or E4M3 operands with per-tensor scaling (every
+// convolution input and weight tensor quantised as round(v 448 / amax) just
+// before use, FP32 accumulation rescaled by the two amax / 448 factors); the
+// stored activations and gradients stay BF16 either way.
+//
+// Layout: BF16 activations in 8-channel planes, channels padded to multiples
+// of 16 (E4M3 copies: 16-channel planes, padded to multiples of 32).  Skip
 // connections are never copied: the encoder's second convolution of a level
 // stores straight into the channel slice of that level's concatenation buffer,
 // and the decoder's second convolution stores its 2x nearest-upsampled output
 // into the other slice one level up ([upsampled | skip], as in the reading of
 // the network).  Max-pooling and the small backward routing steps are
 // memory-bound kernels of their own.
+#include <cuda_fp8.h>
+#include <algorithm>
 #include <stdio.h>
 
 #include "internal.h"
@@ -30,6 +38,8 @@ static const ConvSpec kPlan[kUnetConvs] = {
 
 static int pad16(int c) { return (c + 15) & ~15; }
 
+static int pad32(int c) { return (c + 31) & ~31; }
+
 UnetWeightLayout unet_weight_layout() {
     UnetWeightLayout L{};
     size_t o = 0;
@@ -41,7 +51,13 @@ UnetWeightLayout unet_weight_layout() {
         o = align256(o + (size_t)cip * 9 * cop * 2);
         L.bias[i] = o;
         o = align256(o + (size_t)cop * 4);
+        L.wk8[i] = o;  // E4M3 [cop][9][pad32(ci)]
+        o = align256(o + (size_t)cop * 9 * pad32(kPlan[i].ci));
+        L.wf8[i] = o;  // E4M3 [cip][9][pad32(co)]
+        o = align256(o + (size_t)cip * 9 * pad32(kPlan[i].co));
     }
+    L.amax = o;  // one float per convolution: amax of its weights
+    o = align256(o + kUnetConvs * sizeof(float));
     L.total = o;
     size_t n = 0;
     for (int i = 0; i < kUnetConvs; ++i) n += (size_t)kPlan[i].co * kPlan[i].ci * 9 + kPlan[i].co;
@@ -71,16 +87,45 @@ static void layout_of(const int* C, const int* lvl, int n, int H, int W, size_t*
     *total = o;
 }
 
-size_t unet_act_bytes(int n, int H, int W) {
-    size_t off[kActs], t;
-    layout_of<kActs>(kActC, kActLvl, n, H, W, off, &t);
-    return t;
+// E4M3 copies of the convolution inputs are made just before each convolution
+// into one scratch region (largest input), followed by the amax slots.
+static const int kFwdIn[kUnetConvs][2] = {{0, 16}, {0, 32}, {1, 32}, {1, 48}, {2, 48}, {2, 64}, {3, 64}, {3, 96},
+                                          {2, 160}, {2, 64}, {1, 112}, {1, 48}, {0, 80}, {0, 32}, {0, 32}};
+static const int kBwdIn[kUnetConvs][2] = {{0, 16}, {0, 32}, {0, 32}, {1, 48}, {1, 48}, {2, 64}, {2, 64}, {3, 96},
+                                          {3, 96}, {2, 64}, {2, 64}, {1, 48}, {1, 48}, {0, 32}, {0, 32}};
+constexpr int kAmaxSlots = 64;
+
+static size_t e4m3_scratch(const int (*in)[2], int n, int H, int W) {
+    size_t m = 0;
+    for (int i = 0; i < kUnetConvs; ++i) {
+        const size_t b = level_pixels(n, H, W, in[i][0]) * pad32(in[i][1]);
+        m = b > m ? b : m;
+    }
+    return m;
 }
 
-size_t unet_grad_bytes(int n, int H, int W) {
+struct Fp8Region {
+    size_t q, amax, total;
+};
+
+static Fp8Region fp8_region(size_t base, const int (*in)[2], int n, int H, int W) {
+    Fp8Region r;
+    r.q = align256(base);
+    r.amax = align256(r.q + e4m3_scratch(in, n, H, W));
+    r.total = align256(r.amax + kAmaxSlots * sizeof(float));
+    return r;
+}
+
+size_t unet_act_bytes(int n, int H, int W, int precision) {
+    size_t off[kActs], t;
+    layout_of<kActs>(kActC, kActLvl, n, H, W, off, &t);
+    return precision == MCDI_DENOISE_E4M3 ? fp8_region(t, kFwdIn, n, H, W).total : t;
+}
+
+size_t unet_grad_bytes(int n, int H, int W, int precision) {
     size_t off[kGrads], t;
     layout_of<kGrads>(kGradC, kGradLvl, n, H, W, off, &t);
-    return t;
+    return precision == MCDI_DENOISE_E4M3 ? fp8_region(t, kBwdIn, n, H, W).total : t;
 }
 
 namespace {
@@ -251,6 +296,84 @@ __global__ void pack_weights_kernel(const float* __restrict__ W, const float* __
     if (i < cop) bias[i] = i < co ? b[i] : 0.0f;
 }
 
+// ---------------------------------------------------------------- E4M3
+// max |v| of n BF16 values into *amax (float bits; non-negative floats order
+// like their bit patterns)
+__global__ void amax_bf16_kernel(const bf16* __restrict__ x, long long n8, unsigned* __restrict__ amax) {
+    unsigned m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
+        float f[8];
+        ld8(x + i * 8, f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m = max(m, __float_as_uint(fabsf(f[k])));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
+}
+
+__device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.0f ? 448.0f / amax : 0.0f; }
+
+// 16 floats -> 16 E4M3 codes (round to nearest even, saturating), one uint4
+__device__ __forceinline__ uint4 to_e4m3x16(const float* f, float s) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[4 * i] * s, f[4 * i + 1] * s), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi =
+            __nv_cvt_float2_to_fp8x2(make_float2(f[4 * i + 2] * s, f[4 * i + 3] * s), __NV_SATFINITE, __NV_E4M3);
+        w[i] = lo | (hi << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// BF16 tensor (C channels, 8-channel planes) -> E4M3 copy (pad32(C) channels,
+// 16-channel planes), scale 448 / amax
+__global__ void quant_e4m3_kernel(const bf16* __restrict__ x, int C, int n, int HW, const float* __restrict__ amax,
+                                  uint8_t* __restrict__ q) {
+    const int G16 = ((C + 31) & ~31) >> 4;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * G16 * HW) return;
+    const int p = (int)(i % HW);
+    const long long r = i / HW;
+    const int g = (int)(r % G16), img = (int)(r / G16);
+    const float s = e4m3_scale(*amax);
+    float f[16];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int b = 2 * g + h;
+        if (b < (C >> 3)) ld8(x + (((size_t)img * (C >> 3) + b) * HW + p) * 8, f + 8 * h);
+        else
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[8 * h + k] = 0.0f;
+    }
+    reinterpret_cast<uint4*>(q)[((size_t)img * G16 + g) * HW + p] = to_e4m3x16(f, s);
+}
+
+__global__ void amax_f32_kernel(const float* __restrict__ w, long long n, unsigned* __restrict__ amax) {
+    unsigned m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(w[i])));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
+}
+
+// E4M3 forward weights [cop][9][pad32(ci)] and flipped transposed backward
+// weights [cip][9][pad32(co)], scale 448 / amax of the convolution's weights
+__global__ void pack_weights_e4m3_kernel(const float* __restrict__ W, int ci, int co, const float* __restrict__ amax,
+                                         uint8_t* __restrict__ wk8, uint8_t* __restrict__ wf8) {
+    const int cip = pad16_dev(ci), cop = pad16_dev(co), ci32 = (ci + 31) & ~31, co32 = (co + 31) & ~31;
+    const int cmax_o = co32 > cop ? co32 : cop, cmax_i = ci32 > cip ? ci32 : cip;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)cmax_o * 9 * cmax_i) return;
+    const int c_in = (int)(i % cmax_i);
+    const int tap = (int)((i / cmax_i) % 9);
+    const int c_out = (int)(i / (9LL * cmax_i));
+    const float v = (c_in < ci && c_out < co) ? W[((size_t)c_out * ci + c_in) * 9 + tap] : 0.0f;
+    const uint8_t b = (uint8_t)__nv_cvt_float_to_fp8(v * e4m3_scale(*amax), __NV_SATFINITE, __NV_E4M3);
+    if (c_out < cop && c_in < ci32) wk8[((size_t)c_out * 9 + tap) * ci32 + c_in] = b;
+    if (c_in < cip && c_out < co32) wf8[((size_t)c_in * 9 + (8 - tap)) * co32 + c_out] = b;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- orchestration
@@ -259,26 +382,43 @@ struct Unet {
     UnetWeightLayout L;
     int n, H, W;
     unsigned* err;
+    bool fp8 = false;
+    uint8_t* q = nullptr;     // E4M3 copy of the current convolution's input
+    float* amax = nullptr;    // kAmaxSlots slots, zeroed at the start of a pass
+    int slot = 0;             // next free slot
+};
+
+struct Wsel {  // which packed weights: convolution i, forward or flipped (input gradient)
+    int i;
+    bool dgrad;
 };
 
 static const bf16* wk_of(const Unet& u, int i) { return reinterpret_cast<const bf16*>(u.wbase + u.L.wk[i]); }
 static const bf16* wf_of(const Unet& u, int i) { return reinterpret_cast<const bf16*>(u.wbase + u.L.wf[i]); }
 static const float* b_of(const Unet& u, int i) { return reinterpret_cast<const float*>(u.wbase + u.L.bias[i]); }
 
-static cudaError_t run_conv(const Unet& u, int level, const bf16* x, int cin_pad, const bf16* w, const float* bias,
-                            int cout_pad, int cout_valid, int mode, int relu, bf16* out, int out_ctotal, int out_coff,
-                            float4* out_f32, const bf16* mask, int mask_ctotal, int mask_coff, cudaStream_t s,
-                            const char** why) {
+static int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+#define CHECK(e)                          \
+    do {                                  \
+        cudaError_t _e = (e);             \
+        if (_e != cudaSuccess) return _e; \
+    } while (0)
+
+static ConvDesc conv_desc(int n, int H, int W, int cin_pad, int cin_bytes, const float* bias, int cout_pad,
+                          int cout_valid, int mode, int relu, bf16* out, int out_ctotal, int out_coff, float4* out_f32,
+                          const bf16* mask, int mask_ctotal, int mask_coff, unsigned* err) {
     ConvDesc d{};
     ConvParams& p = d.p;
-    p.n_img = u.n;
-    p.H = u.H >> level;
-    p.W = u.W >> level;
+    p.n_img = n;
+    p.H = H;
+    p.W = W;
     p.tw = conv_pick_tile_w(p.W);
     p.th = 128 / p.tw;
     p.tiles_x = (p.W + p.tw - 1) / p.tw;
     p.tiles_y = (p.H + p.th - 1) / p.th;
     p.cin_pad = cin_pad;
+    p.cin_bytes = cin_bytes;
     p.cout_pad = cout_pad;
     p.cout_valid = cout_valid;
     p.mode = mode;
@@ -291,41 +431,83 @@ static cudaError_t run_conv(const Unet& u, int level, const bf16* x, int cin_pad
     p.mask = mask;
     p.mask_ctotal = mask_ctotal;
     p.mask_coff = mask_coff;
-    p.err = u.err;
-    if (!conv_make_desc(&d, x, w, why)) return cudaErrorInvalidValue;
-    return conv_launch(d, s);
+    p.err = err;
+    return d;
 }
 
-static int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
-
-#define CHECK(e)                          \
-    do {                                  \
-        cudaError_t _e = (e);             \
-        if (_e != cudaSuccess) return _e; \
-    } while (0)
+// One convolution of the network on a BF16 input; in E4M3 mode the input is
+// first quantised (amax pass, then the copy) and the E4M3 weights are used.
+static cudaError_t run_conv(Unet& u, int level, const bf16* x, int cin_pad, Wsel w, const float* bias, int cout_pad,
+                            int cout_valid, int mode, int relu, bf16* out, int out_ctotal, int out_coff,
+                            float4* out_f32, const bf16* mask, int mask_ctotal, int mask_coff, cudaStream_t s,
+                            const char** why) {
+    const int Hl = u.H >> level, Wl = u.W >> level;
+    ConvDesc d = conv_desc(u.n, Hl, Wl, cin_pad, 2 * cin_pad, bias, cout_pad, cout_valid, mode, relu, out, out_ctotal,
+                           out_coff, out_f32, mask, mask_ctotal, mask_coff, u.err);
+    const void* xin = x;
+    const void* win = w.dgrad ? (const void*)wf_of(u, w.i) : (const void*)wk_of(u, w.i);
+    if (u.fp8) {
+        if (u.slot >= kAmaxSlots) {
+            *why = "denoiser: out of amax slots";
+            return cudaErrorInvalidValue;
+        }
+        float* am = u.amax + u.slot++;
+        const long long n8 = (long long)u.n * Hl * Wl * (cin_pad / 8);
+        const int c32 = pad32(cin_pad);
+        amax_bf16_kernel<<<std::min(blocks_for(n8, 256), 2048), 256, 0, s>>>(x, n8, reinterpret_cast<unsigned*>(am));
+        quant_e4m3_kernel<<<blocks_for((long long)u.n * (c32 / 16) * Hl * Wl, 256), 256, 0, s>>>(x, cin_pad, u.n,
+                                                                                                  Hl * Wl, am, u.q);
+        CHECK(cudaGetLastError());
+        xin = u.q;
+        win = u.wbase + (w.dgrad ? u.L.wf8[w.i] : u.L.wk8[w.i]);
+        d.p.cin_pad = c32;
+        d.p.cin_bytes = c32;
+        d.p.fp8 = 1;
+        d.p.x_amax = am;
+        d.p.w_amax = reinterpret_cast<const float*>(u.wbase + u.L.amax) + w.i;
+    }
+    if (!conv_make_desc(&d, xin, win, why)) return cudaErrorInvalidValue;
+    return conv_launch(d, s);
+}
 
 cudaError_t launch_unet_pack_weights(const float* params, void* weights, cudaStream_t s) {
     const UnetWeightLayout L = unet_weight_layout();
     char* base = static_cast<char*>(weights);
+    float* amax = reinterpret_cast<float*>(base + L.amax);
+    CHECK(cudaMemsetAsync(amax, 0, kUnetConvs * sizeof(float), s));
     size_t off = 0;
     for (int i = 0; i < kUnetConvs; ++i) {
         const int ci = kPlan[i].ci, co = kPlan[i].co;
         const long long n = (long long)pad16(co) * 9 * pad16(ci);
+        const long long nw = (long long)co * ci * 9;
         pack_weights_kernel<<<blocks_for(n, 256), 256, 0, s>>>(
             params + off, params + off + (size_t)co * ci * 9, ci, co, reinterpret_cast<bf16*>(base + L.wk[i]),
             reinterpret_cast<bf16*>(base + L.wf[i]), reinterpret_cast<float*>(base + L.bias[i]));
+        amax_f32_kernel<<<std::min(blocks_for(nw, 256), 256), 256, 0, s>>>(params + off, nw,
+                                                                          reinterpret_cast<unsigned*>(amax + i));
+        const long long n8 = (long long)std::max(pad32(co), pad16(co)) * 9 * std::max(pad32(ci), pad16(ci));
+        pack_weights_e4m3_kernel<<<blocks_for(n8, 256), 256, 0, s>>>(params + off, ci, co, amax + i,
+                                                                      reinterpret_cast<uint8_t*>(base + L.wk8[i]),
+                                                                      reinterpret_cast<uint8_t*>(base + L.wf8[i]));
         off += (size_t)co * ci * 9 + co;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_unet_fwd(const void* weights, int n, int H, int W, const float* term, const float* kd,
-                            const float* nrm, int n_aux, float* y, void* acts, unsigned* err, cudaStream_t s,
-                            const char** why) {
+cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, int W, const float* term,
+                            const float* kd, const float* nrm, int n_aux, float* y, void* acts, unsigned* err,
+                            cudaStream_t s, const char** why) {
     Unet u{static_cast<const char*>(weights), unet_weight_layout(), n, H, W, err};
     size_t off[kActs], tot;
     layout_of<kActs>(kActC, kActLvl, n, H, W, off, &tot);
     char* a = static_cast<char*>(acts);
+    if (precision == MCDI_DENOISE_E4M3) {
+        const Fp8Region r = fp8_region(tot, kFwdIn, n, H, W);
+        u.fp8 = true;
+        u.q = reinterpret_cast<uint8_t*>(a + r.q);
+        u.amax = reinterpret_cast<float*>(a + r.amax);
+        CHECK(cudaMemsetAsync(u.amax, 0, kAmaxSlots * sizeof(float), s));
+    }
     auto A = [&](int k) { return reinterpret_cast<bf16*>(a + off[k]); };
     const long long HW = (long long)H * W;
     pack_input_kernel<<<blocks_for(n * HW, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(term),
@@ -340,54 +522,62 @@ cudaError_t launch_unet_fwd(const void* weights, int n, int H, int W, const floa
         return cudaGetLastError();
     };
     // level 0
-    CHECK(run_conv(u, 0, A(X0), 16, wk_of(u, 0), b_of(u, 0), 32, 32, kStore, 1, A(A1), 32, 0, nullptr, nullptr, 0, 0,
+    CHECK(run_conv(u, 0, A(X0), 16, Wsel{0, false}, b_of(u, 0), 32, 32, kStore, 1, A(A1), 32, 0, nullptr, nullptr, 0, 0,
                    s, why));
-    CHECK(run_conv(u, 0, A(A1), 32, wk_of(u, 1), b_of(u, 1), 32, 32, kStore, 1, A(CAT1), 80, 48, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 0, A(A1), 32, Wsel{1, false}, b_of(u, 1), 32, 32, kStore, 1, A(CAT1), 80, 48, nullptr, nullptr, 0,
                    0, s, why));
     CHECK(pool(A(CAT1), 80, 48, 32, 0, A(P1)));
     // level 1
-    CHECK(run_conv(u, 1, A(P1), 32, wk_of(u, 2), b_of(u, 2), 48, 48, kStore, 1, A(A2), 48, 0, nullptr, nullptr, 0, 0,
+    CHECK(run_conv(u, 1, A(P1), 32, Wsel{2, false}, b_of(u, 2), 48, 48, kStore, 1, A(A2), 48, 0, nullptr, nullptr, 0, 0,
                    s, why));
-    CHECK(run_conv(u, 1, A(A2), 48, wk_of(u, 3), b_of(u, 3), 48, 48, kStore, 1, A(CAT2), 112, 64, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 1, A(A2), 48, Wsel{3, false}, b_of(u, 3), 48, 48, kStore, 1, A(CAT2), 112, 64, nullptr, nullptr, 0,
                    0, s, why));
     CHECK(pool(A(CAT2), 112, 64, 48, 1, A(P2)));
     // level 2
-    CHECK(run_conv(u, 2, A(P2), 48, wk_of(u, 4), b_of(u, 4), 64, 64, kStore, 1, A(A3), 64, 0, nullptr, nullptr, 0, 0,
+    CHECK(run_conv(u, 2, A(P2), 48, Wsel{4, false}, b_of(u, 4), 64, 64, kStore, 1, A(A3), 64, 0, nullptr, nullptr, 0, 0,
                    s, why));
-    CHECK(run_conv(u, 2, A(A3), 64, wk_of(u, 5), b_of(u, 5), 64, 64, kStore, 1, A(CAT3), 160, 96, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 2, A(A3), 64, Wsel{5, false}, b_of(u, 5), 64, 64, kStore, 1, A(CAT3), 160, 96, nullptr, nullptr, 0,
                    0, s, why));
     CHECK(pool(A(CAT3), 160, 96, 64, 2, A(P3)));
     // bottleneck (level 3): second conv stores its 2x upsample into the level-2 concatenation
-    CHECK(run_conv(u, 3, A(P3), 64, wk_of(u, 6), b_of(u, 6), 96, 96, kStore, 1, A(B1), 96, 0, nullptr, nullptr, 0, 0,
+    CHECK(run_conv(u, 3, A(P3), 64, Wsel{6, false}, b_of(u, 6), 96, 96, kStore, 1, A(B1), 96, 0, nullptr, nullptr, 0, 0,
                    s, why));
-    CHECK(run_conv(u, 3, A(B1), 96, wk_of(u, 7), b_of(u, 7), 96, 96, kStoreUp2, 1, A(CAT3), 160, 0, nullptr, nullptr,
+    CHECK(run_conv(u, 3, A(B1), 96, Wsel{7, false}, b_of(u, 7), 96, 96, kStoreUp2, 1, A(CAT3), 160, 0, nullptr, nullptr,
                    0, 0, s, why));
     // decoder
-    CHECK(run_conv(u, 2, A(CAT3), 160, wk_of(u, 8), b_of(u, 8), 64, 64, kStore, 1, A(D3A), 64, 0, nullptr, nullptr,
+    CHECK(run_conv(u, 2, A(CAT3), 160, Wsel{8, false}, b_of(u, 8), 64, 64, kStore, 1, A(D3A), 64, 0, nullptr, nullptr,
                    0, 0, s, why));
-    CHECK(run_conv(u, 2, A(D3A), 64, wk_of(u, 9), b_of(u, 9), 64, 64, kStoreUp2, 1, A(CAT2), 112, 0, nullptr,
+    CHECK(run_conv(u, 2, A(D3A), 64, Wsel{9, false}, b_of(u, 9), 64, 64, kStoreUp2, 1, A(CAT2), 112, 0, nullptr,
                    nullptr, 0, 0, s, why));
-    CHECK(run_conv(u, 1, A(CAT2), 112, wk_of(u, 10), b_of(u, 10), 48, 48, kStore, 1, A(D2A), 48, 0, nullptr, nullptr,
+    CHECK(run_conv(u, 1, A(CAT2), 112, Wsel{10, false}, b_of(u, 10), 48, 48, kStore, 1, A(D2A), 48, 0, nullptr, nullptr,
                    0, 0, s, why));
-    CHECK(run_conv(u, 1, A(D2A), 48, wk_of(u, 11), b_of(u, 11), 48, 48, kStoreUp2, 1, A(CAT1), 80, 0, nullptr,
+    CHECK(run_conv(u, 1, A(D2A), 48, Wsel{11, false}, b_of(u, 11), 48, 48, kStoreUp2, 1, A(CAT1), 80, 0, nullptr,
                    nullptr, 0, 0, s, why));
-    CHECK(run_conv(u, 0, A(CAT1), 80, wk_of(u, 12), b_of(u, 12), 32, 32, kStore, 1, A(D1A), 32, 0, nullptr, nullptr,
+    CHECK(run_conv(u, 0, A(CAT1), 80, Wsel{12, false}, b_of(u, 12), 32, 32, kStore, 1, A(D1A), 32, 0, nullptr, nullptr,
                    0, 0, s, why));
-    CHECK(run_conv(u, 0, A(D1A), 32, wk_of(u, 13), b_of(u, 13), 32, 32, kStore, 1, A(D1B), 32, 0, nullptr, nullptr,
+    CHECK(run_conv(u, 0, A(D1A), 32, Wsel{13, false}, b_of(u, 13), 32, 32, kStore, 1, A(D1B), 32, 0, nullptr, nullptr,
                    0, 0, s, why));
-    CHECK(run_conv(u, 0, A(D1B), 32, wk_of(u, 14), b_of(u, 14), 16, 3, kStoreF32, 0, nullptr, 0, 0,
+    CHECK(run_conv(u, 0, A(D1B), 32, Wsel{14, false}, b_of(u, 14), 16, 3, kStoreF32, 0, nullptr, 0, 0,
                    reinterpret_cast<float4*>(y), nullptr, 0, 0, s, why));
     return cudaSuccess;
 }
 
-cudaError_t launch_unet_bwd(const void* weights, int n, int H, int W, const void* acts, const float* gy,
-                            float* gx_term, void* grad_ws, unsigned* err, cudaStream_t s, const char** why) {
+cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, int W, const void* acts,
+                            const float* gy, float* gx_term, void* grad_ws, unsigned* err, cudaStream_t s,
+                            const char** why) {
     Unet u{static_cast<const char*>(weights), unet_weight_layout(), n, H, W, err};
     size_t aoff[kActs], goff[kGrads], t;
     layout_of<kActs>(kActC, kActLvl, n, H, W, aoff, &t);
     layout_of<kGrads>(kGradC, kGradLvl, n, H, W, goff, &t);
     const char* a = static_cast<const char*>(acts);
     char* g = static_cast<char*>(grad_ws);
+    if (precision == MCDI_DENOISE_E4M3) {
+        const Fp8Region r = fp8_region(t, kBwdIn, n, H, W);
+        u.fp8 = true;
+        u.q = reinterpret_cast<uint8_t*>(g + r.q);
+        u.amax = reinterpret_cast<float*>(g + r.amax);
+        CHECK(cudaMemsetAsync(u.amax, 0, kAmaxSlots * sizeof(float), s));
+    }
     auto A = [&](int k) { return reinterpret_cast<const bf16*>(a + aoff[k]); };
     auto G = [&](int k) { return reinterpret_cast<bf16*>(g + goff[k]); };
     const long long P0 = (long long)n * H * W;
@@ -407,41 +597,41 @@ cudaError_t launch_unet_bwd(const void* weights, int n, int H, int W, const void
         return cudaGetLastError();
     };
     // out (32 -> 3): dgrad through the ReLU of dec1b
-    CHECK(run_conv(u, 0, G(GY), 16, wf_of(u, 14), nullptr, 32, 32, kDgradMask, 0, G(GD1B), 32, 0, nullptr, A(D1B), 32,
+    CHECK(run_conv(u, 0, G(GY), 16, Wsel{14, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1B), 32, 0, nullptr, A(D1B), 32,
                    0, s, why));
-    CHECK(run_conv(u, 0, G(GD1B), 32, wf_of(u, 13), nullptr, 32, 32, kDgradMask, 0, G(GD1A), 32, 0, nullptr, A(D1A),
+    CHECK(run_conv(u, 0, G(GD1B), 32, Wsel{13, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1A), 32, 0, nullptr, A(D1A),
                    32, 0, s, why));
-    CHECK(run_conv(u, 0, G(GD1A), 32, wf_of(u, 12), nullptr, 80, 80, kDgradPlain, 0, G(GCAT1), 80, 0, nullptr,
+    CHECK(run_conv(u, 0, G(GD1A), 32, Wsel{12, true}, nullptr, 80, 80, kDgradPlain, 0, G(GCAT1), 80, 0, nullptr,
                    nullptr, 0, 0, s, why));
     CHECK(up_bwd(G(GCAT1), A(CAT1), 80, 48, 1, G(GD2B)));
-    CHECK(run_conv(u, 1, G(GD2B), 48, wf_of(u, 11), nullptr, 48, 48, kDgradMask, 0, G(GD2A), 48, 0, nullptr, A(D2A),
+    CHECK(run_conv(u, 1, G(GD2B), 48, Wsel{11, true}, nullptr, 48, 48, kDgradMask, 0, G(GD2A), 48, 0, nullptr, A(D2A),
                    48, 0, s, why));
-    CHECK(run_conv(u, 1, G(GD2A), 48, wf_of(u, 10), nullptr, 112, 112, kDgradPlain, 0, G(GCAT2), 112, 0, nullptr,
+    CHECK(run_conv(u, 1, G(GD2A), 48, Wsel{10, true}, nullptr, 112, 112, kDgradPlain, 0, G(GCAT2), 112, 0, nullptr,
                    nullptr, 0, 0, s, why));
     CHECK(up_bwd(G(GCAT2), A(CAT2), 112, 64, 2, G(GD3B)));
-    CHECK(run_conv(u, 2, G(GD3B), 64, wf_of(u, 9), nullptr, 64, 64, kDgradMask, 0, G(GD3A), 64, 0, nullptr, A(D3A),
+    CHECK(run_conv(u, 2, G(GD3B), 64, Wsel{9, true}, nullptr, 64, 64, kDgradMask, 0, G(GD3A), 64, 0, nullptr, A(D3A),
                    64, 0, s, why));
-    CHECK(run_conv(u, 2, G(GD3A), 64, wf_of(u, 8), nullptr, 160, 160, kDgradPlain, 0, G(GCAT3), 160, 0, nullptr,
+    CHECK(run_conv(u, 2, G(GD3A), 64, Wsel{8, true}, nullptr, 160, 160, kDgradPlain, 0, G(GCAT3), 160, 0, nullptr,
                    nullptr, 0, 0, s, why));
     CHECK(up_bwd(G(GCAT3), A(CAT3), 160, 96, 3, G(GB2)));
-    CHECK(run_conv(u, 3, G(GB2), 96, wf_of(u, 7), nullptr, 96, 96, kDgradMask, 0, G(GB1), 96, 0, nullptr, A(B1), 96,
+    CHECK(run_conv(u, 3, G(GB2), 96, Wsel{7, true}, nullptr, 96, 96, kDgradMask, 0, G(GB1), 96, 0, nullptr, A(B1), 96,
                    0, s, why));
-    CHECK(run_conv(u, 3, G(GB1), 96, wf_of(u, 6), nullptr, 64, 64, kDgradPlain, 0, G(GP3), 64, 0, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 3, G(GB1), 96, Wsel{6, true}, nullptr, 64, 64, kDgradPlain, 0, G(GP3), 64, 0, nullptr, nullptr, 0,
                    0, s, why));
     CHECK(pool_bwd(G(GCAT3), A(CAT3), 160, 96, 64, G(GP3), 2, G(GE3)));
-    CHECK(run_conv(u, 2, G(GE3), 64, wf_of(u, 5), nullptr, 64, 64, kDgradMask, 0, G(GA3), 64, 0, nullptr, A(A3), 64,
+    CHECK(run_conv(u, 2, G(GE3), 64, Wsel{5, true}, nullptr, 64, 64, kDgradMask, 0, G(GA3), 64, 0, nullptr, A(A3), 64,
                    0, s, why));
-    CHECK(run_conv(u, 2, G(GA3), 64, wf_of(u, 4), nullptr, 48, 48, kDgradPlain, 0, G(GP2), 48, 0, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 2, G(GA3), 64, Wsel{4, true}, nullptr, 48, 48, kDgradPlain, 0, G(GP2), 48, 0, nullptr, nullptr, 0,
                    0, s, why));
     CHECK(pool_bwd(G(GCAT2), A(CAT2), 112, 64, 48, G(GP2), 1, G(GE2)));
-    CHECK(run_conv(u, 1, G(GE2), 48, wf_of(u, 3), nullptr, 48, 48, kDgradMask, 0, G(GA2), 48, 0, nullptr, A(A2), 48,
+    CHECK(run_conv(u, 1, G(GE2), 48, Wsel{3, true}, nullptr, 48, 48, kDgradMask, 0, G(GA2), 48, 0, nullptr, A(A2), 48,
                    0, s, why));
-    CHECK(run_conv(u, 1, G(GA2), 48, wf_of(u, 2), nullptr, 32, 32, kDgradPlain, 0, G(GP1), 32, 0, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 1, G(GA2), 48, Wsel{2, true}, nullptr, 32, 32, kDgradPlain, 0, G(GP1), 32, 0, nullptr, nullptr, 0,
                    0, s, why));
     CHECK(pool_bwd(G(GCAT1), A(CAT1), 80, 48, 32, G(GP1), 0, G(GE1)));
-    CHECK(run_conv(u, 0, G(GE1), 32, wf_of(u, 1), nullptr, 32, 32, kDgradMask, 0, G(GA1), 32, 0, nullptr, A(A1), 32,
+    CHECK(run_conv(u, 0, G(GE1), 32, Wsel{1, true}, nullptr, 32, 32, kDgradMask, 0, G(GA1), 32, 0, nullptr, A(A1), 32,
                    0, s, why));
-    CHECK(run_conv(u, 0, G(GA1), 32, wf_of(u, 0), nullptr, 16, 16, kDgradPlain, 0, G(GX0), 16, 0, nullptr, nullptr, 0,
+    CHECK(run_conv(u, 0, G(GA1), 32, Wsel{0, true}, nullptr, 16, 16, kDgradPlain, 0, G(GX0), 16, 0, nullptr, nullptr, 0,
                    0, s, why));
     unpack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(G(GX0), n, H * W, reinterpret_cast<float4*>(gx_term));
     return cudaGetLastError();
@@ -449,9 +639,22 @@ cudaError_t launch_unet_bwd(const void* weights, int n, int H, int W, const void
 
 cudaError_t launch_conv3x3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* bias,
                            int cout_pad, int relu, void* y, unsigned* err, cudaStream_t s, const char** why) {
-    Unet u{nullptr, {}, n, H, W, err};
-    return run_conv(u, 0, static_cast<const bf16*>(x), cin_pad, static_cast<const bf16*>(w), bias, cout_pad, cout_pad,
-                    kStore, relu, static_cast<bf16*>(y), cout_pad, 0, nullptr, nullptr, 0, 0, s, why);
+    ConvDesc d = conv_desc(n, H, W, cin_pad, 2 * cin_pad, bias, cout_pad, cout_pad, kStore, relu, static_cast<bf16*>(y),
+                           cout_pad, 0, nullptr, nullptr, 0, 0, err);
+    if (!conv_make_desc(&d, x, w, why)) return cudaErrorInvalidValue;
+    return conv_launch(d, s);
+}
+
+cudaError_t launch_conv3x3_e4m3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* x_amax,
+                                const float* w_amax, const float* bias, int cout_pad, int relu, void* y, unsigned* err,
+                                cudaStream_t s, const char** why) {
+    ConvDesc d = conv_desc(n, H, W, cin_pad, cin_pad, bias, cout_pad, cout_pad, kStore, relu, static_cast<bf16*>(y),
+                           cout_pad, 0, nullptr, nullptr, 0, 0, err);
+    d.p.fp8 = 1;
+    d.p.x_amax = x_amax;
+    d.p.w_amax = w_amax;
+    if (!conv_make_desc(&d, x, w, why)) return cudaErrorInvalidValue;
+    return conv_launch(d, s);
 }
 
 }  // namespace mcdi

@@ -101,20 +101,25 @@ cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float
 constexpr int kUnetConvs = 15;
 struct UnetWeightLayout {
     size_t wk[kUnetConvs], wf[kUnetConvs], bias[kUnetConvs];
+    size_t wk8[kUnetConvs], wf8[kUnetConvs], amax;  // E4M3 forms and per-convolution weight amax
     size_t total;
     size_t n_params;  // fp32 parameters in the plan's order (W[co][ci][3][3], then b[co], per conv)
 };
 UnetWeightLayout unet_weight_layout();
-size_t unet_act_bytes(int n, int H, int W);
-size_t unet_grad_bytes(int n, int H, int W);
+size_t unet_act_bytes(int n, int H, int W, int precision);
+size_t unet_grad_bytes(int n, int H, int W, int precision);
 cudaError_t launch_unet_pack_weights(const float* params, void* weights, cudaStream_t s);
-cudaError_t launch_unet_fwd(const void* weights, int n, int H, int W, const float* term, const float* kd,
-                            const float* nrm, int n_aux, float* y, void* acts, unsigned* err, cudaStream_t s,
+cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, int W, const float* term,
+                            const float* kd, const float* nrm, int n_aux, float* y, void* acts, unsigned* err,
+                            cudaStream_t s, const char** why);
+cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, int W, const void* acts,
+                            const float* gy, float* gx_term, void* grad_ws, unsigned* err, cudaStream_t s,
                             const char** why);
-cudaError_t launch_unet_bwd(const void* weights, int n, int H, int W, const void* acts, const float* gy,
-                            float* gx_term, void* grad_ws, unsigned* err, cudaStream_t s, const char** why);
 cudaError_t launch_conv3x3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* bias,
                            int cout_pad, int relu, void* y, unsigned* err, cudaStream_t s, const char** why);
+cudaError_t launch_conv3x3_e4m3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* x_amax,
+                                const float* w_amax, const float* bias, int cout_pad, int relu, void* y, unsigned* err,
+                                cudaStream_t s, const char** why);
 
 cudaError_t launch_composite(const float* kd, const float* dd, const float* ds, long long n, float* c,
                              cudaStream_t s);

@@ -115,6 +115,28 @@ __device__ __forceinline__ uint64_t noswz_desc(uint32_t saddr, uint32_t lbo) {
     return d;
 }
 
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format code 0),
+// K-major, FP32 D, M x N.
+__host__ __device__ constexpr uint32_t e4m3_idesc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+    if constexpr (FP8)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+}
+
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
 __host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -160,10 +182,10 @@ __device__ __forceinline__ size_t plane_off(int img, int G, int g, int H, int W,
 // bias / activation / mask and store of 16 output channels (two 8-channel
 // groups) of one pixel
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
-                                           const float* bias16) {
+                                           const float* bias16, float dq) {
     float f[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+    for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]) * dq;
     const size_t hw = (size_t)p.H * p.W;
     if (p.mode == kDgradMask || p.mode == kDgradPlain) {
         if (p.mode == kDgradMask) {
@@ -209,6 +231,14 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
     }
 }
 
+// accumulator scale: 1 for BF16; (amax_x / 448) (amax_w / 448) for E4M3
+// operands quantised as round(v 448 / amax)
+__device__ __forceinline__ float dequant_factor(const ConvParams& p) {
+    if (!p.fp8) return 1.0f;
+    return (__ldg(p.x_amax) * (1.0f / 448.0f)) * (__ldg(p.w_amax) * (1.0f / 448.0f));
+}
+
+template <bool FP8>
 __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_x,
                                                                const __grid_constant__ CUtensorMap tmap_w,
                                                                const ConvParams p) {
@@ -231,7 +261,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
     const int ty = tile % p.tiles_y;
     const int img = tile / p.tiles_y;
     const int x0 = tx * p.tw, y0 = ty * p.th;
-    const int cpt = p.cin_pad >> 4;  // channel chunks per tap
+    const int cpt = p.cin_bytes >> 5;  // 32-byte channel chunks (one MMA K-step) per tap
     const int n_chunks = 9 * cpt;
 
     if (threadIdx.x == 0) {
@@ -269,15 +299,15 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
             mbar_expect_tx(fb, a_bytes + b_bytes);
             const int tap = k / cpt, cc = k - tap * cpt;
             const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-            const int plane = img * (p.cin_pad >> 3) + 2 * cc;
+            const int plane = img * (p.cin_bytes >> 4) + 2 * cc;
             tma_load_4d(a_dst, &tmap_x, 0, x0 + dx - 1, y0 + dy - 1, plane, fb);
             tma_load_4d(a_dst + a_bytes / 2, &tmap_x, 0, x0 + dx - 1, y0 + dy - 1, plane + 1, fb);
-            tma_load_2d(a_dst + a_bytes, &tmap_w, tap * p.cin_pad + cc * 16, 0, fb);
+            tma_load_2d(a_dst + a_bytes, &tmap_w, tap * p.cin_bytes + cc * 32, 0, fb);
             issued = k + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
-        const uint32_t idesc = bf16_idesc(128, p.cout_pad);
+        const uint32_t idesc = FP8 ? e4m3_idesc(128, p.cout_pad) : bf16_idesc(128, p.cout_pad);
         int k = 0;
         for (; k < n_chunks; ++k) {
             const int s = k % kStages;
@@ -289,12 +319,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
             tc_fence_after();
             const uint32_t a_src = base + (uint32_t)s * stage_bytes;
             const uint64_t adesc = noswz_desc(a_src, a_bytes / 2), bdesc = sw32_desc(a_src + a_bytes);
-            const uint32_t accum = k > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-                : "memory");
+            mma_issue<FP8>(tmem, adesc, bdesc, idesc, k > 0 ? 1u : 0u);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&empty_bar[s]))
                          : "memory");
@@ -315,11 +340,12 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
     const int xx = m % p.tw, yy = m / p.tw;
     const int x = x0 + xx, y = y0 + yy;
     const bool valid = acc_ok && x < p.W && y < p.H;
+    const float dq = dequant_factor(p);
     for (int c0 = 0; c0 < p.cout_pad; c0 += 16) {
         uint32_t v[16];
         // collective load of 16 accumulator columns of this warp's 32 lanes
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr);
+        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr, dq);
         __syncwarp();
     }
 
@@ -369,7 +395,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int R>
+template <int R, bool FP8>
 __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
     extern __shared__ uint8_t smem_raw[];
@@ -383,7 +409,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t wbase = base + (uint32_t)rp.stages * rp.stage_bytes;
     const int S = rp.stages, Nc = rp.nc;
-    const int n_chunks = p.cin_pad >> 4;
+    const int n_chunks = p.cin_bytes >> 5;
     const uint32_t w_chunk = 9u * (uint32_t)Nc * 32u;  // bytes of one chunk's weights, all taps
     const int slice = blockIdx.x % rp.n_slices;
     const int n0 = slice * Nc;
@@ -441,7 +467,8 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
             const int rows = R + 2;
             const bool mine = lane < 2 * rows;
             const int q = lane / rows, hr = lane - q * rows;
-            const size_t plane_elems = (size_t)p.H * p.W * 8;
+            const size_t plane_bytes = (size_t)p.H * p.W * 16;
+            const uint8_t* x_bytes = reinterpret_cast<const uint8_t*>(p.x);
             int g = 0;
             for (int t = first; t < rp.n_tiles; t += step) {
                 int img, x0, y0;
@@ -479,8 +506,8 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
                     if (lane == 0) mbar_expect_tx(fb, total);
                     __syncwarp();
                     if (n_bytes > 0) {
-                        const __nv_bfloat16* src =
-                            p.x + (size_t)(img * (p.cin_pad >> 3) + 2 * c + q) * plane_elems + ((size_t)y * p.W + xa) * 8;
+                        const uint8_t* src = x_bytes + (size_t)(img * (p.cin_bytes >> 4) + 2 * c + q) * plane_bytes +
+                                             ((size_t)y * p.W + xa) * 16;
                         asm volatile(
                             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                                 row_smem + 16u * (uint32_t)lead),
@@ -495,7 +522,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0 && has_work) {
-            const uint32_t idesc = bf16_idesc(128, Nc);
+            const uint32_t idesc = FP8 ? e4m3_idesc(128, Nc) : bf16_idesc(128, Nc);
             bool ok = mbar_wait(smem_u32(&w_bar), 0u);
             if (!ok) failed = 1;
             int g = 0, i = 0;
@@ -529,12 +556,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             const uint64_t adesc = a0 + (uint64_t)(((r + dy) * kHaloW + dx));
-                            asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                                    d0 + (uint32_t)r * rp.acc_stride),
-                                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(tap > 0 ? 1u : acc0)
-                                : "memory");
+                            mma_issue<FP8>(d0 + (uint32_t)r * rp.acc_stride, adesc, bdesc, idesc, tap > 0 ? 1u : acc0);
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -564,6 +586,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
             int img, x0, y0;
             tile_origin(t, &img, &x0, &y0);
             const int x = x0 + m;
+            const float dq = dequant_factor(p);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int y = y0 + r;
@@ -576,9 +599,9 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
                     tmem_ld16_async(tr + (uint32_t)c0, v);
                     if (two) tmem_ld16_async(tr + (uint32_t)c0 + 16u, v + 16);
                     tmem_wait_ld();
-                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0);
+                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq);
                     if (two && valid && n0 + c0 + 16 < p.cout_valid)
-                        epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16);
+                        epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16, dq);
                     __syncwarp();
                 }
             }
@@ -638,7 +661,8 @@ const DeviceLimits& device_limits() {
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4>) != cudaSuccess || optin <= (int)fa.sharedSizeBytes) {
+            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false>) != cudaSuccess ||
+            optin <= (int)fa.sharedSizeBytes) {
             L.sms = 0;
             return;
         }
@@ -665,7 +689,7 @@ bool plan_rows(const ConvParams& p, RowPlan* out) {
     const int sms = lim.sms;
     if (sms <= 0) return false;
     const uint32_t kSmemMax = lim.rows_smem_max, kAlign = 1024u;
-    const int n_chunks = p.cin_pad / 16;
+    const int n_chunks = p.cin_bytes / 32;
     for (int n_slices = 1; 16 * n_slices <= p.cout_pad; ++n_slices) {
         if (p.cout_pad % (16 * n_slices) != 0) continue;
         const int nc = p.cout_pad / n_slices;
@@ -712,26 +736,28 @@ int conv_pick_tile_w(int W) {
     return tw;
 }
 
-bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w, const char** why) {
+bool conv_make_desc(ConvDesc* d, const void* x, const void* w, const char** why) {
     auto enc = encode_fn(why);
     if (!enc) return false;
     const ConvParams& p = d->p;
-    // activations: 8-channel planes [img * cin_pad / 8 + g][H][W][8]
-    const cuuint64_t xdims[4] = {8, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.n_img * (p.cin_pad / 8)};
+    // The maps move bytes: activations are planes of 16-byte pixel rows
+    // ([img * cin_bytes / 16 + plane][H][W][16 B]), weights are K-major rows
+    // of 9 * cin_bytes bytes, BF16 or E4M3 alike.
+    const cuuint64_t xdims[4] = {16, (cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.n_img * (p.cin_bytes / 16)};
     const cuuint64_t xstr[3] = {16, (cuuint64_t)p.W * 16, (cuuint64_t)p.H * p.W * 16};
-    const cuuint32_t xbox[4] = {8, (cuuint32_t)p.tw, (cuuint32_t)p.th, 1};
+    const cuuint32_t xbox[4] = {16, (cuuint32_t)p.tw, (cuuint32_t)p.th, 1};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
-    CUresult r = enc(&d->tmap_x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(x), xdims, xstr,
-                     xbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&d->tmap_x, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void*>(x), xdims, xstr, xbox, ones,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *why = "activation tensor map rejected by the driver";
         return false;
     }
-    const cuuint64_t wdims[2] = {(cuuint64_t)9 * p.cin_pad, (cuuint64_t)p.cout_pad};
-    const cuuint64_t wstr[1] = {(cuuint64_t)9 * p.cin_pad * 2};
-    const cuuint32_t wbox[2] = {16, (cuuint32_t)p.cout_pad};
-    r = enc(&d->tmap_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(w), wdims, wstr, wbox, ones,
+    const cuuint64_t wdims[2] = {(cuuint64_t)9 * p.cin_bytes, (cuuint64_t)p.cout_pad};
+    const cuuint64_t wstr[1] = {(cuuint64_t)9 * p.cin_bytes};
+    const cuuint32_t wbox[2] = {32, (cuuint32_t)p.cout_pad};
+    r = enc(&d->tmap_w, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(w), wdims, wstr, wbox, ones,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -743,13 +769,14 @@ bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w,
     if (d->rows_form) {
         const RowPlan& rp = d->rp;
         d->p.tiles_y = (p.H + rp.rows - 1) / rp.rows;
-        // The same K-major weights [cout][tap][cin] viewed as (16 channels,
-        // cout, tap, chunk): one box lands in shared memory as [tap][nc][16].
-        const cuuint64_t hdims[4] = {16, (cuuint64_t)p.cout_pad, 9, (cuuint64_t)(p.cin_pad / 16)};
-        const cuuint64_t hstr[3] = {(cuuint64_t)9 * p.cin_pad * 2, (cuuint64_t)p.cin_pad * 2, 32};
-        const cuuint32_t hwbox[4] = {16, (cuuint32_t)rp.nc, 9, 1};
-        r = enc(&d->tmap_wh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w), hdims, hstr, hwbox,
-                ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        // The same K-major weights [cout][tap][cin] viewed as (32 bytes of
+        // channels, cout, tap, chunk): one box lands in shared memory as
+        // [tap][nc][32 B].
+        const cuuint64_t hdims[4] = {32, (cuuint64_t)p.cout_pad, 9, (cuuint64_t)(p.cin_bytes / 32)};
+        const cuuint64_t hstr[3] = {(cuuint64_t)9 * p.cin_bytes, (cuuint64_t)p.cin_bytes, 32};
+        const cuuint32_t hwbox[4] = {32, (cuuint32_t)rp.nc, 9, 1};
+        r = enc(&d->tmap_wh, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void*>(w), hdims, hstr, hwbox, ones,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             *why = "halo weight tensor map rejected by the driver";
@@ -763,27 +790,39 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)conv_smem_bytes(256));
         const int lim = (int)device_limits().rows_smem_max;
-        if (attr_err == cudaSuccess && lim > 0)
-            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        if (attr_err == cudaSuccess && lim > 0)
-            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        if (attr_err == cudaSuccess && lim > 0)
-            attr_err = cudaFuncSetAttribute(conv_tc_rows_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        auto set = [&](const void* f, int bytes) {
+            if (attr_err == cudaSuccess && bytes > 0)
+                attr_err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        };
+        set((const void*)conv_tc_kernel<false>, (int)conv_smem_bytes(256));
+        set((const void*)conv_tc_kernel<true>, (int)conv_smem_bytes(256));
+        set((const void*)conv_tc_rows_kernel<1, false>, lim);
+        set((const void*)conv_tc_rows_kernel<2, false>, lim);
+        set((const void*)conv_tc_rows_kernel<4, false>, lim);
+        set((const void*)conv_tc_rows_kernel<1, true>, lim);
+        set((const void*)conv_tc_rows_kernel<2, true>, lim);
+        set((const void*)conv_tc_rows_kernel<4, true>, lim);
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (d.rows_form) {
         const dim3 g(d.rp.grid), t(kRowThreads);
-        if (d.rp.rows == 4) conv_tc_rows_kernel<4><<<g, t, d.rp.smem_bytes, stream>>>(d.tmap_wh, d.p, d.rp);
-        else if (d.rp.rows == 2) conv_tc_rows_kernel<2><<<g, t, d.rp.smem_bytes, stream>>>(d.tmap_wh, d.p, d.rp);
-        else conv_tc_rows_kernel<1><<<g, t, d.rp.smem_bytes, stream>>>(d.tmap_wh, d.p, d.rp);
+        const size_t sm = d.rp.smem_bytes;
+        if (d.p.fp8) {
+            if (d.rp.rows == 4) conv_tc_rows_kernel<4, true><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+            else if (d.rp.rows == 2) conv_tc_rows_kernel<2, true><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+            else conv_tc_rows_kernel<1, true><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+        } else {
+            if (d.rp.rows == 4) conv_tc_rows_kernel<4, false><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+            else if (d.rp.rows == 2) conv_tc_rows_kernel<2, false><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+            else conv_tc_rows_kernel<1, false><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+        }
         return cudaGetLastError();
     }
     const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;
     const size_t smem = conv_smem_bytes(d.p.cout_pad);
-    conv_tc_kernel<<<n_tiles, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
+    if (d.p.fp8) conv_tc_kernel<true><<<n_tiles, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
+    else conv_tc_kernel<false><<<n_tiles, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
     return cudaGetLastError();
 }
 

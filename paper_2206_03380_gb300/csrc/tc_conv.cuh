@@ -23,12 +23,16 @@ struct ConvParams {
     int n_img, H, W;           // spatial size of input and output (up2: output is 2H x 2W)
     int tw, th;                // pixel tile, tw * th = 128
     int tiles_x, tiles_y;
-    int cin_pad;               // input channels (multiple of 16) = MMA K per tap
+    int cin_pad;               // input channels (multiple of 16 for BF16, of 32 for FP8)
+    int cin_bytes;             // bytes of one pixel's input channels (multiple of 32: one MMA K-step)
+    int fp8;                   // 1: E4M3 operands (kind::f8f6f4), else BF16 (kind::f16)
+    const float* x_amax;       // FP8: device amax of the unquantised input (scale 448 / amax)
+    const float* w_amax;       // FP8: device amax of the unquantised weights
     int cout_pad;              // MMA N (multiple of 16, <= 256)
     int cout_valid;            // channels written
     int mode;
     int relu;
-    const __nv_bfloat16* x;    // input activations (the row-tile form copies halo rows directly)
+    const void* x;             // input activations (the row-tile form copies halo rows directly)
     const float* bias;         // [cout_pad] or null
     __nv_bfloat16* out;        // 8-channel planes, out_ctotal channels
     int out_ctotal, out_coff;
@@ -64,12 +68,13 @@ struct ConvDesc {
     ConvParams p;
 };
 
-// Encodes the tensor maps of a BF16 input (n_img, H, W, cin_pad; 8-channel planes) and a
-// K-major BF16 weight matrix [cout_pad][9 * cin_pad]; for 128-pixel-wide row
+// Encodes the tensor maps of an input (n_img, H, W; planes of 16-byte pixel
+// rows, cin_bytes per pixel) and a K-major weight matrix
+// [cout_pad][9 * cin_bytes bytes]; for 128-pixel-wide row
 // tiles whose weights fit in shared memory it also plans the row-tile form and
 // encodes its maps.  Returns false (with a message) when the driver rejects a
 // map.
-bool conv_make_desc(ConvDesc* d, const __nv_bfloat16* x, const __nv_bfloat16* w, const char** why);
+bool conv_make_desc(ConvDesc* d, const void* x, const void* w, const char** why);
 
 // Runs the persistent row-tile kernel when planned, else one CTA per tile.
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream);

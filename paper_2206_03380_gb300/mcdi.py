@@ -38,7 +38,8 @@ class ShadeParams(C.Structure):
 EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh_sizes", "mcdi_build_bvh",
            "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_workspace_size", "mcdi_shade_mc_fwd",
            "mcdi_shade_mc_bwd", "mcdi_denoise_sizes", "mcdi_denoise_pack_weights", "mcdi_denoise_fwd",
-           "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_composite"]
+           "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite"]
+BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
 
@@ -75,17 +76,19 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
     lib.mcdi_denoise_sizes.restype = st
-    lib.mcdi_denoise_sizes.argtypes = [i, i, i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
+    lib.mcdi_denoise_sizes.argtypes = [i, i, i, i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_denoise_pack_weights.restype = st
     lib.mcdi_denoise_pack_weights.argtypes = [P, P, P]
     lib.mcdi_denoise_fwd.restype = st
-    lib.mcdi_denoise_fwd.argtypes = [P, i, i, i, P, P, P, i, P, P, sz, P, P]
+    lib.mcdi_denoise_fwd.argtypes = [P, i, i, i, i, P, P, P, i, P, P, sz, P, P]
     lib.mcdi_denoise_bwd.restype = st
-    lib.mcdi_denoise_bwd.argtypes = [P, i, i, i, P, sz, P, P, P, sz, P, P]
+    lib.mcdi_denoise_bwd.argtypes = [P, i, i, i, i, P, sz, P, P, P, sz, P, P]
     lib.mcdi_composite.restype = st
     lib.mcdi_composite.argtypes = [P, P, P, C.c_longlong, P, P]
     lib.mcdi_conv3x3_bf16.restype = st
     lib.mcdi_conv3x3_bf16.argtypes = [P, i, i, i, i, P, P, i, i, P, P, P]
+    lib.mcdi_conv3x3_e4m3.restype = st
+    lib.mcdi_conv3x3_e4m3.argtypes = [P, i, i, i, i, P, P, P, P, i, i, P, P, P]
     _lib = lib
     return lib
 
@@ -180,10 +183,10 @@ def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeP
                                     _stream(stream)), "shade_mc_bwd")
 
 
-def denoise_sizes(n_img: int, H: int, W: int):
+def denoise_sizes(n_img: int, H: int, W: int, precision: int = BF16):
     a, b, c, d = C.c_size_t(), C.c_size_t(), C.c_size_t(), C.c_size_t()
-    _check(load().mcdi_denoise_sizes(int(n_img), int(H), int(W), C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
-           "denoise_sizes")
+    _check(load().mcdi_denoise_sizes(int(n_img), int(H), int(W), int(precision), C.byref(a), C.byref(b), C.byref(c),
+                                     C.byref(d)), "denoise_sizes")
     return a.value, b.value, c.value, d.value
 
 
@@ -191,18 +194,19 @@ def denoise_pack_weights(params, weights, stream=None):
     _check(load().mcdi_denoise_pack_weights(_ptr(params), _ptr(weights), _stream(stream)), "denoise_pack_weights")
 
 
-def denoise_fwd(weights, term, kd, nrm, y, acts, err, stream=None):
+def denoise_fwd(weights, term, kd, nrm, y, acts, err, stream=None, precision: int = BF16):
     n, H, W = term.shape[:3]
-    _check(load().mcdi_denoise_fwd(_ptr(weights), n, H, W, _ptr(term), _ptr(kd), _ptr(nrm), kd.shape[0], _ptr(y),
-                                   _ptr(acts), acts.numel() * acts.element_size(), _ptr(err), _stream(stream)),
-           "denoise_fwd")
+    _check(load().mcdi_denoise_fwd(_ptr(weights), int(precision), n, H, W, _ptr(term), _ptr(kd), _ptr(nrm),
+                                   kd.shape[0], _ptr(y), _ptr(acts), acts.numel() * acts.element_size(), _ptr(err),
+                                   _stream(stream)), "denoise_fwd")
 
 
-def denoise_bwd(weights, acts, gy, gx, grad_ws, err, stream=None):
+def denoise_bwd(weights, acts, gy, gx, grad_ws, err, stream=None, precision: int = BF16):
     n, H, W = gy.shape[:3]
-    _check(load().mcdi_denoise_bwd(_ptr(weights), n, H, W, _ptr(acts), acts.numel() * acts.element_size(), _ptr(gy),
-                                   _ptr(gx), _ptr(grad_ws), grad_ws.numel() * grad_ws.element_size(), _ptr(err),
-                                   _stream(stream)), "denoise_bwd")
+    _check(load().mcdi_denoise_bwd(_ptr(weights), int(precision), n, H, W, _ptr(acts),
+                                   acts.numel() * acts.element_size(), _ptr(gy), _ptr(gx), _ptr(grad_ws),
+                                   grad_ws.numel() * grad_ws.element_size(), _ptr(err), _stream(stream)),
+           "denoise_bwd")
 
 
 def composite(kd_out, den_cd, den_cs, c, stream=None):
@@ -216,6 +220,14 @@ def conv3x3_bf16(x, w, bias, y, relu, err, stream=None):
     cin = 8 * g
     _check(load().mcdi_conv3x3_bf16(_ptr(x), n, H, W, cin, _ptr(w), _ptr(bias), w.shape[0], int(bool(relu)), _ptr(y),
                                     _ptr(err), _stream(stream)), "conv3x3_bf16")
+
+
+def conv3x3_e4m3(x, w, x_amax, w_amax, bias, y, relu, err, stream=None):
+    """x: E4M3 codes (uint8) [n][cin/16][H][W][16], w: codes [cout][9][cin], x_amax / w_amax: device float32
+    scalars, y: BF16 [n][cout/8][H][W][8]."""
+    n, g, H, W, _ = x.shape
+    _check(load().mcdi_conv3x3_e4m3(_ptr(x), n, H, W, 16 * g, _ptr(w), _ptr(x_amax), _ptr(w_amax), _ptr(bias),
+                                    w.shape[0], int(bool(relu)), _ptr(y), _ptr(err), _stream(stream)), "conv3x3_e4m3")
 
 
 UNET_PLAN = [("enc1a", 9, 32), ("enc1b", 32, 32), ("enc2a", 32, 48), ("enc2b", 48, 48), ("enc3a", 48, 64),
@@ -239,8 +251,9 @@ class Denoiser:
     """Device-resident denoiser for n_img images of H x W: packed weights, saved
     activations, gradient scratch and the error word."""
 
-    def __init__(self, params_flat, n_img: int, H: int, W: int, device="cuda"):
-        wb, ab, gb, n_params = denoise_sizes(n_img, H, W)
+    def __init__(self, params_flat, n_img: int, H: int, W: int, device="cuda", precision: int = BF16):
+        wb, ab, gb, n_params = denoise_sizes(n_img, H, W, precision)
+        self.precision = precision
         p = torch.as_tensor(params_flat, dtype=torch.float32, device=device).contiguous()
         assert p.numel() == n_params, (p.numel(), n_params)
         self.n_img, self.H, self.W = n_img, H, W
@@ -252,10 +265,10 @@ class Denoiser:
         self._params = p
 
     def forward(self, term, kd, nrm, y, stream=None):
-        denoise_fwd(self.weights, term, kd, nrm, y, self.acts, self.err, stream)
+        denoise_fwd(self.weights, term, kd, nrm, y, self.acts, self.err, stream, self.precision)
 
     def backward(self, gy, gx, stream=None):
-        denoise_bwd(self.weights, self.acts, gy, gx, self.grad_ws, self.err, stream)
+        denoise_bwd(self.weights, self.acts, gy, gx, self.grad_ws, self.err, stream, self.precision)
 
 
 # ------------------------------------------------------------------ device-resident objects

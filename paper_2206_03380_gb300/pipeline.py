@@ -20,7 +20,7 @@ from .scenes import Scene
 class ShadingPipeline:
     def __init__(self, scene: Scene, device="cuda", tau: float = 0.0, ray_eps: float = 1e-4,
                  decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True,
-                 denoiser_params=None):
+                 denoiser_params=None, denoiser_precision=0):
         mcdi.load()
         self.scene = scene
         self.device = torch.device(device)
@@ -48,7 +48,8 @@ class ShadingPipeline:
         self.kd_out = torch.zeros(shape, device=dev)
         self.denoiser = None
         if denoiser_params is not None:
-            self.denoiser = mcdi.Denoiser(denoiser_params, 2 * self.N, self.H, self.W, device=dev)
+            self.denoiser = mcdi.Denoiser(denoiser_params, 2 * self.N, self.H, self.W, device=dev,
+                                          precision=denoiser_precision)
             self.denoised = torch.zeros_like(self.terms)
             self.g_terms = torch.zeros_like(self.terms)
         self.mask = (torch.zeros(self.N, self.H, self.W, (self.spp + 31) // 32, dtype=torch.int32, device=dev)

@@ -119,3 +119,58 @@ def test_bf16_storage_rounds_and_stays_close():
     xr = np.round(np.abs(rng.normal(size=(1, 9, 16, 24))) * 8) / 8
     yr = D.unet_forward(xr, routing_weights(False), storage="bf16").numpy()
     np.testing.assert_array_equal(yr[:, 0], xr[:, 0])
+
+
+# ------------------------------------------------------------------ E4M3 (the FP8 path's quantiser)
+def _e4m3_value(code: int) -> float:
+    """The OCP FP8 E4M3 format written out: sign, 4 exponent bits (bias 7), 3
+    mantissa bits; exponent 0 is subnormal; S.1111.111 is NaN, no infinities."""
+    s = -1.0 if code & 0x80 else 1.0
+    e, m = (code >> 3) & 0xF, code & 0x7
+    if e == 0:
+        return s * (m / 8.0) * 2.0 ** -6
+    return s * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+
+
+def test_e4m3_codes_match_the_format_definition():
+    codes = [c for c in range(256) if (c & 0x7F) != 0x7F]  # 254 finite codes
+    vals = np.array([_e4m3_value(c) for c in codes])
+    dec = torch.tensor(codes, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(dec, vals)
+    assert vals.max() == 448.0 and np.min(np.abs(vals[vals != 0])) == 2.0 ** -9
+    # every finite value is a fixed point of the quantiser at scale 1 (amax = 448)
+    t = torch.tensor(vals)
+    np.testing.assert_array_equal(D.e4m3_quantize(t, 448.0).numpy(), vals)
+
+
+def test_e4m3_quantiser_rounds_to_nearest_even_and_saturates():
+    q = lambda v: D.e4m3_quantize(torch.tensor([v], dtype=torch.float64), 448.0).item()
+    assert q(1.0625) == 1.0      # halfway between 1 and 1.125: even mantissa
+    assert q(1.1875) == 1.25     # halfway between 1.125 and 1.25: even mantissa
+    assert q(17.0) == 16.0 and q(19.0) == 20.0
+    assert q(232.0) == 224.0 and q(248.0) == 256.0
+    assert q(500.0) == 448.0 and q(-1e6) == -448.0
+    assert q(2.0 ** -10) == 0.0 and q(1.5 * 2.0 ** -10) == 2.0 ** -9
+    # per-tensor scale: the largest magnitude maps onto 448 and back onto itself
+    t = torch.tensor([0.3, -2.5, 7.25, 0.0])
+    out = D.e4m3_quantize(t, 7.25).numpy()
+    assert out[2] == pytest.approx(7.25, rel=1e-7) and out[3] == 0.0
+    assert np.all(np.abs(out - t.numpy()) <= 7.25 / 448 * 8 + 1e-12)  # within half a step of the coarsest binade
+    assert np.all(D.e4m3_quantize(t, 0.0).numpy() == 0.0)
+
+
+def test_e4m3_storage_network_stays_close_and_its_gradient_is_straight_through():
+    rng = np.random.default_rng(12)
+    weights = D.xavier_weights(77)
+    x = rng.normal(size=(2, 9, 16, 16))
+    gy = rng.normal(size=(2, 3, 16, 16))
+    y64, gx64, _ = D.unet_forward_backward(x, weights, gy)
+    y8, gx8, _ = D.unet_forward_backward(x, weights, gy, storage="e4m3")
+    yb, gxb, _ = D.unet_forward_backward(x, weights, gy, storage="bf16")
+    e8, eb = D.rel_l2(y8, y64), D.rel_l2(yb, y64)
+    assert eb < e8 < 0.1  # coarser than bfloat16 (3 mantissa bits against 7), still the same network
+    # the input gradient runs through 15 quantised convolutions and as many ReLU masks: coarser still
+    assert D.rel_l2(gxb, gx64) < D.rel_l2(gx8, gx64) < 0.6
+    # the same quantisation twice gives the same result (deterministic emulation)
+    y8b = D.unet_forward(x, weights, storage="e4m3")
+    np.testing.assert_array_equal(y8b.numpy(), y8.numpy())
