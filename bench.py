@@ -32,6 +32,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd MC shading Msamples/s & %HBM roofline at 512² 16spp"
+# DRAM bytes (read + write) per call of a stage's kernels at the headline size, from one ncu capture
+# (profiles/dram_traffic_shade_512x512_16spp.md); set to None when those kernels change.
+MEASURED_TRAFFIC = {"shade_fwd": 279.2e6}
 UNIT = "Msamples/s"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -243,6 +246,20 @@ def run_gpu(args, rank, world):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     e2e_value = total_samples / (e2e_ms * 1e-3) / 1e6
 
+    # the same step captured in one CUDA graph and replayed (one host launch per step)
+    pipe.capture(g_den, g_kdout, None)
+    g_ms = []
+    for k in range(args.steps + 3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pipe.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            g_ms.append(e0.elapsed_time(e1))
+    graph_ms = max_over_ranks(float(np.mean(g_ms)), dev)
+
     # roofline of the dominant kernel (algorithmic bytes per launch / event time)
     avg = {st: float(np.mean(v)) for st, v in stage_ms.items()}
     P = N * H * W
@@ -272,7 +289,7 @@ def run_gpu(args, rank, world):
     else:
         achieved = algo[dom] / (avg[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": None, "peak_source": peak_kind,
+                "frac": round(achieved / peak, 5), "traffic": MEASURED_TRAFFIC.get(dom), "peak_source": peak_kind,
                 "algorithmic_bytes": int(algo[dom])}
     den_tf = {k: round(flops[k] / (avg[k] * 1e-3) / 1e12, 2) for k in flops}
     clocks = clk.summary()
@@ -298,15 +315,61 @@ def run_gpu(args, rank, world):
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
         "gpu_launches": launches,
+        "graph": {"ms_per_step": round(graph_ms, 4), "value": round(total_samples / (graph_ms * 1e-3) / 1e6, 2),
+                  "unit": UNIT, "note": "the timed step captured once in a CUDA graph and replayed"},
     }
     result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
+    if args.batch_steps > 0:
+        del pipe
+        torch.cuda.empty_cache()
+        result["step_batch"] = run_step_batch(args.batch_steps, flush, dev, rank, world)
     if args.serving_requests > 0:
-        del pipe, flush
+        del flush
         torch.cuda.empty_cache()
         result["serving"] = run_serving(args.serving_requests, args.serving_rate, dev, rank)
     return result
+
+
+def run_step_batch(steps, flush, dev, rank, world):
+    """The optimisation-step batch: 8 of 200 views at 800^2, 32 spp, on the union of
+    32 spheres and 32 boxes (256^3 grid, ~1.3M triangles), 2048^2 textures and a
+    1024 x 512 probe; tables, BVH, G-buffer, forward, BF16 denoiser forward and
+    input gradient and the adjoint, captured in one CUDA graph and replayed (L2
+    flushed before each replay)."""
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi, scenes
+    from paper_2206_03380_gb300.pipeline import ShadingPipeline
+
+    sc = scenes.union_step_scene(seed=scenes.BASE_SEED + 4 + 1000 * rank if world > 1 else scenes.BASE_SEED + 4)
+    den = mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
+    pipe = ShadingPipeline(sc, device=dev, denoiser_params=den)
+    rng = np.random.default_rng(5)
+    g = [torch.from_numpy(rng.normal(size=(pipe.N, pipe.H, pipe.W, 4)).astype(np.float32)).to(dev)
+         for _ in range(3)]
+    pipe.capture(*g)
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for k in range(steps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pipe.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            ms.append(e0.elapsed_time(e1))
+    if pipe.denoiser.err.item() != 0:
+        raise RuntimeError("denoiser pipeline wait timed out")
+    samples = pipe.covered_pixels() * sc.spp
+    t = max_over_ranks(float(np.mean(ms)), dev)
+    total = sum_over_ranks(float(samples), dev)
+    return {"workload": sc.name, "views": pipe.N, "width": pipe.W, "height": pipe.H, "spp": sc.spp,
+            "triangles": int(sc.tris.shape[0]), "samples_per_step": int(samples), "ms_per_step": round(t, 3),
+            "value": round(total / (t * 1e-3) / 1e6, 2), "unit": UNIT, "steps": steps,
+            "note": "one CUDA graph replay per step"}
 
 
 def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):
@@ -458,6 +521,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="graph replays of the 8-view 800^2 32-spp step on the ~1.3M-triangle mesh (0: skip)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

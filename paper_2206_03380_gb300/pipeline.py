@@ -104,5 +104,25 @@ class ShadingPipeline:
             g_cd, g_cs = self.g_terms[: self.N], self.g_terms[self.N:]
         self.backward(g_cd, g_kdout, g_cs, stream)
 
+    def capture(self, g_cd, g_kdout, g_cs):
+        """Capture one `step` into a CUDA graph (its launches, memsets and the
+        host-encoded tensor maps are baked in with these buffers); `replay()`
+        then reruns the whole step with one launch from the host.  A first step
+        runs uncaptured on a side stream so that one-time set-up (kernel
+        attributes, device queries) stays outside the graph."""
+        dev = self.device
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            self.step(g_cd, g_kdout, g_cs)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step(g_cd, g_kdout, g_cs)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
     def covered_pixels(self) -> int:
         return int((self.gb.pos[..., 3] > 0).sum().item())

@@ -241,6 +241,66 @@ def box_sdf(center, half):
     return f
 
 
+def _box_normal(p, center, half):
+    """Gradient of the box distance: toward the nearest point outside, the face
+    axis of the largest q inside."""
+    v = p - center
+    q = np.abs(v) - half
+    out = np.maximum(q, 0.0)
+    lo = np.linalg.norm(out, axis=1)
+    n_out = np.sign(v) * out / np.maximum(lo, 1e-12)[:, None]
+    ax = np.argmax(q, axis=1)
+    n_in = np.zeros_like(p)
+    n_in[np.arange(p.shape[0]), ax] = np.sign(v[np.arange(p.shape[0]), ax])
+    return np.where((lo > 0)[:, None], n_out, n_in)
+
+
+def sdf_union_mesh(grid: int, n_spheres: int, n_boxes: int, rng, extent=1.35, spread=0.62):
+    """Marching-tetrahedra mesh of the union of seeded spheres (radii 0.05-0.3) and
+    axis-aligned boxes (half extents 0.04-0.22) on a grid^3 lattice; vertex normals
+    from the gradient of the nearest primitive."""
+    centers = rng.uniform(-spread, spread, size=(n_spheres, 3))
+    radii = rng.uniform(0.05, 0.3, size=n_spheres)
+    bc = rng.uniform(-spread, spread, size=(n_boxes, 3))
+    bh = rng.uniform(0.04, 0.22, size=(n_boxes, 3))
+    boxes = [box_sdf(c, h) for c, h in zip(bc, bh)]
+
+    def normal(p):
+        best = np.full(p.shape[0], np.inf)
+        nrm = np.zeros_like(p)
+        for c, r in zip(centers, radii):
+            v = p - c
+            l = np.linalg.norm(v, axis=1)
+            d = l - r
+            take = d < best
+            best = np.where(take, d, best)
+            nrm[take] = v[take] / np.maximum(l[take], 1e-12)[:, None]
+        for f, c, h in zip(boxes, bc, bh):
+            d = f(p)
+            take = d < best
+            best = np.where(take, d, best)
+            if take.any():
+                nrm[take] = _box_normal(p[take], c, h)
+        return nrm
+
+    # Each primitive is evaluated only inside its bounding box grown by two cells;
+    # elsewhere the field keeps a large positive value.  Marching tetrahedra reads
+    # values only for its sign and, on edges where the sign changes, both corners
+    # lie within a cell of the surface, inside some primitive's window.
+    lin = np.linspace(-extent, extent, grid)
+    cell = lin[1] - lin[0]
+    field_ = np.full((grid, grid, grid), 1e3)
+    prims = [(lambda p, c=c, r=r: np.linalg.norm(p - c, axis=-1) - r, c - r, c + r) for c, r in zip(centers, radii)]
+    prims += [(f, c - h, c + h) for f, c, h in zip(boxes, bc, bh)]
+    idx = lambda v: int(np.clip(np.floor((v + extent) / cell), 0, grid - 1))
+    for f, lo, hi in prims:
+        (x0, y0, z0), (x1, y1, z1) = [[idx(v - 2 * cell) for v in lo], [idx(v + 2 * cell) + 1 for v in hi]]
+        Z, Y, X = np.meshgrid(lin[z0:z1], lin[y0:y1], lin[x0:x1], indexing="ij")
+        sub = f(np.stack([X, Y, Z], axis=-1))
+        field_[z0:z1, y0:y1, x0:x1] = np.minimum(field_[z0:z1, y0:y1, x0:x1], sub)
+    return marching_tetrahedra(field_, -extent, extent, normal)
+
+
 # ------------------------------------------------------------------ probes
 def _dirs_of_texels(W: int, H: int):
     phi = 2.0 * np.pi * (np.arange(W) + 0.5) / W
@@ -394,6 +454,24 @@ def sphere_union_scene(seed: int = BASE_SEED + 2, res: int = 512, spp=(8, 4, 4),
     return Scene(f"sphere-union-{tris.shape[0]}tris-{res}x{res}-{sum(spp)}spp", verts, vnrm, tris, env, kd, korm,
                  np.array([-1.0, -1.0, 0.5], np.float32), cams, res, res, spp[0], spp[1], spp[2], seed,
                  {"lobes": lobes})
+
+
+def union_step_scene(seed: int = BASE_SEED + 4, res: int = 800, spp=(16, 8, 8), grid: int = 256,
+                     n_spheres: int = 32, n_boxes: int = 32, tex: int = 2048, env_wh=(1024, 512),
+                     n_views: int = 8) -> Scene:
+    """Optimisation-step batch: 8 of 200 orbit views at 800^2 and 32 spp (16 light,
+    8 cosine, 8 GGX) of the union of 32 seeded spheres and 32 boxes extracted on a
+    256^3 grid (about a million triangles), 2048^2 value-noise textures and a
+    1024 x 512 probe with sun lobes."""
+    rng = np.random.default_rng(seed)
+    verts, vnrm, tris = sdf_union_mesh(grid, n_spheres, n_boxes, rng)
+    kd, korm = pbr_textures(tex, rng)
+    env, lobes = env_with_lobes(env_wh[0], env_wh[1], rng)
+    pick = sorted(rng.choice(200, size=n_views, replace=False).tolist())
+    cams = orbit_cameras(200, pick, 2.4, 45.0, 1.0, rng)
+    return Scene(f"union-{tris.shape[0]}tris-{n_views}x{res}x{res}-{sum(spp)}spp", verts, vnrm, tris, env, kd, korm,
+                 np.array([-1.0, -1.0, 0.5], np.float32), cams, res, res, spp[0], spp[1], spp[2], seed,
+                 {"lobes": lobes, "views": pick})
 
 
 # ------------------------------------------------------------------ serving stream
