@@ -160,20 +160,21 @@ def run_gpu(args, rank, world):
     pipe = ShadingPipeline(sc, device=dev, denoiser_params=den_params)
     N, H, W = pipe.N, pipe.H, pipe.W
     rng = np.random.default_rng(3)
-    # synthetic upstream gradients: of the loss w.r.t. the denoised terms and k_d,out
-    g_den = torch.from_numpy(rng.normal(size=(2 * N, H, W, 4)).astype(np.float32)).to(dev)
-    g_kdout = torch.from_numpy(rng.normal(size=(N, H, W, 4)).astype(np.float32)).to(dev)
-    g_up = [g_den, g_kdout]
+    # the step is driven by the paper's image loss against a synthetic reference image (positive radiance)
+    ref = torch.from_numpy(np.abs(rng.lognormal(-0.5, 1.0, size=(N, H, W, 4))).astype(np.float32)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    stages = ["probe_cdf", "bvh_build", "primary_cast", "shade_fwd", "denoise_fwd", "denoise_bwd", "shade_bwd"]
-    n_launch = {"probe_cdf": 2, "bvh_build": 3 + 12 + 1 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 1,
-                "shade_fwd": 4, "denoise_fwd": 1 + 15 + 3, "denoise_bwd": 1 + 15 + 3 + 3 + 1, "shade_bwd": 1}
+    stages = ["probe_cdf", "bvh_build", "primary_cast", "shade_fwd", "denoise_fwd", "loss", "denoise_bwd",
+              "shade_bwd"]
+    n_launch = {"probe_cdf": 2, "bvh_build": 3 + 12 + 2 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 1,
+                "shade_fwd": 4, "denoise_fwd": 1 + 15 + 3, "loss": 2, "denoise_bwd": 1 + 15 + 3 + 3 + 1,
+                "shade_bwd": 2}
 
     def one_step(ev=None):
         calls = [pipe.build_probe, pipe.build_bvh, pipe.primary, pipe.forward, pipe.denoise,
-                 lambda: pipe.denoise_backward(g_den),
-                 lambda: pipe.backward(pipe.g_terms[:N], g_kdout, pipe.g_terms[N:])]
+                 lambda: pipe.image_loss(ref),
+                 lambda: pipe.denoise_backward(pipe.g_loss_terms),
+                 lambda: pipe.backward(pipe.g_terms[:N], pipe.g_loss_kdout, pipe.g_terms[N:])]
         for k, f in enumerate(calls):
             if ev is not None:
                 ev[k].record(stream)
@@ -216,10 +217,10 @@ def run_gpu(args, rank, world):
     # e2e: host inputs -> device -> the same step -> host outputs, per step
     host_in = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
                [("verts", sc.verts), ("vnrm", sc.vnrm), ("tris", sc.tris), ("env", sc.env)]}
-    host_g = [g.cpu().pin_memory() for g in g_up]
-    outs_dev = [pipe.denoised, pipe.kd_out, pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env]
+    host_ref = ref.cpu().pin_memory()
+    outs_dev = [pipe.loss, pipe.color, pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env]
     host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs_dev]
-    h2d = sum(t.numel() * t.element_size() for t in list(host_in.values()) + host_g)
+    h2d = sum(t.numel() * t.element_size() for t in list(host_in.values()) + [host_ref])
     d2h = sum(t.numel() * t.element_size() for t in host_out)
 
     def e2e_step():
@@ -227,8 +228,7 @@ def run_gpu(args, rank, world):
         pipe.vnrm.copy_(host_in["vnrm"], non_blocking=True)
         pipe.tris.copy_(host_in["tris"], non_blocking=True)
         pipe.env.copy_(host_in["env"], non_blocking=True)
-        for d, h in zip(g_up, host_g):
-            d.copy_(h, non_blocking=True)
+        ref.copy_(host_ref, non_blocking=True)
         one_step()
         for h, d in zip(host_out, outs_dev):
             h.copy_(d, non_blocking=True)
@@ -247,7 +247,7 @@ def run_gpu(args, rank, world):
     e2e_value = total_samples / (e2e_ms * 1e-3) / 1e6
 
     # the same step captured in one CUDA graph and replayed (one host launch per step)
-    pipe.capture(g_den, g_kdout, None)
+    pipe.capture_loss_step(ref)
     g_ms = []
     for k in range(args.steps + 3):
         flush.zero_()
@@ -335,9 +335,9 @@ def run_gpu(args, rank, world):
 def run_step_batch(steps, flush, dev, rank, world):
     """The optimisation-step batch: 8 of 200 views at 800^2, 32 spp, on the union of
     32 spheres and 32 boxes (256^3 grid, ~1.3M triangles), 2048^2 textures and a
-    1024 x 512 probe; tables, BVH, G-buffer, forward, BF16 denoiser forward and
-    input gradient and the adjoint, captured in one CUDA graph and replayed (L2
-    flushed before each replay)."""
+    1024 x 512 probe; tables, BVH, G-buffer, forward, BF16 denoiser, image loss
+    against a synthetic reference, denoiser input gradient and the adjoint,
+    captured in one CUDA graph and replayed (L2 flushed before each replay)."""
     import torch
 
     from paper_2206_03380_gb300 import mcdi, scenes
@@ -347,9 +347,9 @@ def run_step_batch(steps, flush, dev, rank, world):
     den = mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
     pipe = ShadingPipeline(sc, device=dev, denoiser_params=den)
     rng = np.random.default_rng(5)
-    g = [torch.from_numpy(rng.normal(size=(pipe.N, pipe.H, pipe.W, 4)).astype(np.float32)).to(dev)
-         for _ in range(3)]
-    pipe.capture(*g)
+    ref = torch.from_numpy(np.abs(rng.lognormal(-0.5, 1.0, size=(pipe.N, pipe.H, pipe.W, 4))).astype(np.float32))
+    ref = ref.to(dev)  # the graph reads this buffer: it lives until the replays are done
+    pipe.capture_loss_step(ref)
     stream = torch.cuda.current_stream(dev)
     ms = []
     for k in range(steps + 2):

@@ -261,6 +261,55 @@ MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_
 MCDI_API mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float* den_cs, long long n,
                                     float* c, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Cross-bilateral denoiser (App. C "Bilateral Denoiser": the spatial part of
+ * SVGF, evaluated densely over the footprint; gradients to the colours only):
+ *   c_hat(p) = sum_q c(q) w(p, q) / W(p),  W(p) = sum_q w(p, q)
+ *   w(p, q)  = exp(-|p - q|^2 / (2 sigma^2))
+ *            * exp(-|z(p) - z(q)| / (|grad z(p) . (p - q)| + 1e-3 z(p)))
+ *            * max(0, n(p) . n(q))^128
+ * (sigma_z = 1, sigma_n = 128 as in the paper), q over the square of radius
+ * `radius` (< 0: ceil(2 sigma); at most 8) inside the image.  z = (pos - eye)
+ * . forward of the view's camera, grad z the central difference over covered
+ * neighbours (one-sided at borders and coverage edges), n the normalised
+ * G-buffer normal.  Uncovered pixels (gb_pos.w = 0) pass through and are
+ * never neighbours.
+ * gb_pos, gb_nrm [N][H][W] float4 and cams [N] (device): the guides of N
+ * views; the batch c_in / c_out [n_img][H][W] float4 (rgb; w written 0)
+ * holds n_img = K N images, image i filtered with the guides of view i % N,
+ * 1 <= K <= 4.  wsum [N][H][W] float: W(p) written by the forward, read by
+ * the backward.  mcdi_bilateral_bwd: g_in = dL/dc_in from g_out = dL/dc_hat
+ * (overwritten; deterministic, no atomics).  sigma in (0, 8].
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_bilateral_fwd(const float* gb_pos, const float* gb_nrm, const mcdi_camera* cams, int N,
+                                        int H, int W, int n_img, const float* c_in, float sigma, int radius,
+                                        float* c_out, float* wsum, void* stream);
+MCDI_API mcdi_status mcdi_bilateral_bwd(const float* gb_pos, const float* gb_nrm, const mcdi_camera* cams, int N,
+                                        int H, int W, int n_img, const float* wsum, const float* g_out, float sigma,
+                                        int radius, float* g_in, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Image loss of the optimisation step, fused with the composite and its
+ * adjoint (App. A "Image Loss", "Regularizers"; Sec. 4.2 composite):
+ *   c       = kd_out * den_cd + den_cs
+ *   T(x)    = sRGB(log(max(x, 0) + 1))   (negative radiance clamps to 0)
+ *   L_image = mean over the n pixels and 3 channels of |T(c) - T(ref)|
+ *   L_light = mean over the n pixels of |Y(T(den_cd + den_cs)) - V(T(ref))|,
+ *             Y = (r + g + b) / 3, V = max(r, g, b)
+ *   L       = L_image + lambda_light * L_light      (the paper uses 0.15)
+ * kd_out, den_cd, den_cs, ref: n pixels of float4 (rgb, w ignored).
+ * Outputs: c (nullable) the composite; loss (device, 3 doubles) = (L,
+ * L_image, L_light); g_kdout, g_dcd, g_dcs (overwritten, w = 0) = dL/d of
+ * the three inputs (|0| has zero gradient).  Deterministic: FP64 partial
+ * sums per block in `workspace` (mcdi_image_loss_workspace_size bytes),
+ * added in a fixed order.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_image_loss_workspace_size(long long n, size_t* bytes);
+MCDI_API mcdi_status mcdi_image_loss(const float* kd_out, const float* den_cd, const float* den_cs, const float* ref,
+                                     long long n, float lambda_light, float* c, double* loss, float* g_kdout,
+                                     float* g_dcd, float* g_dcs, void* workspace, size_t workspace_bytes,
+                                     void* stream);
+
 /* One 3x3 convolution layer of the denoiser on its own (same kernels):
  * activations are BF16 in 8-channel planes, the layout the denoiser keeps
  * them in: channel c of pixel (x, y) of image i is element

@@ -321,6 +321,70 @@ mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float
                     "composite");
 }
 
+static mcdi_status bilateral_call(bool backward, const float* gb_pos, const float* gb_nrm, const mcdi_camera* cams,
+                                  int N, int H, int W, int n_img, const float* in, float sigma, int radius,
+                                  const float* wsum_in, float* out, float* wsum_out, void* stream, const char* name) {
+    REQUIRE(N >= 1 && H >= 1 && W >= 1 && (long long)N * H * W <= (1LL << 30), "%s: bad image shape", name);
+    REQUIRE(n_img >= N && n_img % N == 0 && n_img / N <= mcdi::bilateral_max_images_per_view(),
+            "%s: n_img must be K * N with 1 <= K <= %d", name, mcdi::bilateral_max_images_per_view());
+    REQUIRE(sigma > 0.0f && sigma <= 8.0f, "%s: sigma must be in (0, 8]", name);
+    const int R = radius < 0 ? (int)ceilf(2.0f * sigma) : radius;
+    REQUIRE(R >= 0 && R <= 8, "%s: radius must be in [0, 8]", name);
+    REQUIRE_BUF16(gb_pos);
+    REQUIRE_BUF16(gb_nrm);
+    REQUIRE(cams != nullptr, "%s: cams is NULL", name);
+    REQUIRE_BUF16(in);
+    REQUIRE_BUF16(out);
+    REQUIRE((backward ? wsum_in : wsum_out) != nullptr, "%s: wsum is NULL", name);
+    return launched(mcdi::launch_bilateral(backward, gb_pos, gb_nrm, cams, N, H, W, n_img, in, sigma, R, wsum_in, out,
+                                           wsum_out, static_cast<cudaStream_t>(stream)),
+                    name);
+}
+
+mcdi_status mcdi_bilateral_fwd(const float* gb_pos, const float* gb_nrm, const mcdi_camera* cams, int N, int H, int W,
+                               int n_img, const float* c_in, float sigma, int radius, float* c_out, float* wsum,
+                               void* stream) {
+    return bilateral_call(false, gb_pos, gb_nrm, cams, N, H, W, n_img, c_in, sigma, radius, nullptr, c_out, wsum,
+                          stream, "bilateral_fwd");
+}
+
+mcdi_status mcdi_bilateral_bwd(const float* gb_pos, const float* gb_nrm, const mcdi_camera* cams, int N, int H, int W,
+                               int n_img, const float* wsum, const float* g_out, float sigma, int radius, float* g_in,
+                               void* stream) {
+    return bilateral_call(true, gb_pos, gb_nrm, cams, N, H, W, n_img, g_out, sigma, radius, wsum, g_in, nullptr,
+                          stream, "bilateral_bwd");
+}
+
+mcdi_status mcdi_image_loss_workspace_size(long long n, size_t* bytes) {
+    REQUIRE(n >= 1 && n <= (1LL << 31), "n must be in [1, 2^31]");
+    REQUIRE(bytes != nullptr, "bytes must be non-NULL");
+    *bytes = mcdi::image_loss_workspace_bytes(n);
+    return ok();
+}
+
+mcdi_status mcdi_image_loss(const float* kd_out, const float* den_cd, const float* den_cs, const float* ref,
+                            long long n, float lambda_light, float* c, double* loss, float* g_kdout, float* g_dcd,
+                            float* g_dcs, void* workspace, size_t workspace_bytes, void* stream) {
+    size_t need = 0;
+    mcdi_status s = mcdi_image_loss_workspace_size(n, &need);
+    if (s != MCDI_OK) return s;
+    REQUIRE_BUF16(kd_out);
+    REQUIRE_BUF16(den_cd);
+    REQUIRE_BUF16(den_cs);
+    REQUIRE_BUF16(ref);
+    REQUIRE_BUF16(g_kdout);
+    REQUIRE_BUF16(g_dcd);
+    REQUIRE_BUF16(g_dcs);
+    REQUIRE(c == nullptr || ((uintptr_t)c & 15u) == 0, "c must be 16-byte aligned");
+    REQUIRE(loss != nullptr && ((uintptr_t)loss & 7u) == 0, "loss must be 3 device doubles");
+    REQUIRE(lambda_light >= 0.0f, "lambda_light must be >= 0");
+    REQUIRE(workspace != nullptr && ((uintptr_t)workspace & 7u) == 0 && workspace_bytes >= need,
+            "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+    return launched(mcdi::launch_image_loss(kd_out, den_cd, den_cs, ref, n, lambda_light, c, loss, g_kdout, g_dcd,
+                                            g_dcs, workspace, static_cast<cudaStream_t>(stream)),
+                    "image_loss");
+}
+
 mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pad, const void* w, const float* bias,
                               int cout_pad, int relu, void* y, unsigned* err, void* stream) {
     REQUIRE(n_img >= 1 && H >= 1 && W >= 1 && (long long)n_img * H * W <= (1LL << 28), "bad image shape");

@@ -121,6 +121,16 @@ cudaError_t launch_conv3x3_e4m3(const void* x, int n, int H, int W, int cin_pad,
                                 const float* w_amax, const float* bias, int cout_pad, int relu, void* y, unsigned* err,
                                 cudaStream_t s, const char** why);
 
+int bilateral_max_images_per_view();
+cudaError_t launch_bilateral(bool backward, const float* gb_pos, const float* gb_nrm, const mcdi_camera* cams, int N,
+                             int H, int W, int n_img, const float* in, float sigma, int R, const float* wsum_in,
+                             float* out, float* wsum_out, cudaStream_t s);
+
+size_t image_loss_workspace_bytes(long long n);
+cudaError_t launch_image_loss(const float* kd, const float* dd, const float* ds, const float* ref, long long n,
+                              float lambda_light, float* c, double* loss, float* g_kd, float* g_dd, float* g_ds,
+                              void* workspace, cudaStream_t s);
+
 cudaError_t launch_composite(const float* kd, const float* dd, const float* ds, long long n, float* c,
                              cudaStream_t s);
 

@@ -38,7 +38,8 @@ class ShadeParams(C.Structure):
 EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh_sizes", "mcdi_build_bvh",
            "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_workspace_size", "mcdi_shade_mc_fwd",
            "mcdi_shade_mc_bwd", "mcdi_denoise_sizes", "mcdi_denoise_pack_weights", "mcdi_denoise_fwd",
-           "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite"]
+           "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite",
+           "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -87,6 +88,14 @@ def load(path: str = LIB_PATH):
     lib.mcdi_composite.argtypes = [P, P, P, C.c_longlong, P, P]
     lib.mcdi_conv3x3_bf16.restype = st
     lib.mcdi_conv3x3_bf16.argtypes = [P, i, i, i, i, P, P, i, i, P, P, P]
+    lib.mcdi_bilateral_fwd.restype = st
+    lib.mcdi_bilateral_fwd.argtypes = [P, P, P, i, i, i, i, P, C.c_float, i, P, P, P]
+    lib.mcdi_bilateral_bwd.restype = st
+    lib.mcdi_bilateral_bwd.argtypes = [P, P, P, i, i, i, i, P, P, C.c_float, i, P, P]
+    lib.mcdi_image_loss_workspace_size.restype = st
+    lib.mcdi_image_loss_workspace_size.argtypes = [C.c_longlong, C.POINTER(sz)]
+    lib.mcdi_image_loss.restype = st
+    lib.mcdi_image_loss.argtypes = [P, P, P, P, C.c_longlong, C.c_float, P, P, P, P, P, P, sz, P]
     lib.mcdi_conv3x3_e4m3.restype = st
     lib.mcdi_conv3x3_e4m3.argtypes = [P, i, i, i, i, P, P, P, P, i, i, P, P, P]
     _lib = lib
@@ -220,6 +229,38 @@ def conv3x3_bf16(x, w, bias, y, relu, err, stream=None):
     cin = 8 * g
     _check(load().mcdi_conv3x3_bf16(_ptr(x), n, H, W, cin, _ptr(w), _ptr(bias), w.shape[0], int(bool(relu)), _ptr(y),
                                     _ptr(err), _stream(stream)), "conv3x3_bf16")
+
+
+def bilateral_fwd(gb_pos, gb_nrm, cams, c_in, sigma, c_out, wsum, radius=-1, stream=None):
+    """Cross-bilateral filter of the [n_img][H][W] float4 batch c_in with the guides of
+    N views (image i uses view i % N); wsum [N][H][W] float32 receives W(p)."""
+    N, H, W = gb_pos.shape[:3]
+    _check(load().mcdi_bilateral_fwd(_ptr(gb_pos), _ptr(gb_nrm), _ptr(cams), N, H, W, c_in.shape[0], _ptr(c_in),
+                                     float(sigma), int(radius), _ptr(c_out), _ptr(wsum), _stream(stream)),
+           "bilateral_fwd")
+
+
+def bilateral_bwd(gb_pos, gb_nrm, cams, wsum, g_out, sigma, g_in, radius=-1, stream=None):
+    N, H, W = gb_pos.shape[:3]
+    _check(load().mcdi_bilateral_bwd(_ptr(gb_pos), _ptr(gb_nrm), _ptr(cams), N, H, W, g_out.shape[0], _ptr(wsum),
+                                     _ptr(g_out), float(sigma), int(radius), _ptr(g_in), _stream(stream)),
+           "bilateral_bwd")
+
+
+def image_loss_workspace_size(n: int) -> int:
+    b = C.c_size_t()
+    _check(load().mcdi_image_loss_workspace_size(int(n), C.byref(b)), "image_loss_workspace_size")
+    return b.value
+
+
+def image_loss(kd_out, den_cd, den_cs, ref, loss, g_kdout, g_dcd, g_dcs, workspace, lambda_light=0.15, c=None,
+               stream=None):
+    """Fused composite + tonemapped L1 image loss + lighting regulariser and its adjoint.
+    float4 planes of n pixels; loss: device float64 (3,) = (L, L_image, L_light)."""
+    n = kd_out.numel() // 4
+    _check(load().mcdi_image_loss(_ptr(kd_out), _ptr(den_cd), _ptr(den_cs), _ptr(ref), n, float(lambda_light),
+                                  _ptr(c), _ptr(loss), _ptr(g_kdout), _ptr(g_dcd), _ptr(g_dcs), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)), "image_loss")
 
 
 def conv3x3_e4m3(x, w, x_amax, w_amax, bias, y, relu, err, stream=None):

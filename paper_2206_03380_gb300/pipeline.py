@@ -20,7 +20,7 @@ from .scenes import Scene
 class ShadingPipeline:
     def __init__(self, scene: Scene, device="cuda", tau: float = 0.0, ray_eps: float = 1e-4,
                  decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True,
-                 denoiser_params=None, denoiser_precision=0):
+                 denoiser_params=None, denoiser_precision=0, bilateral_sigma=None):
         mcdi.load()
         self.scene = scene
         self.device = torch.device(device)
@@ -47,6 +47,13 @@ class ShadingPipeline:
         self.c_d, self.c_s = self.terms[: self.N], self.terms[self.N:]
         self.kd_out = torch.zeros(shape, device=dev)
         self.denoiser = None
+        self.bilateral_sigma = bilateral_sigma
+        if bilateral_sigma is not None:  # the cross-bilateral denoiser instead of the U-Net
+            assert denoiser_params is None
+            self.denoiser = "bilateral"
+            self.denoised = torch.zeros_like(self.terms)
+            self.g_terms = torch.zeros_like(self.terms)
+            self.bl_wsum = torch.zeros((self.N, self.H, self.W), device=dev)
         if denoiser_params is not None:
             self.denoiser = mcdi.Denoiser(denoiser_params, 2 * self.N, self.H, self.W, device=dev,
                                           precision=denoiser_precision)
@@ -56,6 +63,7 @@ class ShadingPipeline:
                      if keep_mask else None)
         self.g_kd, self.g_korm, self.g_nrm = (torch.zeros(shape, device=dev) for _ in range(3))
         self.g_env = torch.zeros_like(self.env)
+        self._loss = None
         self.workspace = None
         if wavefront:
             nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
@@ -83,11 +91,20 @@ class ShadingPipeline:
                           self.g_kd, self.g_korm, self.g_nrm, self.g_env, stream)
 
     def denoise(self, stream=None):
-        """D(c_d), D(c_s) with k_d,out and the normal as guides (Sec. 4.2)."""
-        self.denoiser.forward(self.terms, self.kd_out, self.gb.nrm, self.denoised, stream)
+        """D(c_d), D(c_s): the U-Net with k_d,out and the normal as guides (Sec. 4.2), or
+        the cross-bilateral filter with depth and normal as edge-stopping guides (App. C)."""
+        if self.bilateral_sigma is not None:
+            mcdi.bilateral_fwd(self.gb.pos, self.gb.nrm, self.cams, self.terms, self.bilateral_sigma, self.denoised,
+                               self.bl_wsum, stream=stream)
+        else:
+            self.denoiser.forward(self.terms, self.kd_out, self.gb.nrm, self.denoised, stream)
 
     def denoise_backward(self, g_denoised, stream=None):
-        self.denoiser.backward(g_denoised, self.g_terms, stream)
+        if self.bilateral_sigma is not None:
+            mcdi.bilateral_bwd(self.gb.pos, self.gb.nrm, self.cams, self.bl_wsum, g_denoised, self.bilateral_sigma,
+                               self.g_terms, stream=stream)
+        else:
+            self.denoiser.backward(g_denoised, self.g_terms, stream)
 
     def step(self, g_cd, g_kdout, g_cs, stream=None):
         """One pass of the hot path: tables, BVH, G-buffer, forward, adjoint.
@@ -104,21 +121,73 @@ class ShadingPipeline:
             g_cd, g_cs = self.g_terms[: self.N], self.g_terms[self.N:]
         self.backward(g_cd, g_kdout, g_cs, stream)
 
+    def loss_step(self, ref, stream=None, lambda_light: float = 0.15):
+        """One optimisation step driven by the paper's image loss against ``ref``
+        ([N][H][W] float4, linear radiance): tables, BVH, G-buffer, forward,
+        denoiser, composite + tonemapped L1 loss + lighting regulariser and their
+        adjoint, denoiser input gradient, shading adjoint.  (L, L_image, L_light)
+        stay on the device in ``self.loss``; the composite is ``self.color``."""
+        self.build_probe(stream)
+        self.build_bvh(stream)
+        self.primary(stream)
+        self.forward(stream)
+        self.loss_and_backward(ref, stream, lambda_light)
+
+    def image_loss(self, ref, stream=None, lambda_light: float = 0.15):
+        """Composite + image loss + lighting regulariser and their adjoint on the
+        denoised terms (the raw terms without a denoiser); gradients land in
+        ``self.g_loss_terms`` ([2N] planes: c_d then c_s) and ``self.g_loss_kdout``."""
+        N = self.N
+        if self._loss is None:
+            dev = self.device
+            self._loss = dict(loss=torch.zeros(3, dtype=torch.float64, device=dev),
+                              g_den=torch.zeros_like(self.terms), g_kdout=torch.zeros_like(self.kd_out),
+                              color=torch.zeros_like(self.kd_out),
+                              ws=torch.empty(mcdi.image_loss_workspace_size(N * self.H * self.W), dtype=torch.uint8,
+                                             device=dev))
+        b = self._loss
+        self.loss, self.color = b["loss"], b["color"]
+        self.g_loss_terms, self.g_loss_kdout = b["g_den"], b["g_kdout"]
+        src = self.denoised if self.denoiser is not None else self.terms
+        mcdi.image_loss(self.kd_out, src[:N], src[N:], ref, b["loss"], b["g_kdout"], b["g_den"][:N], b["g_den"][N:],
+                        b["ws"], lambda_light, b["color"], stream)
+
+    def loss_and_backward(self, ref, stream=None, lambda_light: float = 0.15):
+        """The loss part of `loss_step` (after the forward)."""
+        N = self.N
+        if self.denoiser is not None:
+            self.denoise(stream)
+        self.image_loss(ref, stream, lambda_light)
+        g_cd, g_cs = self.g_loss_terms[:N], self.g_loss_terms[N:]
+        if self.denoiser is not None:
+            self.denoise_backward(self.g_loss_terms, stream)
+            g_cd, g_cs = self.g_terms[:N], self.g_terms[N:]
+        self.backward(g_cd, self.g_loss_kdout, g_cs, stream)
+
     def capture(self, g_cd, g_kdout, g_cs):
-        """Capture one `step` into a CUDA graph (its launches, memsets and the
+        """Capture one `step` (synthetic upstream gradients) into a CUDA graph; see `_capture`."""
+        return self._capture(lambda: self.step(g_cd, g_kdout, g_cs))
+
+    def capture_loss_step(self, ref, lambda_light: float = 0.15):
+        """Capture one `loss_step` against ``ref`` into a CUDA graph; see `_capture`."""
+        return self._capture(lambda: self.loss_step(ref, lambda_light=lambda_light))
+
+    def _capture(self, fn):
+        """Capture one step into a CUDA graph (its launches, memsets and the
         host-encoded tensor maps are baked in with these buffers); `replay()`
         then reruns the whole step with one launch from the host.  A first step
         runs uncaptured on a side stream so that one-time set-up (kernel
-        attributes, device queries) stays outside the graph."""
+        attributes, device queries, lazily allocated buffers) stays outside
+        the graph."""
         dev = self.device
         side = torch.cuda.Stream(dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
-            self.step(g_cd, g_kdout, g_cs)
+            fn()
         torch.cuda.current_stream(dev).wait_stream(side)
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self.step(g_cd, g_kdout, g_cs)
+            fn()
         return self.graph
 
     def replay(self):
