@@ -319,6 +319,7 @@ def run_gpu(args, rank, world):
                   "unit": UNIT, "note": "the timed step captured once in a CUDA graph and replayed"},
     }
     result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
+    result["denoiser_bilateral"] = time_bilateral(pipe, flush, stream, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
     if args.batch_steps > 0:
@@ -370,6 +371,32 @@ def run_step_batch(steps, flush, dev, rank, world):
             "triangles": int(sc.tris.shape[0]), "samples_per_step": int(samples), "ms_per_step": round(t, 3),
             "value": round(total / (t * 1e-3) / 1e6, 2), "unit": UNIT, "steps": steps,
             "note": "one CUDA graph replay per step"}
+
+
+def time_bilateral(pipe, flush, stream, steps, sigma=2.0):
+    """The cross-bilateral denoiser (App. C, sigma = 2: 9 x 9 footprint) on the same two
+    512^2 terms: forward and colour-adjoint times (CUDA events, L2 flushed before each)."""
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi
+
+    y, gx = torch.empty_like(pipe.denoised), torch.empty_like(pipe.denoised)
+    g = torch.ones_like(pipe.denoised)
+    wsum = torch.empty((pipe.N, pipe.H, pipe.W), device=pipe.device)
+    fwd, bwd = [], []
+    for k in range(steps + 3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        flush.zero_()
+        ev[0].record(stream)
+        mcdi.bilateral_fwd(pipe.gb.pos, pipe.gb.nrm, pipe.cams, pipe.terms, sigma, y, wsum, stream=stream)
+        ev[1].record(stream)
+        mcdi.bilateral_bwd(pipe.gb.pos, pipe.gb.nrm, pipe.cams, wsum, g, sigma, gx, stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+    return {"sigma": sigma, "fwd_ms": round(float(np.mean(fwd)), 4), "bwd_ms": round(float(np.mean(bwd)), 4)}
 
 
 def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):

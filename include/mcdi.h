@@ -79,8 +79,9 @@ MCDI_API mcdi_status mcdi_build_envmap_cdf(const float* env, int W, int H, float
  * and the build scratch for n_tris triangles (1 <= n_tris <= 2^27).
  * mcdi_build_bvh: verts [n_verts][3] float, tris [n_tris][3] int32 (vertex
  * indices, checked in range on the device: a bad index yields a degenerate
- * triangle, never an out-of-bounds read).  Writes `nodes` and `tri_records`
- * (opaque layout, valid until the caller frees them); `scratch` is
+ * triangle, never an out-of-bounds read).  Writes `nodes` (256-byte aligned)
+ * and `tri_records` (16-byte aligned), opaque layouts valid until the caller
+ * frees them; `scratch` is
  * overwritten.  Build = Morton codes -> LSD radix sort -> Karras hierarchy ->
  * bottom-up bounds -> a depth-first copy with escape links, which shadow rays
  * traverse without a stack.  Deterministic for a given input.
@@ -262,7 +263,7 @@ MCDI_API mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, co
                                     float* c, void* stream);
 
 /* ------------------------------------------------------------------------
- * Cross-bilateral denoiser (App. C "Bilateral Denoiser": the spatial part of
+ * Cross-bilateral denoiser (App. B "Bilateral Denoiser": the spatial part of
  * SVGF, evaluated densely over the footprint; gradients to the colours only):
  *   c_hat(p) = sum_q c(q) w(p, q) / W(p),  W(p) = sum_q w(p, q)
  *   w(p, q)  = exp(-|p - q|^2 / (2 sigma^2))

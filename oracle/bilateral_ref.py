@@ -1,4 +1,4 @@
-"""Cross-bilateral denoiser (App. C "Bilateral Denoiser": the spatial part of
+"""Cross-bilateral denoiser (App. B "Bilateral Denoiser": the spatial part of
 SVGF evaluated densely in the footprint, gradients to the colours only),
 restated in numpy float64.
 

@@ -1,4 +1,4 @@
-// Cross-bilateral denoiser (App. C "Bilateral Denoiser": the spatial part of
+// Cross-bilateral denoiser (App. B "Bilateral Denoiser": the spatial part of
 // SVGF, evaluated densely over the footprint, gradients to the colours only):
 //   c_hat(p) = sum_q c(q) w(p, q) / W(p),   W(p) = sum_q w(p, q)
 //   w(p, q)  = exp(-|p - q|^2 / (2 sigma^2))
@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(kTile* kTile) bilateral_fwd_kernel(const float
     const size_t pix = (size_t)y * W + x;
     const Center p = center_of(sg, gw, tx + R + 1, ty + R + 1);
     if (p.z < 0.0f) {  // uncovered: pass through
-        for (int k = 0; k < K; ++k) c_out[(size_t)(view + k * N) * plane + pix] = sc[k * cw * cw + (ty + R) * cw + tx + R];
+        for (int k = 0; k < K; ++k) {
+            const float4 c = sc[k * cw * cw + (ty + R) * cw + tx + R];
+            c_out[(size_t)(view + k * N) * plane + pix] = make_float4(c.x, c.y, c.z, 0.0f);
+        }
         wsum[gbase + pix] = 0.0f;
         return;
     }

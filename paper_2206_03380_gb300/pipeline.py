@@ -92,7 +92,7 @@ class ShadingPipeline:
 
     def denoise(self, stream=None):
         """D(c_d), D(c_s): the U-Net with k_d,out and the normal as guides (Sec. 4.2), or
-        the cross-bilateral filter with depth and normal as edge-stopping guides (App. C)."""
+        the cross-bilateral filter with depth and normal as edge-stopping guides (App. B)."""
         if self.bilateral_sigma is not None:
             mcdi.bilateral_fwd(self.gb.pos, self.gb.nrm, self.cams, self.terms, self.bilateral_sigma, self.denoised,
                                self.bl_wsum, stream=stream)

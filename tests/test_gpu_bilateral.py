@@ -1,4 +1,4 @@
-"""The cross-bilateral denoiser (App. C) against its oracle: forward, the saved
+"""The cross-bilateral denoiser (App. B) against its oracle: forward, the saved
 weight sums and the colour adjoint, on G-buffers the oracle rendered itself
 (two views, two images per view), plus the identity limit."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the cross-bilateral denoiser oracle (App. C): limits where the
+"""Pins of the cross-bilateral denoiser oracle (App. B): limits where the
 filter reduces to the identity or to a library Gaussian blur, edge stopping on
 depth and normals, exact depth gradients on planes, and the adjoint by the
 dot-product identity."""
