@@ -36,6 +36,9 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
     } while (0)
 
 #define REQUIRE_BUF16(p) REQUIRE((p) != nullptr && aligned16(p), "%s must be a non-NULL 16-byte aligned device pointer", #p)
+// BVH node arrays are read with 32-byte vector loads
+#define REQUIRE_NODES(p) \
+    REQUIRE((p) != nullptr && ((uintptr_t)(p) & 255u) == 0, "%s must be a non-NULL 256-byte aligned device pointer", #p)
 
 mcdi_status check_params(const mcdi_shade_params* prm) {
     REQUIRE(prm != nullptr, "params is NULL");
@@ -54,7 +57,7 @@ mcdi_status shade_common(const mcdi_bvh_view* bvh, const float* env, int Wp, int
     REQUIRE(bvh != nullptr, "bvh is NULL");
     REQUIRE(bvh->n_tris >= 0, "bvh->n_tris must be >= 0");
     if (bvh->n_tris > 0) {
-        REQUIRE_BUF16(bvh->nodes);
+        REQUIRE_NODES(bvh->nodes);
         REQUIRE_BUF16(bvh->tri_records);
     }
     REQUIRE_BUF16(env);
@@ -136,7 +139,7 @@ mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int
     REQUIRE(n_verts >= 1, "n_verts must be >= 1");
     REQUIRE(verts != nullptr && tris != nullptr, "verts / tris must be non-NULL");
     REQUIRE(((uintptr_t)verts & 3u) == 0 && ((uintptr_t)tris & 3u) == 0, "verts / tris must be 4-byte aligned");
-    REQUIRE_BUF16(nodes);
+    REQUIRE_NODES(nodes);
     REQUIRE_BUF16(tri_records);
     REQUIRE(scratch != nullptr && ((uintptr_t)scratch & 255u) == 0, "scratch must be non-NULL 256-byte aligned");
     const mcdi::BvhScratch L = mcdi::bvh_scratch_layout(n_tris);
@@ -152,7 +155,7 @@ mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* verts, cons
                               float* gb_kd, float* gb_korm, void* stream) {
     REQUIRE(bvh != nullptr && bvh->n_tris >= 0, "bvh is NULL or invalid");
     if (bvh->n_tris > 0) {
-        REQUIRE_BUF16(bvh->nodes);
+        REQUIRE_NODES(bvh->nodes);
         REQUIRE_BUF16(bvh->tri_records);
     }
     REQUIRE(verts && vnrm && tris && n_verts >= 1, "mesh arrays must be non-NULL");

@@ -77,9 +77,9 @@ mcdi_status mcdi_build_bvh_noalloc(const float* verts, int n_verts, const int* t
         return noalloc_fail(MCDI_INVALID_ARG, "verts / tris must be non-NULL and n_verts >= 1");
     if (((uintptr_t)verts & 3u) != 0 || ((uintptr_t)tris & 3u) != 0)
         return noalloc_fail(MCDI_INVALID_ARG, "verts / tris must be 4-byte aligned");
-    if (nodes == nullptr || tri_records == nullptr || ((uintptr_t)nodes & 15u) != 0 ||
+    if (nodes == nullptr || tri_records == nullptr || ((uintptr_t)nodes & 255u) != 0 ||
         ((uintptr_t)tri_records & 15u) != 0)
-        return noalloc_fail(MCDI_INVALID_ARG, "nodes / tri_records must be non-NULL 16-byte aligned device pointers");
+        return noalloc_fail(MCDI_INVALID_ARG, "nodes must be 256-byte aligned, tri_records 16-byte aligned (non-NULL device pointers)");
     const mcdi::BvhScratch L = mcdi::bvh_scratch_layout(n_tris);
     if (L.total > kNoallocScratchBytes) return noalloc_fail(MCDI_INVALID_ARG, "mesh needs more scratch than reserved");
     void* scratch = nullptr;
