@@ -94,6 +94,9 @@ __global__ void __launch_bounds__(kShadeThreads) shade_fwd_kernel(ShadeArgs a, f
                                                                   float4* __restrict__ kd_out,
                                                                   float4* __restrict__ c_s,
                                                                   uint32_t* __restrict__ vis_mask) {
+    extern __shared__ float s_marg[];
+    Probe Pr = make_probe(a);
+    stage_marginal(Pr, s_marg);
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long P = (long long)a.N * a.H * a.W;
     if (idx >= P) return;
@@ -105,7 +108,6 @@ __global__ void __launch_bounds__(kShadeThreads) shade_fwd_kernel(ShadeArgs a, f
     const bool covered = load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
                                     cam_origin(a.cams, view), &px);
     f3 cd = mk(0.f, 0.f, 0.f), cs = cd;
-    const Probe Pr = make_probe(a);
     const BvhNode* nodes = static_cast<const BvhNode*>(a.nodes);
     const TriRecord* tris = static_cast<const TriRecord*>(a.tris);
     uint32_t word = 0;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kShadeThreads) shade_fwd_kernel(ShadeArgs a, f
 }
 
 // ---------------------------------------------------------------- adjoint
-__global__ void __launch_bounds__(kShadeThreads) shade_bwd_kernel(ShadeArgs a, const float4* __restrict__ g_cd,
+__global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a, const float4* __restrict__ g_cd,
                                                                   const float4* __restrict__ g_kdout,
                                                                   const float4* __restrict__ g_cs,
                                                                   const uint32_t* __restrict__ vis_mask,
@@ -154,6 +156,9 @@ __global__ void __launch_bounds__(kShadeThreads) shade_bwd_kernel(ShadeArgs a, c
                                                                   float4* __restrict__ g_korm,
                                                                   float4* __restrict__ g_nrm,
                                                                   float4* __restrict__ g_env) {
+    extern __shared__ float s_marg[];
+    Probe Pr = make_probe(a);
+    stage_marginal(Pr, s_marg);
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long P = (long long)a.N * a.H * a.W;
     if (idx >= P) return;
@@ -173,7 +178,6 @@ __global__ void __launch_bounds__(kShadeThreads) shade_bwd_kernel(ShadeArgs a, c
     }
     const float4 gd4 = g_cd[idx], gk4 = g_kdout[idx], gs4 = g_cs[idx];
     const f3 gd = xyz(gd4), gk = xyz(gk4), gs = xyz(gs4);
-    const Probe Pr = make_probe(a);
     const BvhNode* nodes = static_cast<const BvhNode*>(a.nodes);
     const TriRecord* tris = static_cast<const TriRecord*>(a.tris);
     f3 gn = mk(0.f, 0.f, 0.f), gF0 = gn;
@@ -278,7 +282,8 @@ cudaError_t launch_primary_cast(const void* nodes, const void* tris, int n_tris,
 cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
                              cudaStream_t stream) {
     const long long P = (long long)a.N * a.H * a.W;
-    shade_fwd_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, 0, stream>>>(a, c_d, kd_out, c_s, vis_mask);
+    const size_t smem = (size_t)(a.Hp + 1) * sizeof(float);
+    shade_fwd_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, smem, stream>>>(a, c_d, kd_out, c_s, vis_mask);
     return cudaGetLastError();
 }
 
@@ -286,7 +291,8 @@ cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float
                              const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,
                              cudaStream_t stream) {
     const long long P = (long long)a.N * a.H * a.W;
-    shade_bwd_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, 0, stream>>>(a, g_cd, g_kdout, g_cs, vis_mask,
+    const size_t smem = (size_t)(a.Hp + 1) * sizeof(float);
+    shade_bwd_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, smem, stream>>>(a, g_cd, g_kdout, g_cs, vis_mask,
                                                                                g_kd, g_korm, g_nrm, g_env);
     return cudaGetLastError();
 }

@@ -68,6 +68,7 @@ __global__ void wave_reset_kernel(void* ws, long long slots) {
 // a warp's rays for sample j stay together, so the tracer sees coherent
 // batches and no empty slots.
 __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void* ws, float4* __restrict__ kd_out) {
+    extern __shared__ float s_marg[];
     const long long idx0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
@@ -86,7 +87,8 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
         kd_out[idx] = covered ? make_float4(px.kd.x * (1.f - px.m), px.kd.y * (1.f - px.m),
                                             px.kd.z * (1.f - px.m), 0.f)
                               : make_float4(0.f, 0.f, 0.f, 0.f);
-    const Probe Pr = wave_probe(a);
+    Probe Pr = wave_probe(a);
+    stage_marginal(Pr, s_marg);
     const f3 origin = covered ? px.p + px.n * a.ray_eps : mk(0.f, 0.f, 0.f);
     for (int j = 0; j < spp; ++j) {
         const long long s = (long long)j * P + idx;
@@ -233,7 +235,7 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
     wave_reset_kernel<<<1, 1, 0, stream>>>(ws, P * spp);
-    wave_gen_kernel<<<gblocks, kGenThreads, 0, stream>>>(a, ws, kd_out);
+    wave_gen_kernel<<<gblocks, kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream>>>(a, ws, kd_out);
     int dev = 0, sms = 152, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -75,7 +75,10 @@ __device__ __forceinline__ bool slab_hit(const RayInv& r, float4 lo, float4 hi) 
 // layout: returns the next node index (> i), or -1 when the ray is blocked.
 __device__ __forceinline__ int threaded_step(const ThreadedNode* __restrict__ tn, const TriRecord* __restrict__ tris,
                                              const RayInv& r, int i) {
-    const float4 lo = __ldg(&tn[i].lo), hi = __ldg(&tn[i].hi);
+    float4 lo, hi;  // one 32-byte load (the node array is 256-byte aligned, nodes 32 bytes)
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(tn + i));
     const int skip = __float_as_int(lo.w), tri = __float_as_int(hi.w);
     int next = skip;
     if (slab_hit(r, lo, hi)) {
@@ -154,6 +157,17 @@ __device__ __forceinline__ int upper_index(const float* __restrict__ cdf, int n,
     return lo;
 }
 
+// the same search with generic loads (the marginal lives in shared memory)
+__device__ __forceinline__ int upper_index_generic(const float* cdf, int n, float u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cdf[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // (u, v) -> direction: phi = 2 pi u, theta = pi v, y up
 __device__ __forceinline__ f3 dir_from_uv(float u, float v, float* sin_theta) {
     float sp, cp, st, ct;
@@ -166,10 +180,18 @@ __device__ __forceinline__ f3 dir_from_uv(float u, float v, float* sin_theta) {
 struct Probe {
     const float4* env;
     const float* cond;
-    const float* marg;
+    const float* marg;  // read with generic loads: the kernels stage it in shared memory
     int W, H;
     bool on;  // total > 0
 };
+
+// the marginal CDF (H + 1 floats) copied into the block's shared memory; every
+// thread of the block must call this before any of them returns
+__device__ __forceinline__ void stage_marginal(Probe& P, float* s_marg) {
+    for (int i = threadIdx.x; i <= P.H; i += blockDim.x) s_marg[i] = __ldg(P.marg + i);
+    __syncthreads();
+    P.marg = s_marg;
+}
 
 // probe texel of a direction and sin(theta) (accurate near the poles)
 __device__ __forceinline__ int texel_of_dir(const Probe& P, f3 d, float* sin_theta) {
@@ -188,7 +210,7 @@ __device__ __forceinline__ float pdf_light_texel(const Probe& P, int t, float st
     if (!P.on || !(st > 0.0f)) return 0.0f;
     const int j = t / P.W, i = t - j * P.W;
     const float* c = P.cond + (size_t)j * (P.W + 1);
-    const float wr = __ldg(P.marg + j + 1) - __ldg(P.marg + j);
+    const float wr = P.marg[j + 1] - P.marg[j];
     const float wc = __ldg(c + i + 1) - __ldg(c + i);
     return ((float)P.W * (float)P.H * wr * wc) / (2.0f * MCDI_PI * MCDI_PI * st);
 }
@@ -196,8 +218,8 @@ __device__ __forceinline__ float pdf_light_texel(const Probe& P, int t, float st
 // probe sample; returns false if the technique is off
 __device__ __forceinline__ bool sample_light(const Probe& P, float u0, float u1, f3* d, int* texel, float* pdf) {
     if (!P.on) return false;
-    const int j = upper_index(P.marg, P.H, u0);
-    const float m0 = __ldg(P.marg + j), m1 = __ldg(P.marg + j + 1);
+    const int j = upper_index_generic(P.marg, P.H, u0);
+    const float m0 = P.marg[j], m1 = P.marg[j + 1];
     const float* c = P.cond + (size_t)j * (P.W + 1);
     const int i = upper_index(c, P.W, u1);
     const float c0 = __ldg(c + i), c1 = __ldg(c + i + 1);

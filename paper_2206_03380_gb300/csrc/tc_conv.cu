@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
-// Row-tile form, for images at least 65 pixels wide (128-pixel row tiles).
+// Row-tile form, for images at least 48 pixels wide (128-pixel row tiles).
 // A persistent CTA keeps a slice of Nc output channels of the layer's weights
 // resident in shared memory for its whole life ([chunk][tap][Nc][16 ch],
 // 32-byte swizzle, one TMA load per chunk) and loops over tiles of R output
@@ -730,8 +730,11 @@ size_t conv_smem_bytes(int cout_pad) {
 
 }  // namespace
 
+// 128-pixel row tiles from 48 pixels up (narrower rows would leave most of each
+// tile's MMA rows empty); below that the smallest power of two covering W
 int conv_pick_tile_w(int W) {
-    int tw = 128;
+    if (W >= 48) return 128;
+    int tw = 64;
     while (tw > 8 && tw / 2 >= W) tw /= 2;
     return tw;
 }
