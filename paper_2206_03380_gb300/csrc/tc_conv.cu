@@ -121,21 +121,32 @@ __host__ __device__ constexpr uint32_t e4m3_idesc(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <bool FP8>
+// A-operand collector use: kAPlain reads A from shared memory for this MMA
+// only; kAFill also keeps it in the collector buffer, kAUse takes it from
+// there (same A descriptor), kALast takes it and releases the buffer.
+enum ACollector { kAPlain, kAFill, kAUse, kALast };
+
+#define MCDI_MMA(KIND, COLL)                                                                       \
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"                             \
+                 "tcgen05.mma.cta_group::1.kind::" KIND COLL " [%0], %1, %2, %3, p;\n\t}" ::"r"(d), \
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)                                    \
+                 : "memory")
+
+template <bool FP8, int COLL = kAPlain>
 __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
-    if constexpr (FP8)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-            : "memory");
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-            : "memory");
+    if constexpr (FP8) {
+        if constexpr (COLL == kAFill) MCDI_MMA("f8f6f4", ".collector::a::fill");
+        else if constexpr (COLL == kAUse) MCDI_MMA("f8f6f4", ".collector::a::use");
+        else if constexpr (COLL == kALast) MCDI_MMA("f8f6f4", ".collector::a::lastuse");
+        else MCDI_MMA("f8f6f4", "");
+    } else {
+        if constexpr (COLL == kAFill) MCDI_MMA("f16", ".collector::a::fill");
+        else if constexpr (COLL == kAUse) MCDI_MMA("f16", ".collector::a::use");
+        else if constexpr (COLL == kALast) MCDI_MMA("f16", ".collector::a::lastuse");
+        else MCDI_MMA("f16", "");
+    }
 }
+#undef MCDI_MMA
 
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
 __host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
@@ -549,14 +560,26 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
                     const uint64_t b0 = sw32_desc(wbase + (uint32_t)c * w_chunk);
                     const uint64_t b_step = (uint64_t)((uint32_t)Nc * 2u);  // Nc x 32 bytes per tap, in 16-byte units
                     const uint32_t acc0 = c > 0 ? 1u : 0u;
+                    // MMAs grouped by A window: halo row hr and column shift dx feed output rows
+                    // r = hr - dy for every tap row dy with 0 <= r < R, so the window is read from
+                    // shared memory once (collector fill) and reused by the following MMAs.  The
+                    // first MMA into accumulator r of chunk 0 is (hr = r, dx = 0, dy = 0).
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;
-                        const uint64_t bdesc = b0 + (uint64_t)tap * b_step;
+                    for (int hr = 0; hr < R + 2; ++hr) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const uint64_t adesc = a0 + (uint64_t)(((r + dy) * kHaloW + dx));
-                            mma_issue<FP8>(d0 + (uint32_t)r * rp.acc_stride, adesc, bdesc, idesc, tap > 0 ? 1u : acc0);
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint64_t adesc = a0 + (uint64_t)(hr * kHaloW + dx);
+                            const int dy_lo = hr - R + 1 > 0 ? hr - R + 1 : 0, dy_hi = hr < 2 ? hr : 2;
+#pragma unroll
+                            for (int dy = dy_lo; dy <= dy_hi; ++dy) {
+                                const uint32_t d = d0 + (uint32_t)(hr - dy) * rp.acc_stride;
+                                const uint64_t bdesc = b0 + (uint64_t)(dy * 3 + dx) * b_step;
+                                const uint32_t acc = (dx == 0 && dy == 0) ? acc0 : 1u;
+                                if (dy_lo == dy_hi) mma_issue<FP8, kAPlain>(d, adesc, bdesc, idesc, acc);
+                                else if (dy == dy_lo) mma_issue<FP8, kAFill>(d, adesc, bdesc, idesc, acc);
+                                else if (dy == dy_hi) mma_issue<FP8, kALast>(d, adesc, bdesc, idesc, acc);
+                                else mma_issue<FP8, kAUse>(d, adesc, bdesc, idesc, acc);
+                            }
                         }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
