@@ -112,8 +112,14 @@ __device__ __forceinline__ int closest_hit(const BvhNode* __restrict__ nodes, co
     int sp = 0;
     int node = 0;
     for (int iter = 0; iter < n_tris + 1; ++iter) {
-        const float4 a = __ldg(&nodes[node].a), b = __ldg(&nodes[node].b), c = __ldg(&nodes[node].c);
-        const int4 d = __ldg(&nodes[node].d);
+        float4 a, b, c;  // the 64-byte node as two 32-byte loads (node arrays are 256-byte aligned)
+        int4 d;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+            : "l"(nodes + node));
+        asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w), "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w)
+            : "l"(reinterpret_cast<const char*>(nodes + node) + 32));
         float t0 = slab(r, a, make_float2(c.x, c.y), tbest);
         float t1 = slab(r, b, make_float2(c.z, c.w), tbest);
         if (t0 < FLT_MAX && d.x < 0) {
