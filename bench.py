@@ -74,6 +74,11 @@ def init_dist(backend):
     return rank, world
 
 
+def replica_seed(base: int, rank: int, world: int) -> int:
+    """Seed of a replica's synthetic workload: each rank renders its own scene (weak scaling)."""
+    return base + 1000 * rank if world > 1 else base
+
+
 def barrier():
     import torch.distributed as dist
 
@@ -155,7 +160,7 @@ def run_gpu(args, rank, world):
     local = dist_env()[2]
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = scenes.sphere_union_scene(seed=scenes.BASE_SEED + 2 + 1000 * rank if world > 1 else scenes.BASE_SEED + 2)
+    sc = scenes.sphere_union_scene(seed=replica_seed(scenes.BASE_SEED + 2, rank, world))
     den_params = mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
     pipe = ShadingPipeline(sc, device=dev, denoiser_params=den_params)
     N, H, W = pipe.N, pipe.H, pipe.W
@@ -344,7 +349,7 @@ def run_step_batch(steps, flush, dev, rank, world):
     from paper_2206_03380_gb300 import mcdi, scenes
     from paper_2206_03380_gb300.pipeline import ShadingPipeline
 
-    sc = scenes.union_step_scene(seed=scenes.BASE_SEED + 4 + 1000 * rank if world > 1 else scenes.BASE_SEED + 4)
+    sc = scenes.union_step_scene(seed=replica_seed(scenes.BASE_SEED + 4, rank, world))
     den = mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
     pipe = ShadingPipeline(sc, device=dev, denoiser_params=den)
     rng = np.random.default_rng(5)
