@@ -173,7 +173,7 @@ def run_gpu(args, rank, world):
               "shade_bwd"]
     n_launch = {"probe_cdf": 2, "bvh_build": 3 + 12 + 2 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 1,
                 "shade_fwd": 4, "denoise_fwd": 1 + 15 + 3, "loss": 2, "denoise_bwd": 1 + 15 + 3 + 3 + 1,
-                "shade_bwd": 2}
+                "shade_bwd": 1}
 
     def one_step(ev=None):
         calls = [pipe.build_probe, pipe.build_bvh, pipe.primary, pipe.forward, pipe.denoise,
@@ -434,7 +434,7 @@ def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):
     f, b = float(np.mean(fwd)), float(np.mean(bwd))
     return {"fwd_ms": round(f, 4), "bwd_ms": round(b, 4), "fwd_tflops": round(conv_flops / (f * 1e-3) / 1e12, 2),
             "bwd_tflops": round(conv_flops / (b * 1e-3) / 1e12, 2),
-            "note": "E4M3 operands with per-tensor scaling (amax pass + quantised copy before each convolution)"}
+            "note": "E4M3 operands with per-tensor scaling (amax folded into each producer, quantised copy before each convolution)"}
 
 
 def run_serving(n_requests, rate, dev, rank):

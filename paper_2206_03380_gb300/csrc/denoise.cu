@@ -93,7 +93,8 @@ static const int kFwdIn[kUnetConvs][2] = {{0, 16}, {0, 32}, {1, 32}, {1, 48}, {2
                                           {2, 160}, {2, 64}, {1, 112}, {1, 48}, {0, 80}, {0, 32}, {0, 32}};
 static const int kBwdIn[kUnetConvs][2] = {{0, 16}, {0, 32}, {0, 32}, {1, 48}, {1, 48}, {2, 64}, {2, 64}, {3, 96},
                                           {3, 96}, {2, 64}, {2, 64}, {1, 48}, {1, 48}, {0, 32}, {0, 32}};
-constexpr int kAmaxSlots = 64;
+constexpr int kAmaxSlots = 64;  // one per tensor: an Act (forward) or Grad (backward) index
+static_assert(kActs <= kAmaxSlots && kGrads <= kAmaxSlots, "amax slots");
 
 static size_t e4m3_scratch(const int (*in)[2], int n, int H, int W) {
     size_t m = 0;
@@ -164,29 +165,57 @@ __device__ __forceinline__ void st8(bf16* p, const float* f) {
     *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// max |v| of 8 values about to be stored as BF16, folded into a running max
+__device__ __forceinline__ float max8(float m, const float* f) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) m = fmaxf(m, fabsf(f[c]));
+    return m;
+}
+
+// A thread's running max |value| of what it stored, published for the E4M3
+// consumer of the tensor (float bits in *amax, null in BF16 mode): rounded to
+// BF16 like the stored values (monotonic, so it is the max over the stored
+// tensor), reduced over the warp, one atomic per warp.  Every lane of the
+// warp calls it.
+__device__ __forceinline__ void warp_amax(unsigned* amax, float m) {
+    if (amax == nullptr) return;
+    const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(__bfloat162float(__float2bfloat16_rn(m))));
+    if ((threadIdx.x & 31) == 0 && w) atomicMax(amax, w);
+}
+
 // network input: [term.rgb, k_d.rgb, normal.xyz, 0 x 7] per pixel (16
 // channels, two planes); image i uses guide planes of image i % n_aux
 __global__ void pack_input_kernel(const float4* __restrict__ term, const float4* __restrict__ kd,
-                                  const float4* __restrict__ nrm, int n_img, int n_aux, int HW, bf16* __restrict__ x) {
+                                  const float4* __restrict__ nrm, int n_img, int n_aux, int HW, bf16* __restrict__ x,
+                                  unsigned* amax) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n_img * HW) return;
-    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
-    const long long g = (long long)(img % n_aux) * HW + p;
-    const float4 t = term[i], k = kd[g], n = nrm[g];
-    const float f0[8] = {t.x, t.y, t.z, k.x, k.y, k.z, n.x, n.y}, f1[8] = {n.z, 0, 0, 0, 0, 0, 0, 0};
-    st8(x + (((size_t)img * 2 + 0) * HW + p) * 8, f0);
-    st8(x + (((size_t)img * 2 + 1) * HW + p) * 8, f1);
+    float m = 0.0f;
+    if (i < (long long)n_img * HW) {
+        const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
+        const long long g = (long long)(img % n_aux) * HW + p;
+        const float4 t = term[i], k = kd[g], n = nrm[g];
+        const float f0[8] = {t.x, t.y, t.z, k.x, k.y, k.z, n.x, n.y}, f1[8] = {n.z, 0, 0, 0, 0, 0, 0, 0};
+        st8(x + (((size_t)img * 2 + 0) * HW + p) * 8, f0);
+        st8(x + (((size_t)img * 2 + 1) * HW + p) * 8, f1);
+        m = max8(max8(m, f0), f1);
+    }
+    warp_amax(amax, m);
 }
 
 // upstream gradient (rgb of float4) -> 16-channel BF16 (channels 3..15 zero)
-__global__ void pack_grad_kernel(const float4* __restrict__ gy, int n_img, int HW, bf16* __restrict__ g) {
+__global__ void pack_grad_kernel(const float4* __restrict__ gy, int n_img, int HW, bf16* __restrict__ g,
+                                 unsigned* amax) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n_img * HW) return;
-    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
-    const float4 v = gy[i];
-    const float f0[8] = {v.x, v.y, v.z, 0, 0, 0, 0, 0}, f1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    st8(g + (((size_t)img * 2 + 0) * HW + p) * 8, f0);
-    st8(g + (((size_t)img * 2 + 1) * HW + p) * 8, f1);
+    float m = 0.0f;
+    if (i < (long long)n_img * HW) {
+        const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
+        const float4 v = gy[i];
+        const float f0[8] = {v.x, v.y, v.z, 0, 0, 0, 0, 0}, f1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        st8(g + (((size_t)img * 2 + 0) * HW + p) * 8, f0);
+        st8(g + (((size_t)img * 2 + 1) * HW + p) * 8, f1);
+        m = max8(m, f0);
+    }
+    warp_amax(amax, m);
 }
 
 // input gradient of the network (channels 0..2 = the term) -> float4
@@ -214,66 +243,79 @@ __device__ __forceinline__ bool split_index(long long i, int groups, int H, int 
 
 // 2x2 max-pool of channels [coff, coff + C) of src (Ctot channels, H x W) into dst (C channels)
 __global__ void maxpool2_kernel(const bf16* __restrict__ src, int Ctot, int coff, int C, int n, int H, int W,
-                                bf16* __restrict__ dst) {
+                                bf16* __restrict__ dst, unsigned* amax) {
     const int Ho = H >> 1, Wo = W >> 1;
     int img, g, yo, xo;
-    if (!split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Ho, Wo, &img, &g, &yo, &xo, n)) return;
-    float m[8], v[8];
-    const bf16* s = src + poff(img, Ctot >> 3, (coff >> 3) + g, H, W, 2 * yo, 2 * xo);
-    for (int k = 0; k < 4; ++k) {
-        ld8(s + ((size_t)(k >> 1) * W + (k & 1)) * 8, v);
+    float a = 0.0f;
+    if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Ho, Wo, &img, &g, &yo, &xo, n)) {
+        float m[8], v[8];
+        const bf16* s = src + poff(img, Ctot >> 3, (coff >> 3) + g, H, W, 2 * yo, 2 * xo);
+        for (int k = 0; k < 4; ++k) {
+            ld8(s + ((size_t)(k >> 1) * W + (k & 1)) * 8, v);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) m[c] = k == 0 ? v[c] : fmaxf(m[c], v[c]);
+            for (int c = 0; c < 8; ++c) m[c] = k == 0 ? v[c] : fmaxf(m[c], v[c]);
+        }
+        st8(dst + poff(img, C >> 3, g, Ho, Wo, yo, xo), m);
+        a = max8(a, m);
     }
-    st8(dst + poff(img, C >> 3, g, Ho, Wo, yo, xo), m);
+    warp_amax(amax, a);
 }
 
 // gradient through "nearest 2x upsample then ReLU output": g_low = sum of the
 // 2x2 block of g_cat[0 : C] times [activation > 0], the activation read from
 // the upsampled copy in cat (top-left of the block)
 __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int C, int n,
-                               int Hl, int Wl, bf16* __restrict__ glow) {
+                               int Hl, int Wl, bf16* __restrict__ glow, unsigned* amax) {
     int img, g, y, x;
-    if (!split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Hl, Wl, &img, &g, &y, &x, n)) return;
-    const int H2 = 2 * Hl, W2 = 2 * Wl;
-    const size_t o = poff(img, Ctot >> 3, g, H2, W2, 2 * y, 2 * x);
-    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, v[8], a[8];
-    for (int k = 0; k < 4; ++k) {
-        ld8(gcat + o + ((size_t)(k >> 1) * W2 + (k & 1)) * 8, v);
+    float m = 0.0f;
+    if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Hl, Wl, &img, &g, &y, &x, n)) {
+        const int H2 = 2 * Hl, W2 = 2 * Wl;
+        const size_t o = poff(img, Ctot >> 3, g, H2, W2, 2 * y, 2 * x);
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, v[8], a[8];
+        for (int k = 0; k < 4; ++k) {
+            ld8(gcat + o + ((size_t)(k >> 1) * W2 + (k & 1)) * 8, v);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) s[c] += v[c];
+            for (int c = 0; c < 8; ++c) s[c] += v[c];
+        }
+        ld8(cat + o, a);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s[c] = a[c] > 0.0f ? s[c] : 0.0f;
+        st8(glow + poff(img, C >> 3, g, Hl, Wl, y, x), s);
+        m = max8(m, s);
     }
-    ld8(cat + o, a);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) s[c] = a[c] > 0.0f ? s[c] : 0.0f;
-    st8(glow + poff(img, C >> 3, g, Hl, Wl, y, x), s);
+    warp_amax(amax, m);
 }
 
 // gradient of an encoder output E (stored in cat at channel offset ecoff) that
 // feeds both the skip slice and the 2x2 max-pool: g_E = (g_cat skip slice +
 // pool gradient routed to the window's first maximum) * [E > 0]
 __global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int ecoff,
-                                int C, const bf16* __restrict__ gpool, int n, int H, int W, bf16* __restrict__ gE) {
+                                int C, const bf16* __restrict__ gpool, int n, int H, int W, bf16* __restrict__ gE,
+                                unsigned* amax) {
     int img, g, y, x;
-    if (!split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, H, W, &img, &g, &y, &x, n)) return;
-    const int xo = x >> 1, yo = y >> 1, me = (x & 1) + 2 * (y & 1);
-    const int G = Ctot >> 3, ge = (ecoff >> 3) + g;
-    const size_t w0 = poff(img, G, ge, H, W, 2 * yo, 2 * xo);
-    float win[4][8];
-    for (int k = 0; k < 4; ++k) ld8(cat + w0 + ((size_t)(k >> 1) * W + (k & 1)) * 8, win[k]);
-    float gs[8], gp[8];
-    ld8(gcat + poff(img, G, ge, H, W, y, x), gs);
-    ld8(gpool + poff(img, C >> 3, g, H >> 1, W >> 1, yo, xo), gp);
-    float out[8];
+    float m = 0.0f;
+    if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, H, W, &img, &g, &y, &x, n)) {
+        const int xo = x >> 1, yo = y >> 1, me = (x & 1) + 2 * (y & 1);
+        const int G = Ctot >> 3, ge = (ecoff >> 3) + g;
+        const size_t w0 = poff(img, G, ge, H, W, 2 * yo, 2 * xo);
+        float win[4][8];
+        for (int k = 0; k < 4; ++k) ld8(cat + w0 + ((size_t)(k >> 1) * W + (k & 1)) * 8, win[k]);
+        float gs[8], gp[8];
+        ld8(gcat + poff(img, G, ge, H, W, y, x), gs);
+        ld8(gpool + poff(img, C >> 3, g, H >> 1, W >> 1, yo, xo), gp);
+        float out[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        int arg = 0;
-        for (int k = 1; k < 4; ++k)
-            if (win[k][c] > win[arg][c]) arg = k;
-        const float v = gs[c] + (arg == me ? gp[c] : 0.0f);
-        out[c] = win[me][c] > 0.0f ? v : 0.0f;
+        for (int c = 0; c < 8; ++c) {
+            int arg = 0;
+            for (int k = 1; k < 4; ++k)
+                if (win[k][c] > win[arg][c]) arg = k;
+            const float v = gs[c] + (arg == me ? gp[c] : 0.0f);
+            out[c] = win[me][c] > 0.0f ? v : 0.0f;
+        }
+        st8(gE + poff(img, C >> 3, g, H, W, y, x), out);
+        m = max8(m, out);
     }
-    st8(gE + poff(img, C >> 3, g, H, W, y, x), out);
+    warp_amax(amax, m);
 }
 
 // fp32 [co][ci][3][3] + [co] (the plan's parameters, concatenated) -> packed
@@ -297,20 +339,6 @@ __global__ void pack_weights_kernel(const float* __restrict__ W, const float* __
 }
 
 // ---------------------------------------------------------------- E4M3
-// max |v| of n BF16 values into *amax (float bits; non-negative floats order
-// like their bit patterns)
-__global__ void amax_bf16_kernel(const bf16* __restrict__ x, long long n8, unsigned* __restrict__ amax) {
-    unsigned m = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
-        float f[8];
-        ld8(x + i * 8, f);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) m = max(m, __float_as_uint(fabsf(f[k])));
-    }
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
-}
-
 __device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.0f ? 448.0f / amax : 0.0f; }
 
 // 16 floats -> 16 E4M3 codes (round to nearest even, saturating), one uint4
@@ -384,8 +412,9 @@ struct Unet {
     unsigned* err;
     bool fp8 = false;
     uint8_t* q = nullptr;     // E4M3 copy of the current convolution's input
-    float* amax = nullptr;    // kAmaxSlots slots, zeroed at the start of a pass
-    int slot = 0;             // next free slot
+    float* amax = nullptr;    // one slot per tensor (Act or Grad index), zeroed at the start of a pass
+    // where a producer publishes the amax of tensor k (null in BF16 mode or k < 0)
+    unsigned* out(int k) const { return fp8 && k >= 0 ? reinterpret_cast<unsigned*>(amax + k) : nullptr; }
 };
 
 struct Wsel {  // which packed weights: convolution i, forward or flipped (input gradient)
@@ -435,26 +464,27 @@ static ConvDesc conv_desc(int n, int H, int W, int cin_pad, int cin_bytes, const
     return d;
 }
 
-// One convolution of the network on a BF16 input; in E4M3 mode the input is
-// first quantised (amax pass, then the copy) and the E4M3 weights are used.
-static cudaError_t run_conv(Unet& u, int level, const bf16* x, int cin_pad, Wsel w, const float* bias, int cout_pad,
-                            int cout_valid, int mode, int relu, bf16* out, int out_ctotal, int out_coff,
-                            float4* out_f32, const bf16* mask, int mask_ctotal, int mask_coff, cudaStream_t s,
-                            const char** why) {
+// One convolution of the network on a BF16 input (tensor x_slot, written by
+// producers that published its amax) into tensor out_slot (-1: no E4M3
+// consumer).  In E4M3 mode the input is first quantised with its amax and the
+// E4M3 weights are used.
+static cudaError_t run_conv(Unet& u, int level, const bf16* x, int x_slot, int cin_pad, Wsel w, const float* bias,
+                            int cout_pad, int cout_valid, int mode, int relu, bf16* out, int out_slot, int out_ctotal,
+                            int out_coff, float4* out_f32, const bf16* mask, int mask_ctotal, int mask_coff,
+                            cudaStream_t s, const char** why) {
     const int Hl = u.H >> level, Wl = u.W >> level;
     ConvDesc d = conv_desc(u.n, Hl, Wl, cin_pad, 2 * cin_pad, bias, cout_pad, cout_valid, mode, relu, out, out_ctotal,
                            out_coff, out_f32, mask, mask_ctotal, mask_coff, u.err);
+    d.p.out_amax = u.out(out_slot);
     const void* xin = x;
     const void* win = w.dgrad ? (const void*)wf_of(u, w.i) : (const void*)wk_of(u, w.i);
     if (u.fp8) {
-        if (u.slot >= kAmaxSlots) {
-            *why = "denoiser: out of amax slots";
+        if (x_slot < 0 || x_slot >= kAmaxSlots) {
+            *why = "denoiser: bad amax slot";
             return cudaErrorInvalidValue;
         }
-        float* am = u.amax + u.slot++;
-        const long long n8 = (long long)u.n * Hl * Wl * (cin_pad / 8);
+        const float* am = u.amax + x_slot;
         const int c32 = pad32(cin_pad);
-        amax_bf16_kernel<<<std::min(blocks_for(n8, 256), 2048), 256, 0, s>>>(x, n8, reinterpret_cast<unsigned*>(am));
         quant_e4m3_kernel<<<blocks_for((long long)u.n * (c32 / 16) * Hl * Wl, 256), 256, 0, s>>>(x, cin_pad, u.n,
                                                                                                   Hl * Wl, am, u.q);
         CHECK(cudaGetLastError());
@@ -513,51 +543,52 @@ cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, in
     pack_input_kernel<<<blocks_for(n * HW, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(term),
                                                                reinterpret_cast<const float4*>(kd),
                                                                reinterpret_cast<const float4*>(nrm), n, n_aux,
-                                                               (int)HW, A(X0));
+                                                               (int)HW, A(X0), u.out(X0));
     CHECK(cudaGetLastError());
-    auto pool = [&](const bf16* src, int Ctot, int coff, int C, int level, bf16* dst) {
+    auto pool = [&](const bf16* src, int Ctot, int coff, int C, int level, int dst_slot) {
         const int Hl = H >> level, Wl = W >> level;
         const long long work = (long long)n * (Hl / 2) * (Wl / 2) * (C / 8);
-        maxpool2_kernel<<<blocks_for(work, 256), 256, 0, s>>>(src, Ctot, coff, C, n, Hl, Wl, dst);
+        maxpool2_kernel<<<blocks_for(work, 256), 256, 0, s>>>(src, Ctot, coff, C, n, Hl, Wl, A(dst_slot),
+                                                              u.out(dst_slot));
         return cudaGetLastError();
     };
     // level 0
-    CHECK(run_conv(u, 0, A(X0), 16, Wsel{0, false}, b_of(u, 0), 32, 32, kStore, 1, A(A1), 32, 0, nullptr, nullptr, 0, 0,
-                   s, why));
-    CHECK(run_conv(u, 0, A(A1), 32, Wsel{1, false}, b_of(u, 1), 32, 32, kStore, 1, A(CAT1), 80, 48, nullptr, nullptr, 0,
-                   0, s, why));
-    CHECK(pool(A(CAT1), 80, 48, 32, 0, A(P1)));
+    CHECK(run_conv(u, 0, A(X0), X0, 16, Wsel{0, false}, b_of(u, 0), 32, 32, kStore, 1, A(A1), A1, 32, 0, nullptr,
+                   nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 0, A(A1), A1, 32, Wsel{1, false}, b_of(u, 1), 32, 32, kStore, 1, A(CAT1), CAT1, 80, 48, nullptr,
+                   nullptr, 0, 0, s, why));
+    CHECK(pool(A(CAT1), 80, 48, 32, 0, P1));
     // level 1
-    CHECK(run_conv(u, 1, A(P1), 32, Wsel{2, false}, b_of(u, 2), 48, 48, kStore, 1, A(A2), 48, 0, nullptr, nullptr, 0, 0,
-                   s, why));
-    CHECK(run_conv(u, 1, A(A2), 48, Wsel{3, false}, b_of(u, 3), 48, 48, kStore, 1, A(CAT2), 112, 64, nullptr, nullptr, 0,
-                   0, s, why));
-    CHECK(pool(A(CAT2), 112, 64, 48, 1, A(P2)));
+    CHECK(run_conv(u, 1, A(P1), P1, 32, Wsel{2, false}, b_of(u, 2), 48, 48, kStore, 1, A(A2), A2, 48, 0, nullptr,
+                   nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 1, A(A2), A2, 48, Wsel{3, false}, b_of(u, 3), 48, 48, kStore, 1, A(CAT2), CAT2, 112, 64,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(pool(A(CAT2), 112, 64, 48, 1, P2));
     // level 2
-    CHECK(run_conv(u, 2, A(P2), 48, Wsel{4, false}, b_of(u, 4), 64, 64, kStore, 1, A(A3), 64, 0, nullptr, nullptr, 0, 0,
-                   s, why));
-    CHECK(run_conv(u, 2, A(A3), 64, Wsel{5, false}, b_of(u, 5), 64, 64, kStore, 1, A(CAT3), 160, 96, nullptr, nullptr, 0,
-                   0, s, why));
-    CHECK(pool(A(CAT3), 160, 96, 64, 2, A(P3)));
+    CHECK(run_conv(u, 2, A(P2), P2, 48, Wsel{4, false}, b_of(u, 4), 64, 64, kStore, 1, A(A3), A3, 64, 0, nullptr,
+                   nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 2, A(A3), A3, 64, Wsel{5, false}, b_of(u, 5), 64, 64, kStore, 1, A(CAT3), CAT3, 160, 96,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(pool(A(CAT3), 160, 96, 64, 2, P3));
     // bottleneck (level 3): second conv stores its 2x upsample into the level-2 concatenation
-    CHECK(run_conv(u, 3, A(P3), 64, Wsel{6, false}, b_of(u, 6), 96, 96, kStore, 1, A(B1), 96, 0, nullptr, nullptr, 0, 0,
-                   s, why));
-    CHECK(run_conv(u, 3, A(B1), 96, Wsel{7, false}, b_of(u, 7), 96, 96, kStoreUp2, 1, A(CAT3), 160, 0, nullptr, nullptr,
-                   0, 0, s, why));
+    CHECK(run_conv(u, 3, A(P3), P3, 64, Wsel{6, false}, b_of(u, 6), 96, 96, kStore, 1, A(B1), B1, 96, 0, nullptr,
+                   nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 3, A(B1), B1, 96, Wsel{7, false}, b_of(u, 7), 96, 96, kStoreUp2, 1, A(CAT3), CAT3, 160, 0,
+                   nullptr, nullptr, 0, 0, s, why));
     // decoder
-    CHECK(run_conv(u, 2, A(CAT3), 160, Wsel{8, false}, b_of(u, 8), 64, 64, kStore, 1, A(D3A), 64, 0, nullptr, nullptr,
-                   0, 0, s, why));
-    CHECK(run_conv(u, 2, A(D3A), 64, Wsel{9, false}, b_of(u, 9), 64, 64, kStoreUp2, 1, A(CAT2), 112, 0, nullptr,
-                   nullptr, 0, 0, s, why));
-    CHECK(run_conv(u, 1, A(CAT2), 112, Wsel{10, false}, b_of(u, 10), 48, 48, kStore, 1, A(D2A), 48, 0, nullptr, nullptr,
-                   0, 0, s, why));
-    CHECK(run_conv(u, 1, A(D2A), 48, Wsel{11, false}, b_of(u, 11), 48, 48, kStoreUp2, 1, A(CAT1), 80, 0, nullptr,
-                   nullptr, 0, 0, s, why));
-    CHECK(run_conv(u, 0, A(CAT1), 80, Wsel{12, false}, b_of(u, 12), 32, 32, kStore, 1, A(D1A), 32, 0, nullptr, nullptr,
-                   0, 0, s, why));
-    CHECK(run_conv(u, 0, A(D1A), 32, Wsel{13, false}, b_of(u, 13), 32, 32, kStore, 1, A(D1B), 32, 0, nullptr, nullptr,
-                   0, 0, s, why));
-    CHECK(run_conv(u, 0, A(D1B), 32, Wsel{14, false}, b_of(u, 14), 16, 3, kStoreF32, 0, nullptr, 0, 0,
+    CHECK(run_conv(u, 2, A(CAT3), CAT3, 160, Wsel{8, false}, b_of(u, 8), 64, 64, kStore, 1, A(D3A), D3A, 64, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 2, A(D3A), D3A, 64, Wsel{9, false}, b_of(u, 9), 64, 64, kStoreUp2, 1, A(CAT2), CAT2, 112, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 1, A(CAT2), CAT2, 112, Wsel{10, false}, b_of(u, 10), 48, 48, kStore, 1, A(D2A), D2A, 48, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 1, A(D2A), D2A, 48, Wsel{11, false}, b_of(u, 11), 48, 48, kStoreUp2, 1, A(CAT1), CAT1, 80, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 0, A(CAT1), CAT1, 80, Wsel{12, false}, b_of(u, 12), 32, 32, kStore, 1, A(D1A), D1A, 32, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 0, A(D1A), D1A, 32, Wsel{13, false}, b_of(u, 13), 32, 32, kStore, 1, A(D1B), D1B, 32, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(run_conv(u, 0, A(D1B), D1B, 32, Wsel{14, false}, b_of(u, 14), 16, 3, kStoreF32, 0, nullptr, -1, 0, 0,
                    reinterpret_cast<float4*>(y), nullptr, 0, 0, s, why));
     return cudaSuccess;
 }
@@ -581,58 +612,60 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
     auto A = [&](int k) { return reinterpret_cast<const bf16*>(a + aoff[k]); };
     auto G = [&](int k) { return reinterpret_cast<bf16*>(g + goff[k]); };
     const long long P0 = (long long)n * H * W;
-    pack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(gy), n, H * W, G(GY));
+    pack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(gy), n, H * W, G(GY),
+                                                         u.out(GY));
     CHECK(cudaGetLastError());
-    auto up_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int C, int low_level, bf16* glow) {
+    auto up_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int C, int low_level, int glow) {
         const int Hl = H >> low_level, Wl = W >> low_level;
         const long long work = (long long)n * Hl * Wl * (C / 8);
-        up2_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, C, n, Hl, Wl, glow);
+        up2_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, C, n, Hl, Wl, G(glow), u.out(glow));
         return cudaGetLastError();
     };
     auto pool_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int ecoff, int C, const bf16* gpool, int level,
-                        bf16* gE) {
+                        int gE) {
         const int Hl = H >> level, Wl = W >> level;
         const long long work = (long long)n * Hl * Wl * (C / 8);
-        pool_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, ecoff, C, gpool, n, Hl, Wl, gE);
+        pool_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, ecoff, C, gpool, n, Hl, Wl, G(gE),
+                                                              u.out(gE));
         return cudaGetLastError();
     };
     // out (32 -> 3): dgrad through the ReLU of dec1b
-    CHECK(run_conv(u, 0, G(GY), 16, Wsel{14, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1B), 32, 0, nullptr, A(D1B), 32,
-                   0, s, why));
-    CHECK(run_conv(u, 0, G(GD1B), 32, Wsel{13, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1A), 32, 0, nullptr, A(D1A),
-                   32, 0, s, why));
-    CHECK(run_conv(u, 0, G(GD1A), 32, Wsel{12, true}, nullptr, 80, 80, kDgradPlain, 0, G(GCAT1), 80, 0, nullptr,
+    CHECK(run_conv(u, 0, G(GY), GY, 16, Wsel{14, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1B), GD1B, 32, 0, nullptr,
+                   A(D1B), 32, 0, s, why));
+    CHECK(run_conv(u, 0, G(GD1B), GD1B, 32, Wsel{13, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1A), GD1A, 32, 0,
+                   nullptr, A(D1A), 32, 0, s, why));
+    CHECK(run_conv(u, 0, G(GD1A), GD1A, 32, Wsel{12, true}, nullptr, 80, 80, kDgradPlain, 0, G(GCAT1), -1, 80, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(up_bwd(G(GCAT1), A(CAT1), 80, 48, 1, GD2B));
+    CHECK(run_conv(u, 1, G(GD2B), GD2B, 48, Wsel{11, true}, nullptr, 48, 48, kDgradMask, 0, G(GD2A), GD2A, 48, 0,
+                   nullptr, A(D2A), 48, 0, s, why));
+    CHECK(run_conv(u, 1, G(GD2A), GD2A, 48, Wsel{10, true}, nullptr, 112, 112, kDgradPlain, 0, G(GCAT2), -1, 112, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(up_bwd(G(GCAT2), A(CAT2), 112, 64, 2, GD3B));
+    CHECK(run_conv(u, 2, G(GD3B), GD3B, 64, Wsel{9, true}, nullptr, 64, 64, kDgradMask, 0, G(GD3A), GD3A, 64, 0,
+                   nullptr, A(D3A), 64, 0, s, why));
+    CHECK(run_conv(u, 2, G(GD3A), GD3A, 64, Wsel{8, true}, nullptr, 160, 160, kDgradPlain, 0, G(GCAT3), -1, 160, 0,
+                   nullptr, nullptr, 0, 0, s, why));
+    CHECK(up_bwd(G(GCAT3), A(CAT3), 160, 96, 3, GB2));
+    CHECK(run_conv(u, 3, G(GB2), GB2, 96, Wsel{7, true}, nullptr, 96, 96, kDgradMask, 0, G(GB1), GB1, 96, 0, nullptr,
+                   A(B1), 96, 0, s, why));
+    CHECK(run_conv(u, 3, G(GB1), GB1, 96, Wsel{6, true}, nullptr, 64, 64, kDgradPlain, 0, G(GP3), -1, 64, 0, nullptr,
                    nullptr, 0, 0, s, why));
-    CHECK(up_bwd(G(GCAT1), A(CAT1), 80, 48, 1, G(GD2B)));
-    CHECK(run_conv(u, 1, G(GD2B), 48, Wsel{11, true}, nullptr, 48, 48, kDgradMask, 0, G(GD2A), 48, 0, nullptr, A(D2A),
-                   48, 0, s, why));
-    CHECK(run_conv(u, 1, G(GD2A), 48, Wsel{10, true}, nullptr, 112, 112, kDgradPlain, 0, G(GCAT2), 112, 0, nullptr,
+    CHECK(pool_bwd(G(GCAT3), A(CAT3), 160, 96, 64, G(GP3), 2, GE3));
+    CHECK(run_conv(u, 2, G(GE3), GE3, 64, Wsel{5, true}, nullptr, 64, 64, kDgradMask, 0, G(GA3), GA3, 64, 0, nullptr,
+                   A(A3), 64, 0, s, why));
+    CHECK(run_conv(u, 2, G(GA3), GA3, 64, Wsel{4, true}, nullptr, 48, 48, kDgradPlain, 0, G(GP2), -1, 48, 0, nullptr,
                    nullptr, 0, 0, s, why));
-    CHECK(up_bwd(G(GCAT2), A(CAT2), 112, 64, 2, G(GD3B)));
-    CHECK(run_conv(u, 2, G(GD3B), 64, Wsel{9, true}, nullptr, 64, 64, kDgradMask, 0, G(GD3A), 64, 0, nullptr, A(D3A),
-                   64, 0, s, why));
-    CHECK(run_conv(u, 2, G(GD3A), 64, Wsel{8, true}, nullptr, 160, 160, kDgradPlain, 0, G(GCAT3), 160, 0, nullptr,
+    CHECK(pool_bwd(G(GCAT2), A(CAT2), 112, 64, 48, G(GP2), 1, GE2));
+    CHECK(run_conv(u, 1, G(GE2), GE2, 48, Wsel{3, true}, nullptr, 48, 48, kDgradMask, 0, G(GA2), GA2, 48, 0, nullptr,
+                   A(A2), 48, 0, s, why));
+    CHECK(run_conv(u, 1, G(GA2), GA2, 48, Wsel{2, true}, nullptr, 32, 32, kDgradPlain, 0, G(GP1), -1, 32, 0, nullptr,
                    nullptr, 0, 0, s, why));
-    CHECK(up_bwd(G(GCAT3), A(CAT3), 160, 96, 3, G(GB2)));
-    CHECK(run_conv(u, 3, G(GB2), 96, Wsel{7, true}, nullptr, 96, 96, kDgradMask, 0, G(GB1), 96, 0, nullptr, A(B1), 96,
-                   0, s, why));
-    CHECK(run_conv(u, 3, G(GB1), 96, Wsel{6, true}, nullptr, 64, 64, kDgradPlain, 0, G(GP3), 64, 0, nullptr, nullptr, 0,
-                   0, s, why));
-    CHECK(pool_bwd(G(GCAT3), A(CAT3), 160, 96, 64, G(GP3), 2, G(GE3)));
-    CHECK(run_conv(u, 2, G(GE3), 64, Wsel{5, true}, nullptr, 64, 64, kDgradMask, 0, G(GA3), 64, 0, nullptr, A(A3), 64,
-                   0, s, why));
-    CHECK(run_conv(u, 2, G(GA3), 64, Wsel{4, true}, nullptr, 48, 48, kDgradPlain, 0, G(GP2), 48, 0, nullptr, nullptr, 0,
-                   0, s, why));
-    CHECK(pool_bwd(G(GCAT2), A(CAT2), 112, 64, 48, G(GP2), 1, G(GE2)));
-    CHECK(run_conv(u, 1, G(GE2), 48, Wsel{3, true}, nullptr, 48, 48, kDgradMask, 0, G(GA2), 48, 0, nullptr, A(A2), 48,
-                   0, s, why));
-    CHECK(run_conv(u, 1, G(GA2), 48, Wsel{2, true}, nullptr, 32, 32, kDgradPlain, 0, G(GP1), 32, 0, nullptr, nullptr, 0,
-                   0, s, why));
-    CHECK(pool_bwd(G(GCAT1), A(CAT1), 80, 48, 32, G(GP1), 0, G(GE1)));
-    CHECK(run_conv(u, 0, G(GE1), 32, Wsel{1, true}, nullptr, 32, 32, kDgradMask, 0, G(GA1), 32, 0, nullptr, A(A1), 32,
-                   0, s, why));
-    CHECK(run_conv(u, 0, G(GA1), 32, Wsel{0, true}, nullptr, 16, 16, kDgradPlain, 0, G(GX0), 16, 0, nullptr, nullptr, 0,
-                   0, s, why));
+    CHECK(pool_bwd(G(GCAT1), A(CAT1), 80, 48, 32, G(GP1), 0, GE1));
+    CHECK(run_conv(u, 0, G(GE1), GE1, 32, Wsel{1, true}, nullptr, 32, 32, kDgradMask, 0, G(GA1), GA1, 32, 0, nullptr,
+                   A(A1), 32, 0, s, why));
+    CHECK(run_conv(u, 0, G(GA1), GA1, 32, Wsel{0, true}, nullptr, 16, 16, kDgradPlain, 0, G(GX0), GX0, 16, 0, nullptr,
+                   nullptr, 0, 0, s, why));
     unpack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(G(GX0), n, H * W, reinterpret_cast<float4*>(gx_term));
     return cudaGetLastError();
 }

@@ -193,7 +193,7 @@ __device__ __forceinline__ size_t plane_off(int img, int G, int g, int H, int W,
 // bias / activation / mask and store of 16 output channels (two 8-channel
 // groups) of one pixel
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
-                                           const float* bias16, float dq) {
+                                           const float* bias16, float dq, float* amax) {
     float f[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]) * dq;
@@ -211,6 +211,8 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
                 if (!(__bfloat162float(h.y) > 0.0f)) f[2 * i + 1] = 0.0f;
             }
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) *amax = fmaxf(*amax, fabsf(f[i]));
         __nv_bfloat16* o = p.out + plane_off(img, p.out_ctotal >> 3, (p.out_coff + c0) >> 3, p.H, p.W, y, x);
         store8_bf16(o, f);
         store8_bf16(o + hw * 8, f + 8);
@@ -220,6 +222,7 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
     for (int i = 0; i < 16; ++i) {
         f[i] += bias16 ? bias16[i] : 0.0f;
         if (p.relu) f[i] = fmaxf(f[i], 0.0f);
+        *amax = fmaxf(*amax, fabsf(f[i]));
     }
     if (p.mode == kStoreF32) {
         p.out_f32[((size_t)img * p.H + y) * p.W + x] = make_float4(f[0], f[1], f[2], 0.0f);
@@ -240,6 +243,16 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
         store8_bf16(o, f);
         store8_bf16(o + hw * 8, f + 8);
     }
+}
+
+// Publish a thread's running max |value| of the stored output: rounded to BF16
+// like the stored values (rounding is monotonic, so this is the max over the
+// stored tensor), reduced over the warp, one atomic per warp.
+__device__ __forceinline__ void publish_amax(unsigned* out_amax, float m, unsigned mask) {
+    if (out_amax == nullptr) return;
+    const unsigned b = __float_as_uint(__bfloat162float(__float2bfloat16_rn(m)));
+    const unsigned w = __reduce_max_sync(mask, b);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1 && w) atomicMax(out_amax, w);
 }
 
 // accumulator scale: 1 for BF16; (amax_x / 448) (amax_w / 448) for E4M3
@@ -352,13 +365,15 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
     const int x = x0 + xx, y = y0 + yy;
     const bool valid = acc_ok && x < p.W && y < p.H;
     const float dq = dequant_factor(p);
+    float amax = 0.0f;
     for (int c0 = 0; c0 < p.cout_pad; c0 += 16) {
         uint32_t v[16];
         // collective load of 16 accumulator columns of this warp's 32 lanes
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr, dq);
+        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr, dq, &amax);
         __syncwarp();
     }
+    publish_amax(p.out_amax, amax, 0xffffffffu);
 
     // ---- teardown
     tc_fence_before();
@@ -596,6 +611,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
     } else {
         const int q = warp & 3;
         const int m = q * 32 + lane;
+        float amax = 0.0f;
         int i = 0;
         for (int t = first; t < rp.n_tiles; t += step, ++i) {
             const int b = i & 1;
@@ -622,9 +638,9 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
                     tmem_ld16_async(tr + (uint32_t)c0, v);
                     if (two) tmem_ld16_async(tr + (uint32_t)c0 + 16u, v + 16);
                     tmem_wait_ld();
-                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq);
+                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax);
                     if (two && valid && n0 + c0 + 16 < p.cout_valid)
-                        epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16, dq);
+                        epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16, dq, &amax);
                     __syncwarp();
                 }
             }
@@ -632,6 +648,7 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
         }
+        publish_amax(p.out_amax, amax, 0xffffffffu);
     }
 
     tc_fence_before();

@@ -40,6 +40,7 @@ struct ConvParams {
     const __nv_bfloat16* mask; // 8-channel planes, same spatial size as the output
     int mask_ctotal, mask_coff;
     unsigned* err;             // device error word (set on a wait timeout)
+    unsigned* out_amax;        // nullable: max |stored value| of the output (float bits), for E4M3 consumers
 };
 
 // Launch plan of the row-tile form (tiles of `rows` x 128 pixels, weights of
