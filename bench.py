@@ -325,6 +325,7 @@ def run_gpu(args, rank, world):
     }
     result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
     result["denoiser_bilateral"] = time_bilateral(pipe, flush, stream, args.steps)
+    result["shadow_rays"] = shadow_ray_figures(pipe, flush, stream, args.steps, samples_per_step)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
     if args.batch_steps > 0:
@@ -379,7 +380,7 @@ def run_step_batch(steps, flush, dev, rank, world):
 
 
 def time_bilateral(pipe, flush, stream, steps, sigma=2.0):
-    """The cross-bilateral denoiser (App. C, sigma = 2: 9 x 9 footprint) on the same two
+    """The cross-bilateral denoiser (App. B, sigma = 2: 9 x 9 footprint) on the same two
     512^2 terms: forward and colour-adjoint times (CUDA events, L2 flushed before each)."""
     import torch
 
@@ -402,6 +403,68 @@ def time_bilateral(pipe, flush, stream, steps, sigma=2.0):
             fwd.append(ev[0].elapsed_time(ev[1]))
             bwd.append(ev[1].elapsed_time(ev[2]))
     return {"sigma": sigma, "fwd_ms": round(float(np.mean(fwd)), 4), "bwd_ms": round(float(np.mean(bwd)), 4)}
+
+
+# per-test FP32 operations of the traversal, counted from the source: a slab
+# test is 6 subtracts + 6 multiplies + 11 min/max + 1 multiply + 1 compare; a
+# two-sided Moller-Trumbore test that runs to the end is 2 cross products (9 ops
+# each), 4 dot products (5 each), 1 reciprocal, 3 subtracts, 3 multiplies,
+# 1 add and 6 compares (early outs make it shorter: an upper bound)
+SLAB_OPS, TRI_OPS = 25, 52
+NODE_BYTES, TRI_BYTES, RAY_BYTES = 32, 48, 32
+
+
+def shadow_ray_figures(pipe, flush, stream, steps, samples):
+    """The shadow-ray tracer of the forward pass timed alone (CUDA events, L2
+    flushed before each launch) and its counters: node visits and triangle
+    tests per ray, the bytes it requests from the memory system (32-byte ray
+    record, 32-byte nodes, 48-byte triangle records, one flag byte per blocked
+    ray) against a measured L2 read bandwidth, and FP32 operations per sample."""
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi
+
+    pipe.forward(stream)
+    st = torch.zeros(5, dtype=torch.int64, device=pipe.device)
+    mcdi.shadow_ray_stats(pipe.bvh, pipe.N, pipe.H, pipe.W, pipe.params, pipe.workspace, st, stream)
+    torch.cuda.synchronize()
+    rays, visits, tests, blocked, differ = (int(v) for v in st.cpu())
+    ms = []
+    for k in range(steps + 3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        flush.zero_()
+        ev[0].record(stream)
+        mcdi.shadow_ray_retrace(pipe.bvh, pipe.N, pipe.H, pipe.W, pipe.params, pipe.workspace, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            ms.append(ev[0].elapsed_time(ev[1]))
+    t = float(np.mean(ms))
+    # L2 read bandwidth: 16-byte L1-bypassing loads over buffers that stay in L2, best of sizes and repeats
+    sink = torch.zeros(1, dtype=torch.int32, device=pipe.device)
+    l2 = 0.0
+    for mib in (8, 16, 32):
+        buf = torch.zeros(mib << 18, dtype=torch.int32, device=pipe.device)
+        passes = 40
+        for k in range(4):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            mcdi.read_sweep(buf, 1, sink, stream)  # bring it into L2
+            ev[0].record(stream)
+            mcdi.read_sweep(buf, passes, sink, stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            l2 = max(l2, (mib << 20) * passes / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9)
+        del buf
+    req = rays * RAY_BYTES + visits * NODE_BYTES + tests * TRI_BYTES + blocked
+    req_gbs = req / (t * 1e-3) / 1e9
+    return {"kernel": "wave_trace_kernel", "ms": round(t, 4), "rays": rays, "disagree_with_forward": differ,
+            "node_visits_per_ray": round(visits / max(rays, 1), 2),
+            "tri_tests_per_ray": round(tests / max(rays, 1), 2), "blocked_frac": round(blocked / max(rays, 1), 4),
+            "requested_bytes": req, "requested_gbs": round(req_gbs, 1), "l2_read_peak_gbs": round(l2, 1),
+            "l2_peak_source": "measured (read sweep over 8-32 MiB)",
+            "frac_of_l2_read_peak": round(req_gbs / l2, 4) if l2 > 0 else None,
+            "traversal_fp32_ops_per_sample": round((visits * SLAB_OPS + tests * TRI_OPS) / max(samples, 1), 1),
+            "traversal_gops": round((visits * SLAB_OPS + tests * TRI_OPS) / (t * 1e-3) / 1e9, 1)}
 
 
 def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):

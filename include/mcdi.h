@@ -216,6 +216,36 @@ MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* en
                               void* stream);
 
 /* ------------------------------------------------------------------------
+ * Measurement aids for the shadow-ray traversal (the visibility term of the
+ * Sec. 3.1 estimator, traced as in App. A), not part of the hot path.  Both
+ * take the BVH, image shape and params of a preceding mcdi_shade_mc_fwd that
+ * ran with `workspace` (its compacted shadow rays are still there) and launch
+ * on `stream` after it.
+ *
+ * mcdi_shadow_ray_stats re-traces those rays one per thread with counters and
+ * OVERWRITES stats[5] (device, 8-byte aligned): [0] rays, [1] node visits
+ * (one 32-byte node fetch and one slab test each), [2] triangle tests (48-byte
+ * triangle record fetch each), [3] rays blocked, [4] rays whose result differs
+ * from the forward pass's (0 when the two traversals agree).
+ *
+ * mcdi_shadow_ray_retrace runs the forward pass's tracer kernel again over
+ * the same rays (it sets the same hit flags, so the forward's outputs and the
+ * workspace stay valid): the tracer timed on its own.
+ *
+ * mcdi_read_sweep reads `bytes` (a multiple of 16, buf 16-byte aligned) of
+ * device memory `passes` times with L2-cached, L1-bypassing 16-byte loads;
+ * *sink (device) is written only in a case that does not occur for real data.
+ * Timed over a buffer that fits in L2 it measures the L2 read bandwidth.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_shadow_ray_stats(const mcdi_bvh_view* bvh, int N, int H, int W,
+                                           const mcdi_shade_params* params, const void* workspace,
+                                           size_t workspace_bytes, unsigned long long* stats, void* stream);
+MCDI_API mcdi_status mcdi_shadow_ray_retrace(const mcdi_bvh_view* bvh, int N, int H, int W,
+                                             const mcdi_shade_params* params, void* workspace,
+                                             size_t workspace_bytes, void* stream);
+MCDI_API mcdi_status mcdi_read_sweep(const void* buf, size_t bytes, int passes, unsigned* sink, void* stream);
+
+/* ------------------------------------------------------------------------
  * Differentiable denoiser (Sec. 4.2 "Neural denoisers": a U-Net applied to
  * the demodulated diffuse and the specular terms separately; App. B).
  * The network: widths 32/48/64/96 over four levels, two 3x3 zero-padded

@@ -217,6 +217,72 @@ mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp
                     "shade_mc_fwd");
 }
 
+}  // extern "C"
+
+namespace {
+
+// the BVH, image shape and sample counts of a forward pass whose workspace is
+// reused by the traversal-statistics calls
+mcdi_status wave_common(const mcdi_bvh_view* bvh, int N, int H, int W, const mcdi_shade_params* prm,
+                        const void* workspace, size_t workspace_bytes, mcdi::ShadeArgs* a) {
+    REQUIRE(bvh != nullptr, "bvh is NULL");
+    REQUIRE(bvh->n_tris >= 0, "bvh->n_tris must be >= 0");
+    if (bvh->n_tris > 0) {
+        REQUIRE_NODES(bvh->nodes);
+        REQUIRE_BUF16(bvh->tri_records);
+    }
+    size_t need = 0;
+    mcdi_status s = mcdi_shade_workspace_size(N, H, W, prm, &need);
+    if (s != MCDI_OK) return s;
+    REQUIRE(workspace != nullptr && ((uintptr_t)workspace & 255u) == 0,
+            "workspace must be a non-NULL 256-byte aligned device pointer");
+    REQUIRE(workspace_bytes >= need, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+    *a = mcdi::ShadeArgs{};
+    a->nodes = bvh->nodes;
+    a->tris = bvh->tri_records;
+    a->n_tris = bvh->n_tris;
+    a->N = N;
+    a->H = H;
+    a->W = W;
+    a->n_light = prm->n_light;
+    a->n_cos = prm->n_cos;
+    a->n_ggx = prm->n_ggx;
+    return MCDI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcdi_status mcdi_shadow_ray_stats(const mcdi_bvh_view* bvh, int N, int H, int W, const mcdi_shade_params* params,
+                                  const void* workspace, size_t workspace_bytes, unsigned long long* stats,
+                                  void* stream) {
+    mcdi::ShadeArgs a;
+    mcdi_status s = wave_common(bvh, N, H, W, params, workspace, workspace_bytes, &a);
+    if (s != MCDI_OK) return s;
+    REQUIRE(stats != nullptr && ((uintptr_t)stats & 7u) == 0, "stats must be a non-NULL 8-byte aligned device pointer");
+    return launched(mcdi::launch_shadow_ray_stats(a, workspace, stats, static_cast<cudaStream_t>(stream)),
+                    "shadow_ray_stats");
+}
+
+mcdi_status mcdi_shadow_ray_retrace(const mcdi_bvh_view* bvh, int N, int H, int W, const mcdi_shade_params* params,
+                                    void* workspace, size_t workspace_bytes, void* stream) {
+    mcdi::ShadeArgs a;
+    mcdi_status s = wave_common(bvh, N, H, W, params, workspace, workspace_bytes, &a);
+    if (s != MCDI_OK) return s;
+    return launched(mcdi::launch_shadow_ray_retrace(a, workspace, static_cast<cudaStream_t>(stream)),
+                    "shadow_ray_retrace");
+}
+
+mcdi_status mcdi_read_sweep(const void* buf, size_t bytes, int passes, unsigned* sink, void* stream) {
+    REQUIRE(buf != nullptr && aligned16(buf), "buf must be a non-NULL 16-byte aligned device pointer");
+    REQUIRE(bytes >= 16 && bytes % 16 == 0, "bytes must be a positive multiple of 16");
+    REQUIRE(passes >= 1, "passes must be >= 1");
+    REQUIRE(sink != nullptr && ((uintptr_t)sink & 3u) == 0, "sink must be a non-NULL 4-byte aligned device pointer");
+    return launched(mcdi::launch_read_sweep(buf, bytes, passes, sink, static_cast<cudaStream_t>(stream)),
+                    "read_sweep");
+}
+
 mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
                               const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
                               const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,

@@ -92,6 +92,12 @@ cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, fl
 size_t shade_workspace_bytes(long long pixels, int spp);
 cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
                                   void* ws, cudaStream_t stream);
+cudaError_t launch_shadow_ray_stats(const ShadeArgs& a, const void* ws, unsigned long long* stats,
+                                    cudaStream_t stream);
+cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t stream);
+
+// ---- measurement aid (measure.cu): L2-resident read sweep
+cudaError_t launch_read_sweep(const void* buf, size_t bytes, int passes, unsigned* sink, cudaStream_t stream);
 
 cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float4* g_kdout, const float4* g_cs,
                              const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,

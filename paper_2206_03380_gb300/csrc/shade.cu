@@ -148,6 +148,13 @@ __global__ void __launch_bounds__(kShadeThreads) shade_fwd_kernel(ShadeArgs a, f
 }
 
 // ---------------------------------------------------------------- adjoint
+// A CTA covers 32 consecutive pixels with kBwdQuarters warps; warp q handles
+// the samples j = q, q + 4, ... of its lane's pixel (in increasing j) and the
+// per-pixel partial sums of the four warps are added in order q = 0..3, so
+// every pixel's gradient has one fixed summation order.
+constexpr int kBwdQuarters = kShadeThreads / 32;
+constexpr int kBwdPartials = 8;  // g_n (3), g_F0 (3), g_co, g_alpha
+
 __global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a, const float4* __restrict__ g_cd,
                                                                   const float4* __restrict__ g_kdout,
                                                                   const float4* __restrict__ g_cs,
@@ -156,36 +163,34 @@ __global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a
                                                                   float4* __restrict__ g_korm,
                                                                   float4* __restrict__ g_nrm,
                                                                   float4* __restrict__ g_env) {
-    extern __shared__ float s_marg[];
+    extern __shared__ float s_marg[];  // marginal CDF, then [kBwdQuarters][kBwdPartials][32] partial sums
     Probe Pr = make_probe(a);
     stage_marginal(Pr, s_marg);
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float* s_part = s_marg + ((a.Hp + 1 + 3) & ~3);
+    const int lane = threadIdx.x & 31, quarter = threadIdx.x >> 5;
+    const long long idx = (long long)blockIdx.x * 32 + lane;
     const long long P = (long long)a.N * a.H * a.W;
-    if (idx >= P) return;
-    const int view = (int)(idx / ((long long)a.H * a.W));
+    const bool in_range = idx < P;
+    const int view = in_range ? (int)(idx / ((long long)a.H * a.W)) : 0;
     const uint32_t pix = (uint32_t)(idx - (long long)view * a.H * a.W);
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int nwords = (spp + 31) >> 5;
-    Pixel px;
-    const bool covered = load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
-                                    cam_origin(a.cams, view), &px);
-    if (!covered) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        g_kd[idx] = z;
-        g_korm[idx] = z;
-        g_nrm[idx] = z;
-        return;
-    }
-    const float4 gd4 = g_cd[idx], gk4 = g_kdout[idx], gs4 = g_cs[idx];
-    const f3 gd = xyz(gd4), gk = xyz(gk4), gs = xyz(gs4);
-    const BvhNode* nodes = static_cast<const BvhNode*>(a.nodes);
-    const TriRecord* tris = static_cast<const TriRecord*>(a.tris);
+    Pixel px{};
+    const bool covered = in_range && load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
+                                                cam_origin(a.cams, view), &px);
     f3 gn = mk(0.f, 0.f, 0.f), gF0 = gn;
     float g_co = 0.f, g_alpha = 0.f;
+    f3 gd = gn, gk = gn, gs = gn;
+    if (covered) {
+        gd = xyz(g_cd[idx]);
+        gk = xyz(g_kdout[idx]);
+        gs = xyz(g_cs[idx]);
+    }
+    const BvhNode* nodes = static_cast<const BvhNode*>(a.nodes);
+    const TriRecord* tris = static_cast<const TriRecord*>(a.tris);
     const float a2 = px.a2;
-    uint32_t word = 0;
-    for (int j = 0; j < spp; ++j) {
-        if (vis_mask && (j & 31) == 0) word = vis_mask[(size_t)idx * nwords + (j >> 5)];
+    for (int j = covered ? quarter : spp; j < spp; j += kBwdQuarters) {
+        const uint32_t word = vis_mask ? vis_mask[(size_t)idx * nwords + (j >> 5)] : 0u;
         f3 wi;
         int t;
         float ci, inv_denom;
@@ -247,8 +252,31 @@ __global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a
             }
             ge = sum;
         }
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(g_env + t, make_float4(ge.x, ge.y, ge.z, 0.f));
+        if (lane == __ffs(peers) - 1) atomicAdd(g_env + t, make_float4(ge.x, ge.y, ge.z, 0.f));
     }
+    // the four warps' partial sums of each pixel, added in warp order by warp 0
+    const float part[kBwdPartials] = {gn.x, gn.y, gn.z, gF0.x, gF0.y, gF0.z, g_co, g_alpha};
+#pragma unroll
+    for (int k = 0; k < kBwdPartials; ++k) s_part[(quarter * kBwdPartials + k) * 32 + lane] = part[k];
+    __syncthreads();
+    if (quarter != 0 || !in_range) return;
+    if (!covered) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        g_kd[idx] = z;
+        g_korm[idx] = z;
+        g_nrm[idx] = z;
+        return;
+    }
+    float sum[kBwdPartials];
+#pragma unroll
+    for (int k = 0; k < kBwdPartials; ++k) {
+        sum[k] = s_part[k * 32 + lane];
+        for (int q = 1; q < kBwdQuarters; ++q) sum[k] += s_part[(q * kBwdPartials + k) * 32 + lane];
+    }
+    gn = mk(sum[0], sum[1], sum[2]);
+    gF0 = mk(sum[3], sum[4], sum[5]);
+    g_co = sum[6];
+    g_alpha = sum[7];
     gn = gn + px.wo * g_co;
     const float ng = dot(px.n, gn);
     const f3 gN = (gn - px.n * ng) * (1.0f / px.lN);
@@ -291,9 +319,9 @@ cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float
                              const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,
                              cudaStream_t stream) {
     const long long P = (long long)a.N * a.H * a.W;
-    const size_t smem = (size_t)(a.Hp + 1) * sizeof(float);
-    shade_bwd_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, smem, stream>>>(a, g_cd, g_kdout, g_cs, vis_mask,
-                                                                               g_kd, g_korm, g_nrm, g_env);
+    const size_t smem = (size_t)(((a.Hp + 1 + 3) & ~3) + kBwdQuarters * kBwdPartials * 32) * sizeof(float);
+    shade_bwd_kernel<<<grid_for(P, 32), kShadeThreads, smem, stream>>>(a, g_cd, g_kdout, g_cs, vis_mask, g_kd, g_korm,
+                                                                    g_nrm, g_env);
     return cudaGetLastError();
 }
 

@@ -64,17 +64,25 @@ __global__ void wave_reset_kernel(void* ws, long long slots) {
     B.counter[1] = 0u;
 }
 
+// A CTA covers 32 consecutive pixels with kGenQuarters warps; warp q draws the
+// samples j = q, q + 4, q + 8, ... of its lane's pixel (strided, so every warp
+// gets a mix of the three techniques), which keeps four times as many
+// independent sample chains in flight as one thread per pixel would.
 // Active shadow rays are appended densely (one atomic per warp and sample):
-// a warp's rays for sample j stay together, so the tracer sees coherent
-// batches and no empty slots.
+// a warp's rays for sample j stay together (32 neighbouring pixels, one
+// technique), so the tracer sees coherent batches and no empty slots.  What
+// a sample writes goes to its own slot j * P + pixel, so the results do not
+// depend on which warp drew it.
+constexpr int kGenQuarters = kGenThreads / 32;
+
 __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void* ws, float4* __restrict__ kd_out) {
     extern __shared__ float s_marg[];
-    const long long idx0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, quarter = threadIdx.x >> 5;
+    const long long idx0 = (long long)blockIdx.x * 32 + lane;
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const long long slots = P * spp;
     WaveBuffers B = wave_buffers(ws, slots);
-    const int lane = threadIdx.x & 31;
     const bool in_range = idx0 < P;
     const long long idx = in_range ? idx0 : P - 1;  // out-of-range lanes idle but join the warp votes
     const int view = (int)(idx / ((long long)a.H * a.W));
@@ -83,14 +91,14 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
     const mcdi_camera& C = a.cams[view];
     const bool covered = in_range && load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
                                                 mk(C.origin[0], C.origin[1], C.origin[2]), &px);
-    if (in_range)
+    if (in_range && quarter == 0)
         kd_out[idx] = covered ? make_float4(px.kd.x * (1.f - px.m), px.kd.y * (1.f - px.m),
                                             px.kd.z * (1.f - px.m), 0.f)
                               : make_float4(0.f, 0.f, 0.f, 0.f);
     Probe Pr = wave_probe(a);
     stage_marginal(Pr, s_marg);
     const f3 origin = covered ? px.p + px.n * a.ray_eps : mk(0.f, 0.f, 0.f);
-    for (int j = 0; j < spp; ++j) {
+    for (int j = quarter; j < spp; j += kGenQuarters) {
         const long long s = (long long)j * P + idx;
         f3 wi = mk(0.f, 0.f, 0.f), cd = wi, cs = wi;
         bool active = false;
@@ -222,11 +230,85 @@ __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, co
     c_s[idx] = make_float4(cs.x, cs.y, cs.z, 0.f);
 }
 
+// Traversal statistics: the rays of the last forward pass re-traced one per
+// thread, with counters (stats[0] rays, [1] node visits = 32-byte node fetches
+// and slab tests, [2] triangle tests, [3] rays blocked, [4] rays whose result
+// differs from the forward's hit flag).  Warp sums, one 64-bit atomic each.
+__global__ void __launch_bounds__(kTraceThreads) wave_stats_kernel(const void* __restrict__ nodes,
+                                                                   const TriRecord* __restrict__ tris, int n_tris,
+                                                                   const void* ws, long long slots,
+                                                                   unsigned long long* __restrict__ stats) {
+    WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
+    const long long n_rays = (long long)B.counter[0];
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    const ThreadedNode* tn = threaded_nodes(nodes, n_tris > 0 ? n_tris : 1);
+    const int end = 2 * n_tris - 1;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_rays;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float4 o = B.ray_o[k], d = B.ray_d[k];
+        const RayInv r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
+        const int slot = __float_as_int(o.w);
+        bool blocked = false;
+        unsigned tests = 0;
+        for (int i = 0; i < end;) {
+            ++c[1];
+            i = threaded_step<true>(tn, tris, r, i, &tests);
+            if (i < 0) {
+                blocked = true;
+                break;
+            }
+        }
+        c[0] += 1;
+        c[2] += tests;
+        c[3] += blocked;
+        c[4] += blocked != (B.hit[slot] != 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        unsigned long long v = c[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + q, v);
+    }
+}
+
 }  // namespace
 
+// byte offset of the ray counters in the forward workspace
+static size_t wave_counter_offset(long long slots) {
+    return align256((size_t)slots * 16) * 2 + align256((size_t)slots * 24) + align256((size_t)slots);
+}
+
+cudaError_t launch_shadow_ray_stats(const ShadeArgs& a, const void* ws, unsigned long long* stats,
+                                    cudaStream_t stream) {
+    const long long slots = (long long)a.N * a.H * a.W * (a.n_light + a.n_cos + a.n_ggx);
+    cudaError_t e = cudaMemsetAsync(stats, 0, 5 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    wave_stats_kernel<<<sms * 8, kTraceThreads, 0, stream>>>(a.nodes, static_cast<const TriRecord*>(a.tris), a.n_tris,
+                                                             ws, slots, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t stream) {
+    const long long slots = (long long)a.N * a.H * a.W * (a.n_light + a.n_cos + a.n_ggx);
+    // rewind the work queue head; the rays, and the hit flags they set again, stay as they are
+    cudaError_t e = cudaMemsetAsync(static_cast<char*>(ws) + wave_counter_offset(slots) + sizeof(unsigned), 0,
+                                    sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152, per_sm = 8;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    wave_trace_kernel<<<sms * per_sm, kTraceThreads, 0, stream>>>(a.nodes, static_cast<const TriRecord*>(a.tris),
+                                                                  a.n_tris, ws, slots);
+    return cudaGetLastError();
+}
+
 size_t shade_workspace_bytes(long long P, int spp) {
-    const long long slots = P * spp;
-    return align256((size_t)slots * 16) * 2 + align256((size_t)slots * 24) + align256((size_t)slots) + 256;
+    return wave_counter_offset(P * spp) + 256;
 }
 
 cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
@@ -235,7 +317,8 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
     wave_reset_kernel<<<1, 1, 0, stream>>>(ws, P * spp);
-    wave_gen_kernel<<<gblocks, kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream>>>(a, ws, kd_out);
+    wave_gen_kernel<<<(int)((P + 31) / 32), kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream>>>(a, ws,
+                                                                                                       kd_out);
     int dev = 0, sms = 152, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -73,8 +73,10 @@ __device__ __forceinline__ bool slab_hit(const RayInv& r, float4 lo, float4 hi) 
 
 // One step of stackless any-hit traversal at node i of the depth-first
 // layout: returns the next node index (> i), or -1 when the ray is blocked.
+// kCount adds the triangle tests made to *tri_tests (traversal statistics).
+template <bool kCount = false>
 __device__ __forceinline__ int threaded_step(const ThreadedNode* __restrict__ tn, const TriRecord* __restrict__ tris,
-                                             const RayInv& r, int i) {
+                                             const RayInv& r, int i, unsigned* tri_tests = nullptr) {
     float4 lo, hi;  // one 32-byte load (the node array is 256-byte aligned, nodes 32 bytes)
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
@@ -82,8 +84,12 @@ __device__ __forceinline__ int threaded_step(const ThreadedNode* __restrict__ tn
     const int skip = __float_as_int(lo.w), tri = __float_as_int(hi.w);
     int next = skip;
     if (slab_hit(r, lo, hi)) {
-        if (tri < 0) next = i + 1;
-        else if (tri_hit(r, tris, tri, nullptr, nullptr) < FLT_MAX) return -1;
+        if (tri < 0) {
+            next = i + 1;
+        } else {
+            if (kCount) ++*tri_tests;
+            if (tri_hit(r, tris, tri, nullptr, nullptr) < FLT_MAX) return -1;
+        }
     }
     return next > i ? next : i + 1;  // strictly increasing: at most 2 n - 1 steps
 }

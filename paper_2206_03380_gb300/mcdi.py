@@ -39,7 +39,8 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_build_bvh_noalloc", "mcdi_primary_cast", "mcdi_shade_workspace_size", "mcdi_shade_mc_fwd",
            "mcdi_shade_mc_bwd", "mcdi_denoise_sizes", "mcdi_denoise_pack_weights", "mcdi_denoise_fwd",
            "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite",
-           "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd"]
+           "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd",
+           "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -76,6 +77,12 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shade_mc_bwd.restype = st
     lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
+    lib.mcdi_shadow_ray_stats.restype = st
+    lib.mcdi_shadow_ray_stats.argtypes = [C.POINTER(BvhView), i, i, i, C.POINTER(ShadeParams), P, sz, P, P]
+    lib.mcdi_shadow_ray_retrace.restype = st
+    lib.mcdi_shadow_ray_retrace.argtypes = [C.POINTER(BvhView), i, i, i, C.POINTER(ShadeParams), P, sz, P]
+    lib.mcdi_read_sweep.restype = st
+    lib.mcdi_read_sweep.argtypes = [P, sz, i, P, P]
     lib.mcdi_denoise_sizes.restype = st
     lib.mcdi_denoise_sizes.argtypes = [i, i, i, i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_denoise_pack_weights.restype = st
@@ -190,6 +197,28 @@ def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeP
                                     _ptr(cams), N, H, W, C.byref(params), _ptr(g_cd), _ptr(g_kdout), _ptr(g_cs),
                                     _ptr(vis_mask), _ptr(g_kd), _ptr(g_korm), _ptr(g_nrm), _ptr(g_env),
                                     _stream(stream)), "shade_mc_bwd")
+
+
+def shadow_ray_stats(bvh: "Bvh", N: int, H: int, W: int, params: ShadeParams, workspace, stats, stream=None):
+    """Counters of the shadow rays a forward pass left in ``workspace``: stats (5 int64, device) gets
+    rays, node visits, triangle tests, rays blocked, rays disagreeing with the forward's hit flag."""
+    assert stats.dtype == torch.int64 and stats.numel() >= 5
+    _check(load().mcdi_shadow_ray_stats(C.byref(bvh.view), int(N), int(H), int(W), C.byref(params),
+                                        _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(stats),
+                                        _stream(stream)), "shadow_ray_stats")
+
+
+def shadow_ray_retrace(bvh: "Bvh", N: int, H: int, W: int, params: ShadeParams, workspace, stream=None):
+    """The forward pass's tracer kernel alone, again over the rays left in ``workspace``."""
+    _check(load().mcdi_shadow_ray_retrace(C.byref(bvh.view), int(N), int(H), int(W), C.byref(params),
+                                          _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                          _stream(stream)), "shadow_ray_retrace")
+
+
+def read_sweep(buf, passes: int, sink, stream=None):
+    """Read all of ``buf`` ``passes`` times with L2-cached 16-byte loads (sink: int32 device scalar)."""
+    _check(load().mcdi_read_sweep(_ptr(buf), buf.numel() * buf.element_size(), int(passes), _ptr(sink),
+                                  _stream(stream)), "read_sweep")
 
 
 def denoise_sizes(n_img: int, H: int, W: int, precision: int = BF16):
