@@ -288,32 +288,42 @@ __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __rest
 
 // gradient of an encoder output E (stored in cat at channel offset ecoff) that
 // feeds both the skip slice and the 2x2 max-pool: g_E = (g_cat skip slice +
-// pool gradient routed to the window's first maximum) * [E > 0]
+// pool gradient routed to the window's first maximum) * [E > 0].  One thread
+// per 2x2 window and 8-channel group reads the window once.
 __global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int ecoff,
                                 int C, const bf16* __restrict__ gpool, int n, int H, int W, bf16* __restrict__ gE,
                                 unsigned* amax) {
-    int img, g, y, x;
+    const int Ho = H >> 1, Wo = W >> 1;
+    int img, g, yo, xo;
     float m = 0.0f;
-    if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, H, W, &img, &g, &y, &x, n)) {
-        const int xo = x >> 1, yo = y >> 1, me = (x & 1) + 2 * (y & 1);
+    if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Ho, Wo, &img, &g, &yo, &xo, n)) {
         const int G = Ctot >> 3, ge = (ecoff >> 3) + g;
         const size_t w0 = poff(img, G, ge, H, W, 2 * yo, 2 * xo);
-        float win[4][8];
-        for (int k = 0; k < 4; ++k) ld8(cat + w0 + ((size_t)(k >> 1) * W + (k & 1)) * 8, win[k]);
-        float gs[8], gp[8];
-        ld8(gcat + poff(img, G, ge, H, W, y, x), gs);
-        ld8(gpool + poff(img, C >> 3, g, H >> 1, W >> 1, yo, xo), gp);
-        float out[8];
+        float win[4][8], gs[4][8], gp[8];
+        for (int k = 0; k < 4; ++k) {
+            const size_t o = w0 + ((size_t)(k >> 1) * W + (k & 1)) * 8;
+            ld8(cat + o, win[k]);
+            ld8(gcat + o, gs[k]);
+        }
+        ld8(gpool + poff(img, C >> 3, g, Ho, Wo, yo, xo), gp);
+        int arg[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            int arg = 0;
+            arg[c] = 0;
             for (int k = 1; k < 4; ++k)
-                if (win[k][c] > win[arg][c]) arg = k;
-            const float v = gs[c] + (arg == me ? gp[c] : 0.0f);
-            out[c] = win[me][c] > 0.0f ? v : 0.0f;
+                if (win[k][c] > win[arg[c]][c]) arg[c] = k;
         }
-        st8(gE + poff(img, C >> 3, g, H, W, y, x), out);
-        m = max8(m, out);
+        const size_t e0 = poff(img, C >> 3, g, H, W, 2 * yo, 2 * xo);
+        for (int k = 0; k < 4; ++k) {
+            float out[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float v = gs[k][c] + (arg[c] == k ? gp[c] : 0.0f);
+                out[c] = win[k][c] > 0.0f ? v : 0.0f;
+            }
+            st8(gE + e0 + ((size_t)(k >> 1) * W + (k & 1)) * 8, out);
+            m = max8(m, out);
+        }
     }
     warp_amax(amax, m);
 }
@@ -624,7 +634,7 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
     auto pool_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int ecoff, int C, const bf16* gpool, int level,
                         int gE) {
         const int Hl = H >> level, Wl = W >> level;
-        const long long work = (long long)n * Hl * Wl * (C / 8);
+        const long long work = (long long)n * (Hl / 2) * (Wl / 2) * (C / 8);
         pool_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, ecoff, C, gpool, n, Hl, Wl, G(gE),
                                                               u.out(gE));
         return cudaGetLastError();

@@ -190,19 +190,31 @@ __device__ __forceinline__ size_t plane_off(int img, int G, int g, int H, int W,
     return ((((size_t)img * G + g) * H + y) * W + x) * 8;
 }
 
+// the ReLU mask words of 16 channels (two 8-channel groups) of one pixel
+__device__ __forceinline__ void load_mask16(const ConvParams& p, int c0, int img, int x, int y, uint4* m) {
+    const __nv_bfloat16* mk = p.mask + plane_off(img, p.mask_ctotal >> 3, (p.mask_coff + c0) >> 3, p.H, p.W, y, x);
+    m[0] = __ldg(reinterpret_cast<const uint4*>(mk));
+    m[1] = __ldg(reinterpret_cast<const uint4*>(mk + (size_t)p.H * p.W * 8));
+}
+
 // bias / activation / mask and store of 16 output channels (two 8-channel
-// groups) of one pixel
+// groups) of one pixel; mpre: the pixel's mask words when already loaded
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
-                                           const float* bias16, float dq, float* amax) {
+                                           const float* bias16, float dq, float* amax, const uint4* mpre = nullptr) {
     float f[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]) * dq;
     const size_t hw = (size_t)p.H * p.W;
     if (p.mode == kDgradMask || p.mode == kDgradPlain) {
         if (p.mode == kDgradMask) {
-            const __nv_bfloat16* mk =
-                p.mask + plane_off(img, p.mask_ctotal >> 3, (p.mask_coff + c0) >> 3, p.H, p.W, y, x);
-            const uint4 m0 = *reinterpret_cast<const uint4*>(mk), m1 = *reinterpret_cast<const uint4*>(mk + hw * 8);
+            uint4 mm[2];
+            if (mpre) {
+                mm[0] = mpre[0];
+                mm[1] = mpre[1];
+            } else {
+                load_mask16(p, c0, img, x, y, mm);
+            }
+            const uint4 m0 = mm[0], m1 = mm[1];
             const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -421,8 +433,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int R, bool FP8>
-__global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
+template <int R, bool FP8, bool MP>
+__global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ float s_bias[256];
@@ -612,9 +624,25 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
         const int q = warp & 3;
         const int m = q * 32 + lane;
         float amax = 0.0f;
+        // MP (ReLU-masked input gradients with at most 64 channels per CTA): the
+        // mask words of the next row are loaded while the current row drains
+        // (and those of a tile's first row before its accumulator wait), so
+        // their latency does not stall the epilogue
+        const bool pref = MP && p.mode == kDgradMask && Nc <= 4 * 16;
+        uint4 mnext[8];
+        auto load_row = [&](int img, int x, int y) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k * 16 < Nc && x < p.W && y < p.H && n0 + k * 16 < p.cout_valid)
+                    load_mask16(p, n0 + k * 16, img, x, y, mnext + 2 * k);
+        };
         int i = 0;
         for (int t = first; t < rp.n_tiles; t += step, ++i) {
             const int b = i & 1;
+            int img, x0, y0;
+            tile_origin(t, &img, &x0, &y0);
+            const int x = x0 + m;
+            if (pref) load_row(img, x, y0);
             const bool ok = mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)(i >> 1) & 1u);
             __syncwarp();
             if (!__all_sync(0xffffffffu, ok)) {
@@ -622,15 +650,36 @@ __global__ void __launch_bounds__(kRowThreads) conv_tc_rows_kernel(const __grid_
                 break;
             }
             tc_fence_after();
-            int img, x0, y0;
-            tile_origin(t, &img, &x0, &y0);
-            const int x = x0 + m;
             const float dq = dequant_factor(p);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int y = y0 + r;
                 const bool valid = x < p.W && y < p.H;
                 const uint32_t tr = tmem + (uint32_t)(b * R + r) * rp.acc_stride + ((uint32_t)(q * 32) << 16);
+                if (pref) {
+                    uint4 mcur[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) mcur[k] = mnext[k];
+                    if (r + 1 < R) load_row(img, x, y + 1);
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int c0 = cc * 32;
+                        if (c0 < Nc) {
+                            uint32_t v[32];
+                            const bool two = c0 + 16 < Nc;
+                            tmem_ld16_async(tr + (uint32_t)c0, v);
+                            if (two) tmem_ld16_async(tr + (uint32_t)c0 + 16u, v + 16);
+                            tmem_wait_ld();
+                            if (valid && n0 + c0 < p.cout_valid)
+                                epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, mcur + 4 * cc);
+                            if (two && valid && n0 + c0 + 16 < p.cout_valid)
+                                epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16, dq, &amax,
+                                           mcur + 4 * cc + 2);
+                            __syncwarp();
+                        }
+                    }
+                    continue;
+                }
                 // two 16-column loads in flight per wait
                 for (int c0 = 0; c0 < Nc; c0 += 32) {
                     uint32_t v[32];
@@ -701,7 +750,7 @@ const DeviceLimits& device_limits() {
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false>) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false, false>) != cudaSuccess ||
             optin <= (int)fa.sharedSizeBytes) {
             L.sms = 0;
             return;
@@ -829,37 +878,47 @@ bool conv_make_desc(ConvDesc* d, const void* x, const void* w, const char** why)
     return true;
 }
 
+template <bool FP8, bool MP>
+static void set_rows_smem(int bytes, cudaError_t* err) {
+    const void* fs[3] = {(const void*)conv_tc_rows_kernel<1, FP8, MP>, (const void*)conv_tc_rows_kernel<2, FP8, MP>,
+                         (const void*)conv_tc_rows_kernel<4, FP8, MP>};
+    for (const void* f : fs)
+        if (*err == cudaSuccess && bytes > 0)
+            *err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <bool FP8, bool MP>
+static void launch_rows(const ConvDesc& d, cudaStream_t stream) {
+    const dim3 g(d.rp.grid), t(kRowThreads);
+    const size_t sm = d.rp.smem_bytes;
+    if (d.rp.rows == 4) conv_tc_rows_kernel<4, FP8, MP><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+    else if (d.rp.rows == 2) conv_tc_rows_kernel<2, FP8, MP><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+    else conv_tc_rows_kernel<1, FP8, MP><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+}
+
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         const int lim = (int)device_limits().rows_smem_max;
-        auto set = [&](const void* f, int bytes) {
-            if (attr_err == cudaSuccess && bytes > 0)
-                attr_err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        };
-        set((const void*)conv_tc_kernel<false>, (int)conv_smem_bytes(256));
-        set((const void*)conv_tc_kernel<true>, (int)conv_smem_bytes(256));
-        set((const void*)conv_tc_rows_kernel<1, false>, lim);
-        set((const void*)conv_tc_rows_kernel<2, false>, lim);
-        set((const void*)conv_tc_rows_kernel<4, false>, lim);
-        set((const void*)conv_tc_rows_kernel<1, true>, lim);
-        set((const void*)conv_tc_rows_kernel<2, true>, lim);
-        set((const void*)conv_tc_rows_kernel<4, true>, lim);
+        const int tile = (int)conv_smem_bytes(256);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute((const void*)conv_tc_kernel<false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, tile);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute((const void*)conv_tc_kernel<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, tile);
+        set_rows_smem<false, false>(lim, &attr_err);
+        set_rows_smem<true, false>(lim, &attr_err);
+        set_rows_smem<false, true>(lim, &attr_err);
+        set_rows_smem<true, true>(lim, &attr_err);
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (d.rows_form) {
-        const dim3 g(d.rp.grid), t(kRowThreads);
-        const size_t sm = d.rp.smem_bytes;
-        if (d.p.fp8) {
-            if (d.rp.rows == 4) conv_tc_rows_kernel<4, true><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-            else if (d.rp.rows == 2) conv_tc_rows_kernel<2, true><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-            else conv_tc_rows_kernel<1, true><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-        } else {
-            if (d.rp.rows == 4) conv_tc_rows_kernel<4, false><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-            else if (d.rp.rows == 2) conv_tc_rows_kernel<2, false><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-            else conv_tc_rows_kernel<1, false><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-        }
+        // masked input gradients whose mask words fit the prefetch registers take the prefetching variant
+        const bool mp = d.p.mode == kDgradMask && d.rp.nc <= 64;
+        if (d.p.fp8) mp ? launch_rows<true, true>(d, stream) : launch_rows<true, false>(d, stream);
+        else mp ? launch_rows<false, true>(d, stream) : launch_rows<false, false>(d, stream);
         return cudaGetLastError();
     }
     const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;
