@@ -198,22 +198,18 @@ __device__ __forceinline__ void load_mask16(const ConvParams& p, int c0, int img
 }
 
 // bias / activation / mask and store of 16 output channels (two 8-channel
-// groups) of one pixel; mpre: the pixel's mask words when already loaded
+// groups) of one pixel; pre: the pixel's mask words are already in (ma, mb)
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
-                                           const float* bias16, float dq, float* amax, const uint4* mpre = nullptr) {
+                                           const float* bias16, float dq, float* amax, bool pre = false,
+                                           uint4 ma = uint4{}, uint4 mb = uint4{}) {
     float f[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]) * dq;
     const size_t hw = (size_t)p.H * p.W;
     if (p.mode == kDgradMask || p.mode == kDgradPlain) {
         if (p.mode == kDgradMask) {
-            uint4 mm[2];
-            if (mpre) {
-                mm[0] = mpre[0];
-                mm[1] = mpre[1];
-            } else {
-                load_mask16(p, c0, img, x, y, mm);
-            }
+            uint4 mm[2] = {ma, mb};
+            if (!pre) load_mask16(p, c0, img, x, y, mm);
             const uint4 m0 = mm[0], m1 = mm[1];
             const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
@@ -423,8 +419,11 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
 // output row instead of 9.
 //   warp 0          weight TMA (lane 0), halo row copies (one lane per row),
 //   warp 1 lane 0   MMA issuer; accumulators of tile i in TMEM buffer i & 1,
-//   warps 2..5      epilogue (TMEM lane quarter = warp % 4).
-constexpr int kRowThreads = 192;
+//   warps 2..9      epilogue: TMEM lane quarter warp % 4, and the two warps of
+//                   a quarter take alternate 16-column chunks of each row.
+constexpr int kRowThreads = 320;
+constexpr int kEpiWarps = kRowThreads / 32 - 2;
+constexpr int kEpiSplit = kEpiWarps / 4;  // epilogue warps per TMEM lane quarter
 constexpr int kRowMaxStages = 6;
 constexpr int kHaloW = 130;
 constexpr int kMaxRows = 4;
@@ -461,7 +460,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accf_bar[b]), 1);
-            mbar_init(smem_u32(&acce_bar[b]), 4);
+            mbar_init(smem_u32(&acce_bar[b]), kEpiWarps);
         }
         mbar_init(smem_u32(&w_bar), 1);
         failed = 0;
@@ -621,20 +620,30 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
         }
         __syncwarp();
     } else {
-        const int q = warp & 3;
+        const int q = warp & 3, h = (warp - 2) >> 2;
         const int m = q * 32 + lane;
         float amax = 0.0f;
+        // this warp's 16-column chunks of a row: 16 h, 16 (h + kEpiSplit), ...,
+        // drained two per TMEM-load wait
+        const int cfirst = 16 * h, cstep = 16 * kEpiSplit;
         // MP (ReLU-masked input gradients with at most 64 channels per CTA): the
         // mask words of the next row are loaded while the current row drains
         // (and those of a tile's first row before its accumulator wait), so
         // their latency does not stall the epilogue
-        const bool pref = MP && p.mode == kDgradMask && Nc <= 4 * 16;
-        uint4 mnext[8];
+        const bool pref = MP && p.mode == kDgradMask && Nc <= 2 * cstep;
+        uint4 na0{}, na1{}, nb0{}, nb1{};  // next row's mask words of chunks cfirst (a) and cfirst + cstep (b)
         auto load_row = [&](int img, int x, int y) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k * 16 < Nc && x < p.W && y < p.H && n0 + k * 16 < p.cout_valid)
-                    load_mask16(p, n0 + k * 16, img, x, y, mnext + 2 * k);
+            uint4 w[2];
+            if (cfirst < Nc && x < p.W && y < p.H && n0 + cfirst < p.cout_valid) {
+                load_mask16(p, n0 + cfirst, img, x, y, w);
+                na0 = w[0];
+                na1 = w[1];
+            }
+            if (cfirst + cstep < Nc && x < p.W && y < p.H && n0 + cfirst + cstep < p.cout_valid) {
+                load_mask16(p, n0 + cfirst + cstep, img, x, y, w);
+                nb0 = w[0];
+                nb1 = w[1];
+            }
         };
         int i = 0;
         for (int t = first; t < rp.n_tiles; t += step, ++i) {
@@ -651,45 +660,25 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
             }
             tc_fence_after();
             const float dq = dequant_factor(p);
-#pragma unroll
+            constexpr int kRowUnroll = MP ? 1 : R;  // the prefetch registers leave no room for a 4x unroll
+#pragma unroll kRowUnroll
             for (int r = 0; r < R; ++r) {
                 const int y = y0 + r;
                 const bool valid = x < p.W && y < p.H;
                 const uint32_t tr = tmem + (uint32_t)(b * R + r) * rp.acc_stride + ((uint32_t)(q * 32) << 16);
-                if (pref) {
-                    uint4 mcur[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) mcur[k] = mnext[k];
-                    if (r + 1 < R) load_row(img, x, y + 1);
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        const int c0 = cc * 32;
-                        if (c0 < Nc) {
-                            uint32_t v[32];
-                            const bool two = c0 + 16 < Nc;
-                            tmem_ld16_async(tr + (uint32_t)c0, v);
-                            if (two) tmem_ld16_async(tr + (uint32_t)c0 + 16u, v + 16);
-                            tmem_wait_ld();
-                            if (valid && n0 + c0 < p.cout_valid)
-                                epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, mcur + 4 * cc);
-                            if (two && valid && n0 + c0 + 16 < p.cout_valid)
-                                epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16, dq, &amax,
-                                           mcur + 4 * cc + 2);
-                            __syncwarp();
-                        }
-                    }
-                    continue;
-                }
-                // two 16-column loads in flight per wait
-                for (int c0 = 0; c0 < Nc; c0 += 32) {
+                const uint4 ca0 = na0, ca1 = na1, cb0 = nb0, cb1 = nb1;
+                if (pref && r + 1 < R) load_row(img, x, y + 1);
+                for (int c0 = cfirst; c0 < Nc; c0 += 2 * cstep) {
                     uint32_t v[32];
-                    const bool two = c0 + 16 < Nc;
+                    const int c1 = c0 + cstep;
+                    const bool two = c1 < Nc;
                     tmem_ld16_async(tr + (uint32_t)c0, v);
-                    if (two) tmem_ld16_async(tr + (uint32_t)c0 + 16u, v + 16);
+                    if (two) tmem_ld16_async(tr + (uint32_t)c1, v + 16);
                     tmem_wait_ld();
-                    if (valid && n0 + c0 < p.cout_valid) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax);
-                    if (two && valid && n0 + c0 + 16 < p.cout_valid)
-                        epilogue16(p, v + 16, n0 + c0 + 16, img, x, y, s_bias + c0 + 16, dq, &amax);
+                    if (valid && n0 + c0 < p.cout_valid)
+                        epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, pref, ca0, ca1);
+                    if (two && valid && n0 + c1 < p.cout_valid)
+                        epilogue16(p, v + 16, n0 + c1, img, x, y, s_bias + c1, dq, &amax, pref, cb0, cb1);
                     __syncwarp();
                 }
             }
