@@ -312,6 +312,11 @@ __device__ __forceinline__ void child_box(int link, const float4* box_int, const
     hi = __ldcg(b + 1);
 }
 
+// Bottom-up boxes: one thread per leaf climbs while it is the second to
+// arrive at a node.  It carries its subtree's box in registers, so at a node
+// it needs only the sibling's box; the node's links and parent (written by the
+// hierarchy kernel) are loaded before its arrival counter, which leaves one
+// dependent load per level after the atomic.
 __global__ void __launch_bounds__(256) refit_kernel(int n, BvhNode* __restrict__ nodes,
                                                     const int* __restrict__ parent_int,
                                                     const int* __restrict__ parent_leaf, uint32_t* __restrict__ flags,
@@ -319,21 +324,28 @@ __global__ void __launch_bounds__(256) refit_kernel(int n, BvhNode* __restrict__
                                                     const float4* __restrict__ box_leaf) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    int me = ~p;  // link of the subtree this thread carries (leaf p)
+    float4 lo = box_leaf[2 * (size_t)p], hi = box_leaf[2 * (size_t)p + 1];
     int node = parent_leaf[p];
     // at most n - 1 steps: each internal node is completed by exactly one thread
     for (int steps = 0; node >= 0 && steps < n; ++steps) {
+        const int4 d = __ldcg(&nodes[node].d);
+        const int up = __ldcg(parent_int + node);
         __threadfence();
         if (atomicAdd(flags + node, 1u) == 0u) return;  // first arrival: the sibling finishes this node
-        const int4 d = __ldcg(&nodes[node].d);
-        float4 l0, h0, l1, h1;
-        child_box(d.x, box_int, box_leaf, l0, h0);
-        child_box(d.y, box_int, box_leaf, l1, h1);
+        const bool left = d.x == me;
+        float4 sl, sh;
+        child_box(left ? d.y : d.x, box_int, box_leaf, sl, sh);
+        const float4 l0 = left ? lo : sl, h0 = left ? hi : sh, l1 = left ? sl : lo, h1 = left ? sh : hi;
         nodes[node].a = make_float4(l0.x, h0.x, l0.y, h0.y);
         nodes[node].b = make_float4(l1.x, h1.x, l1.y, h1.y);
         nodes[node].c = make_float4(l0.z, h0.z, l1.z, h1.z);
-        box_int[2 * (size_t)node] = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
-        box_int[2 * (size_t)node + 1] = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
-        node = parent_int[node];
+        lo = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
+        hi = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
+        box_int[2 * (size_t)node] = lo;
+        box_int[2 * (size_t)node + 1] = hi;
+        me = node;
+        node = up;
     }
 }
 

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
                 B.ray_d[r] = make_float4(wi.x, wi.y, wi.z, 0.0f);
             }
         }
-        if (!in_range) continue;
+        if (!covered) continue;  // the accumulation skips the slots of uncovered pixels
         B.hit[s] = 0;
         B.contrib[0 * slots + s] = cd.x;
         B.contrib[1 * slots + s] = cd.y;
@@ -211,6 +211,15 @@ __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, co
     const int nwords = (spp + 31) >> 5;
     const long long slots = P * spp;
     WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
+    // the same coverage test as the generator, which wrote no slots for uncovered pixels
+    const float4 pos = a.gb_pos[idx], nrm = a.gb_nrm[idx];
+    if (!(pos.w > 0.0f) || !(dot(xyz(nrm), xyz(nrm)) > 0.0f)) {
+        c_d[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        c_s[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (vis_mask)
+            for (int w = 0; w < nwords; ++w) vis_mask[(size_t)idx * nwords + w] = 0u;
+        return;
+    }
     const float hv = 1.0f - a.tau;
     f3 cd = mk(0.f, 0.f, 0.f), cs = cd;
     uint32_t word = 0;
