@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
 // escape links: the whole traversal state is one index); every
 // kTraceStepsPerRefill node visits the warp refills the lanes that are idle
 // from the global slot counter.
-__global__ void __launch_bounds__(kTraceThreads) wave_trace_kernel(const void* __restrict__ nodes,
+__global__ void __launch_bounds__(kTraceThreads, 16) wave_trace_kernel(const void* __restrict__ nodes,
                                                                    const TriRecord* __restrict__ tris, int n_tris,
                                                                    void* ws, long long slots) {
     WaveBuffers B = wave_buffers(ws, slots);
