@@ -414,6 +414,18 @@ SLAB_OPS, TRI_OPS = 25, 52
 NODE_BYTES, TRI_BYTES, RAY_BYTES = 32, 48, 32
 
 
+def alu_peak_gops():
+    """Nominal FP32 lane-operation rate: SMs x 128 lanes x the maximum SM clock."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return sms * 128 * mhz * 1e6 / 1e9
+
+
 def shadow_ray_figures(pipe, flush, stream, steps, samples):
     """The shadow-ray tracer of the forward pass timed alone (CUDA events, L2
     flushed before each launch) and its counters: node visits and triangle
@@ -464,7 +476,9 @@ def shadow_ray_figures(pipe, flush, stream, steps, samples):
             "l2_peak_source": "measured (read sweep over 8-32 MiB)",
             "frac_of_l2_read_peak": round(req_gbs / l2, 4) if l2 > 0 else None,
             "traversal_fp32_ops_per_sample": round((visits * SLAB_OPS + tests * TRI_OPS) / max(samples, 1), 1),
-            "traversal_gops": round((visits * SLAB_OPS + tests * TRI_OPS) / (t * 1e-3) / 1e9, 1)}
+            "traversal_gops": round((visits * SLAB_OPS + tests * TRI_OPS) / (t * 1e-3) / 1e9, 1),
+            "alu_peak_gops": round(alu_peak_gops(), 1),
+            "alu_peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (one operation per lane per cycle)"}
 
 
 def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):
@@ -495,9 +509,40 @@ def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):
     if den.err.item() != 0:
         raise RuntimeError("E4M3 denoiser pipeline wait timed out")
     f, b = float(np.mean(fwd)), float(np.mean(bwd))
-    return {"fwd_ms": round(f, 4), "bwd_ms": round(b, 4), "fwd_tflops": round(conv_flops / (f * 1e-3) / 1e12, 2),
-            "bwd_tflops": round(conv_flops / (b * 1e-3) / 1e12, 2),
-            "note": "E4M3 operands with per-tensor scaling (amax folded into each producer, quantised copy before each convolution)"}
+    peak, how = fp8_peak(stream)
+    out = {"fwd_ms": round(f, 4), "bwd_ms": round(b, 4), "fwd_tflops": round(conv_flops / (f * 1e-3) / 1e12, 2),
+           "bwd_tflops": round(conv_flops / (b * 1e-3) / 1e12, 2), "e4m3_peak_tflops": peak, "peak_source": how,
+           "note": "E4M3 operands with per-tensor scaling (amax folded into each producer, quantised copy before each "
+                   "convolution)"}
+    if peak:
+        out["fwd_frac"] = round(conv_flops / (f * 1e-3) / 1e12 / peak, 4)
+        out["bwd_frac"] = round(conv_flops / (b * 1e-3) / 1e12 / peak, 4)
+    return out
+
+
+def fp8_peak(stream, n=8192, reps=10):
+    """Dense E4M3 peak measured with the vendor library (torch._scaled_mm, FP32 accumulation,
+    per-tensor scales, BF16 output) on an n x n x n product, best of reps: the denominator of the
+    E4M3 denoiser's tensor fraction.  A measurement aid only; the denoiser never calls it."""
+    import torch
+
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return round(2.0 * n ** 3 / (best * 1e-3) / 1e12, 1), f"measured (torch._scaled_mm e4m3 {n}^3, best of {reps})"
+    except Exception as e:  # the library path may be missing on some builds
+        return None, f"unavailable: {type(e).__name__}: {str(e)[:80]}"
 
 
 def run_serving(n_requests, rate, dev, rank):

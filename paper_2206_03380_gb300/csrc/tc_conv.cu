@@ -773,6 +773,10 @@ bool plan_rows(const ConvParams& p, RowPlan* out) {
         const int nc = p.cout_pad / n_slices;
         const uint32_t acc_stride = pow2_at_least((uint32_t)nc);
         const uint32_t w_bytes = (uint32_t)n_chunks * 9u * (uint32_t)nc * 32u;
+        // the largest R that fits, except that a plan of two CTAs per SM with
+        // R >= 2 is preferred to one of a single CTA with a larger R
+        RowPlan single{};
+        bool have_single = false;
         for (int R = kMaxRows; R >= 1; R >>= 1) {
             const uint32_t tmem_cols = pow2_at_least(2u * (uint32_t)R * acc_stride);
             if (tmem_cols > 512u) continue;
@@ -787,14 +791,26 @@ bool plan_rows(const ConvParams& p, RowPlan* out) {
             if (w_bytes + 2u * rp.stage_bytes + kAlign > kSmemMax) continue;
             rp.n_tiles = p.n_img * ((p.H + R - 1) / R) * p.tiles_x;
             if (R > 1 && 2 * n_slices * rp.n_tiles < 3 * sms) continue;
-            const bool two = w_bytes + 3u * rp.stage_bytes + kAlign <= lim.rows_smem_two && 2u * tmem_cols <= 512u;
+            // two CTAs per SM (their MMA streams interleave on the tensor core) as
+            // soon as each fits a two-stage halo ring beside its weights
+            const bool two = w_bytes + 2u * rp.stage_bytes + kAlign <= lim.rows_smem_two && 2u * tmem_cols <= 512u;
             const uint32_t budget = two ? lim.rows_smem_two : kSmemMax;
             int S = (int)((budget - kAlign - w_bytes) / rp.stage_bytes);
             rp.stages = S > kRowMaxStages ? kRowMaxStages : S;
             rp.smem_bytes = (uint32_t)rp.stages * rp.stage_bytes + w_bytes + kAlign;
             const int per_slice = (two ? 2 : 1) * sms / n_slices;
             rp.grid = n_slices * (per_slice < rp.n_tiles ? per_slice : rp.n_tiles);
-            *out = rp;
+            if (two || R == 1) {
+                *out = have_single && !(two && R >= 2) ? single : rp;
+                return true;
+            }
+            if (!have_single) {
+                single = rp;
+                have_single = true;
+            }
+        }
+        if (have_single) {
+            *out = single;
             return true;
         }
     }
