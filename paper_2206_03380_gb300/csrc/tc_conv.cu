@@ -773,8 +773,8 @@ bool plan_rows(const ConvParams& p, RowPlan* out) {
         const int nc = p.cout_pad / n_slices;
         const uint32_t acc_stride = pow2_at_least((uint32_t)nc);
         const uint32_t w_bytes = (uint32_t)n_chunks * 9u * (uint32_t)nc * 32u;
-        // the largest R that fits, except that a plan of two CTAs per SM with
-        // R >= 2 is preferred to one of a single CTA with a larger R
+        // the largest R that fits, except that a plan of two CTAs per SM is
+        // preferred to one of a single CTA with a larger R
         RowPlan single{};
         bool have_single = false;
         for (int R = kMaxRows; R >= 1; R >>= 1) {
@@ -801,7 +801,7 @@ bool plan_rows(const ConvParams& p, RowPlan* out) {
             const int per_slice = (two ? 2 : 1) * sms / n_slices;
             rp.grid = n_slices * (per_slice < rp.n_tiles ? per_slice : rp.n_tiles);
             if (two || R == 1) {
-                *out = have_single && !(two && R >= 2) ? single : rp;
+                *out = have_single && !two ? single : rp;
                 return true;
             }
             if (!have_single) {
