@@ -65,6 +65,7 @@ class ShadingPipeline:
         self.g_env = torch.zeros_like(self.env)
         self._loss = None
         self.workspace = None
+        self._fork = None  # side stream of tables_and_geometry
         if wavefront:
             nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
             self.workspace = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
@@ -106,13 +107,24 @@ class ShadingPipeline:
         else:
             self.denoiser.backward(g_denoised, self.g_terms, stream)
 
+    def tables_and_geometry(self, stream=None):
+        """Probe tables on a forked stream, concurrently with the BVH build and the
+        G-buffer cast (the two share no buffers), joined before anything reads the
+        tables; inside a captured graph the fork and join become graph edges."""
+        cur = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if self._fork is None:
+            self._fork = torch.cuda.Stream(self.device)
+        self._fork.wait_stream(cur)
+        self.build_probe(self._fork)
+        self.build_bvh(stream)
+        self.primary(stream)
+        cur.wait_stream(self._fork)
+
     def step(self, g_cd, g_kdout, g_cs, stream=None):
         """One pass of the hot path: tables, BVH, G-buffer, forward, adjoint.
         With a denoiser, g_cd / g_cs are gradients of the denoised terms and pass
         through the denoiser's input gradient first."""
-        self.build_probe(stream)
-        self.build_bvh(stream)
-        self.primary(stream)
+        self.tables_and_geometry(stream)
         self.forward(stream)
         if self.denoiser is not None:
             self.denoise(stream)
@@ -127,9 +139,7 @@ class ShadingPipeline:
         denoiser, composite + tonemapped L1 loss + lighting regulariser and their
         adjoint, denoiser input gradient, shading adjoint.  (L, L_image, L_light)
         stay on the device in ``self.loss``; the composite is ``self.color``."""
-        self.build_probe(stream)
-        self.build_bvh(stream)
-        self.primary(stream)
+        self.tables_and_geometry(stream)
         self.forward(stream)
         self.loss_and_backward(ref, stream, lambda_light)
 
