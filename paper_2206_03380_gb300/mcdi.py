@@ -341,6 +341,30 @@ class Denoiser:
         denoise_bwd(self.weights, self.acts, gy, gx, self.grad_ws, self.err, stream, self.precision)
 
 
+class Denoise(torch.autograd.Function):
+    """y = Denoise.apply(term, kd, nrm, denoiser): the U-Net on n_img noisy terms with
+    k_d,out and normal guides (image i uses the guides of image i % n_aux).
+
+    Differentiable with respect to the noisy terms only (Sec. 4.2: the gradient
+    reaches the shading through the denoiser's input; its weights are locked and
+    the guides are constants).  The saved activations live in the Denoiser, so a
+    second forward through the same Denoiser before this backward overwrites them.
+    """
+
+    @staticmethod
+    def forward(ctx, term, kd, nrm, denoiser: "Denoiser"):
+        y = torch.empty_like(term)
+        denoiser.forward(term.contiguous(), kd.contiguous(), nrm.contiguous(), y)
+        ctx.denoiser = denoiser
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        gx = torch.empty_like(gy)
+        ctx.denoiser.backward(gy.contiguous(), gx)
+        return gx, None, None, None
+
+
 # ------------------------------------------------------------------ device-resident objects
 def _empty_bytes(n: int, device) -> torch.Tensor:
     # 256-byte aligned raw buffer

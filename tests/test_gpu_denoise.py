@@ -130,6 +130,28 @@ def test_unet_forward_and_input_gradient_match_oracle(cuda_lib, H, W):
     assert f64_f <= 2e-2 and f64_b <= 0.2
 
 
+def test_denoise_autograd_function_matches_direct_calls(cuda_lib):
+    """Denoise.apply inside a torch graph: the forward and the term gradient are exactly
+    the direct Denoiser calls; the guides get no gradient (the weights are locked)."""
+    mcdi = cuda_lib
+    rng = np.random.default_rng(77)
+    term, kd, nrm = make_inputs(rng, 1, 32, 48)
+    den = mcdi.Denoiser(mcdi.flatten_unet_params(D.xavier_weights(7)), term.shape[0], 32, 48)
+    t = lambda a: torch.from_numpy(a).cuda().contiguous()
+    x = t(term).requires_grad_(True)
+    kd_t, nrm_t = t(kd).requires_grad_(True), t(nrm)
+    w = t(rng.normal(size=term.shape).astype(np.float32))
+    y = mcdi.Denoise.apply(x, kd_t, nrm_t, den)
+    (y * w).sum().backward()
+    y_ref, gx_ref = torch.zeros_like(y), torch.zeros_like(y)
+    den.forward(t(term), t(kd), t(nrm), y_ref)
+    den.backward(w, gx_ref)
+    torch.cuda.synchronize()
+    assert den.err.item() == 0
+    assert torch.equal(y.detach(), y_ref) and torch.equal(x.grad, gx_ref)
+    assert kd_t.grad is None
+
+
 def test_unet_forward_at_headline_size(cuda_lib):
     """512 x 512, the two terms of one view (the benchmark's denoiser launch), forward only."""
     mcdi = cuda_lib
