@@ -335,6 +335,7 @@ def run_gpu(args, rank, world):
     result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
     result["denoiser_bilateral"] = time_bilateral(pipe, flush, stream, args.steps)
     result["shadow_rays"] = shadow_ray_figures(pipe, flush, stream, args.steps, samples_per_step)
+    result["bvh"] = time_bvh_refit(pipe, flush, stream, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
     if args.batch_steps > 0:
@@ -488,6 +489,29 @@ def shadow_ray_figures(pipe, flush, stream, steps, samples):
             "traversal_gops": round((visits * SLAB_OPS + tests * TRI_OPS) / (t * 1e-3) / 1e9, 1),
             "alu_peak_gops": round(alu_peak_gops(), 1),
             "alu_peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (one operation per lane per cycle)"}
+
+
+def time_bvh_refit(pipe, flush, stream, steps):
+    """The headline mesh's BVH built from scratch and refitted (bounds only, same
+    triangles): CUDA events around each call, L2 flushed before each."""
+    import torch
+
+    out = {}
+    for name, fn in (("build_ms", lambda: pipe.bvh.build(pipe.verts, pipe.tris, stream)),
+                     ("refit_ms", lambda: pipe.bvh.refit(pipe.verts, pipe.tris, stream))):
+        ms = []
+        for k in range(steps + 3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            flush.zero_()
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ms.append(ev[0].elapsed_time(ev[1]))
+        out[name] = round(float(np.mean(ms)), 4)
+    out["note"] = "refit keeps the leaf order and hierarchy of the last build (vertices moved, same triangles)"
+    return out
 
 
 def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):

@@ -91,6 +91,22 @@ MCDI_API mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* 
                            void* tri_records, void* scratch, size_t scratch_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * mcdi_refit_bvh: bounds-only update for a mesh whose vertices moved but
+ * whose triangles (the tris array and n_tris) are those of the last
+ * mcdi_build_bvh into the same nodes, tri_records and scratch (for example
+ * the fixed-topology stage of a reconstruction, where each iteration moves
+ * vertices only).  The leaf order and hierarchy of that build are kept; the
+ * triangle records, every box and the depth-first copy are recomputed from
+ * `verts`, so traversal results are exact for the new positions, while the
+ * tree's quality degrades as vertices move away from where it was built.
+ * `scratch` must hold what that build left there (do not reuse it in
+ * between; mcdi_build_bvh_noalloc leaves nothing to refit).  Arguments and
+ * errors as mcdi_build_bvh.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_refit_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
+                           void* tri_records, void* scratch, size_t scratch_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * mcdi_build_bvh_noalloc: the same build as mcdi_build_bvh (identical nodes
  * and triangle records for the same mesh) with no scratch argument.  The
  * paper has no counterpart; this entry point exists for callers that cannot

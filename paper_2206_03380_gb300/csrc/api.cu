@@ -149,6 +149,22 @@ mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int
                     "build_bvh");
 }
 
+mcdi_status mcdi_refit_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
+                           void* tri_records, void* scratch, size_t scratch_bytes, void* stream) {
+    REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
+    REQUIRE(n_verts >= 1, "n_verts must be >= 1");
+    REQUIRE(verts != nullptr && tris != nullptr, "verts / tris must be non-NULL");
+    REQUIRE(((uintptr_t)verts & 3u) == 0 && ((uintptr_t)tris & 3u) == 0, "verts / tris must be 4-byte aligned");
+    REQUIRE_NODES(nodes);
+    REQUIRE_BUF16(tri_records);
+    REQUIRE(scratch != nullptr && ((uintptr_t)scratch & 255u) == 0, "scratch must be non-NULL 256-byte aligned");
+    const mcdi::BvhScratch L = mcdi::bvh_scratch_layout(n_tris);
+    REQUIRE(scratch_bytes >= L.total, "scratch too small: %zu < %zu bytes", scratch_bytes, L.total);
+    return launched(mcdi::launch_refit_bvh(verts, n_verts, tris, n_tris, nodes, tri_records, scratch, L,
+                                           static_cast<cudaStream_t>(stream)),
+                    "refit_bvh");
+}
+
 mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* verts, const float* vnrm, const int* tris,
                               int n_verts, const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
                               const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos, float* gb_nrm,

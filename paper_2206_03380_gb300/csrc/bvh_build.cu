@@ -449,4 +449,33 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
     return cudaGetLastError();
 }
 
+// New vertex positions, same triangles: the leaf order (the final sort pass's
+// values), the hierarchy links and the parent arrays from the last build stay;
+// triangle records, leaf boxes, internal boxes and the depth-first copy are
+// recomputed (3 or 4 launches instead of 19).
+cudaError_t launch_refit_bvh(const float* verts, int n_verts, const int* tris, int n, void* nodes_v, void* recs_v,
+                             void* scratch, const BvhScratch& L, cudaStream_t stream) {
+    char* s = static_cast<char*>(scratch);
+    // four 8-bit passes end in the first key/value buffer
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(s + L.vals0);
+    int* parent_int = reinterpret_cast<int*>(s + L.parent_int);
+    int* parent_leaf = reinterpret_cast<int*>(s + L.parent_leaf);
+    uint32_t* flags = reinterpret_cast<uint32_t*>(s + L.flags);
+    float4* box_int = reinterpret_cast<float4*>(s + L.box_int);
+    float4* box_leaf = reinterpret_cast<float4*>(s + L.box_leaf);
+    BvhNode* nodes = static_cast<BvhNode*>(nodes_v);
+    TriRecord* recs = static_cast<TriRecord*>(recs_v);
+    const int g256 = (n + 255) / 256;
+    leaf_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, order, recs, box_leaf, flags);
+    if (n == 1) single_leaf_root_kernel<<<1, 1, 0, stream>>>(nodes, box_leaf);
+    else refit_kernel<<<g256, 256, 0, stream>>>(n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
+    char* nb = static_cast<char*>(nodes_v);
+    ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
+    const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
+    const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
+    threaded_kernel<<<(2 * n - 1 + 255) / 256, 256, 0, stream>>>(
+        n, nodes, parent_int, parent_leaf, box_int, box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
+    return cudaGetLastError();
+}
+
 }  // namespace mcdi

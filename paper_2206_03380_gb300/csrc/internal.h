@@ -58,6 +58,8 @@ cudaError_t launch_envmap_cdf(const float* env, int W, int H, float* cond, float
 
 cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
                              void* tri_records, void* scratch, const BvhScratch& layout, cudaStream_t stream);
+cudaError_t launch_refit_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
+                             void* tri_records, void* scratch, const BvhScratch& layout, cudaStream_t stream);
 
 struct ShadeArgs {
     const void* nodes;

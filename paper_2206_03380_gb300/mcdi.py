@@ -40,7 +40,7 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_shade_mc_bwd", "mcdi_denoise_sizes", "mcdi_denoise_pack_weights", "mcdi_denoise_fwd",
            "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite",
            "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd",
-           "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep"]
+           "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep", "mcdi_refit_bvh"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -64,6 +64,8 @@ def load(path: str = LIB_PATH):
     lib.mcdi_bvh_sizes.argtypes = [i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_build_bvh.restype = st
     lib.mcdi_build_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
+    lib.mcdi_refit_bvh.restype = st
+    lib.mcdi_refit_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
     lib.mcdi_build_bvh_noalloc.restype = st
     lib.mcdi_build_bvh_noalloc.argtypes = [P, i, P, i, P, P, P]
     lib.mcdi_primary_cast.restype = st
@@ -153,6 +155,13 @@ def build_bvh(verts, tris, nodes, tri_records, scratch, stream=None):
     _check(load().mcdi_build_bvh(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(nodes),
                                  _ptr(tri_records), _ptr(scratch), scratch.numel() * scratch.element_size(),
                                  _stream(stream)), "build_bvh")
+
+
+def refit_bvh(verts, tris, nodes, tri_records, scratch, stream=None):
+    """Bounds-only update after the vertices moved (same triangles as the last build into these buffers)."""
+    _check(load().mcdi_refit_bvh(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(nodes),
+                                 _ptr(tri_records), _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                 _stream(stream)), "refit_bvh")
 
 
 def build_bvh_noalloc(verts, tris, nodes, tri_records, stream=None):
@@ -389,6 +398,11 @@ class Bvh:
 
     def build(self, verts, tris, stream=None) -> "Bvh":
         build_bvh(verts, tris, self.nodes, self.tri_records, self.scratch, stream)
+        return self
+
+    def refit(self, verts, tris, stream=None) -> "Bvh":
+        """New vertex positions, the triangles of the last build: boxes only."""
+        refit_bvh(verts, tris, self.nodes, self.tri_records, self.scratch, stream)
         return self
 
 
