@@ -383,10 +383,13 @@ def run_step_batch(steps, flush, dev, rank, world):
     samples = pipe.covered_pixels() * sc.spp
     t = max_over_ranks(float(np.mean(ms)), dev)
     total = sum_over_ranks(float(samples), dev)
+    # the tracer and the BVH at 1.3M triangles, where the BVH (~110 MB) no longer sits in L2
+    rays = shadow_ray_figures(pipe, flush, stream, min(steps, 5), samples)
+    bvh = time_bvh_refit(pipe, flush, stream, min(steps, 5))
     return {"workload": sc.name, "views": pipe.N, "width": pipe.W, "height": pipe.H, "spp": sc.spp,
             "triangles": int(sc.tris.shape[0]), "samples_per_step": int(samples), "ms_per_step": round(t, 3),
             "value": round(total / (t * 1e-3) / 1e6, 2), "unit": UNIT, "steps": steps,
-            "note": "one CUDA graph replay per step"}
+            "note": "one CUDA graph replay per step", "shadow_rays": rays, "bvh": bvh}
 
 
 def time_bilateral(pipe, flush, stream, steps, sigma=2.0):
@@ -696,9 +699,22 @@ def main(argv=None):
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="graph replays of the 8-view 800^2 32-spp step on the ~1.3M-triangle mesh (0: skip)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the optimisation-step batch and print its figures (a profiling aid)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    if args.batch_only:
+        import torch
+
+        rank, world = init_dist("nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(dist_env()[2])
+        dev = torch.device("cuda", dist_env()[2])
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        res = {"step_batch": run_step_batch(max(args.batch_steps, 1), flush, dev, rank, world)}
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
     if args.impl == "reference":
         rank, world = init_dist("gloo")
         res = run_reference(args, rank, world)
