@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kTile* kTile) bilateral_fwd_kernel(const float
                                                                      int W, int K, const float4* __restrict__ c_in,
                                                                      float inv2s2, int R, float4* __restrict__ c_out,
                                                                      float* __restrict__ wsum) {
+    pdl_prologue();
     extern __shared__ float4 smem[];
     const int view = blockIdx.z;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kTile* kTile) bilateral_bwd_kernel(const float
                                                                      int W, int K, const float* __restrict__ wsum,
                                                                      const float4* __restrict__ g_out, float inv2s2,
                                                                      int R, float4* __restrict__ g_in) {
+    pdl_prologue();
     extern __shared__ float4 smem[];
     const int view = blockIdx.z;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
@@ -246,13 +248,13 @@ cudaError_t launch_bilateral(bool backward, const float* gb_pos, const float* gb
         if (e != cudaSuccess) return e;
     }
     if (backward)
-        bilateral_bwd_kernel<<<grid, kTile * kTile, smem, s>>>(
-            reinterpret_cast<const float4*>(gb_pos), reinterpret_cast<const float4*>(gb_nrm), cams, N, H, W, K, wsum_in,
-            reinterpret_cast<const float4*>(in), inv2s2, R, reinterpret_cast<float4*>(out));
+        launch_k(bilateral_bwd_kernel, grid, kTile * kTile, smem, s, reinterpret_cast<const float4*>(gb_pos),
+                 reinterpret_cast<const float4*>(gb_nrm), cams, N, H, W, K, wsum_in,
+                 reinterpret_cast<const float4*>(in), inv2s2, R, reinterpret_cast<float4*>(out));
     else
-        bilateral_fwd_kernel<<<grid, kTile * kTile, smem, s>>>(
-            reinterpret_cast<const float4*>(gb_pos), reinterpret_cast<const float4*>(gb_nrm), cams, N, H, W, K,
-            reinterpret_cast<const float4*>(in), inv2s2, R, reinterpret_cast<float4*>(out), wsum_out);
+        launch_k(bilateral_fwd_kernel, grid, kTile * kTile, smem, s, reinterpret_cast<const float4*>(gb_pos),
+                 reinterpret_cast<const float4*>(gb_nrm), cams, N, H, W, K, reinterpret_cast<const float4*>(in), inv2s2,
+                 R, reinterpret_cast<float4*>(out), wsum_out);
     return cudaGetLastError();
 }
 

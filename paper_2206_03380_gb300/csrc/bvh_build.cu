@@ -43,6 +43,7 @@ __device__ __forceinline__ void load_tri(const float* __restrict__ verts, int n_
 }
 
 __global__ void init_bounds_kernel(uint32_t* bounds) {
+    pdl_prologue();
     if (threadIdx.x < 3) bounds[threadIdx.x] = f2ord(FLT_MAX);
     else if (threadIdx.x < 6) bounds[threadIdx.x] = f2ord(-FLT_MAX);
 }
@@ -50,6 +51,7 @@ __global__ void init_bounds_kernel(uint32_t* bounds) {
 __global__ void __launch_bounds__(256) centroid_bounds_kernel(const float* __restrict__ verts, int n_verts,
                                                               const int* __restrict__ tris, int n,
                                                               uint32_t* __restrict__ bounds) {
+    pdl_prologue();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
     if (k < n) {
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(256) morton_kernel(const float* __restrict__ v
                                                      const int* __restrict__ tris, int n,
                                                      const uint32_t* __restrict__ bounds, uint32_t* __restrict__ keys,
                                                      uint32_t* __restrict__ vals) {
+    pdl_prologue();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     f3 a, b, c;
@@ -124,6 +127,7 @@ __global__ void __launch_bounds__(256) morton_kernel(const float* __restrict__ v
 // ---- radix sort: one 8-bit digit per pass ----
 __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift,
                                                                   int nblocks, uint32_t* __restrict__ hist) {
+    pdl_prologue();
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -140,6 +144,7 @@ __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint32_t
 // one block per digit: exclusive scan of that digit's counts across tiles
 __global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t* __restrict__ hist, int nblocks,
                                                          uint32_t* __restrict__ digit_tot) {
+    pdl_prologue();
     uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
     __shared__ uint32_t warp_tot[8];
     __shared__ uint32_t carry;
@@ -174,6 +179,7 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int n, int shift, int nblocks,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_tot, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out) {
+    pdl_prologue();
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t wc[kWarps][256];  // per-warp digit counters, then per-warp offsets
     __shared__ uint32_t dbase[256];       // global start of each digit
@@ -247,6 +253,7 @@ __device__ __forceinline__ int common_prefix(const uint32_t* __restrict__ keys, 
 __global__ void __launch_bounds__(256) karras_kernel(const uint32_t* __restrict__ keys, int n,
                                                      BvhNode* __restrict__ nodes, int* __restrict__ parent_int,
                                                      int* __restrict__ parent_leaf) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int d = (common_prefix(keys, n, i, i + 1) - common_prefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -280,6 +287,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(const float* __restrict__ ver
                                                    const int* __restrict__ tris, int n,
                                                    const uint32_t* __restrict__ order, TriRecord* __restrict__ recs,
                                                    float4* __restrict__ box_leaf, uint32_t* __restrict__ flags) {
+    pdl_prologue();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     if (p < n - 1) flags[p] = 0u;
@@ -322,6 +330,7 @@ __global__ void __launch_bounds__(256) refit_kernel(int n, BvhNode* __restrict__
                                                     const int* __restrict__ parent_leaf, uint32_t* __restrict__ flags,
                                                     float4* __restrict__ box_int,
                                                     const float4* __restrict__ box_leaf) {
+    pdl_prologue();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int me = ~p;  // link of the subtree this thread carries (leaf p)
@@ -351,6 +360,7 @@ __global__ void __launch_bounds__(256) refit_kernel(int n, BvhNode* __restrict__
 
 // one triangle: a root whose two links both point at leaf 0
 __global__ void single_leaf_root_kernel(BvhNode* nodes, const float4* box_leaf) {
+    pdl_prologue();
     const float4 lo = box_leaf[0], hi = box_leaf[1];
     nodes[0].a = make_float4(lo.x, hi.x, lo.y, hi.y);
     nodes[0].b = nodes[0].a;
@@ -370,6 +380,7 @@ __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __r
                                                        const float4* __restrict__ box_int,
                                                        const float4* __restrict__ box_leaf, float4* gap,
                                                        int gap_vec4, ThreadedNode* __restrict__ out) {
+    pdl_prologue();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     // zero the alignment gap before this array, so that equal meshes give equal bytes
     if (v < gap_vec4) gap[v] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -422,30 +433,30 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
     TriRecord* recs = static_cast<TriRecord*>(recs_v);
 
     const int g256 = (n + 255) / 256;
-    init_bounds_kernel<<<1, 32, 0, stream>>>(bounds);
-    centroid_bounds_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, bounds);
-    morton_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, bounds, keys[0], vals[0]);
+    launch_k(init_bounds_kernel, 1, 32, 0, stream, bounds);
+    launch_k(centroid_bounds_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds);
+    launch_k(morton_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds, keys[0], vals[0]);
     int cur = 0;
     for (int shift = 0; shift < 32; shift += 8) {
-        digit_hist_kernel<<<L.nblocks, kSortThreads, 0, stream>>>(keys[cur], n, shift, L.nblocks, hist);
-        digit_scan_kernel<<<256, 256, 0, stream>>>(hist, L.nblocks, dtot);
-        digit_scatter_kernel<<<L.nblocks, kSortThreads, 0, stream>>>(keys[cur], vals[cur], n, shift, L.nblocks, hist,
-                                                                     dtot, keys[cur ^ 1], vals[cur ^ 1]);
+        launch_k(digit_hist_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], n, shift, L.nblocks, hist);
+        launch_k(digit_scan_kernel, 256, 256, 0, stream, hist, L.nblocks, dtot);
+        launch_k(digit_scatter_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], vals[cur], n, shift, L.nblocks,
+                 hist, dtot, keys[cur ^ 1], vals[cur ^ 1]);
         cur ^= 1;
     }
-    leaf_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, vals[cur], recs, box_leaf, flags);
+    launch_k(leaf_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, vals[cur], recs, box_leaf, flags);
     if (n == 1) {
-        single_leaf_root_kernel<<<1, 1, 0, stream>>>(nodes, box_leaf);
+        launch_k(single_leaf_root_kernel, 1, 1, 0, stream, nodes, box_leaf);
     } else {
-        karras_kernel<<<(n - 1 + 255) / 256, 256, 0, stream>>>(keys[cur], n, nodes, parent_int, parent_leaf);
-        refit_kernel<<<g256, 256, 0, stream>>>(n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
+        launch_k(karras_kernel, (n - 1 + 255) / 256, 256, 0, stream, keys[cur], n, nodes, parent_int, parent_leaf);
+        launch_k(refit_kernel, g256, 256, 0, stream, n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
     }
     char* nb = static_cast<char*>(nodes_v);
     ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
     const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
     const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
-    threaded_kernel<<<(2 * n - 1 + 255) / 256, 256, 0, stream>>>(
-        n, nodes, parent_int, parent_leaf, box_int, box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
+    launch_k(threaded_kernel, (2 * n - 1 + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf, box_int,
+             box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
     return cudaGetLastError();
 }
 
@@ -466,15 +477,15 @@ cudaError_t launch_refit_bvh(const float* verts, int n_verts, const int* tris, i
     BvhNode* nodes = static_cast<BvhNode*>(nodes_v);
     TriRecord* recs = static_cast<TriRecord*>(recs_v);
     const int g256 = (n + 255) / 256;
-    leaf_kernel<<<g256, 256, 0, stream>>>(verts, n_verts, tris, n, order, recs, box_leaf, flags);
-    if (n == 1) single_leaf_root_kernel<<<1, 1, 0, stream>>>(nodes, box_leaf);
-    else refit_kernel<<<g256, 256, 0, stream>>>(n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
+    launch_k(leaf_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, order, recs, box_leaf, flags);
+    if (n == 1) launch_k(single_leaf_root_kernel, 1, 1, 0, stream, nodes, box_leaf);
+    else launch_k(refit_kernel, g256, 256, 0, stream, n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
     char* nb = static_cast<char*>(nodes_v);
     ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
     const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
     const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
-    threaded_kernel<<<(2 * n - 1 + 255) / 256, 256, 0, stream>>>(
-        n, nodes, parent_int, parent_leaf, box_int, box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
+    launch_k(threaded_kernel, (2 * n - 1 + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf, box_int,
+             box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pdl.cuh"
+
 #define MCDI_PI 3.14159265358979323846f
 #define MCDI_INV_PI 0.318309886183790671538f
 

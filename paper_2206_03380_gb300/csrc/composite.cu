@@ -8,6 +8,7 @@ namespace {
 
 __global__ void composite_kernel(const float4* __restrict__ kd, const float4* __restrict__ dd,
                                  const float4* __restrict__ ds, long long n, float4* __restrict__ c) {
+    pdl_prologue();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 k = kd[i], a = dd[i], b = ds[i];
@@ -18,9 +19,8 @@ __global__ void composite_kernel(const float4* __restrict__ kd, const float4* __
 
 cudaError_t launch_composite(const float* kd, const float* dd, const float* ds, long long n, float* c,
                              cudaStream_t s) {
-    composite_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(
-        reinterpret_cast<const float4*>(kd), reinterpret_cast<const float4*>(dd), reinterpret_cast<const float4*>(ds),
-        n, reinterpret_cast<float4*>(c));
+    launch_k(composite_kernel, (int)((n + 255) / 256), 256, 0, s, reinterpret_cast<const float4*>(kd),
+             reinterpret_cast<const float4*>(dd), reinterpret_cast<const float4*>(ds), n, reinterpret_cast<float4*>(c));
     return cudaGetLastError();
 }
 

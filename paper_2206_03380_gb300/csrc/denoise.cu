@@ -188,6 +188,7 @@ __device__ __forceinline__ void warp_amax(unsigned* amax, float m) {
 __global__ void pack_input_kernel(const float4* __restrict__ term, const float4* __restrict__ kd,
                                   const float4* __restrict__ nrm, int n_img, int n_aux, int HW, bf16* __restrict__ x,
                                   unsigned* amax) {
+    pdl_prologue();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float m = 0.0f;
     if (i < (long long)n_img * HW) {
@@ -205,6 +206,7 @@ __global__ void pack_input_kernel(const float4* __restrict__ term, const float4*
 // upstream gradient (rgb of float4) -> 16-channel BF16 (channels 3..15 zero)
 __global__ void pack_grad_kernel(const float4* __restrict__ gy, int n_img, int HW, bf16* __restrict__ g,
                                  unsigned* amax) {
+    pdl_prologue();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float m = 0.0f;
     if (i < (long long)n_img * HW) {
@@ -220,6 +222,7 @@ __global__ void pack_grad_kernel(const float4* __restrict__ gy, int n_img, int H
 
 // input gradient of the network (channels 0..2 = the term) -> float4
 __global__ void unpack_grad_kernel(const bf16* __restrict__ g, int n_img, int HW, float4* __restrict__ gx) {
+    pdl_prologue();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n_img * HW) return;
     const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
@@ -244,6 +247,7 @@ __device__ __forceinline__ bool split_index(long long i, int groups, int H, int 
 // 2x2 max-pool of channels [coff, coff + C) of src (Ctot channels, H x W) into dst (C channels)
 __global__ void maxpool2_kernel(const bf16* __restrict__ src, int Ctot, int coff, int C, int n, int H, int W,
                                 bf16* __restrict__ dst, unsigned* amax) {
+    pdl_prologue();
     const int Ho = H >> 1, Wo = W >> 1;
     int img, g, yo, xo;
     float a = 0.0f;
@@ -266,6 +270,7 @@ __global__ void maxpool2_kernel(const bf16* __restrict__ src, int Ctot, int coff
 // the upsampled copy in cat (top-left of the block)
 __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int C, int n,
                                int Hl, int Wl, bf16* __restrict__ glow, unsigned* amax) {
+    pdl_prologue();
     int img, g, y, x;
     float m = 0.0f;
     if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Hl, Wl, &img, &g, &y, &x, n)) {
@@ -293,6 +298,7 @@ __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __rest
 __global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int ecoff,
                                 int C, const bf16* __restrict__ gpool, int n, int H, int W, bf16* __restrict__ gE,
                                 unsigned* amax) {
+    pdl_prologue();
     const int Ho = H >> 1, Wo = W >> 1;
     int img, g, yo, xo;
     float m = 0.0f;
@@ -334,6 +340,7 @@ __global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __res
 // and zero-padded FP32 biases
 __global__ void pack_weights_kernel(const float* __restrict__ W, const float* __restrict__ b, int ci, int co,
                                     bf16* __restrict__ wk, bf16* __restrict__ wf, float* __restrict__ bias) {
+    pdl_prologue();
     const int cip = pad16_dev(ci), cop = pad16_dev(co);
     const long long n = (long long)cop * 9 * cip;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -368,6 +375,7 @@ __device__ __forceinline__ uint4 to_e4m3x16(const float* f, float s) {
 // 16-channel planes), scale 448 / amax
 __global__ void quant_e4m3_kernel(const bf16* __restrict__ x, int C, int n, int HW, const float* __restrict__ amax,
                                   uint8_t* __restrict__ q) {
+    pdl_prologue();
     const int G16 = ((C + 31) & ~31) >> 4;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n * G16 * HW) return;
@@ -388,6 +396,7 @@ __global__ void quant_e4m3_kernel(const bf16* __restrict__ x, int C, int n, int 
 }
 
 __global__ void amax_f32_kernel(const float* __restrict__ w, long long n, unsigned* __restrict__ amax) {
+    pdl_prologue();
     unsigned m = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         m = max(m, __float_as_uint(fabsf(w[i])));
@@ -399,6 +408,7 @@ __global__ void amax_f32_kernel(const float* __restrict__ w, long long n, unsign
 // weights [cip][9][pad32(co)], scale 448 / amax of the convolution's weights
 __global__ void pack_weights_e4m3_kernel(const float* __restrict__ W, int ci, int co, const float* __restrict__ amax,
                                          uint8_t* __restrict__ wk8, uint8_t* __restrict__ wf8) {
+    pdl_prologue();
     const int cip = pad16_dev(ci), cop = pad16_dev(co), ci32 = (ci + 31) & ~31, co32 = (co + 31) & ~31;
     const int cmax_o = co32 > cop ? co32 : cop, cmax_i = ci32 > cip ? ci32 : cip;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -495,8 +505,8 @@ static cudaError_t run_conv(Unet& u, int level, const bf16* x, int x_slot, int c
         }
         const float* am = u.amax + x_slot;
         const int c32 = pad32(cin_pad);
-        quant_e4m3_kernel<<<blocks_for((long long)u.n * (c32 / 16) * Hl * Wl, 256), 256, 0, s>>>(x, cin_pad, u.n,
-                                                                                                  Hl * Wl, am, u.q);
+        launch_k(quant_e4m3_kernel, blocks_for((long long)u.n * (c32 / 16) * Hl * Wl, 256), 256, 0, s, x, cin_pad, u.n,
+                 Hl * Wl, am, u.q);
         CHECK(cudaGetLastError());
         xin = u.q;
         win = u.wbase + (w.dgrad ? u.L.wf8[w.i] : u.L.wk8[w.i]);
@@ -520,15 +530,14 @@ cudaError_t launch_unet_pack_weights(const float* params, void* weights, cudaStr
         const int ci = kPlan[i].ci, co = kPlan[i].co;
         const long long n = (long long)pad16(co) * 9 * pad16(ci);
         const long long nw = (long long)co * ci * 9;
-        pack_weights_kernel<<<blocks_for(n, 256), 256, 0, s>>>(
-            params + off, params + off + (size_t)co * ci * 9, ci, co, reinterpret_cast<bf16*>(base + L.wk[i]),
-            reinterpret_cast<bf16*>(base + L.wf[i]), reinterpret_cast<float*>(base + L.bias[i]));
-        amax_f32_kernel<<<std::min(blocks_for(nw, 256), 256), 256, 0, s>>>(params + off, nw,
-                                                                          reinterpret_cast<unsigned*>(amax + i));
+        launch_k(pack_weights_kernel, blocks_for(n, 256), 256, 0, s, params + off, params + off + (size_t)co * ci * 9,
+                 ci, co, reinterpret_cast<bf16*>(base + L.wk[i]), reinterpret_cast<bf16*>(base + L.wf[i]),
+                 reinterpret_cast<float*>(base + L.bias[i]));
+        launch_k(amax_f32_kernel, std::min(blocks_for(nw, 256), 256), 256, 0, s, params + off, nw,
+                 reinterpret_cast<unsigned*>(amax + i));
         const long long n8 = (long long)std::max(pad32(co), pad16(co)) * 9 * std::max(pad32(ci), pad16(ci));
-        pack_weights_e4m3_kernel<<<blocks_for(n8, 256), 256, 0, s>>>(params + off, ci, co, amax + i,
-                                                                      reinterpret_cast<uint8_t*>(base + L.wk8[i]),
-                                                                      reinterpret_cast<uint8_t*>(base + L.wf8[i]));
+        launch_k(pack_weights_e4m3_kernel, blocks_for(n8, 256), 256, 0, s, params + off, ci, co, amax + i,
+                 reinterpret_cast<uint8_t*>(base + L.wk8[i]), reinterpret_cast<uint8_t*>(base + L.wf8[i]));
         off += (size_t)co * ci * 9 + co;
     }
     return cudaGetLastError();
@@ -550,16 +559,15 @@ cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, in
     }
     auto A = [&](int k) { return reinterpret_cast<bf16*>(a + off[k]); };
     const long long HW = (long long)H * W;
-    pack_input_kernel<<<blocks_for(n * HW, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(term),
-                                                               reinterpret_cast<const float4*>(kd),
-                                                               reinterpret_cast<const float4*>(nrm), n, n_aux,
-                                                               (int)HW, A(X0), u.out(X0));
+    launch_k(pack_input_kernel, blocks_for(n * HW, 256), 256, 0, s, reinterpret_cast<const float4*>(term),
+             reinterpret_cast<const float4*>(kd), reinterpret_cast<const float4*>(nrm), n, n_aux, (int)HW, A(X0),
+             u.out(X0));
     CHECK(cudaGetLastError());
     auto pool = [&](const bf16* src, int Ctot, int coff, int C, int level, int dst_slot) {
         const int Hl = H >> level, Wl = W >> level;
         const long long work = (long long)n * (Hl / 2) * (Wl / 2) * (C / 8);
-        maxpool2_kernel<<<blocks_for(work, 256), 256, 0, s>>>(src, Ctot, coff, C, n, Hl, Wl, A(dst_slot),
-                                                              u.out(dst_slot));
+        launch_k(maxpool2_kernel, blocks_for(work, 256), 256, 0, s, src, Ctot, coff, C, n, Hl, Wl, A(dst_slot),
+                 u.out(dst_slot));
         return cudaGetLastError();
     };
     // level 0
@@ -622,21 +630,21 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
     auto A = [&](int k) { return reinterpret_cast<const bf16*>(a + aoff[k]); };
     auto G = [&](int k) { return reinterpret_cast<bf16*>(g + goff[k]); };
     const long long P0 = (long long)n * H * W;
-    pack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(gy), n, H * W, G(GY),
-                                                         u.out(GY));
+    launch_k(pack_grad_kernel, blocks_for(P0, 256), 256, 0, s, reinterpret_cast<const float4*>(gy), n, H * W, G(GY),
+             u.out(GY));
     CHECK(cudaGetLastError());
     auto up_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int C, int low_level, int glow) {
         const int Hl = H >> low_level, Wl = W >> low_level;
         const long long work = (long long)n * Hl * Wl * (C / 8);
-        up2_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, C, n, Hl, Wl, G(glow), u.out(glow));
+        launch_k(up2_bwd_kernel, blocks_for(work, 256), 256, 0, s, gcat, cat, Ctot, C, n, Hl, Wl, G(glow), u.out(glow));
         return cudaGetLastError();
     };
     auto pool_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int ecoff, int C, const bf16* gpool, int level,
                         int gE) {
         const int Hl = H >> level, Wl = W >> level;
         const long long work = (long long)n * (Hl / 2) * (Wl / 2) * (C / 8);
-        pool_bwd_kernel<<<blocks_for(work, 256), 256, 0, s>>>(gcat, cat, Ctot, ecoff, C, gpool, n, Hl, Wl, G(gE),
-                                                              u.out(gE));
+        launch_k(pool_bwd_kernel, blocks_for(work, 256), 256, 0, s, gcat, cat, Ctot, ecoff, C, gpool, n, Hl, Wl, G(gE),
+                 u.out(gE));
         return cudaGetLastError();
     };
     // out (32 -> 3): dgrad through the ReLU of dec1b
@@ -676,7 +684,7 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
                    A(A1), 32, 0, s, why));
     CHECK(run_conv(u, 0, G(GA1), GA1, 32, Wsel{0, true}, nullptr, 16, 16, kDgradPlain, 0, G(GX0), GX0, 16, 0, nullptr,
                    nullptr, 0, 0, s, why));
-    unpack_grad_kernel<<<blocks_for(P0, 256), 256, 0, s>>>(G(GX0), n, H * W, reinterpret_cast<float4*>(gx_term));
+    launch_k(unpack_grad_kernel, blocks_for(P0, 256), 256, 0, s, G(GX0), n, H * W, reinterpret_cast<float4*>(gx_term));
     return cudaGetLastError();
 }
 

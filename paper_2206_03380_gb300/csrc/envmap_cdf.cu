@@ -50,6 +50,7 @@ __device__ double block_exclusive_scan(double v, double* total) {
 // One block per probe row j: conditional CDF of the row and its sum R_j.
 __global__ void __launch_bounds__(kCdfThreads) row_cdf_kernel(const float4* __restrict__ env, int W, int H,
                                                                float* __restrict__ cond, double* __restrict__ row_sum) {
+    pdl_prologue();
     const int j = blockIdx.x;
     const int chunk = (W + kCdfThreads - 1) / kCdfThreads;
     const int i0 = min(W, threadIdx.x * chunk), i1 = min(W, i0 + chunk);
@@ -85,6 +86,7 @@ constexpr int kMargThreads = 1024;
 // Single block: marginal CDF over the row sums and the normaliser T.
 __global__ void __launch_bounds__(kMargThreads) marg_cdf_kernel(const double* __restrict__ row_sum, int H,
                                                                  float* __restrict__ marg, double* __restrict__ total) {
+    pdl_prologue();
     const int chunk = (H + kMargThreads - 1) / kMargThreads;
     const int j0 = min(H, threadIdx.x * chunk), j1 = min(H, j0 + chunk);
     double local = 0.0;
@@ -109,8 +111,8 @@ __global__ void __launch_bounds__(kMargThreads) marg_cdf_kernel(const double* __
 
 cudaError_t launch_envmap_cdf(const float* env, int W, int H, float* cond, float* marg, double* row_sum,
                               double* total, cudaStream_t stream) {
-    row_cdf_kernel<<<H, kCdfThreads, 0, stream>>>(reinterpret_cast<const float4*>(env), W, H, cond, row_sum);
-    marg_cdf_kernel<<<1, kMargThreads, 0, stream>>>(row_sum, H, marg, total);
+    launch_k(row_cdf_kernel, H, kCdfThreads, 0, stream, reinterpret_cast<const float4*>(env), W, H, cond, row_sum);
+    launch_k(marg_cdf_kernel, 1, kMargThreads, 0, stream, row_sum, H, marg, total);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kLossThreads) image_loss_kernel(
     const float4* __restrict__ kd, const float4* __restrict__ dd, const float4* __restrict__ ds,
     const float4* __restrict__ ref, long long n, float inv_img, float lam_inv_pix, float4* __restrict__ c_out,
     float4* __restrict__ g_kd, float4* __restrict__ g_dd, float4* __restrict__ g_ds, double* __restrict__ partials) {
+    pdl_prologue();
     float s_img = 0.0f, s_light = 0.0f;  // a few pixels per thread; blocks reduce in FP64
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float4 k4 = kd[i], a4 = dd[i], b4 = ds[i], r4 = ref[i];
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(kLossThreads) image_loss_kernel(
 __global__ void __launch_bounds__(kLossThreads) loss_finish_kernel(const double* __restrict__ partials, int n_blocks,
                                                                    long long n, double lam,
                                                                    double* __restrict__ loss) {
+    pdl_prologue();
     __shared__ double red[2][kLossThreads];
     double img = 0.0, light = 0.0;
     for (int b = threadIdx.x; b < n_blocks; b += kLossThreads) {
@@ -125,12 +127,12 @@ cudaError_t launch_image_loss(const float* kd, const float* dd, const float* ds,
                               void* workspace, cudaStream_t s) {
     const int blocks = loss_blocks(n);
     double* partials = static_cast<double*>(workspace);
-    image_loss_kernel<<<blocks, kLossThreads, 0, s>>>(
-        reinterpret_cast<const float4*>(kd), reinterpret_cast<const float4*>(dd), reinterpret_cast<const float4*>(ds),
-        reinterpret_cast<const float4*>(ref), n, (float)(1.0 / (3.0 * (double)n)),
-        (float)((double)lambda_light / (double)n), reinterpret_cast<float4*>(c), reinterpret_cast<float4*>(g_kd),
-        reinterpret_cast<float4*>(g_dd), reinterpret_cast<float4*>(g_ds), partials);
-    loss_finish_kernel<<<1, kLossThreads, 0, s>>>(partials, blocks, n, (double)lambda_light, loss);
+    launch_k(image_loss_kernel, blocks, kLossThreads, 0, s, reinterpret_cast<const float4*>(kd),
+             reinterpret_cast<const float4*>(dd), reinterpret_cast<const float4*>(ds),
+             reinterpret_cast<const float4*>(ref), n, (float)(1.0 / (3.0 * (double)n)),
+             (float)((double)lambda_light / (double)n), reinterpret_cast<float4*>(c), reinterpret_cast<float4*>(g_kd),
+             reinterpret_cast<float4*>(g_dd), reinterpret_cast<float4*>(g_ds), partials);
+    launch_k(loss_finish_kernel, 1, kLossThreads, 0, s, partials, blocks, n, (double)lambda_light, loss);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ constexpr int kSweepThreads = 512;
 // the loads cannot be dropped.
 __global__ void __launch_bounds__(kSweepThreads) read_sweep_kernel(const uint4* __restrict__ buf, long long n16,
                                                                    int passes, unsigned* __restrict__ sink) {
+    pdl_prologue();
     uint32_t acc = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (int p = 0; p < passes; ++p) {
@@ -34,8 +35,8 @@ cudaError_t launch_read_sweep(const void* buf, size_t bytes, int passes, unsigne
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    read_sweep_kernel<<<sms * 4, kSweepThreads, 0, stream>>>(static_cast<const uint4*>(buf), (long long)(bytes / 16),
-                                                             passes, sink);
+    launch_k(read_sweep_kernel, sms * 4, kSweepThreads, 0, stream, static_cast<const uint4*>(buf),
+             (long long)(bytes / 16), passes, sink);
     return cudaGetLastError();
 }
 

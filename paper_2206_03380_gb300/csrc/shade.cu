@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kShadeThreads) primary_cast_kernel(
     int N, int H, int W, const float4* __restrict__ tex_kd, const float4* __restrict__ tex_korm, int S, float uv_ox,
     float uv_oz, float uv_s, float4* __restrict__ gb_pos, float4* __restrict__ gb_nrm, float4* __restrict__ gb_kd,
     float4* __restrict__ gb_korm) {
+    pdl_prologue();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)N * H * W) return;
     const int view = (int)(idx / ((long long)H * W));
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kShadeThreads) shade_fwd_kernel(ShadeArgs a, f
                                                                   float4* __restrict__ kd_out,
                                                                   float4* __restrict__ c_s,
                                                                   uint32_t* __restrict__ vis_mask) {
+    pdl_prologue();
     extern __shared__ float s_marg[];
     Probe Pr = make_probe(a);
     stage_marginal(Pr, s_marg);
@@ -163,6 +165,7 @@ __global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a
                                                                   float4* __restrict__ g_korm,
                                                                   float4* __restrict__ g_nrm,
                                                                   float4* __restrict__ g_env) {
+    pdl_prologue();
     extern __shared__ float s_marg[];  // marginal CDF, then [kBwdQuarters][kBwdPartials][32] partial sums
     Probe Pr = make_probe(a);
     stage_marginal(Pr, s_marg);
@@ -299,11 +302,11 @@ cudaError_t launch_primary_cast(const void* nodes, const void* tris, int n_tris,
                                 float uv_oz, float uv_s, float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm,
                                 cudaStream_t stream) {
     const long long P = (long long)N * H * W;
-    primary_cast_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, 0, stream>>>(
-        static_cast<const BvhNode*>(nodes), static_cast<const TriRecord*>(tris), n_tris, verts, vnrm, tri_idx,
-        n_verts, cams, N, H, W, reinterpret_cast<const float4*>(tex_kd), reinterpret_cast<const float4*>(tex_korm),
-        tex_size, uv_ox, uv_oz, uv_s, reinterpret_cast<float4*>(gb_pos), reinterpret_cast<float4*>(gb_nrm),
-        reinterpret_cast<float4*>(gb_kd), reinterpret_cast<float4*>(gb_korm));
+    launch_k(primary_cast_kernel, grid_for(P, kShadeThreads), kShadeThreads, 0, stream,
+             static_cast<const BvhNode*>(nodes), static_cast<const TriRecord*>(tris), n_tris, verts, vnrm, tri_idx,
+             n_verts, cams, N, H, W, reinterpret_cast<const float4*>(tex_kd), reinterpret_cast<const float4*>(tex_korm),
+             tex_size, uv_ox, uv_oz, uv_s, reinterpret_cast<float4*>(gb_pos), reinterpret_cast<float4*>(gb_nrm),
+             reinterpret_cast<float4*>(gb_kd), reinterpret_cast<float4*>(gb_korm));
     return cudaGetLastError();
 }
 
@@ -311,7 +314,7 @@ cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, fl
                              cudaStream_t stream) {
     const long long P = (long long)a.N * a.H * a.W;
     const size_t smem = (size_t)(a.Hp + 1) * sizeof(float);
-    shade_fwd_kernel<<<grid_for(P, kShadeThreads), kShadeThreads, smem, stream>>>(a, c_d, kd_out, c_s, vis_mask);
+    launch_k(shade_fwd_kernel, grid_for(P, kShadeThreads), kShadeThreads, smem, stream, a, c_d, kd_out, c_s, vis_mask);
     return cudaGetLastError();
 }
 
@@ -320,8 +323,8 @@ cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float
                              cudaStream_t stream) {
     const long long P = (long long)a.N * a.H * a.W;
     const size_t smem = (size_t)(((a.Hp + 1 + 3) & ~3) + kBwdQuarters * kBwdPartials * 32) * sizeof(float);
-    shade_bwd_kernel<<<grid_for(P, 32), kShadeThreads, smem, stream>>>(a, g_cd, g_kdout, g_cs, vis_mask, g_kd, g_korm,
-                                                                    g_nrm, g_env);
+    launch_k(shade_bwd_kernel, grid_for(P, 32), kShadeThreads, smem, stream, a, g_cd, g_kdout, g_cs, vis_mask, g_kd,
+             g_korm, g_nrm, g_env);
     return cudaGetLastError();
 }
 

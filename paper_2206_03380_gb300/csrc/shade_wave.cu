@@ -59,6 +59,7 @@ __device__ __forceinline__ Probe wave_probe(const ShadeArgs& a) {
 }
 
 __global__ void wave_reset_kernel(void* ws, long long slots) {
+    pdl_prologue();
     WaveBuffers B = wave_buffers(ws, slots);
     B.counter[0] = 0u;
     B.counter[1] = 0u;
@@ -76,6 +77,7 @@ __global__ void wave_reset_kernel(void* ws, long long slots) {
 constexpr int kGenQuarters = kGenThreads / 32;
 
 __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void* ws, float4* __restrict__ kd_out) {
+    pdl_prologue();
     extern __shared__ float s_marg[];
     const int lane = threadIdx.x & 31, quarter = threadIdx.x >> 5;
     const long long idx0 = (long long)blockIdx.x * 32 + lane;
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
 __global__ void __launch_bounds__(kTraceThreads, 16) wave_trace_kernel(const void* __restrict__ nodes,
                                                                    const TriRecord* __restrict__ tris, int n_tris,
                                                                    void* ws, long long slots) {
+    pdl_prologue();
     WaveBuffers B = wave_buffers(ws, slots);
     const long long n_rays = (long long)*((volatile unsigned*)B.counter);
     const unsigned full = 0xffffffffu;
@@ -204,6 +207,7 @@ __global__ void __launch_bounds__(kTraceThreads, 16) wave_trace_kernel(const voi
 __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, const void* ws,
                                                                  float4* __restrict__ c_d, float4* __restrict__ c_s,
                                                                  uint32_t* __restrict__ vis_mask) {
+    pdl_prologue();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long P = (long long)a.N * a.H * a.W;
     if (idx >= P) return;
@@ -247,6 +251,7 @@ __global__ void __launch_bounds__(kTraceThreads) wave_stats_kernel(const void* _
                                                                    const TriRecord* __restrict__ tris, int n_tris,
                                                                    const void* ws, long long slots,
                                                                    unsigned long long* __restrict__ stats) {
+    pdl_prologue();
     WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
     const long long n_rays = (long long)B.counter[0];
     unsigned long long c[5] = {0, 0, 0, 0, 0};
@@ -295,8 +300,8 @@ cudaError_t launch_shadow_ray_stats(const ShadeArgs& a, const void* ws, unsigned
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    wave_stats_kernel<<<sms * 8, kTraceThreads, 0, stream>>>(a.nodes, static_cast<const TriRecord*>(a.tris), a.n_tris,
-                                                             ws, slots, stats);
+    launch_k(wave_stats_kernel, sms * 8, kTraceThreads, 0, stream, a.nodes, static_cast<const TriRecord*>(a.tris),
+             a.n_tris, ws, slots, stats);
     return cudaGetLastError();
 }
 
@@ -311,8 +316,8 @@ cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
     if (per_sm < 1) per_sm = 1;
-    wave_trace_kernel<<<sms * per_sm, kTraceThreads, 0, stream>>>(a.nodes, static_cast<const TriRecord*>(a.tris),
-                                                                  a.n_tris, ws, slots);
+    launch_k(wave_trace_kernel, sms * per_sm, kTraceThreads, 0, stream, a.nodes, static_cast<const TriRecord*>(a.tris),
+             a.n_tris, ws, slots);
     return cudaGetLastError();
 }
 
@@ -325,17 +330,17 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
-    wave_reset_kernel<<<1, 1, 0, stream>>>(ws, P * spp);
-    wave_gen_kernel<<<(int)((P + 31) / 32), kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream>>>(a, ws,
-                                                                                                       kd_out);
+    launch_k(wave_reset_kernel, 1, 1, 0, stream, ws, P * spp);
+    launch_k(wave_gen_kernel, (int)((P + 31) / 32), kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream, a, ws,
+             kd_out);
     int dev = 0, sms = 152, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
     if (per_sm < 1) per_sm = 1;
-    wave_trace_kernel<<<sms * per_sm, kTraceThreads, 0, stream>>>(a.nodes, static_cast<const TriRecord*>(a.tris),
-                                                                  a.n_tris, ws, P * spp);
-    wave_accum_kernel<<<gblocks, kGenThreads, 0, stream>>>(a, ws, c_d, c_s, vis_mask);
+    launch_k(wave_trace_kernel, sms * per_sm, kTraceThreads, 0, stream, a.nodes, static_cast<const TriRecord*>(a.tris),
+             a.n_tris, ws, P * spp);
+    launch_k(wave_accum_kernel, gblocks, kGenThreads, 0, stream, a, ws, c_d, c_s, vis_mask);
     return cudaGetLastError();
 }
 

@@ -274,6 +274,7 @@ template <bool FP8>
 __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_x,
                                                                const __grid_constant__ CUtensorMap tmap_w,
                                                                const ConvParams p) {
+    pdl_prologue();
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], acc_bar;
     __shared__ uint32_t tmem_slot;
@@ -435,6 +436,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 template <int R, bool FP8, bool MP>
 __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
+    pdl_prologue();
     extern __shared__ uint8_t smem_raw[];
     __shared__ float s_bias[256];
     __shared__ __align__(8) uint64_t full_bar[kRowMaxStages], empty_bar[kRowMaxStages], accf_bar[2], acce_bar[2],
@@ -896,9 +898,9 @@ template <bool FP8, bool MP>
 static void launch_rows(const ConvDesc& d, cudaStream_t stream) {
     const dim3 g(d.rp.grid), t(kRowThreads);
     const size_t sm = d.rp.smem_bytes;
-    if (d.rp.rows == 4) conv_tc_rows_kernel<4, FP8, MP><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-    else if (d.rp.rows == 2) conv_tc_rows_kernel<2, FP8, MP><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
-    else conv_tc_rows_kernel<1, FP8, MP><<<g, t, sm, stream>>>(d.tmap_wh, d.p, d.rp);
+    if (d.rp.rows == 4) launch_k(conv_tc_rows_kernel<4, FP8, MP>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else if (d.rp.rows == 2) launch_k(conv_tc_rows_kernel<2, FP8, MP>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else launch_k(conv_tc_rows_kernel<1, FP8, MP>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
 }
 
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
@@ -928,8 +930,8 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     }
     const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;
     const size_t smem = conv_smem_bytes(d.p.cout_pad);
-    if (d.p.fp8) conv_tc_kernel<true><<<n_tiles, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
-    else conv_tc_kernel<false><<<n_tiles, kConvThreads, smem, stream>>>(d.tmap_x, d.tmap_w, d.p);
+    if (d.p.fp8) launch_k(conv_tc_kernel<true>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
+    else launch_k(conv_tc_kernel<false>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
     return cudaGetLastError();
 }
 
