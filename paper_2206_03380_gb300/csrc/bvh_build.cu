@@ -124,21 +124,30 @@ __global__ void __launch_bounds__(256) morton_kernel(const float* __restrict__ v
     vals[k] = (uint32_t)k;
 }
 
-// ---- radix sort: one 8-bit digit per pass ----
+// ---- radix sort: 30-bit Morton keys in three passes of one 10-bit digit ----
+// (LSD and stable, so equal keys keep their triangle order)
+constexpr int kDigits = 1 << kSortDigitBits;
+constexpr int kDigitsPerThread = kDigits / kSortThreads;
+
 __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift,
                                                                   int nblocks, uint32_t* __restrict__ hist) {
     pdl_prologue();
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[kDigits];
+#pragma unroll
+    for (int q = 0; q < kDigitsPerThread; ++q) h[q * kSortThreads + threadIdx.x] = 0;
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * kSortTile;
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const size_t i = base + (size_t)it * kSortThreads + threadIdx.x;
-        if (i < (size_t)n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        if (i < (size_t)n) atomicAdd(&h[(keys[i] >> shift) & (kDigits - 1)], 1u);
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+#pragma unroll
+    for (int q = 0; q < kDigitsPerThread; ++q) {
+        const int d = q * kSortThreads + threadIdx.x;
+        hist[(size_t)d * nblocks + blockIdx.x] = h[d];
+    }
 }
 
 // one block per digit: exclusive scan of that digit's counts across tiles
@@ -181,14 +190,21 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
     uint32_t* __restrict__ vals_out) {
     pdl_prologue();
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t wc[kWarps][256];  // per-warp digit counters, then per-warp offsets
-    __shared__ uint32_t dbase[256];       // global start of each digit
+    __shared__ uint32_t wc[kWarps][kDigits];  // per-warp digit counters, then per-warp offsets
+    __shared__ uint32_t dbase[kDigits];       // global start of each digit in this tile
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int w = 0; w < kWarps; ++w) wc[w][threadIdx.x] = 0;
-    {  // exclusive scan of the 256 digit totals
+    for (int w = 0; w < kWarps; ++w)
+#pragma unroll
+        for (int q = 0; q < kDigitsPerThread; ++q) wc[w][q * kSortThreads + threadIdx.x] = 0;
+    {  // exclusive scan of the digit totals: thread t owns digits [t * kDigitsPerThread, +kDigitsPerThread)
         __shared__ uint32_t wt[kWarps];
-        const uint32_t v = digit_tot[threadIdx.x];
-        uint32_t inc = v;
+        uint32_t v[kDigitsPerThread], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kDigitsPerThread; ++q) {
+            v[q] = digit_tot[threadIdx.x * kDigitsPerThread + q];
+            sum += v[q];
+        }
+        uint32_t inc = sum;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
@@ -196,9 +212,14 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
         }
         if (lane == 31) wt[warp] = inc;
         __syncthreads();
-        uint32_t woff = 0;
-        for (int w = 0; w < warp; ++w) woff += wt[w];
-        dbase[threadIdx.x] = woff + inc - v + hist[(size_t)threadIdx.x * nblocks + blockIdx.x];
+        uint32_t run = inc - sum;
+        for (int w = 0; w < warp; ++w) run += wt[w];
+#pragma unroll
+        for (int q = 0; q < kDigitsPerThread; ++q) {
+            const int d = threadIdx.x * kDigitsPerThread + q;
+            dbase[d] = run + hist[(size_t)d * nblocks + blockIdx.x];
+            run += v[q];
+        }
     }
     __syncthreads();
     // warp w ranks elements [base + w*256, base + (w+1)*256) in order, 32 at a time
@@ -211,7 +232,7 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
         const bool valid = i < (size_t)n;
         key[it] = valid ? keys_in[i] : 0u;
         val[it] = valid ? vals_in[i] : 0u;
-        const uint32_t d = valid ? ((key[it] >> shift) & 255u) : (256u + lane);
+        const uint32_t d = valid ? ((key[it] >> shift) & (kDigits - 1)) : ((uint32_t)kDigits + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = 0;
         if (valid) before = wc[warp][d];
@@ -221,11 +242,14 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
         rank[it] = before + __popc(peers & lt);
     }
     __syncthreads();
-    {  // per digit: exclusive scan over warps (warp order = element order)
+    // per digit: exclusive scan over warps (warp order = element order)
+#pragma unroll
+    for (int q = 0; q < kDigitsPerThread; ++q) {
+        const int d = q * kSortThreads + threadIdx.x;
         uint32_t run = 0;
         for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = wc[w][threadIdx.x];
-            wc[w][threadIdx.x] = run;
+            const uint32_t c = wc[w][d];
+            wc[w][d] = run;
             run += c;
         }
     }
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
     for (int it = 0; it < kSortItems; ++it) {
         const size_t i = base + (size_t)it * 32 + lane;
         if (i < (size_t)n) {
-            const uint32_t d = (key[it] >> shift) & 255u;
+            const uint32_t d = (key[it] >> shift) & (kDigits - 1);
             const uint32_t pos = dbase[d] + wc[warp][d] + rank[it];
             keys_out[pos] = key[it];
             vals_out[pos] = val[it];
@@ -437,9 +461,10 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
     launch_k(centroid_bounds_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds);
     launch_k(morton_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds, keys[0], vals[0]);
     int cur = 0;
-    for (int shift = 0; shift < 32; shift += 8) {
+    for (int pass = 0; pass < kSortPasses; ++pass) {
+        const int shift = pass * kSortDigitBits;
         launch_k(digit_hist_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], n, shift, L.nblocks, hist);
-        launch_k(digit_scan_kernel, 256, 256, 0, stream, hist, L.nblocks, dtot);
+        launch_k(digit_scan_kernel, kDigits, 256, 0, stream, hist, L.nblocks, dtot);
         launch_k(digit_scatter_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], vals[cur], n, shift, L.nblocks,
                  hist, dtot, keys[cur ^ 1], vals[cur ^ 1]);
         cur ^= 1;
@@ -463,12 +488,12 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
 // New vertex positions, same triangles: the leaf order (the final sort pass's
 // values), the hierarchy links and the parent arrays from the last build stay;
 // triangle records, leaf boxes, internal boxes and the depth-first copy are
-// recomputed (3 or 4 launches instead of 19).
+// recomputed (3 launches instead of 16).
 cudaError_t launch_refit_bvh(const float* verts, int n_verts, const int* tris, int n, void* nodes_v, void* recs_v,
                              void* scratch, const BvhScratch& L, cudaStream_t stream) {
     char* s = static_cast<char*>(scratch);
-    // four 8-bit passes end in the first key/value buffer
-    const uint32_t* order = reinterpret_cast<const uint32_t*>(s + L.vals0);
+    // the sort's passes alternate between the two key/value buffers
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(s + (kSortPasses % 2 ? L.vals1 : L.vals0));
     int* parent_int = reinterpret_cast<int*>(s + L.parent_int);
     int* parent_leaf = reinterpret_cast<int*>(s + L.parent_leaf);
     uint32_t* flags = reinterpret_cast<uint32_t*>(s + L.flags);

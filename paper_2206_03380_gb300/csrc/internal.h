@@ -19,6 +19,9 @@ struct BvhScratch {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortDigitBits = 10;  // 30-bit Morton keys: three passes
+constexpr int kSortPasses = 3;
+static_assert(kSortDigitBits * kSortPasses >= 30, "the passes must cover the 30 key bits");
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -33,8 +36,8 @@ inline BvhScratch bvh_scratch_layout(int n) {
     s.keys1 = o; o = align256(o + un * sizeof(uint32_t));
     s.vals0 = o; o = align256(o + un * sizeof(uint32_t));
     s.vals1 = o; o = align256(o + un * sizeof(uint32_t));
-    s.hist = o; o = align256(o + (size_t)256 * s.nblocks * sizeof(uint32_t));
-    s.digit_tot = o; o = align256(o + 256 * sizeof(uint32_t));
+    s.hist = o; o = align256(o + ((size_t)1 << kSortDigitBits) * s.nblocks * sizeof(uint32_t));
+    s.digit_tot = o; o = align256(o + ((size_t)1 << kSortDigitBits) * sizeof(uint32_t));
     s.parent_int = o; o = align256(o + ni * sizeof(int));
     s.parent_leaf = o; o = align256(o + un * sizeof(int));
     s.flags = o; o = align256(o + ni * sizeof(uint32_t));
