@@ -70,10 +70,10 @@ enum Act { X0, A1, CAT1, P1, A2, CAT2, P2, A3, CAT3, P3, B1, D3A, D2A, D1A, D1B,
 static const int kActC[kActs] = {16, 32, 80, 32, 48, 112, 48, 64, 160, 64, 96, 64, 48, 32, 32};
 static const int kActLvl[kActs] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 2, 1, 0, 0};
 enum Grad { GY, GD1B, GD1A, GCAT1, GD2B, GD2A, GCAT2, GD3B, GD3A, GCAT3, GB2, GB1, GP3, GE3, GA3, GP2, GE2, GA2,
-            GP1, GE1, GA1, GX0, kGrads };
+            GP1, GE1, GA1, kGrads };
 static const int kGradC[kGrads] = {16, 32, 32, 80, 48, 48, 112, 64, 64, 160, 96, 96, 64, 64, 64, 48, 48, 48,
-                                   32, 32, 32, 16};
-static const int kGradLvl[kGrads] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0};
+                                   32, 32, 32};
+static const int kGradLvl[kGrads] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0};
 
 static size_t level_pixels(int n, int H, int W, int l) { return (size_t)n * (H >> l) * (W >> l); }
 
@@ -218,17 +218,6 @@ __global__ void pack_grad_kernel(const float4* __restrict__ gy, int n_img, int H
         m = max8(m, f0);
     }
     warp_amax(amax, m);
-}
-
-// input gradient of the network (channels 0..2 = the term) -> float4
-__global__ void unpack_grad_kernel(const bf16* __restrict__ g, int n_img, int HW, float4* __restrict__ gx) {
-    pdl_prologue();
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)n_img * HW) return;
-    const int img = (int)(i / HW), p = (int)(i - (long long)img * HW);
-    float f[8];
-    ld8(g + ((size_t)img * 2 * HW + p) * 8, f);
-    gx[i] = make_float4(f[0], f[1], f[2], 0.0f);
 }
 
 // thread index -> (img, group, y, x) with x fastest
@@ -488,10 +477,17 @@ static ConvDesc conv_desc(int n, int H, int W, int cin_pad, int cin_bytes, const
 // producers that published its amax) into tensor out_slot (-1: no E4M3
 // consumer).  In E4M3 mode the input is first quantised with its amax and the
 // E4M3 weights are used.
+struct PoolTo {  // a 2x2 max-pool of the convolution's output, into tensor `slot`
+    bf16* out = nullptr;
+    int ctotal = 0;
+    int slot = -1;
+    bool* done = nullptr;  // set when the convolution's epilogue wrote it
+};
+
 static cudaError_t run_conv(Unet& u, int level, const bf16* x, int x_slot, int cin_pad, Wsel w, const float* bias,
                             int cout_pad, int cout_valid, int mode, int relu, bf16* out, int out_slot, int out_ctotal,
                             int out_coff, float4* out_f32, const bf16* mask, int mask_ctotal, int mask_coff,
-                            cudaStream_t s, const char** why) {
+                            cudaStream_t s, const char** why, PoolTo pool = PoolTo{}) {
     const int Hl = u.H >> level, Wl = u.W >> level;
     ConvDesc d = conv_desc(u.n, Hl, Wl, cin_pad, 2 * cin_pad, bias, cout_pad, cout_valid, mode, relu, out, out_ctotal,
                            out_coff, out_f32, mask, mask_ctotal, mask_coff, u.err);
@@ -517,6 +513,12 @@ static cudaError_t run_conv(Unet& u, int level, const bf16* x, int x_slot, int c
         d.p.w_amax = reinterpret_cast<const float*>(u.wbase + u.L.amax) + w.i;
     }
     if (!conv_make_desc(&d, xin, win, why)) return cudaErrorInvalidValue;
+    if (pool.out && d.rows_form && d.rp.rows % 2 == 0 && d.rp.nc <= 64 && mode == kStore) {
+        d.p.pool_out = pool.out;
+        d.p.pool_ctotal = pool.ctotal;
+        d.p.pool_amax = u.out(pool.slot);
+        *pool.done = true;
+    }
     return conv_launch(d, s);
 }
 
@@ -573,21 +575,24 @@ cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, in
     // level 0
     CHECK(run_conv(u, 0, A(X0), X0, 16, Wsel{0, false}, b_of(u, 0), 32, 32, kStore, 1, A(A1), A1, 32, 0, nullptr,
                    nullptr, 0, 0, s, why));
+    bool pooled = false;
     CHECK(run_conv(u, 0, A(A1), A1, 32, Wsel{1, false}, b_of(u, 1), 32, 32, kStore, 1, A(CAT1), CAT1, 80, 48, nullptr,
-                   nullptr, 0, 0, s, why));
-    CHECK(pool(A(CAT1), 80, 48, 32, 0, P1));
+                   nullptr, 0, 0, s, why, PoolTo{A(P1), 32, P1, &pooled}));
+    if (!pooled) CHECK(pool(A(CAT1), 80, 48, 32, 0, P1));
     // level 1
     CHECK(run_conv(u, 1, A(P1), P1, 32, Wsel{2, false}, b_of(u, 2), 48, 48, kStore, 1, A(A2), A2, 48, 0, nullptr,
                    nullptr, 0, 0, s, why));
+    pooled = false;
     CHECK(run_conv(u, 1, A(A2), A2, 48, Wsel{3, false}, b_of(u, 3), 48, 48, kStore, 1, A(CAT2), CAT2, 112, 64,
-                   nullptr, nullptr, 0, 0, s, why));
-    CHECK(pool(A(CAT2), 112, 64, 48, 1, P2));
+                   nullptr, nullptr, 0, 0, s, why, PoolTo{A(P2), 48, P2, &pooled}));
+    if (!pooled) CHECK(pool(A(CAT2), 112, 64, 48, 1, P2));
     // level 2
     CHECK(run_conv(u, 2, A(P2), P2, 48, Wsel{4, false}, b_of(u, 4), 64, 64, kStore, 1, A(A3), A3, 64, 0, nullptr,
                    nullptr, 0, 0, s, why));
+    pooled = false;
     CHECK(run_conv(u, 2, A(A3), A3, 64, Wsel{5, false}, b_of(u, 5), 64, 64, kStore, 1, A(CAT3), CAT3, 160, 96,
-                   nullptr, nullptr, 0, 0, s, why));
-    CHECK(pool(A(CAT3), 160, 96, 64, 2, P3));
+                   nullptr, nullptr, 0, 0, s, why, PoolTo{A(P3), 64, P3, &pooled}));
+    if (!pooled) CHECK(pool(A(CAT3), 160, 96, 64, 2, P3));
     // bottleneck (level 3): second conv stores its 2x upsample into the level-2 concatenation
     CHECK(run_conv(u, 3, A(P3), P3, 64, Wsel{6, false}, b_of(u, 6), 96, 96, kStore, 1, A(B1), B1, 96, 0, nullptr,
                    nullptr, 0, 0, s, why));
@@ -682,9 +687,9 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
     CHECK(pool_bwd(G(GCAT1), A(CAT1), 80, 48, 32, G(GP1), 0, GE1));
     CHECK(run_conv(u, 0, G(GE1), GE1, 32, Wsel{1, true}, nullptr, 32, 32, kDgradMask, 0, G(GA1), GA1, 32, 0, nullptr,
                    A(A1), 32, 0, s, why));
-    CHECK(run_conv(u, 0, G(GA1), GA1, 32, Wsel{0, true}, nullptr, 16, 16, kDgradPlain, 0, G(GX0), GX0, 16, 0, nullptr,
-                   nullptr, 0, 0, s, why));
-    launch_k(unpack_grad_kernel, blocks_for(P0, 256), 256, 0, s, G(GX0), n, H * W, reinterpret_cast<float4*>(gx_term));
+    // the input gradient of the term channels (0..2) straight out of the last convolution's epilogue, as float4
+    CHECK(run_conv(u, 0, G(GA1), GA1, 32, Wsel{0, true}, nullptr, 16, 3, kStoreF32, 0, nullptr, -1, 0, 0,
+                   reinterpret_cast<float4*>(gx_term), nullptr, 0, 0, s, why));
     return cudaGetLastError();
 }
 

@@ -201,7 +201,7 @@ __device__ __forceinline__ void load_mask16(const ConvParams& p, int c0, int img
 // groups) of one pixel; pre: the pixel's mask words are already in (ma, mb)
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
                                            const float* bias16, float dq, float* amax, bool pre = false,
-                                           uint4 ma = uint4{}, uint4 mb = uint4{}) {
+                                           uint4 ma = uint4{}, uint4 mb = uint4{}, uint32_t* keep = nullptr) {
     float f[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]) * dq;
@@ -231,6 +231,13 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
         f[i] += bias16 ? bias16[i] : 0.0f;
         if (p.relu) f[i] = fmaxf(f[i], 0.0f);
         *amax = fmaxf(*amax, fabsf(f[i]));
+    }
+    if (keep) {  // the 16 stored values as packed BF16 pairs
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+            keep[i] = *reinterpret_cast<uint32_t*>(&h);
+        }
     }
     if (p.mode == kStoreF32) {
         p.out_f32[((size_t)img * p.H + y) * p.W + x] = make_float4(f[0], f[1], f[2], 0.0f);
@@ -433,7 +440,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int R, bool FP8, bool MP>
+template <int R, bool FP8, bool MP, bool PL>
 __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
     pdl_prologue();
@@ -647,6 +654,13 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
                 nb1 = w[1];
             }
         };
+        // 2x2 max-pool of the stored values: the two pixels of a window are neighbouring
+        // lanes, its two rows consecutive rows of this thread (R even, tiles start on even
+        // rows and columns); the maxima are taken on the stored BF16 values
+        // (PL: the instantiation for the convolutions that feed a pooling layer)
+        const bool pool = PL && R % 2 == 0 && p.pool_out != nullptr && p.mode == kStore && Nc <= 2 * cstep;
+        float pool_amax = 0.0f;
+        uint32_t ha[8], hb[8];  // the even row's stored values of chunks c0 / c1, packed BF16 pairs
         int i = 0;
         for (int t = first; t < rp.n_tiles; t += step, ++i) {
             const int b = i & 1;
@@ -662,7 +676,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
             }
             tc_fence_after();
             const float dq = dequant_factor(p);
-            constexpr int kRowUnroll = MP ? 1 : R;  // the prefetch registers leave no room for a 4x unroll
+            constexpr int kRowUnroll = MP || PL ? 1 : R;  // prefetch / pool registers leave no room to unroll
 #pragma unroll kRowUnroll
             for (int r = 0; r < R; ++r) {
                 const int y = y0 + r;
@@ -677,10 +691,51 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
                     tmem_ld16_async(tr + (uint32_t)c0, v);
                     if (two) tmem_ld16_async(tr + (uint32_t)c1, v + 16);
                     tmem_wait_ld();
-                    if (valid && n0 + c0 < p.cout_valid)
-                        epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, pref, ca0, ca1);
-                    if (two && valid && n0 + c1 < p.cout_valid)
-                        epilogue16(p, v + 16, n0 + c1, img, x, y, s_bias + c1, dq, &amax, pref, cb0, cb1);
+                    uint32_t ka[8], kb[8];
+                    const bool va = valid && n0 + c0 < p.cout_valid, vb = two && valid && n0 + c1 < p.cout_valid;
+                    if (va) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, pref, ca0, ca1, ka);
+                    if (vb) epilogue16(p, v + 16, n0 + c1, img, x, y, s_bias + c1, dq, &amax, pref, cb0, cb1, kb);
+                    if (pool) {
+                        if ((r & 1) == 0) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                ha[k] = ka[k];
+                                hb[k] = kb[k];
+                            }
+                        } else {
+                            const int Hp = p.H >> 1, Wp = p.W >> 1;
+                            auto pool_store = [&](const uint32_t* h, const uint32_t* k, int c, bool ok) {
+                                uint32_t w[8];
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&h[j]);
+                                    __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&k[j]);
+                                    a = __hmax2(a, b);
+                                    uint32_t u = *reinterpret_cast<uint32_t*>(&a);
+                                    const uint32_t o = __shfl_xor_sync(0xffffffffu, u, 1);
+                                    a = __hmax2(a, *reinterpret_cast<const __nv_bfloat162*>(&o));
+                                    w[j] = *reinterpret_cast<uint32_t*>(&a);
+                                }
+                                if ((lane & 1) == 0 && ok) {
+                                    __nv_bfloat16* dst = p.pool_out + plane_off(img, p.pool_ctotal >> 3, c >> 3, Hp, Wp,
+                                                                                y >> 1, x >> 1);
+                                    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                                    *reinterpret_cast<uint4*>(dst + (size_t)Hp * Wp * 8) =
+                                        make_uint4(w[4], w[5], w[6], w[7]);
+                                    if (p.pool_amax) {
+#pragma unroll
+                                        for (int j = 0; j < 8; ++j) {
+                                            const float2 f2 = __bfloat1622float2(
+                                                *reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+                                            pool_amax = fmaxf(pool_amax, fmaxf(fabsf(f2.x), fabsf(f2.y)));
+                                        }
+                                    }
+                                }
+                            };
+                            pool_store(ha, ka, n0 + c0, va);
+                            pool_store(hb, kb, n0 + c1, vb);
+                        }
+                    }
                     __syncwarp();
                 }
             }
@@ -689,6 +744,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
             if (lane == 0) mbar_arrive(smem_u32(&acce_bar[b]));
         }
         publish_amax(p.out_amax, amax, 0xffffffffu);
+        if (pool) publish_amax(p.pool_amax, pool_amax, 0xffffffffu);
     }
 
     tc_fence_before();
@@ -741,7 +797,7 @@ const DeviceLimits& device_limits() {
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false, false>) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false, false, false>) != cudaSuccess ||
             optin <= (int)fa.sharedSizeBytes) {
             L.sms = 0;
             return;
@@ -885,22 +941,23 @@ bool conv_make_desc(ConvDesc* d, const void* x, const void* w, const char** why)
     return true;
 }
 
-template <bool FP8, bool MP>
+template <bool FP8, bool MP, bool PL>
 static void set_rows_smem(int bytes, cudaError_t* err) {
-    const void* fs[3] = {(const void*)conv_tc_rows_kernel<1, FP8, MP>, (const void*)conv_tc_rows_kernel<2, FP8, MP>,
-                         (const void*)conv_tc_rows_kernel<4, FP8, MP>};
+    const void* fs[3] = {(const void*)conv_tc_rows_kernel<1, FP8, MP, PL>,
+                         (const void*)conv_tc_rows_kernel<2, FP8, MP, PL>,
+                         (const void*)conv_tc_rows_kernel<4, FP8, MP, PL>};
     for (const void* f : fs)
         if (*err == cudaSuccess && bytes > 0)
             *err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <bool FP8, bool MP>
+template <bool FP8, bool MP, bool PL>
 static void launch_rows(const ConvDesc& d, cudaStream_t stream) {
     const dim3 g(d.rp.grid), t(kRowThreads);
     const size_t sm = d.rp.smem_bytes;
-    if (d.rp.rows == 4) launch_k(conv_tc_rows_kernel<4, FP8, MP>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
-    else if (d.rp.rows == 2) launch_k(conv_tc_rows_kernel<2, FP8, MP>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
-    else launch_k(conv_tc_rows_kernel<1, FP8, MP>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    if (d.rp.rows == 4) launch_k(conv_tc_rows_kernel<4, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else if (d.rp.rows == 2) launch_k(conv_tc_rows_kernel<2, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else launch_k(conv_tc_rows_kernel<1, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
 }
 
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
@@ -915,17 +972,27 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
         if (attr_err == cudaSuccess)
             attr_err = cudaFuncSetAttribute((const void*)conv_tc_kernel<true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tile);
-        set_rows_smem<false, false>(lim, &attr_err);
-        set_rows_smem<true, false>(lim, &attr_err);
-        set_rows_smem<false, true>(lim, &attr_err);
-        set_rows_smem<true, true>(lim, &attr_err);
+        set_rows_smem<false, false, false>(lim, &attr_err);
+        set_rows_smem<true, false, false>(lim, &attr_err);
+        set_rows_smem<false, true, false>(lim, &attr_err);
+        set_rows_smem<true, true, false>(lim, &attr_err);
+        set_rows_smem<false, false, true>(lim, &attr_err);
+        set_rows_smem<true, false, true>(lim, &attr_err);
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (d.rows_form) {
         // masked input gradients whose mask words fit the prefetch registers take the prefetching variant
         const bool mp = d.p.mode == kDgradMask && d.rp.nc <= 64;
-        if (d.p.fp8) mp ? launch_rows<true, true>(d, stream) : launch_rows<true, false>(d, stream);
-        else mp ? launch_rows<false, true>(d, stream) : launch_rows<false, false>(d, stream);
+        const bool pl = d.p.pool_out != nullptr;  // conv_make_desc keeps it only where the plan can pool
+        if (d.p.fp8) {
+            if (mp) launch_rows<true, true, false>(d, stream);
+            else if (pl) launch_rows<true, false, true>(d, stream);
+            else launch_rows<true, false, false>(d, stream);
+        } else {
+            if (mp) launch_rows<false, true, false>(d, stream);
+            else if (pl) launch_rows<false, false, true>(d, stream);
+            else launch_rows<false, false, false>(d, stream);
+        }
         return cudaGetLastError();
     }
     const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;

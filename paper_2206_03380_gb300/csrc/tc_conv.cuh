@@ -43,6 +43,12 @@ struct ConvParams {
     int mask_ctotal, mask_coff;
     unsigned* err;             // device error word (set on a wait timeout)
     unsigned* out_amax;        // nullable: max |stored value| of the output (float bits), for E4M3 consumers
+    // nullable (kStore in the row-tile form with an even number of rows per tile, at most 64 channels per
+    // CTA): the 2x2 max-pool of the stored channels, into 8-channel planes of pool_ctotal channels at
+    // (H / 2, W / 2), output channel c at pool channel c; pool_amax as out_amax for the pooled tensor
+    __nv_bfloat16* pool_out;
+    int pool_ctotal;
+    unsigned* pool_amax;
 };
 
 // Launch plan of the row-tile form (tiles of `rows` x 128 pixels, weights of
