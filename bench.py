@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd MC shading Msamples/s & %HBM roofline at 512² 16spp"
 # DRAM bytes (read + write) per call of a stage's kernels at the headline size, from one ncu capture
 # (profiles/dram_traffic_shade_512x512_16spp.md); set to None when those kernels change.
-MEASURED_TRAFFIC = {"shade_fwd": 201.8e6}
+MEASURED_TRAFFIC = {"shade_fwd": 201.9e6}
 UNIT = "Msamples/s"
 L2_FLUSH_BYTES = 512 << 20
 
