@@ -45,6 +45,11 @@ REC_DTYPE = np.dtype([("wi", "<f8", (3,)), ("inv_denom", "<f8"), ("vis", "<f8"),
                       ("texel", "<i4"), ("active", "<i4"), ("technique", "<i4"), ("occluded", "<i4")])
 
 
+class _EdgeParams(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("stream", C.c_uint32), ("n_samples", C.c_int), ("tau", C.c_double),
+                ("ray_eps", C.c_double), ("eta", C.c_double)]
+
+
 class _Params(C.Structure):
     _fields_ = [("n_light", C.c_int), ("n_cos", C.c_int), ("n_ggx", C.c_int), ("stream", C.c_uint32),
                 ("seed", C.c_uint64), ("tau", C.c_double), ("ray_eps", C.c_double), ("want_margin", C.c_int)]
@@ -95,6 +100,8 @@ def _declare(lib):
         "orc_frozen_eval": (None, [P, i, i, P, P, P, P, P]),
         "orc_frozen_adjoint": (None, [P, i, i, P, P, P, P, P, P, P, P, P]),
         "orc_sample_rec_size": (i, []),
+        "orc_edge_table": (i, [P, i, P]),
+        "orc_shadow_edge_grad": (None, [P, P, i, P, i, P, i, i, P, P, P, i, P, P, _EdgeParams, P, P]),
         "orc_pdf_light_n": (None, [P, P, i, i, d, P, i, P]),
         "orc_sample_light_n": (None, [P, P, i, i, d, P, i, P, P, P]),
         "orc_sample_cosine_n": (None, [P, P, i, P]),
@@ -317,6 +324,36 @@ def shade_fwd(verts, tris, env, cond32, marg32, total, gb_rows, cam_pos_rows, ct
                          _p(gb_rows), _p(cam), _p(ctr), n, prm, _p(out), _p(vis),
                          _p(recs) if recs is not None else None)
     return out, vis, recs
+
+
+def edge_table(tris):
+    """(E, 4) int32 edge records (a, b, c1, c2) in first-half-edge order."""
+    tris = _i32(tris).reshape(-1, 3)
+    out = np.zeros((max(3 * len(tris), 1), 4), np.int32)
+    n = load().orc_edge_table(_p(tris), len(tris), _p(out))
+    return out[:n].copy()
+
+
+def shadow_edge_grad(verts, tris, edges, env, gb_rows, cam_pos_rows, ctr_rows, gcd, gcs, *, n_samples, seed,
+                     stream=2, tau=1.0, ray_eps=1e-4, eta=1e-4, want_records=True):
+    """Edge-sampling estimate of the shadow-visibility gradient with respect to
+    the vertex positions.  Returns (g_verts (V, 3), rec (n, M, 4) or None);
+    rec holds per sample (weight, decision margin, edge index, s)."""
+    verts, tris, env = _f32(verts).reshape(-1, 3), _i32(tris).reshape(-1, 3), _f32(env)
+    edges = _i32(edges).reshape(-1, 4)
+    gb_rows = _f32(gb_rows).reshape(-1, 16)
+    n = gb_rows.shape[0]
+    cam = _f64(cam_pos_rows).reshape(n, 3)
+    ctr = np.ascontiguousarray(ctr_rows, dtype=np.uint32).reshape(n, 2)
+    gcd, gcs = _f64(gcd).reshape(n, 3), _f64(gcs).reshape(n, 3)
+    g = np.zeros((len(verts), 3))
+    rec = np.zeros((n, n_samples, 4)) if want_records else None
+    H, W = env.shape[:2]
+    prm = _EdgeParams(int(seed), int(stream), int(n_samples), float(tau), float(ray_eps), float(eta))
+    load().orc_shadow_edge_grad(_p(verts), _p(tris), len(tris), _p(edges), len(edges), _p(env), W, H, _p(gb_rows),
+                                _p(cam), _p(ctr), n, _p(gcd), _p(gcs), prm, _p(g),
+                                _p(rec) if rec is not None else None)
+    return g, rec
 
 
 def param_rows(gb_rows):

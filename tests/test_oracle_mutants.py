@@ -14,6 +14,7 @@ from tests import test_oracle_bsdf as B
 from tests import test_oracle_estimator as E
 from tests import test_oracle_probe as P
 from tests import test_oracle_random as R
+from tests import test_oracle_shadow_grad as S
 from tests import test_oracle_visibility as V
 
 
@@ -82,6 +83,21 @@ MUTANTS = [
      [_adjoint_fd]),
     ("adjoint: metallic through F0 with the wrong sign", "g_m += -gk[c] * kd[c] + gF0[c] * (kd[c] - 0.04);",
      "g_m += -gk[c] * kd[c] + gF0[c] * (0.04 - kd[c]);", [_adjoint_fd]),
+    ("edge gradient: outward normal flipped", "double sg = s1 > 0.0 ? -1.0 : 1.0, nout[3], wp[3];",
+     "double sg = s1 > 0.0 ? 1.0 : -1.0, nout[3], wp[3];", [lambda o: S.test_single_triangle_matches_lambert(o, 1.0)]),
+    ("edge gradient: endpoint weights swapped", "g_verts[3 * (size_t)E4[0] + c] += wt * (1.0 - s) * nout[c];",
+     "g_verts[3 * (size_t)E4[0] + c] += wt * s * nout[c];", [lambda o: S.test_single_triangle_matches_lambert(o, 1.0)]),
+    ("edge gradient: 1/r^2 of the Jacobian dropped", "double J = norm3(wxab) / (rr * rr);",
+     "double J = norm3(wxab) / rr;", [lambda o: S.test_single_triangle_matches_lambert(o, 1.0)]),
+    ("edge gradient: silhouette test skipped", "if (!(s1 * s2 > 0.0)) continue;", "if (!(s1 * s1 > 0.0)) continue;",
+     [S.test_quad_interior_edge_is_not_a_silhouette]),
+    ("edge gradient: outer ray not checked", "if (blocked) continue;", "if (blocked && 0) continue;",
+     [lambda o: S.test_hidden_occluder_edges_contribute_nothing(o, False)]),
+    ("edge table: wrong opposite vertex", "edges[4 * n + 3] = tris[3 * t2 + (i2 + 2) % 3];",
+     "edges[4 * n + 3] = tris[3 * t2 + (i2 + 1) % 3];", [S.test_edge_table_closed_and_open_meshes]),
+    ("edge gradient: specular without cos_o", "gw += L[c] * gs[c] * D * G2 * orc_schlick(F0, vh) / (4.0 * co);",
+     "gw += L[c] * gs[c] * D * G2 * orc_schlick(F0, vh) / 4.0;",
+     [lambda o: S.test_matches_finite_differences_of_the_forward_estimator(o, "specular")]),
 ]
 
 
