@@ -338,6 +338,7 @@ def run_gpu(args, rank, world):
     result["denoiser_bilateral"] = time_bilateral(pipe, flush, stream, args.steps)
     result["shadow_rays"] = shadow_ray_figures(pipe, flush, stream, args.steps, samples_per_step)
     result["bvh"] = time_bvh_refit(pipe, flush, stream, args.steps)
+    result["shadow_edge_grad"] = time_shadow_edge_grad(pipe, flush, stream, args.steps)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sc, n_pix=args.cpu_pixels)
     if args.batch_steps > 0:
@@ -516,6 +517,50 @@ def time_bvh_refit(pipe, flush, stream, steps):
                 ms.append(ev[0].elapsed_time(ev[1]))
         out[name] = round(float(np.mean(ms)), 4)
     out["note"] = "refit keeps the leaf order and hierarchy of the last build (vertices moved, same triangles)"
+    return out
+
+
+def time_shadow_edge_grad(pipe, flush, stream, steps, samples_per_pixel=16):
+    """The shadow-visibility gradient (edge sampling of the blocked set's
+    boundary; off in the timed step, as in the paper's main results) on the
+    headline G-buffer: the edge-table build and one gradient pass with
+    `samples_per_pixel` edge samples, CUDA events around each, L2 flushed
+    before each; plus the fraction of edge samples that land on a visible
+    silhouette (uniform edge choice over the whole mesh)."""
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi
+
+    sc = pipe.scene
+    prm = mcdi.make_params(sc.n_light, sc.n_cos, sc.n_ggx, sc.seed, tau=1.0)
+    et = mcdi.EdgeTable.allocate(sc.tris.shape[0], pipe.device)
+    ones = torch.ones_like(pipe.kd_out)
+    g = torch.zeros_like(pipe.verts)
+    M = samples_per_pixel
+    w = torch.empty(pipe.N * pipe.H * pipe.W, M, device=pipe.device)
+    out = {}
+    for name, fn in (("edge_table_ms", lambda: et.build(pipe.tris, stream)),
+                     ("grad_ms", lambda: mcdi.shadow_edge_grad(pipe.bvh, pipe.verts, et, pipe.probe, pipe.gb,
+                                                               pipe.cams, prm, M, ones, ones, g, None,
+                                                               stream=stream))):
+        ms = []
+        for k in range(steps + 3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            flush.zero_()
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ms.append(ev[0].elapsed_time(ev[1]))
+        out[name] = round(float(np.mean(ms)), 4)
+    mcdi.shadow_edge_grad(pipe.bvh, pipe.verts, et, pipe.probe, pipe.gb, pipe.cams, prm, M, ones, ones, g, w,
+                          stream=stream)
+    torch.cuda.synchronize()
+    out.update({"edge_samples_per_pixel": M, "edges": int(et.count.item()),
+                "contributing_fraction": round(float((w != 0).float().mean().item()), 6),
+                "launches": {"edge_table": 6, "grad": 1},
+                "note": "not part of the timed step (the paper leaves shadow-visibility gradients off by default)"})
     return out
 
 

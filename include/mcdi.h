@@ -232,6 +232,56 @@ MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* en
                               void* stream);
 
 /* ------------------------------------------------------------------------
+ * Shadow-visibility gradients (the ablation of the paper's appendix
+ * "Visibility gradients from shadows"; off in the paper's main results, where
+ * visibility is detached, Sec. 3.1 "Shadow gradients").  The gradient of
+ *   sum <g_cd, c_d> + <g_cs, c_s>
+ * with respect to the mesh's vertex positions through the shadow rays'
+ * blocked set: with H = 1 - tau B, the boundary term
+ *   -tau sum over silhouette edges (seen from o = p + ray_eps n) of
+ *    int_0^1 g(w) V+ n_out . ((1 - s) da + s db) |w x (b - a)| / r^2 ds,
+ * x = a + s (b - a), r = |x - o|, w = (x - o) / r, n_out the unit normal of
+ * the plane (o, a, b) away from the edge's faces, V+ = 1 when the ray along
+ * normalize(w + eta n_out) reaches the probe, and g the forward integrand
+ * L(w) (n.w) [g_cd / pi + g_cs f_s(w)] (specular only where the lobe is on).
+ * An edge is on the silhouette when its two faces lie strictly on one side of
+ * that plane, or when it has one face.  Estimated by edge sampling: each pixel
+ * draws n_edge_samples edges uniformly, edge e = floor(u0 E) computed as
+ * ((x0 >> 8) * E) >> 24 from the Philox output x0 of counter (pixel, view, j,
+ * 2) (the forward uses stream word 0, a decorrelated adjoint 1), s = u1, and
+ * weighs each by E / n_edge_samples.
+ *
+ * mcdi_edge_table_workspace_size (host): scratch bytes for n_tris triangles.
+ * mcdi_build_edge_table: tris [n_tris][3] int32 (indices in [0, n_verts)) ->
+ *   edges [3 n_tris][4] int32 (capacity for every half-edge; 16-byte
+ *   aligned): one record (a, b, c1, c2) per undirected edge in the order of
+ *   its first half-edge 3 t + i (a = v_i, b = v_(i+1), c1 = v_(i+2) of that
+ *   face, c2 the opposite vertex of the next face on the edge or -1 on a
+ *   boundary; further faces of a non-manifold edge are ignored), and
+ *   *n_edges (device int) the number of records, or -1 if the hash table
+ *   overflowed (it cannot with the scratch size given above).  Deterministic.
+ * mcdi_shadow_edge_grad: bvh and verts [n_verts][3] float (4-byte aligned) of
+ *   the same mesh, the edge table (edges, n_edges on the device, max_edges its
+ *   capacity in records), the probe and the G-buffer / cameras of the
+ *   forward, params (seed, tau and ray_eps are used), n_edge_samples >= 0,
+ *   0 < eta <= 0.1, g_cd and g_cs [N][H][W] float4.  g_verts [n_verts][3]
+ *   float is ACCUMULATED (zero it first).  sample_w (nullable) [N][H][W]
+ *   [n_edge_samples] float receives each sample's weight
+ *   -tau g J E / n_edge_samples (0 when the sample does not contribute).
+ *   Edge records whose indices are out of range are skipped.
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_edge_table_workspace_size(int n_tris, size_t* bytes);
+MCDI_API mcdi_status mcdi_build_edge_table(const int* tris, int n_tris, int* edges, int* n_edges, void* workspace,
+                                           size_t workspace_bytes, void* stream);
+MCDI_API mcdi_status mcdi_shadow_edge_grad(const mcdi_bvh_view* bvh, const float* verts, int n_verts,
+                                           const int* edges, const int* n_edges, int max_edges, const float* env,
+                                           int Wp, int Hp, const float* gb_pos, const float* gb_nrm,
+                                           const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N,
+                                           int H, int W, const mcdi_shade_params* params, int n_edge_samples,
+                                           float eta, const float* g_cd, const float* g_cs, float* g_verts,
+                                           float* sample_w, void* stream);
+
+/* ------------------------------------------------------------------------
  * Measurement aids for the shadow-ray traversal (the visibility term of the
  * Sec. 3.1 estimator, traced as in App. A), not part of the hot path.  Both
  * take the BVH, image shape and params of a preceding mcdi_shade_mc_fwd that

@@ -290,6 +290,92 @@ mcdi_status mcdi_shadow_ray_retrace(const mcdi_bvh_view* bvh, int N, int H, int 
                     "shadow_ray_retrace");
 }
 
+mcdi_status mcdi_edge_table_workspace_size(int n_tris, size_t* bytes) {
+    REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
+    REQUIRE(bytes != nullptr, "bytes is NULL");
+    *bytes = mcdi::edge_scratch_layout(n_tris).total;
+    return ok();
+}
+
+mcdi_status mcdi_build_edge_table(const int* tris, int n_tris, int* edges, int* n_edges, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+    REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
+    REQUIRE(tris != nullptr && ((uintptr_t)tris & 3u) == 0, "tris must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE_BUF16(edges);
+    REQUIRE(n_edges != nullptr && ((uintptr_t)n_edges & 3u) == 0,
+            "n_edges must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE(workspace != nullptr && ((uintptr_t)workspace & 255u) == 0,
+            "workspace must be a non-NULL 256-byte aligned device pointer");
+    const mcdi::EdgeScratch L = mcdi::edge_scratch_layout(n_tris);
+    REQUIRE(workspace_bytes >= L.total, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+    return launched(mcdi::launch_build_edge_table(tris, n_tris, reinterpret_cast<int4*>(edges), n_edges, workspace,
+                                                  L, static_cast<cudaStream_t>(stream)),
+                    "build_edge_table");
+}
+
+mcdi_status mcdi_shadow_edge_grad(const mcdi_bvh_view* bvh, const float* verts, int n_verts, const int* edges,
+                                  const int* n_edges, int max_edges, const float* env, int Wp, int Hp,
+                                  const float* gb_pos, const float* gb_nrm, const float* gb_kd, const float* gb_korm,
+                                  const mcdi_camera* cams, int N, int H, int W, const mcdi_shade_params* params,
+                                  int n_edge_samples, float eta, const float* g_cd, const float* g_cs,
+                                  float* g_verts, float* sample_w, void* stream) {
+    REQUIRE(bvh != nullptr && bvh->n_tris >= 0, "bvh is NULL or invalid");
+    if (bvh->n_tris > 0) {
+        REQUIRE_NODES(bvh->nodes);
+        REQUIRE_BUF16(bvh->tri_records);
+    }
+    REQUIRE(n_verts >= 1, "n_verts must be >= 1");
+    REQUIRE(verts != nullptr && ((uintptr_t)verts & 3u) == 0, "verts must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE_BUF16(edges);
+    REQUIRE(n_edges != nullptr && ((uintptr_t)n_edges & 3u) == 0,
+            "n_edges must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE(max_edges >= 0, "max_edges must be >= 0");
+    REQUIRE_BUF16(env);
+    REQUIRE(Wp >= 1 && Wp <= 8192 && Hp >= 1 && Hp <= 4096, "probe size %dx%d out of range", Wp, Hp);
+    REQUIRE_BUF16(gb_pos);
+    REQUIRE_BUF16(gb_nrm);
+    REQUIRE_BUF16(gb_kd);
+    REQUIRE_BUF16(gb_korm);
+    REQUIRE(cams != nullptr && ((uintptr_t)cams & 3u) == 0, "cams must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE(N >= 1 && H >= 1 && W >= 1, "image shape must be positive");
+    REQUIRE((long long)H * W <= 0xffffffffLL, "too many pixels per view");
+    REQUIRE(n_edge_samples >= 0 && n_edge_samples <= 4096, "n_edge_samples must be in [0, 4096]");
+    REQUIRE((long long)N * H * W * n_edge_samples <= (1LL << 37), "N*H*W*n_edge_samples too large");
+    REQUIRE(eta > 0.0f && eta <= 0.1f, "eta must be in (0, 0.1]");
+    REQUIRE(params != nullptr, "params is NULL");
+    REQUIRE(params->tau >= 0.0f && params->tau <= 1.0f, "tau must be in [0, 1]");
+    REQUIRE(params->ray_eps >= 0.0f && params->ray_eps < 1e30f, "ray_eps must be finite and >= 0");
+    REQUIRE_BUF16(g_cd);
+    REQUIRE_BUF16(g_cs);
+    REQUIRE(g_verts != nullptr && ((uintptr_t)g_verts & 3u) == 0,
+            "g_verts must be a non-NULL 4-byte aligned device pointer");
+    REQUIRE(sample_w == nullptr || ((uintptr_t)sample_w & 3u) == 0, "sample_w must be 4-byte aligned");
+    mcdi::ShadeArgs a{};
+    a.nodes = bvh->nodes;
+    a.tris = bvh->tri_records;
+    a.n_tris = bvh->n_tris;
+    a.env = reinterpret_cast<const float4*>(env);
+    a.Wp = Wp;
+    a.Hp = Hp;
+    a.gb_pos = reinterpret_cast<const float4*>(gb_pos);
+    a.gb_nrm = reinterpret_cast<const float4*>(gb_nrm);
+    a.gb_kd = reinterpret_cast<const float4*>(gb_kd);
+    a.gb_korm = reinterpret_cast<const float4*>(gb_korm);
+    a.cams = cams;
+    a.N = N;
+    a.H = H;
+    a.W = W;
+    a.seed = params->seed;
+    a.tau = params->tau;
+    a.ray_eps = params->ray_eps;
+    a.stream_word = 2;
+    return launched(mcdi::launch_shadow_edge_grad(a, verts, n_verts, reinterpret_cast<const int4*>(edges), n_edges,
+                                                  max_edges, n_edge_samples, eta, reinterpret_cast<const float4*>(g_cd),
+                                                  reinterpret_cast<const float4*>(g_cs), g_verts, sample_w,
+                                                  static_cast<cudaStream_t>(stream)),
+                    "shadow_edge_grad");
+}
+
 mcdi_status mcdi_read_sweep(const void* buf, size_t bytes, int passes, unsigned* sink, void* stream) {
     REQUIRE(buf != nullptr && aligned16(buf), "buf must be a non-NULL 16-byte aligned device pointer");
     REQUIRE(bytes >= 16 && bytes % 16 == 0, "bytes must be a positive multiple of 16");

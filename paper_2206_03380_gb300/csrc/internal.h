@@ -101,6 +101,19 @@ cudaError_t launch_shadow_ray_stats(const ShadeArgs& a, const void* ws, unsigned
                                     cudaStream_t stream);
 cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t stream);
 
+// ---- shadow-visibility gradients by edge sampling (shadow_grad.cu)
+struct EdgeScratch {
+    size_t keys, first, second, slot_of, tile_count, tile_off, err, total;
+    size_t cap;   // hash-table slots (a power of two >= 2 x the half-edges)
+    int n_tiles;  // compaction tiles of half-edges
+};
+EdgeScratch edge_scratch_layout(int n_tris);
+cudaError_t launch_build_edge_table(const int* tris, int n_tris, int4* edges, int* n_edges, void* scratch,
+                                    const EdgeScratch& layout, cudaStream_t stream);
+cudaError_t launch_shadow_edge_grad(const ShadeArgs& a, const float* verts, int n_verts, const int4* edges,
+                                    const int* n_edges, int max_edges, int n_samples, float eta, const float4* g_cd,
+                                    const float4* g_cs, float* g_verts, float* sample_w, cudaStream_t stream);
+
 // ---- measurement aid (measure.cu): L2-resident read sweep
 cudaError_t launch_read_sweep(const void* buf, size_t bytes, int passes, unsigned* sink, cudaStream_t stream);
 

@@ -40,7 +40,8 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_shade_mc_bwd", "mcdi_denoise_sizes", "mcdi_denoise_pack_weights", "mcdi_denoise_fwd",
            "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite",
            "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd",
-           "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep", "mcdi_refit_bvh"]
+           "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep", "mcdi_refit_bvh",
+           "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -84,6 +85,13 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shadow_ray_retrace.restype = st
     lib.mcdi_shadow_ray_retrace.argtypes = [C.POINTER(BvhView), i, i, i, C.POINTER(ShadeParams), P, sz, P]
     lib.mcdi_read_sweep.restype = st
+    lib.mcdi_edge_table_workspace_size.restype = st
+    lib.mcdi_edge_table_workspace_size.argtypes = [i, C.POINTER(sz)]
+    lib.mcdi_build_edge_table.restype = st
+    lib.mcdi_build_edge_table.argtypes = [P, i, P, P, P, sz, P]
+    lib.mcdi_shadow_edge_grad.restype = st
+    lib.mcdi_shadow_edge_grad.argtypes = [C.POINTER(BvhView), P, i, P, P, i, P, i, i, P, P, P, P, P, i, i, i,
+                                          C.POINTER(ShadeParams), i, C.c_float, P, P, P, P, P]
     lib.mcdi_read_sweep.argtypes = [P, sz, i, P, P]
     lib.mcdi_denoise_sizes.restype = st
     lib.mcdi_denoise_sizes.argtypes = [i, i, i, i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
@@ -375,6 +383,48 @@ class Denoise(torch.autograd.Function):
 
 
 # ------------------------------------------------------------------ device-resident objects
+def edge_table_workspace_size(n_tris: int) -> int:
+    b = C.c_size_t()
+    _check(load().mcdi_edge_table_workspace_size(int(n_tris), C.byref(b)), "edge_table_workspace_size")
+    return b.value
+
+
+def build_edge_table(tris, edges, n_edges, workspace, stream=None):
+    """tris (T, 3) int32 -> edges (3T, 4) int32 records (a, b, c1, c2) in first-half-edge order, n_edges (1,) int32."""
+    _check(load().mcdi_build_edge_table(_ptr(tris), tris.shape[0], _ptr(edges), _ptr(n_edges), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), _stream(stream)),
+           "build_edge_table")
+
+
+def shadow_edge_grad(bvh: "Bvh", verts, edges: "EdgeTable", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams,
+                     n_edge_samples: int, g_cd, g_cs, g_verts, sample_w=None, eta=1e-4, stream=None):
+    """Edge-sampling estimate of the shadow-visibility gradient, ACCUMULATED into g_verts (V, 3) float32."""
+    N, H, W = gb.pos.shape[:3]
+    Hp, Wp = probe.env.shape[:2]
+    _check(load().mcdi_shadow_edge_grad(C.byref(bvh.view), _ptr(verts), verts.shape[0], _ptr(edges.records),
+                                        _ptr(edges.count), edges.records.shape[0], _ptr(probe.env), Wp, Hp,
+                                        _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm), _ptr(cams), N, H, W,
+                                        C.byref(params), int(n_edge_samples), float(eta), _ptr(g_cd), _ptr(g_cs),
+                                        _ptr(g_verts), _ptr(sample_w), _stream(stream)), "shadow_edge_grad")
+
+
+@dataclass
+class EdgeTable:
+    records: torch.Tensor    # (3 T, 4) int32
+    count: torch.Tensor      # (1,) int32, on the device
+    workspace: torch.Tensor
+
+    @classmethod
+    def allocate(cls, n_tris: int, device="cuda") -> "EdgeTable":
+        return cls(torch.empty(3 * n_tris, 4, dtype=torch.int32, device=device),
+                   torch.zeros(1, dtype=torch.int32, device=device),
+                   _empty_bytes(edge_table_workspace_size(n_tris), device))
+
+    def build(self, tris, stream=None) -> "EdgeTable":
+        build_edge_table(tris, self.records, self.count, self.workspace, stream)
+        return self
+
+
 def _empty_bytes(n: int, device) -> torch.Tensor:
     # 256-byte aligned raw buffer
     return torch.empty((max(n, 1) + 255) // 256 * 256, dtype=torch.uint8, device=device)

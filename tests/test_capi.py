@@ -75,3 +75,25 @@ def test_argument_checks_without_gpu(lib):
     assert b"gb_pos" in lib.mcdi_last_error()
     tau_bad = mcdi.make_params(4, 2, 2, 1, tau=1.5)
     assert lib.mcdi_shade_mc_fwd(*args, C.byref(tau_bad), *outs) == mcdi.INVALID_ARG
+
+
+def test_edge_gradient_argument_checks_without_gpu(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    n = C.c_size_t()
+    assert lib.mcdi_edge_table_workspace_size(0, C.byref(n)) == mcdi.INVALID_ARG
+    assert lib.mcdi_edge_table_workspace_size(1000, C.byref(n)) == mcdi.OK
+    # hash table of 8192 slots (>= 2 x 3000 half-edges) of 16 bytes, then per-half-edge slots
+    assert n.value >= 8192 * 16 + 3000 * 4
+    p = C.c_void_p(4096)
+    assert lib.mcdi_build_edge_table(p, 1000, p, p, p, n.value - 1, None) == mcdi.INVALID_ARG
+    assert b"workspace" in lib.mcdi_last_error()
+    bvh = mcdi.BvhView(None, None, 0)
+    prm = mcdi.make_params(4, 2, 2, 1, tau=1.0)
+    args = [C.byref(bvh), p, 10, p, p, 30, p, 32, 16, p, p, p, p, p, 1, 8, 8, C.byref(prm)]
+    assert lib.mcdi_shadow_edge_grad(*args, 4, C.c_float(0.0), p, p, p, None, None) == mcdi.INVALID_ARG
+    assert b"eta" in lib.mcdi_last_error()
+    assert lib.mcdi_shadow_edge_grad(*args, -1, C.c_float(1e-4), p, p, p, None, None) == mcdi.INVALID_ARG
+    assert lib.mcdi_shadow_edge_grad(*args, 4, C.c_float(1e-4), p, C.c_void_p(4100), p, None,
+                                     None) == mcdi.INVALID_ARG
+    assert b"g_cs" in lib.mcdi_last_error()
