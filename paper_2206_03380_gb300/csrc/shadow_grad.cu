@@ -205,7 +205,40 @@ __device__ __forceinline__ void scatter3(float* g, int i, f3 d) {
     atomicAdd(g + 3 * (size_t)i + 2, d.z);
 }
 
-// one thread per (pixel, edge sample)
+// Any hit for one ray with the whole warp: lane k walks the k-th of 32 equal
+// segments of the depth-first node array along the escape links.  A lane that
+// starts inside a subtree skips the box tests of its ancestors outside the
+// segment, which only adds box tests: a triangle the ray hits has every
+// ancestor box hit (boxes are conservative), so some lane reaches its leaf,
+// and the result equals the one-lane traversal's.  All lanes call this with
+// the same ray; the loop runs uniformly and ends when a lane finds a hit or
+// every lane has left its segment (each step moves strictly forward).
+__device__ __forceinline__ bool warp_any_hit(const void* nodes, const TriRecord* __restrict__ tris, int n_tris,
+                                             const RayInv& r, int lane) {
+    if (n_tris <= 0) return false;
+    const ThreadedNode* tn = threaded_nodes(nodes, n_tris);
+    const int m = 2 * n_tris - 1, seg = (m + 31) / 32;
+    int i = lane * seg;
+    const int hi = min(m, i + seg);
+    bool found = false;
+    for (;;) {
+        const bool active = i < hi;
+        if (!__any_sync(0xffffffffu, active)) return false;
+        if (active) {
+            i = threaded_step(tn, tris, r, i);
+            if (i < 0) {
+                found = true;
+                i = hi;
+            }
+        }
+        if (__any_sync(0xffffffffu, found)) return true;
+    }
+}
+
+// One thread per (pixel, edge sample).  The rare samples that reach the outer
+// ray (silhouette, above the horizon) are traced one after another by the
+// whole warp, so that each grazing ray's long chain of dependent node fetches
+// is split 32 ways.
 __global__ void __launch_bounds__(kGradThreads) shadow_edge_grad_kernel(
     ShadeArgs a, const float* __restrict__ verts, int n_verts, const int4* __restrict__ edges,
     const int* __restrict__ n_edges_dev, int max_edges, int M, float eta, const float4* __restrict__ g_cd,
@@ -213,27 +246,34 @@ __global__ void __launch_bounds__(kGradThreads) shadow_edge_grad_kernel(
     pdl_prologue();
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long P = (long long)a.N * a.H * a.W;
-    if (tid >= P * M) return;
-    const long long idx = tid / M;
+    const bool in_range = tid < P * M;
+    const long long idx = in_range ? tid / M : 0;
     const int j = (int)(tid - idx * M);
-    float wt = 0.0f;
+    const int lane = threadIdx.x & 31;
     const int E = min(max(*n_edges_dev, 0), max_edges);
     const int view = (int)(idx / ((long long)a.H * a.W));
     const uint32_t pix = (uint32_t)(idx - (long long)view * a.H * a.W);
-    Pixel px{};
-    const bool covered = load_pixel(a.gb_pos[idx], a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
-                                    mk(a.cams[view].origin[0], a.cams[view].origin[1], a.cams[view].origin[2]), &px);
+    // position and normal only (the shading setup waits for the few samples that reach the outer ray);
+    // n is formed exactly as load_pixel forms it
+    const float4 pos = in_range ? a.gb_pos[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const f3 N = in_range ? xyz(a.gb_nrm[idx]) : mk(0.f, 0.f, 0.f);
+    const float l2 = dot(N, N);
+    bool cand = false;
+    f3 o{}, w{}, nout{}, ab{};
+    float s = 0.f, r2 = 1.f, ci = 0.f;
+    int4 ed{};
     do {
-        if (!covered || E <= 0) break;
+        if (!(pos.w > 0.0f) || !(l2 > 0.0f) || E <= 0) break;
+        const f3 nrm = N * (1.0f / sqrtf(l2));
         const uint4 x = philox4x32_10(make_uint4(pix, (uint32_t)view, (uint32_t)j, a.stream_word),
                                       make_uint2((uint32_t)(a.seed & 0xffffffffull), (uint32_t)(a.seed >> 32)));
         const int e = (int)(((unsigned long long)(x.x >> 8) * (unsigned)E) >> 24);
-        const float s = (float)(x.y >> 8) * 5.9604644775390625e-8f;
-        const int4 ed = __ldg(edges + e);
+        s = (float)(x.y >> 8) * 5.9604644775390625e-8f;
+        ed = __ldg(edges + e);
         if ((unsigned)ed.x >= (unsigned)n_verts || (unsigned)ed.y >= (unsigned)n_verts ||
             (unsigned)ed.z >= (unsigned)n_verts || ed.w >= n_verts)
             break;
-        const f3 o = px.p + px.n * a.ray_eps;
+        o = xyz(pos) + nrm * a.ray_eps;
         const f3 va = load_vert(verts, ed.x), vb = load_vert(verts, ed.y);
         const f3 m = cross(va - o, vb - o);
         const float lm = sqrtf(dot(m, m));
@@ -241,15 +281,32 @@ __global__ void __launch_bounds__(kGradThreads) shadow_edge_grad_kernel(
         const float s1 = dot(m, load_vert(verts, ed.z) - o);
         const float s2 = ed.w >= 0 ? dot(m, load_vert(verts, ed.w) - o) : s1;
         if (!(s1 * s2 > 0.0f)) break;  // both faces on one side of the plane (o, a, b): silhouette
-        const f3 ab = vb - va;
+        ab = vb - va;
         const f3 d = va + ab * s - o;
-        const float r2 = dot(d, d), r = sqrtf(r2);
-        const f3 w = d * (1.0f / r);
-        const float ci = dot(px.n, w);
+        r2 = dot(d, d);
+        w = d * (1.0f / sqrtf(r2));
+        ci = dot(nrm, w);
         if (!(ci > 0.0f)) break;
-        const f3 nout = m * ((s1 > 0.0f ? -1.0f : 1.0f) / lm);
-        if (any_hit(a.nodes, static_cast<const TriRecord*>(a.tris), a.n_tris, make_ray(o, normalize(w + nout * eta))))
-            break;
+        nout = m * ((s1 > 0.0f ? -1.0f : 1.0f) / lm);
+        cand = true;
+    } while (false);
+    // the outer rays of this warp's candidates, each traced by all 32 lanes
+    bool open = false;
+    const f3 dir = normalize(w + nout * eta);
+    for (unsigned todo = __ballot_sync(0xffffffffu, cand); todo; todo &= todo - 1u) {
+        const int src = __ffs(todo) - 1;
+        const f3 ro = mk(__shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src),
+                         __shfl_sync(0xffffffffu, o.z, src));
+        const f3 rd = mk(__shfl_sync(0xffffffffu, dir.x, src), __shfl_sync(0xffffffffu, dir.y, src),
+                         __shfl_sync(0xffffffffu, dir.z, src));
+        const bool hit = warp_any_hit(a.nodes, static_cast<const TriRecord*>(a.tris), a.n_tris, make_ray(ro, rd), lane);
+        if (lane == src) open = !hit;
+    }
+    float wt = 0.0f;
+    if (open) {
+        Pixel px{};
+        load_pixel(pos, a.gb_nrm[idx], a.gb_kd[idx], a.gb_korm[idx],
+                   mk(a.cams[view].origin[0], a.cams[view].origin[1], a.cams[view].origin[2]), &px);
         Probe Pr;
         Pr.W = a.Wp;
         Pr.H = a.Hp;
@@ -269,14 +326,15 @@ __global__ void __launch_bounds__(kGradThreads) shadow_edge_grad_kernel(
                             px.F0.z + (1.f - px.F0.z) * q);
             gw += (L.x * gs.x * F.x + L.y * gs.y * F.y + L.z * gs.z * F.z) * D * G2 / (4.0f * px.co);
         }
-        const float J = sqrtf(dot(cross(w, ab), cross(w, ab))) / r2;
+        const f3 c = cross(w, ab);
+        const float J = sqrtf(dot(c, c)) / r2;
         wt = -a.tau * gw * J * ((float)E / (float)M);
         if (wt != 0.0f) {
             scatter3(g_verts, ed.x, nout * (wt * (1.0f - s)));
             scatter3(g_verts, ed.y, nout * (wt * s));
         }
-    } while (false);
-    if (sample_w) sample_w[tid] = wt;
+    }
+    if (sample_w && in_range) sample_w[tid] = wt;
 }
 
 inline size_t edge_table_cap(int n_tris) {

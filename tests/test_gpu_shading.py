@@ -45,10 +45,13 @@ def upload_gb(pipe, gb_rows):
 
 
 # ------------------------------------------------------------------ probe tables
-@pytest.mark.parametrize("kind", ["sun", "lobes", "black_rows", "black"])
+@pytest.mark.parametrize("kind", ["sun", "lobes", "black_rows", "black", "largest"])
 def test_envmap_cdf_matches_oracle(cuda_lib, orc, kind):
     rng = np.random.default_rng(5)
-    if kind == "sun":
+    if kind == "largest":  # the largest probe the ABI accepts, 8192 x 4096 (512 MiB)
+        env = np.exp(rng.normal(0.0, 1.0, size=(4096, 8192, 4))).astype(np.float32)
+        env[..., 3] = 0.0
+    elif kind == "sun":
         env, _ = scenes.env_with_sun_texel(32, 16, rng)
     elif kind == "lobes":
         env, _ = scenes.env_with_lobes(512, 256, rng)

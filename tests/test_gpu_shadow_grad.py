@@ -60,9 +60,13 @@ def _run(mcdi, pipe, et, prm, M, gcd, gcs, want_w=True):
     return g.cpu().numpy().astype(np.float64), (w.cpu().numpy() if want_w else None)
 
 
-@pytest.mark.parametrize("which", ["parity", "headline", "shuffled"])
+@pytest.mark.parametrize("which", ["parity", "headline", "shuffled", "single", "fan"])
 def test_edge_table_matches_oracle(cuda_lib, orc, which):
-    if which == "parity":
+    if which == "single":  # three boundary edges
+        tris = np.array([[4, 9, 2]], np.int32)
+    elif which == "fan":  # four faces on the edge (0, 1): the first two are kept, in half-edge order
+        tris = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4], [5, 1, 0], [2, 3, 4]], np.int32)
+    elif which == "parity":
         tris = scenes.parity_scene().tris
     elif which == "headline":
         tris = scenes.sphere_union_scene().tris
