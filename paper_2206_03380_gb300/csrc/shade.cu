@@ -27,21 +27,6 @@ __device__ __forceinline__ f3 cam_origin(const mcdi_camera* cams, int view) {
 }
 
 // ---------------------------------------------------------------- G-buffer
-__device__ __forceinline__ float4 bilinear(const float4* __restrict__ tex, int S, float u, float v) {
-    const float x = u * (float)S - 0.5f, y = v * (float)S - 0.5f;
-    const float x0 = floorf(x), y0 = floorf(y);
-    const float fx = x - x0, fy = y - y0;
-    const int xi0 = min(max((int)x0, 0), S - 1), xi1 = min(max((int)x0 + 1, 0), S - 1);
-    const int yi0 = min(max((int)y0, 0), S - 1), yi1 = min(max((int)y0 + 1, 0), S - 1);
-    const float4 t00 = __ldg(tex + (size_t)yi0 * S + xi0), t10 = __ldg(tex + (size_t)yi0 * S + xi1);
-    const float4 t01 = __ldg(tex + (size_t)yi1 * S + xi0), t11 = __ldg(tex + (size_t)yi1 * S + xi1);
-    auto lerp = [](float a, float b, float t) { return a + (b - a) * t; };
-    return make_float4(lerp(lerp(t00.x, t10.x, fx), lerp(t01.x, t11.x, fx), fy),
-                       lerp(lerp(t00.y, t10.y, fx), lerp(t01.y, t11.y, fx), fy),
-                       lerp(lerp(t00.z, t10.z, fx), lerp(t01.z, t11.z, fx), fy),
-                       lerp(lerp(t00.w, t10.w, fx), lerp(t01.w, t11.w, fx), fy));
-}
-
 __global__ void __launch_bounds__(kShadeThreads) primary_cast_kernel(
     const BvhNode* __restrict__ nodes, const TriRecord* __restrict__ tris, int n_tris, const float* __restrict__ verts,
     const float* __restrict__ vnrm, const int* __restrict__ tri_idx, int n_verts, const mcdi_camera* __restrict__ cams,
@@ -55,35 +40,14 @@ __global__ void __launch_bounds__(kShadeThreads) primary_cast_kernel(
     const int pix = (int)(idx - (long long)view * H * W);
     const int x = pix % W, y = pix / W;
     const mcdi_camera& C = cams[view];
-    const float sx = (2.0f * ((float)x + 0.5f) / (float)W - 1.0f) * C.tan_half_fovy * C.aspect;
-    const float sy = (1.0f - 2.0f * ((float)y + 0.5f) / (float)H) * C.tan_half_fovy;
     const f3 o = mk(C.origin[0], C.origin[1], C.origin[2]);
-    const f3 d = normalize(mk(C.forward[0] + sx * C.right[0] + sy * C.up[0],
-                              C.forward[1] + sx * C.right[1] + sy * C.up[1],
-                              C.forward[2] + sx * C.right[2] + sy * C.up[2]));
+    const f3 d = camera_dir(C, x, y, W, H);
     float t, u = 0.f, v = 0.f;
     const int leaf = closest_hit(nodes, tris, n_tris, make_ray(o, d), &t, &u, &v);
     float4 P = make_float4(0.f, 0.f, 0.f, 0.f), Nn = P, KD = P, KORM = P;
-    if (leaf >= 0) {
-        const int k = __float_as_int(__ldg(&tris[leaf].v0.w));
-        const int i0 = tri_idx[3 * (size_t)k], i1 = tri_idx[3 * (size_t)k + 1], i2 = tri_idx[3 * (size_t)k + 2];
-        if ((unsigned)i0 < (unsigned)n_verts && (unsigned)i1 < (unsigned)n_verts && (unsigned)i2 < (unsigned)n_verts) {
-            const float w = 1.0f - u - v;
-            float pp[3], nn[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                pp[c] = w * verts[3 * (size_t)i0 + c] + u * verts[3 * (size_t)i1 + c] + v * verts[3 * (size_t)i2 + c];
-                nn[c] = w * vnrm[3 * (size_t)i0 + c] + u * vnrm[3 * (size_t)i1 + c] + v * vnrm[3 * (size_t)i2 + c];
-            }
-            P = make_float4(pp[0], pp[1], pp[2], 1.0f);
-            Nn = make_float4(nn[0], nn[1], nn[2], 0.0f);
-            const float tu = (pp[0] - uv_ox) * uv_s, tv = (pp[2] - uv_oz) * uv_s;
-            KD = bilinear(tex_kd, S, tu, tv);
-            KORM = bilinear(tex_korm, S, tu, tv);
-            KD.w = 0.f;
-            KORM.w = 0.f;
-        }
-    }
+    if (leaf >= 0)
+        gbuffer_hit(tris, leaf, u, v, verts, vnrm, tri_idx, n_verts, tex_kd, tex_korm, S, uv_ox, uv_oz, uv_s, &P, &Nn,
+                    &KD, &KORM);
     gb_pos[idx] = P;
     gb_nrm[idx] = Nn;
     gb_kd[idx] = KD;

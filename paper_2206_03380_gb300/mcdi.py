@@ -41,7 +41,8 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_denoise_bwd", "mcdi_conv3x3_bf16", "mcdi_conv3x3_e4m3", "mcdi_composite",
            "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd",
            "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep", "mcdi_refit_bvh",
-           "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad"]
+           "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad",
+           "mcdi_raster_workspace_size", "mcdi_raster_gbuffer"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -72,6 +73,11 @@ def load(path: str = LIB_PATH):
     lib.mcdi_primary_cast.restype = st
     lib.mcdi_primary_cast.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
                                       P, P, P, P, P]
+    lib.mcdi_raster_workspace_size.restype = st
+    lib.mcdi_raster_workspace_size.argtypes = [i, i, i, i, C.POINTER(sz)]
+    lib.mcdi_raster_gbuffer.restype = st
+    lib.mcdi_raster_gbuffer.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
+                                        P, P, P, P, P, sz, P]
     lib.mcdi_shade_workspace_size.restype = st
     lib.mcdi_shade_workspace_size.argtypes = [i, i, i, C.POINTER(ShadeParams), C.POINTER(sz)]
     lib.mcdi_shade_mc_fwd.restype = st
@@ -185,6 +191,22 @@ def primary_cast(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uv
                                     _ptr(cams), cams.shape[0], H, W, _ptr(tex_kd), _ptr(tex_korm), tex_kd.shape[0],
                                     uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm), _stream(stream)),
            "primary_cast")
+
+
+def raster_workspace_size(N: int, H: int, W: int, n_tris: int) -> int:
+    b = C.c_size_t()
+    _check(load().mcdi_raster_workspace_size(int(N), int(H), int(W), int(n_tris), C.byref(b)), "raster_workspace_size")
+    return b.value
+
+
+def raster_gbuffer(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, workspace, stream=None):
+    """The G-buffer by rasterising the BVH's triangle records (same outputs as primary_cast)."""
+    uv = (C.c_float * 3)(*[float(x) for x in uvmap])
+    _check(load().mcdi_raster_gbuffer(C.byref(bvh.view), _ptr(verts), _ptr(vnrm), _ptr(tris), verts.shape[0],
+                                      _ptr(cams), cams.shape[0], int(H), int(W), _ptr(tex_kd), _ptr(tex_korm),
+                                      tex_kd.shape[0], uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm),
+                                      _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)),
+           "raster_gbuffer")
 
 
 def shade_workspace_size(N: int, H: int, W: int, params: ShadeParams) -> int:

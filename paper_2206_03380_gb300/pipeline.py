@@ -20,7 +20,7 @@ from .scenes import Scene
 class ShadingPipeline:
     def __init__(self, scene: Scene, device="cuda", tau: float = 0.0, ray_eps: float = 1e-4,
                  decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True,
-                 denoiser_params=None, denoiser_precision=0, bilateral_sigma=None):
+                 denoiser_params=None, denoiser_precision=0, bilateral_sigma=None, raster: bool = True):
         mcdi.load()
         self.scene = scene
         self.device = torch.device(device)
@@ -69,6 +69,11 @@ class ShadingPipeline:
         if wavefront:
             nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
             self.workspace = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
+        # G-buffer by rasterisation (depth buffer + index map), else by the closest-hit ray cast
+        self.raster_ws = None
+        if raster:
+            nbytes = mcdi.raster_workspace_size(self.N, self.H, self.W, scene.tris.shape[0])
+            self.raster_ws = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
 
     # ---- the steps
     def build_probe(self, stream=None):
@@ -78,8 +83,12 @@ class ShadingPipeline:
         self.bvh.build(self.verts, self.tris, stream)
 
     def primary(self, stream=None):
-        mcdi.primary_cast(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
-                          self.tex_korm, self.uvmap, self.gb, stream)
+        if self.raster_ws is not None:
+            mcdi.raster_gbuffer(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
+                                self.tex_korm, self.uvmap, self.gb, self.raster_ws, stream)
+        else:
+            mcdi.primary_cast(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
+                              self.tex_korm, self.uvmap, self.gb, stream)
 
     def forward(self, stream=None):
         mcdi.shade_mc_fwd(self.bvh, self.probe, self.gb, self.cams, self.params, self.c_d, self.kd_out, self.c_s,

@@ -157,8 +157,9 @@ def test_bvh_depth_first_escape_links(cuda_lib, scene):
 
 
 # ------------------------------------------------------------------ G-buffer
-def test_primary_cast_matches_oracle(cuda_lib, orc, scene, oracle_gb):
-    pipe = make_pipe(scene)
+@pytest.mark.parametrize("raster", [True, False])
+def test_primary_cast_matches_oracle(cuda_lib, orc, scene, oracle_gb, raster):
+    pipe = make_pipe(scene, raster=raster)
     pipe.build_bvh()
     pipe.primary()
     g = np.concatenate([to_np(pipe.gb.pos), to_np(pipe.gb.nrm), to_np(pipe.gb.kd), to_np(pipe.gb.korm)], -1)
