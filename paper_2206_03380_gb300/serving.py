@@ -2,8 +2,8 @@
 
 Requests of uneven resolution and sample count arrive over time (a Poisson
 stream).  Meshes, their BVHs, textures and the probes' sampling tables stay
-resident on the device.  A request runs the forward hot path — G-buffer ray
-cast, Monte Carlo direct illumination (Sec. 3.1, 4.1), the BF16 U-Net
+resident on the device.  A request runs the forward hot path — rasterised
+G-buffer, Monte Carlo direct illumination (Sec. 3.1, 4.1), the BF16 U-Net
 denoiser on c_d and c_s (Sec. 4.2) and the composite c = k_d D(c_d) + D(c_s)
 — as libmcdi launches on one of a few CUDA streams.
 
@@ -74,14 +74,14 @@ class ServingEngine:
         torch.cuda.synchronize(dev)
 
     # ---- memory
-    @staticmethod
-    def footprint(req: RenderRequest) -> int:
+    def footprint(self, req: RenderRequest) -> int:
         P = req.res * req.res
         prm = mcdi.make_params(*split_spp(req.spp), seed=1)
         ws = mcdi.shade_workspace_size(1, req.res, req.res, prm)
         _, acts, _, _ = mcdi.denoise_sizes(2, req.res, req.res)
+        rws = mcdi.raster_workspace_size(1, req.res, req.res, self.scenes[req.scene].bvh.n_tris)
         # G-buffer 4 planes, 2 terms, k_d out, 2 denoised, colour: float4 each
-        return P * 16 * (4 + 2 + 1 + 2 + 1) + ws + acts
+        return P * 16 * (4 + 2 + 1 + 2 + 1) + ws + acts + rws
 
     def _alloc(self, req: RenderRequest):
         dev, r = self.dev, req.res
@@ -90,16 +90,18 @@ class ServingEngine:
         ws = mcdi.shade_workspace_size(1, r, r, prm)
         _, acts, _, _ = mcdi.denoise_sizes(2, r, r)
         gb = mcdi.GBuffer(f4(1), f4(1), f4(1), f4(1))
+        rws = mcdi.raster_workspace_size(1, r, r, self.scenes[req.scene].bvh.n_tris)
         return dict(prm=prm, gb=gb, terms=f4(2), kd_out=f4(1), den=f4(2), color=f4(1),
                     ws=torch.empty((ws + 255) // 256 * 256, dtype=torch.uint8, device=dev),
+                    rws=torch.empty((rws + 255) // 256 * 256, dtype=torch.uint8, device=dev),
                     acts=torch.empty((acts + 255) // 256 * 256, dtype=torch.uint8, device=dev))
 
     def _launch(self, req: RenderRequest, b: dict, stream):
         sc, pr = self.scenes[req.scene], self.probes[req.probe]
         cams = sc.cams[req.view:req.view + 1]
         r = req.res
-        mcdi.primary_cast(sc.bvh, sc.verts, sc.vnrm, sc.tris, cams, r, r, sc.tex_kd, sc.tex_korm, sc.uvmap, b["gb"],
-                          stream)
+        mcdi.raster_gbuffer(sc.bvh, sc.verts, sc.vnrm, sc.tris, cams, r, r, sc.tex_kd, sc.tex_korm, sc.uvmap, b["gb"],
+                            b["rws"], stream)
         c_d, c_s = b["terms"][0:1], b["terms"][1:2]
         mcdi.shade_mc_fwd(sc.bvh, pr, b["gb"], cams, b["prm"], c_d, b["kd_out"], c_s, None, b["ws"], stream)
         mcdi.denoise_fwd(self.den_weights, b["terms"], b["kd_out"], b["gb"].nrm, b["den"], b["acts"], self.err, stream)
