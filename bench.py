@@ -1,7 +1,7 @@
 """Benchmark: forward + backward Monte Carlo direct-illumination shading.
 
 A step is one pass of the hot path over one synthetic batch: probe sampling
-tables, LBVH over this iteration's mesh, G-buffer ray cast, forward MIS
+tables, LBVH over this iteration's mesh, rasterised G-buffer, forward MIS
 estimator with shadow rays, the U-Net denoiser on c_d and c_s, its input
 gradient, and the shading adjoint (Sec. 3-4 of the paper).  The
 workload is the 512 x 512, 16 spp (8 light / 4 cosine / 4 GGX) view of the
