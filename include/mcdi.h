@@ -161,19 +161,20 @@ MCDI_API mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* ve
 
 /* ------------------------------------------------------------------------
  * The same G-buffer by rasterisation, as the paper produces it (nvdiffrast,
- * Sec. 3.1).  Every triangle record of the built BVH (bvh->tri_records, the
- * mesh's triangles in leaf order) is scan-converted over its screen box,
- * clipped at a near plane 1e-6 in front of the eye; each pixel of the box is
- * decided by the ray cast's own FP32 test of the camera ray through the pixel
- * centre against that record, so coverage and depth are exactly the ray
- * cast's.  The nearest hit wins (ties: the lowest original triangle index);
- * its entries are written as by mcdi_primary_cast, with the same arguments.
- * workspace: mcdi_raster_workspace_size(N, H, W, bvh->n_tris) bytes, 256-byte
- * aligned (a 64-bit depth buffer and an index map), overwritten.
+ * Sec. 3.1), from the mesh alone (verts [n_verts][3], tris [n_tris][3]; no
+ * BVH, so it can run concurrently with mcdi_build_bvh).  Every triangle is
+ * scan-converted over its screen box, clipped at a near plane 1e-6 in front
+ * of the eye; each pixel of the box is decided by the ray cast's own FP32 test
+ * of the camera ray through the pixel centre against v0, v1 - v0, v2 - v0, so
+ * it covers the pixels the ray cast covers with the same triangles; the
+ * attributes agree with the ray cast's to FP32 rounding.  The nearest hit
+ * wins (ties: the lowest triangle index); its entries are written as by
+ * mcdi_primary_cast.  workspace: mcdi_raster_workspace_size(N, H, W) bytes,
+ * 256-byte aligned (a 64-bit depth buffer), overwritten.
  * ------------------------------------------------------------------------ */
-MCDI_API mcdi_status mcdi_raster_workspace_size(int N, int H, int W, int n_tris, size_t* bytes);
-MCDI_API mcdi_status mcdi_raster_gbuffer(const mcdi_bvh_view* bvh, const float* verts, const float* vnrm,
-                                         const int* tris, int n_verts, const mcdi_camera* cams, int N, int H, int W,
+MCDI_API mcdi_status mcdi_raster_workspace_size(int N, int H, int W, size_t* bytes);
+MCDI_API mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, const int* tris, int n_verts,
+                                         int n_tris, const mcdi_camera* cams, int N, int H, int W,
                                          const float* tex_kd, const float* tex_korm, int tex_size, const float* uvmap,
                                          float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
                                          size_t workspace_bytes, void* stream);

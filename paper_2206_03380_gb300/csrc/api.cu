@@ -192,24 +192,24 @@ mcdi_status mcdi_primary_cast(const mcdi_bvh_view* bvh, const float* verts, cons
                     "primary_cast");
 }
 
-mcdi_status mcdi_raster_workspace_size(int N, int H, int W, int n_tris, size_t* bytes) {
+mcdi_status mcdi_raster_workspace_size(int N, int H, int W, size_t* bytes) {
     REQUIRE(N >= 1 && H >= 1 && W >= 1 && (long long)N * H * W <= (1LL << 31) - 1, "bad image shape");
-    REQUIRE(n_tris >= 0, "n_tris must be >= 0");
     REQUIRE(bytes != nullptr, "bytes is NULL");
-    *bytes = mcdi::raster_workspace_bytes((long long)N * H * W, n_tris);
+    *bytes = mcdi::raster_workspace_bytes((long long)N * H * W);
     return ok();
 }
 
-mcdi_status mcdi_raster_gbuffer(const mcdi_bvh_view* bvh, const float* verts, const float* vnrm, const int* tris,
-                                int n_verts, const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
+                                const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
                                 const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos, float* gb_nrm,
                                 float* gb_kd, float* gb_korm, void* workspace, size_t workspace_bytes, void* stream) {
-    REQUIRE(bvh != nullptr && bvh->n_tris >= 0, "bvh is NULL or invalid");
-    if (bvh->n_tris > 0) REQUIRE_BUF16(bvh->tri_records);
-    REQUIRE(verts && vnrm && tris && n_verts >= 1, "mesh arrays must be non-NULL");
+    REQUIRE(verts && vnrm && n_verts >= 1, "verts / vnrm must be non-NULL and n_verts >= 1");
+    REQUIRE(n_tris >= 0 && (n_tris == 0 || tris != nullptr), "tris must be non-NULL when n_tris > 0");
+    REQUIRE(((uintptr_t)verts & 3u) == 0 && ((uintptr_t)vnrm & 3u) == 0 && ((uintptr_t)tris & 3u) == 0,
+            "verts / vnrm / tris must be 4-byte aligned");
     REQUIRE(cams != nullptr && ((uintptr_t)cams & 3u) == 0, "cams must be a non-NULL 4-byte aligned device pointer");
     REQUIRE(N >= 1 && H >= 1 && W >= 1 && (long long)N * H * W <= (1LL << 31) - 1, "bad image shape");
-    REQUIRE((long long)N * bvh->n_tris <= (1LL << 31) - 1, "N*n_tris too large");
+    REQUIRE((long long)N * n_tris <= (1LL << 31) - 1, "N*n_tris too large");
     REQUIRE(tex_size >= 1 && tex_size <= 16384, "tex_size out of range");
     REQUIRE_BUF16(tex_kd);
     REQUIRE_BUF16(tex_korm);
@@ -220,11 +220,11 @@ mcdi_status mcdi_raster_gbuffer(const mcdi_bvh_view* bvh, const float* verts, co
     REQUIRE_BUF16(gb_korm);
     REQUIRE(workspace != nullptr && ((uintptr_t)workspace & 255u) == 0,
             "workspace must be a non-NULL 256-byte aligned device pointer");
-    const size_t need = mcdi::raster_workspace_bytes((long long)N * H * W, bvh->n_tris);
+    const size_t need = mcdi::raster_workspace_bytes((long long)N * H * W);
     REQUIRE(workspace_bytes >= need, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
-    return launched(mcdi::launch_raster_gbuffer(bvh->tri_records, bvh->n_tris, verts, vnrm, tris, n_verts, cams, N, H,
-                                                W, tex_kd, tex_korm, tex_size, uvmap[0], uvmap[1], uvmap[2], gb_pos,
-                                                gb_nrm, gb_kd, gb_korm, workspace, static_cast<cudaStream_t>(stream)),
+    return launched(mcdi::launch_raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm,
+                                                tex_size, uvmap[0], uvmap[1], uvmap[2], gb_pos, gb_nrm, gb_kd, gb_korm,
+                                                workspace, static_cast<cudaStream_t>(stream)),
                     "raster_gbuffer");
 }
 

@@ -30,18 +30,6 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-__device__ __forceinline__ void load_tri(const float* __restrict__ verts, int n_verts, const int* __restrict__ tris,
-                                         int k, f3& a, f3& b, f3& c) {
-    const int i0 = tris[3 * (size_t)k], i1 = tris[3 * (size_t)k + 1], i2 = tris[3 * (size_t)k + 2];
-    if ((unsigned)i0 >= (unsigned)n_verts || (unsigned)i1 >= (unsigned)n_verts || (unsigned)i2 >= (unsigned)n_verts) {
-        a = b = c = mk(0.f, 0.f, 0.f);  // bad index: degenerate triangle, never hit
-        return;
-    }
-    a = mk(verts[3 * (size_t)i0], verts[3 * (size_t)i0 + 1], verts[3 * (size_t)i0 + 2]);
-    b = mk(verts[3 * (size_t)i1], verts[3 * (size_t)i1 + 1], verts[3 * (size_t)i1 + 2]);
-    c = mk(verts[3 * (size_t)i2], verts[3 * (size_t)i2 + 1], verts[3 * (size_t)i2 + 2]);
-}
-
 __global__ void init_bounds_kernel(uint32_t* bounds) {
     pdl_prologue();
     if (threadIdx.x < 3) bounds[threadIdx.x] = f2ord(FLT_MAX);

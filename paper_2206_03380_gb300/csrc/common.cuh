@@ -52,6 +52,21 @@ __device__ __forceinline__ float2 sample_uniforms(unsigned long long seed, uint3
     return make_float2((float)(x.x >> 8) * 5.9604644775390625e-8f, (float)(x.y >> 8) * 5.9604644775390625e-8f);
 }
 
+// ---------------------------------------------------------------- mesh
+// triangle k's corners; a bad vertex index gives a degenerate triangle at the
+// origin, which no ray hits
+__device__ __forceinline__ void load_tri(const float* __restrict__ verts, int n_verts, const int* __restrict__ tris,
+                                         int k, f3& a, f3& b, f3& c) {
+    const int i0 = tris[3 * (size_t)k], i1 = tris[3 * (size_t)k + 1], i2 = tris[3 * (size_t)k + 2];
+    if ((unsigned)i0 >= (unsigned)n_verts || (unsigned)i1 >= (unsigned)n_verts || (unsigned)i2 >= (unsigned)n_verts) {
+        a = b = c = mk(0.f, 0.f, 0.f);  // bad index: degenerate triangle, never hit
+        return;
+    }
+    a = mk(verts[3 * (size_t)i0], verts[3 * (size_t)i0 + 1], verts[3 * (size_t)i0 + 2]);
+    b = mk(verts[3 * (size_t)i1], verts[3 * (size_t)i1 + 1], verts[3 * (size_t)i1 + 2]);
+    c = mk(verts[3 * (size_t)i2], verts[3 * (size_t)i2 + 1], verts[3 * (size_t)i2 + 2]);
+}
+
 // ---------------------------------------------------------------- BVH layout
 // Internal node of a binary BVH, 64 bytes: the bounds of both children (so one
 // node fetch tests two boxes) and the two child links.  link >= 0: internal

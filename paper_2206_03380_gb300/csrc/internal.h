@@ -91,12 +91,12 @@ cudaError_t launch_primary_cast(const void* nodes, const void* tris, int n_tris,
                                 float uv_oz, float uv_s, float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm,
                                 cudaStream_t stream);
 
-size_t raster_workspace_bytes(long long pixels, int n_tris);
-cudaError_t launch_raster_gbuffer(const void* tri_records, int n_tris, const float* verts, const float* vnrm,
-                                  const int* tri_idx, int n_verts, const mcdi_camera* cams, int N, int H, int W,
-                                  const float* tex_kd, const float* tex_korm, int tex_size, float uv_ox, float uv_oz,
-                                  float uv_s, float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm,
-                                  void* workspace, cudaStream_t stream);
+size_t raster_workspace_bytes(long long pixels);
+cudaError_t launch_raster_gbuffer(const float* verts, const float* vnrm, const int* tri_idx, int n_verts, int n_tris,
+                                  const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                                  const float* tex_korm, int tex_size, float uv_ox, float uv_oz, float uv_s,
+                                  float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
+                                  cudaStream_t stream);
 
 cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
                              cudaStream_t stream);

@@ -2,11 +2,14 @@
 // nvdiffrast, Sec. 3.1): every triangle is scan-converted over the pixels of
 // its screen bounding box, and each candidate pixel is decided by the same
 // FP32 ray/triangle test the ray-cast G-buffer uses (the camera ray through
-// the pixel centre against the triangle's record), so coverage and depth are
-// exactly the ray cast's.  The nearest hit per pixel wins through a 64-bit
-// atomicMin of (t bits, original triangle index): depth first, then the lowest
-// triangle index on an exact tie.  A resolve pass then writes the G-buffer
-// entries from the winning triangle as the ray cast does.
+// the pixel centre against v0, e1 = v1 - v0, e2 = v2 - v0, the values of the
+// BVH's triangle records), so it covers the pixels the ray cast covers, with
+// the same triangles.
+// The nearest hit per pixel wins through a 64-bit atomicMin of (t bits,
+// triangle index): depth first, then the lowest triangle index on an exact tie.
+// A resolve pass then writes the G-buffer entries from the winning triangle as
+// the ray cast does.  The mesh alone is read, not the BVH, so the pass can run
+// concurrently with the BVH build.
 #include "common.cuh"
 #include "internal.h"
 #include "shading.cuh"
@@ -20,22 +23,10 @@ constexpr float kNearPlane = 1e-6f;   // the part of a triangle closer to the ey
 constexpr float kBoxSlack = 1.0f / 64.0f;  // pixels of slack around the projected box
 constexpr unsigned long long kEmpty = ~0ull;
 
-__global__ void __launch_bounds__(kRasterThreads) zclear_kernel(unsigned long long* z, long long n, int* inv,
-                                                                int n_tris) {
+__global__ void __launch_bounds__(kRasterThreads) zclear_kernel(unsigned long long* z, long long n) {
     pdl_prologue();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) z[i] = kEmpty;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_tris; i += stride) inv[i] = -1;
-}
-
-// original triangle index -> record index of the BVH leaf order
-__global__ void __launch_bounds__(kRasterThreads) inverse_map_kernel(const TriRecord* __restrict__ tris, int n_tris,
-                                                                     int* inv) {
-    pdl_prologue();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_tris) return;
-    const int orig = __float_as_int(__ldg(&tris[k].v0.w));
-    if ((unsigned)orig < (unsigned)n_tris) inv[orig] = k;
 }
 
 // pixel coordinates (continuous, pixel centres at integers) of a camera-space point
@@ -89,18 +80,19 @@ __device__ __forceinline__ bool screen_box(const mcdi_camera& C, const f3 p[3], 
     return true;
 }
 
-__device__ __forceinline__ void raster_pixel(const mcdi_camera& C, const TriRecord* __restrict__ tris, int k, int orig,
-                                             int x, int y, int W, int H, unsigned long long* zview) {
+__device__ __forceinline__ void raster_pixel(const mcdi_camera& C, f3 v0, f3 e1, f3 e2, int k, int x, int y, int W,
+                                             int H, unsigned long long* zview) {
     const f3 o = mk(C.origin[0], C.origin[1], C.origin[2]);
-    const float t = tri_hit(make_ray(o, camera_dir(C, x, y, W, H)), tris, k, nullptr, nullptr);
+    const float t = tri_hit_v(make_ray(o, camera_dir(C, x, y, W, H)), v0, e1, e2, nullptr, nullptr);
     if (t < FLT_MAX) {
-        const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)orig;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)k;
         atomicMin(zview + (size_t)y * W + x, key);
     }
 }
 
-// one thread per (view, triangle record)
-__global__ void __launch_bounds__(kRasterThreads) raster_kernel(const TriRecord* __restrict__ tris, int n_tris,
+// one thread per (view, triangle)
+__global__ void __launch_bounds__(kRasterThreads) raster_kernel(const float* __restrict__ verts, int n_verts,
+                                                                const int* __restrict__ tri_idx, int n_tris,
                                                                 const mcdi_camera* __restrict__ cams, int N, int H,
                                                                 int W, unsigned long long* z) {
     pdl_prologue();
@@ -111,57 +103,65 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(const TriRecord*
     const mcdi_camera& C = cams[view];
     unsigned long long* zview = z + (size_t)view * H * W;
     int4 box = make_int4(0, 0, -1, -1);
-    int orig = 0;
+    f3 a{}, e1{}, e2{};
     bool ok = false;
     if (in_range) {
-        const float4 v0 = __ldg(&tris[k].v0), e1 = __ldg(&tris[k].e1), e2 = __ldg(&tris[k].e2);
-        orig = __float_as_int(v0.w);
-        const f3 p[3] = {xyz(v0), xyz(v0) + xyz(e1), xyz(v0) + xyz(e2)};
+        f3 b, c;
+        load_tri(verts, n_verts, tri_idx, k, a, b, c);
+        e1 = b - a;
+        e2 = c - a;
+        const f3 p[3] = {a, a + e1, a + e2};
         ok = screen_box(C, p, W, H, &box);
     }
     const int bw = box.z - box.x + 1, bh = box.w - box.y + 1;
     const bool big = ok && bw * bh > kBigArea;
     if (ok && !big)
         for (int y = box.y; y <= box.w; ++y)
-            for (int x = box.x; x <= box.z; ++x) raster_pixel(C, tris, k, orig, x, y, W, H, zview);
+            for (int x = box.x; x <= box.z; ++x) raster_pixel(C, a, e1, e2, k, x, y, W, H, zview);
     // large boxes: the whole warp walks each one's pixels
     const int lane = threadIdx.x & 31;
     for (unsigned todo = __ballot_sync(0xffffffffu, big); todo; todo &= todo - 1u) {
         const int src = __ffs(todo) - 1;
         const int sv = __shfl_sync(0xffffffffu, view, src), sk = __shfl_sync(0xffffffffu, k, src);
-        const int so = __shfl_sync(0xffffffffu, orig, src);
+        const f3 sa = mk(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src),
+                         __shfl_sync(0xffffffffu, a.z, src));
+        const f3 s1 = mk(__shfl_sync(0xffffffffu, e1.x, src), __shfl_sync(0xffffffffu, e1.y, src),
+                         __shfl_sync(0xffffffffu, e1.z, src));
+        const f3 s2 = mk(__shfl_sync(0xffffffffu, e2.x, src), __shfl_sync(0xffffffffu, e2.y, src),
+                         __shfl_sync(0xffffffffu, e2.z, src));
         const int x0 = __shfl_sync(0xffffffffu, box.x, src), y0 = __shfl_sync(0xffffffffu, box.y, src);
         const int w = __shfl_sync(0xffffffffu, bw, src), n = w * __shfl_sync(0xffffffffu, bh, src);
         const mcdi_camera& SC = cams[sv];
         unsigned long long* sz = z + (size_t)sv * H * W;
-        for (int i = lane; i < n; i += 32) raster_pixel(SC, tris, sk, so, x0 + i % w, y0 + i / w, W, H, sz);
+        for (int i = lane; i < n; i += 32) raster_pixel(SC, sa, s1, s2, sk, x0 + i % w, y0 + i / w, W, H, sz);
     }
 }
 
 // the G-buffer entries of every pixel from its winning triangle
 __global__ void __launch_bounds__(kRasterThreads) resolve_kernel(
-    const TriRecord* __restrict__ tris, int n_tris, const int* __restrict__ inv, const unsigned long long* __restrict__ z,
-    const float* __restrict__ verts, const float* __restrict__ vnrm, const int* __restrict__ tri_idx, int n_verts,
-    const mcdi_camera* __restrict__ cams, int N, int H, int W, const float4* __restrict__ tex_kd,
-    const float4* __restrict__ tex_korm, int S, float uv_ox, float uv_oz, float uv_s, float4* __restrict__ gb_pos,
-    float4* __restrict__ gb_nrm, float4* __restrict__ gb_kd, float4* __restrict__ gb_korm) {
+    const unsigned long long* __restrict__ z, const float* __restrict__ verts, const float* __restrict__ vnrm,
+    const int* __restrict__ tri_idx, int n_verts, int n_tris, const mcdi_camera* __restrict__ cams, int N, int H, int W,
+    const float4* __restrict__ tex_kd, const float4* __restrict__ tex_korm, int S, float uv_ox, float uv_oz,
+    float uv_s, float4* __restrict__ gb_pos, float4* __restrict__ gb_nrm, float4* __restrict__ gb_kd,
+    float4* __restrict__ gb_korm) {
     pdl_prologue();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)N * H * W) return;
     float4 P = make_float4(0.f, 0.f, 0.f, 0.f), Nn = P, KD = P, KORM = P;
     const unsigned long long key = z[idx];
-    const int orig = (int)(unsigned)(key & 0xffffffffull);
-    const int leaf = key != kEmpty && (unsigned)orig < (unsigned)n_tris ? inv[orig] : -1;
-    if (leaf >= 0) {
+    const int k = (int)(unsigned)(key & 0xffffffffull);
+    if (key != kEmpty && (unsigned)k < (unsigned)n_tris) {
         const int view = (int)(idx / ((long long)H * W));
         const int pix = (int)(idx - (long long)view * H * W);
         const mcdi_camera& C = cams[view];
+        f3 a, b, c;
+        load_tri(verts, n_verts, tri_idx, k, a, b, c);
         float u = 0.f, v = 0.f;
-        const float t = tri_hit(make_ray(mk(C.origin[0], C.origin[1], C.origin[2]), camera_dir(C, pix % W, pix / W, W, H)),
-                                tris, leaf, &u, &v);
+        const float t = tri_hit_v(make_ray(mk(C.origin[0], C.origin[1], C.origin[2]), camera_dir(C, pix % W, pix / W, W, H)),
+                                  a, b - a, c - a, &u, &v);
         if (t < FLT_MAX)
-            gbuffer_hit(tris, leaf, u, v, verts, vnrm, tri_idx, n_verts, tex_kd, tex_korm, S, uv_ox, uv_oz, uv_s, &P,
-                        &Nn, &KD, &KORM);
+            gbuffer_hit(k, u, v, verts, vnrm, tri_idx, n_verts, tex_kd, tex_korm, S, uv_ox, uv_oz, uv_s, &P, &Nn, &KD,
+                        &KORM);
     }
     gb_pos[idx] = P;
     gb_nrm[idx] = Nn;
@@ -173,32 +173,26 @@ inline int blocks_for(long long n) { return (int)((n + kRasterThreads - 1) / kRa
 
 }  // namespace
 
-size_t raster_workspace_bytes(long long pixels, int n_tris) {
-    return align256((size_t)(pixels > 0 ? pixels : 1) * sizeof(unsigned long long)) +
-           align256((size_t)(n_tris > 0 ? n_tris : 1) * sizeof(int));
+size_t raster_workspace_bytes(long long pixels) {
+    return align256((size_t)(pixels > 0 ? pixels : 1) * sizeof(unsigned long long));
 }
 
-cudaError_t launch_raster_gbuffer(const void* tri_records, int n_tris, const float* verts, const float* vnrm,
-                                  const int* tri_idx, int n_verts, const mcdi_camera* cams, int N, int H, int W,
-                                  const float* tex_kd, const float* tex_korm, int tex_size, float uv_ox, float uv_oz,
-                                  float uv_s, float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm,
-                                  void* workspace, cudaStream_t stream) {
+cudaError_t launch_raster_gbuffer(const float* verts, const float* vnrm, const int* tri_idx, int n_verts, int n_tris,
+                                  const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                                  const float* tex_korm, int tex_size, float uv_ox, float uv_oz, float uv_s,
+                                  float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
+                                  cudaStream_t stream) {
     const long long P = (long long)N * H * W;
     auto* z = static_cast<unsigned long long*>(workspace);
-    int* inv = reinterpret_cast<int*>(static_cast<char*>(workspace) + align256((size_t)P * sizeof(unsigned long long)));
-    const TriRecord* tris = static_cast<const TriRecord*>(tri_records);
-    const int clear_blocks = blocks_for(P > n_tris ? P : n_tris) < 4096 ? blocks_for(P > n_tris ? P : n_tris) : 4096;
-    launch_k(zclear_kernel, clear_blocks, kRasterThreads, 0, stream, z, P, inv, n_tris);
-    if (n_tris > 0) {
-        launch_k(inverse_map_kernel, blocks_for(n_tris), kRasterThreads, 0, stream, tris, n_tris, inv);
-        launch_k(raster_kernel, blocks_for((long long)N * n_tris), kRasterThreads, 0, stream, tris, n_tris, cams, N, H,
-                 W, z);
-    }
-    launch_k(resolve_kernel, blocks_for(P), kRasterThreads, 0, stream, tris, n_tris, (const int*)inv,
-             (const unsigned long long*)z, verts, vnrm, tri_idx, n_verts, cams, N, H, W,
-             reinterpret_cast<const float4*>(tex_kd), reinterpret_cast<const float4*>(tex_korm), tex_size, uv_ox,
-             uv_oz, uv_s, reinterpret_cast<float4*>(gb_pos), reinterpret_cast<float4*>(gb_nrm),
-             reinterpret_cast<float4*>(gb_kd), reinterpret_cast<float4*>(gb_korm));
+    launch_k(zclear_kernel, blocks_for(P) < 4096 ? blocks_for(P) : 4096, kRasterThreads, 0, stream, z, P);
+    if (n_tris > 0)
+        launch_k(raster_kernel, blocks_for((long long)N * n_tris), kRasterThreads, 0, stream, verts, n_verts, tri_idx,
+                 n_tris, cams, N, H, W, z);
+    launch_k(resolve_kernel, blocks_for(P), kRasterThreads, 0, stream, (const unsigned long long*)z, verts, vnrm,
+             tri_idx, n_verts, n_tris, cams, N, H, W, reinterpret_cast<const float4*>(tex_kd),
+             reinterpret_cast<const float4*>(tex_korm), tex_size, uv_ox, uv_oz, uv_s,
+             reinterpret_cast<float4*>(gb_pos), reinterpret_cast<float4*>(gb_nrm), reinterpret_cast<float4*>(gb_kd),
+             reinterpret_cast<float4*>(gb_korm));
     return cudaGetLastError();
 }
 

@@ -36,16 +36,14 @@ __device__ __forceinline__ float slab(const RayInv& r, float4 xy, float2 z, floa
     return t0 <= t1 ? t0 : FLT_MAX;
 }
 
-// Moller-Trumbore, two-sided, edges inclusive; returns t (> 0) or +inf
-__device__ __forceinline__ float tri_hit(const RayInv& r, const TriRecord* __restrict__ tris, int k, float* bu,
-                                         float* bv) {
-    const float4 v0 = __ldg(&tris[k].v0), e1v = __ldg(&tris[k].e1), e2v = __ldg(&tris[k].e2);
-    const f3 e1 = xyz(e1v), e2 = xyz(e2v);
+// Moller-Trumbore, two-sided, edges inclusive, for the triangle v0 + u e1 + v e2;
+// returns t (> 0) or +inf
+__device__ __forceinline__ float tri_hit_v(const RayInv& r, f3 v0, f3 e1, f3 e2, float* bu, float* bv) {
     const f3 p = cross(r.d, e2);
     const float det = dot(e1, p);
     if (det == 0.0f) return FLT_MAX;
     const float inv = 1.0f / det;
-    const f3 s = r.o - xyz(v0);
+    const f3 s = r.o - v0;
     const float u = dot(s, p) * inv;
     if (u < 0.0f || u > 1.0f) return FLT_MAX;
     const f3 q = cross(s, e1);
@@ -58,6 +56,13 @@ __device__ __forceinline__ float tri_hit(const RayInv& r, const TriRecord* __res
         *bv = v;
     }
     return t;
+}
+
+// the same test against triangle record k
+__device__ __forceinline__ float tri_hit(const RayInv& r, const TriRecord* __restrict__ tris, int k, float* bu,
+                                         float* bv) {
+    const float4 v0 = __ldg(&tris[k].v0), e1 = __ldg(&tris[k].e1), e2 = __ldg(&tris[k].e2);
+    return tri_hit_v(r, xyz(v0), xyz(e1), xyz(e2), bu, bv);
 }
 
 // slab test of a box given by its corners (xyz of lo and hi); same rounding
@@ -342,16 +347,15 @@ __device__ __forceinline__ float4 bilinear(const float4* __restrict__ tex, int S
                        lerp(lerp(t00.w, t10.w, fx), lerp(t01.w, t11.w, fx), fy));
 }
 
-// The G-buffer entries of a primary hit on triangle record `leaf` at
+// The G-buffer entries of a primary hit on triangle k (original index) at
 // barycentrics (u, v): interpolated position and normal, and the textures at
-// the planar coordinate of the position; all zeros for bad vertex indices.
-__device__ __forceinline__ void gbuffer_hit(const TriRecord* __restrict__ tris, int leaf, float u, float v,
-                                            const float* __restrict__ verts, const float* __restrict__ vnrm,
+// the planar coordinate of the position; left as they are for bad vertex indices.
+__device__ __forceinline__ void gbuffer_hit(int k, float u, float v, const float* __restrict__ verts,
+                                            const float* __restrict__ vnrm,
                                             const int* __restrict__ tri_idx, int n_verts,
                                             const float4* __restrict__ tex_kd, const float4* __restrict__ tex_korm,
                                             int S, float uv_ox, float uv_oz, float uv_s, float4* P, float4* Nn,
                                             float4* KD, float4* KORM) {
-    const int k = __float_as_int(__ldg(&tris[leaf].v0.w));
     const int i0 = tri_idx[3 * (size_t)k], i1 = tri_idx[3 * (size_t)k + 1], i2 = tri_idx[3 * (size_t)k + 2];
     if ((unsigned)i0 >= (unsigned)n_verts || (unsigned)i1 >= (unsigned)n_verts || (unsigned)i2 >= (unsigned)n_verts)
         return;

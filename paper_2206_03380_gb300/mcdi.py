@@ -74,10 +74,10 @@ def load(path: str = LIB_PATH):
     lib.mcdi_primary_cast.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
                                       P, P, P, P, P]
     lib.mcdi_raster_workspace_size.restype = st
-    lib.mcdi_raster_workspace_size.argtypes = [i, i, i, i, C.POINTER(sz)]
+    lib.mcdi_raster_workspace_size.argtypes = [i, i, i, C.POINTER(sz)]
     lib.mcdi_raster_gbuffer.restype = st
-    lib.mcdi_raster_gbuffer.argtypes = [C.POINTER(BvhView), P, P, P, i, P, i, i, i, P, P, i, C.POINTER(C.c_float),
-                                        P, P, P, P, P, sz, P]
+    lib.mcdi_raster_gbuffer.argtypes = [P, P, P, i, i, P, i, i, i, P, P, i, C.POINTER(C.c_float), P, P, P, P, P, sz,
+                                        P]
     lib.mcdi_shade_workspace_size.restype = st
     lib.mcdi_shade_workspace_size.argtypes = [i, i, i, C.POINTER(ShadeParams), C.POINTER(sz)]
     lib.mcdi_shade_mc_fwd.restype = st
@@ -193,19 +193,19 @@ def primary_cast(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uv
            "primary_cast")
 
 
-def raster_workspace_size(N: int, H: int, W: int, n_tris: int) -> int:
+def raster_workspace_size(N: int, H: int, W: int) -> int:
     b = C.c_size_t()
-    _check(load().mcdi_raster_workspace_size(int(N), int(H), int(W), int(n_tris), C.byref(b)), "raster_workspace_size")
+    _check(load().mcdi_raster_workspace_size(int(N), int(H), int(W), C.byref(b)), "raster_workspace_size")
     return b.value
 
 
-def raster_gbuffer(bvh: "Bvh", verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, workspace, stream=None):
-    """The G-buffer by rasterising the BVH's triangle records (same outputs as primary_cast)."""
+def raster_gbuffer(verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, workspace, stream=None):
+    """The G-buffer by rasterising the mesh (same outputs as primary_cast; no BVH needed)."""
     uv = (C.c_float * 3)(*[float(x) for x in uvmap])
-    _check(load().mcdi_raster_gbuffer(C.byref(bvh.view), _ptr(verts), _ptr(vnrm), _ptr(tris), verts.shape[0],
-                                      _ptr(cams), cams.shape[0], int(H), int(W), _ptr(tex_kd), _ptr(tex_korm),
-                                      tex_kd.shape[0], uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm),
-                                      _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)),
+    _check(load().mcdi_raster_gbuffer(_ptr(verts), _ptr(vnrm), _ptr(tris), verts.shape[0], tris.shape[0], _ptr(cams),
+                                      cams.shape[0], int(H), int(W), _ptr(tex_kd), _ptr(tex_korm), tex_kd.shape[0], uv,
+                                      _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), _stream(stream)),
            "raster_gbuffer")
 
 

@@ -72,7 +72,7 @@ class ShadingPipeline:
         # G-buffer by rasterisation (depth buffer + index map), else by the closest-hit ray cast
         self.raster_ws = None
         if raster:
-            nbytes = mcdi.raster_workspace_size(self.N, self.H, self.W, scene.tris.shape[0])
+            nbytes = mcdi.raster_workspace_size(self.N, self.H, self.W)
             self.raster_ws = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
 
     # ---- the steps
@@ -84,7 +84,7 @@ class ShadingPipeline:
 
     def primary(self, stream=None):
         if self.raster_ws is not None:
-            mcdi.raster_gbuffer(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
+            mcdi.raster_gbuffer(self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
                                 self.tex_korm, self.uvmap, self.gb, self.raster_ws, stream)
         else:
             mcdi.primary_cast(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
@@ -117,16 +117,21 @@ class ShadingPipeline:
             self.denoiser.backward(g_denoised, self.g_terms, stream)
 
     def tables_and_geometry(self, stream=None):
-        """Probe tables on a forked stream, concurrently with the BVH build and the
-        G-buffer cast (the two share no buffers), joined before anything reads the
-        tables; inside a captured graph the fork and join become graph edges."""
+        """Probe tables and the rasterised G-buffer (which reads the mesh, not the
+        BVH) on a forked stream, concurrently with the BVH build (they share no
+        buffers), joined before anything reads them; inside a captured graph the
+        fork and join become graph edges.  The ray-cast G-buffer needs the BVH and
+        follows it on the calling stream."""
         cur = stream if stream is not None else torch.cuda.current_stream(self.device)
         if self._fork is None:
             self._fork = torch.cuda.Stream(self.device)
         self._fork.wait_stream(cur)
         self.build_probe(self._fork)
+        if self.raster_ws is not None:
+            self.primary(self._fork)
         self.build_bvh(stream)
-        self.primary(stream)
+        if self.raster_ws is None:
+            self.primary(stream)
         cur.wait_stream(self._fork)
 
     def step(self, g_cd, g_kdout, g_cs, stream=None):

@@ -79,7 +79,7 @@ class ServingEngine:
         prm = mcdi.make_params(*split_spp(req.spp), seed=1)
         ws = mcdi.shade_workspace_size(1, req.res, req.res, prm)
         _, acts, _, _ = mcdi.denoise_sizes(2, req.res, req.res)
-        rws = mcdi.raster_workspace_size(1, req.res, req.res, self.scenes[req.scene].bvh.n_tris)
+        rws = mcdi.raster_workspace_size(1, req.res, req.res)
         # G-buffer 4 planes, 2 terms, k_d out, 2 denoised, colour: float4 each
         return P * 16 * (4 + 2 + 1 + 2 + 1) + ws + acts + rws
 
@@ -90,7 +90,7 @@ class ServingEngine:
         ws = mcdi.shade_workspace_size(1, r, r, prm)
         _, acts, _, _ = mcdi.denoise_sizes(2, r, r)
         gb = mcdi.GBuffer(f4(1), f4(1), f4(1), f4(1))
-        rws = mcdi.raster_workspace_size(1, r, r, self.scenes[req.scene].bvh.n_tris)
+        rws = mcdi.raster_workspace_size(1, r, r)
         return dict(prm=prm, gb=gb, terms=f4(2), kd_out=f4(1), den=f4(2), color=f4(1),
                     ws=torch.empty((ws + 255) // 256 * 256, dtype=torch.uint8, device=dev),
                     rws=torch.empty((rws + 255) // 256 * 256, dtype=torch.uint8, device=dev),
@@ -100,8 +100,8 @@ class ServingEngine:
         sc, pr = self.scenes[req.scene], self.probes[req.probe]
         cams = sc.cams[req.view:req.view + 1]
         r = req.res
-        mcdi.raster_gbuffer(sc.bvh, sc.verts, sc.vnrm, sc.tris, cams, r, r, sc.tex_kd, sc.tex_korm, sc.uvmap, b["gb"],
-                            b["rws"], stream)
+        mcdi.raster_gbuffer(sc.verts, sc.vnrm, sc.tris, cams, r, r, sc.tex_kd, sc.tex_korm, sc.uvmap, b["gb"], b["rws"],
+                            stream)
         c_d, c_s = b["terms"][0:1], b["terms"][1:2]
         mcdi.shade_mc_fwd(sc.bvh, pr, b["gb"], cams, b["prm"], c_d, b["kd_out"], c_s, None, b["ws"], stream)
         mcdi.denoise_fwd(self.den_weights, b["terms"], b["kd_out"], b["gb"].nrm, b["den"], b["acts"], self.err, stream)

@@ -1,11 +1,15 @@
 """The rasterised G-buffer (mcdi_raster_gbuffer; the paper rasterises primary
 visibility, Sec. 3.1) against the closest-hit ray cast, whose FP32 camera-ray /
-triangle test it reuses for every pixel it covers: both must find the same
-triangle at the same depth, so their G-buffers agree bit for bit except where
-two triangles give the very same FP32 depth (the two break such ties
-differently).  Covered: the headline mesh at 512², several ragged views, a
-view with geometry behind the eye (near-plane clipping), and one triangle that
-covers thousands of pixels (the warp-wide path for large screen boxes)."""
+triangle test it reuses for every pixel it covers (on v0, v1 - v0, v2 - v0
+formed from the mesh as the BVH's records are): both must cover the same pixels
+and find the same triangle, except at a few pixels where two triangles give the
+very same FP32 depth or the camera ray passes through a triangle edge (the
+two kernels may take such decisions differently); the interpolated attributes agree
+to FP32 rounding (the same expressions, compiled into two kernels, round
+differently in the last place).  Covered: the headline mesh at 512², several
+ragged views, a view with geometry behind the eye (near-plane clipping), and
+one triangle that covers thousands of pixels (the warp-wide path for large
+screen boxes)."""
 import numpy as np
 import pytest
 import torch
@@ -29,14 +33,23 @@ def _gbuffers(sc):
 
 
 def _agree(r, c, max_ties):
-    same = np.all(r.view(np.int32) == c.view(np.int32), axis=1)
-    diff = ~same
-    assert diff.sum() <= max_ties, diff.sum()
-    # a tie: both covered, the same point along the ray (positions agree to rounding)
-    both = (r[diff, 3] > 0) & (c[diff, 3] > 0)
-    assert np.all(both)
-    assert np.abs(r[diff, 0:3] - c[diff, 0:3]).max(initial=0.0) < 1e-4
-    return same.mean()
+    cov_r, cov_c = r[:, 3] > 0, c[:, 3] > 0
+    assert (cov_r != cov_c).sum() <= max_ties, (cov_r != cov_c).sum()
+    both = cov_r & cov_c
+    pos_err = np.abs(r[:, 0:3] - c[:, 0:3]).max(1) / (1.0 + np.abs(c[:, 0:3]).max(1))
+    # a few rows may take another triangle: a depth tie, or a camera ray through a triangle edge whose FP32
+    # hit test rounds differently in the two kernels; every other row is the same triangle, with attributes
+    # equal to FP32 rounding
+    tie = both & (pos_err > 1e-5)
+    assert tie.sum() <= max_ties, tie.sum()
+    same = both & ~tie
+    # at a shared edge the two may also take the neighbouring triangle at the same point: positions agree,
+    # normals and texture coordinates interpolate the other triangle's corners
+    for cols, tol in ((slice(4, 7), 1e-5), (slice(8, 15), 1e-4)):
+        err = np.abs(r[same, cols] - c[same, cols]).max(1)
+        assert (err > tol).mean() <= 1e-3 and err.max(initial=0.0) <= 1e-3, ((err > tol).mean(), err.max())
+    assert np.all(r[~cov_r] == 0) and np.all(c[~cov_c] == 0)
+    return same.sum() / max(both.sum(), 1)
 
 
 def test_raster_equals_ray_cast_headline(cuda_lib):
@@ -68,4 +81,4 @@ def test_raster_large_triangle(cuda_lib):
     sc = scenes.Scene(**{**base.__dict__, "verts": verts, "vnrm": vn, "tris": tris, "cams": cam})
     r, c = _gbuffers(sc)
     assert (r[:, 3] > 0).sum() > 1000  # far more than the per-thread limit of 64 pixels
-    assert np.array_equal(r.view(np.int32), c.view(np.int32))
+    assert _agree(r, c, max_ties=0) == 1.0
