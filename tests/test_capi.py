@@ -97,3 +97,20 @@ def test_edge_gradient_argument_checks_without_gpu(lib):
     assert lib.mcdi_shadow_edge_grad(*args, 4, C.c_float(1e-4), p, C.c_void_p(4100), p, None,
                                      None) == mcdi.INVALID_ARG
     assert b"g_cs" in lib.mcdi_last_error()
+
+
+def test_raster_argument_checks_without_gpu(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    n = C.c_size_t()
+    assert lib.mcdi_raster_workspace_size(1, 0, 8, C.byref(n)) == mcdi.INVALID_ARG
+    assert lib.mcdi_raster_workspace_size(2, 8, 16, C.byref(n)) == mcdi.OK and n.value >= 2 * 8 * 16 * 8
+    p = C.c_void_p(4096)
+    uv = (C.c_float * 3)(0.0, 0.0, 1.0)
+    args = [p, p, p, 10, 4, p, 2, 8, 16, p, p, 64, uv, p, p, p, p, p]
+    assert lib.mcdi_raster_gbuffer(*args, n.value - 1, None) == mcdi.INVALID_ARG
+    assert b"workspace" in lib.mcdi_last_error()
+    bad = list(args)
+    bad[13] = C.c_void_p(4100)  # gb_pos not 16-byte aligned
+    assert lib.mcdi_raster_gbuffer(*bad, n.value, None) == mcdi.INVALID_ARG
+    assert b"gb_pos" in lib.mcdi_last_error()
