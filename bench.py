@@ -32,9 +32,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd MC shading Msamples/s & %HBM roofline at 512² 16spp"
-# DRAM bytes (read + write) per call of a stage's kernels at the headline size, from one ncu capture
-# (profiles/dram_traffic_shade_512x512_16spp.md); set to None when those kernels change.
-MEASURED_TRAFFIC = {"shade_fwd": 201.9e6}
+# DRAM bytes (read + write) per launch at the headline size, from one ncu capture of the kernel as it
+# stands (profiles/); an entry is removed when its kernels change.
+MEASURED_TRAFFIC = {}
 UNIT = "Msamples/s"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -150,6 +150,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+
+# ------------------------------------------------------------------ algorithmic bytes
+def tracer_structure_bytes(n_tris: int) -> int:
+    """Bytes of the traversal structure the shadow-ray tracer reads: the nodes it walks and the
+    48-byte triangle records."""
+    from paper_2206_03380_gb300 import mcdi
+
+    return mcdi.tracer_structure_bytes(n_tris)
+
+
+def algorithmic_bytes(P: int, spp: int, structure: int, probe, env) -> dict:
+    """Algorithmic HBM bytes per launch of the shading stages at P pixels (all pixels of the views):
+
+    forward   per pixel: G-buffer payload in 48 B (position, normal, k_d, k_orm: 12 B each), outputs
+              c_d / k_d,out / c_s 36 B, visibility spp/8 B; once: the traversal structure, the probe
+              (16 B per texel as stored) and its tables
+    tracer    the traversal structure once and the visibility bits (spp/8 B per pixel)
+    backward  per pixel: upstream gradients 36 B, G-buffer payload 48 B, visibility spp/8 B, gradients
+              of k_d, k_orm and N 36 B; once: probe and tables, probe gradient written (12 B per texel)
+    """
+    vis = spp / 8.0
+    probe_bytes = env.nbytes + probe.cond.numel() * 4 + probe.marg.numel() * 4
+    texels = env.shape[0] * env.shape[1]
+    return {"shade_fwd": P * (48 + 36 + vis) + structure + probe_bytes,
+            "wave_trace": structure + P * vis,
+            "shade_bwd": P * (36 + 48 + vis + 36) + probe_bytes + 12 * texels}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world):
     import torch
@@ -245,7 +273,8 @@ def run_gpu(args, rank, world):
     # e2e: host inputs -> device -> the captured step -> host outputs, per step (the graph reads the
     # device buffers the host copies land in)
     host_in = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
-               [("verts", sc.verts), ("vnrm", sc.vnrm), ("tris", sc.tris), ("env", sc.env)]}
+               [("verts", sc.verts), ("vnrm", sc.vnrm), ("tris", sc.tris), ("env", sc.env),
+                ("tex_kd", sc.tex_kd), ("tex_korm", sc.tex_korm)]}
     host_ref = ref.cpu().pin_memory()
     outs_dev = [pipe.loss, pipe.color, pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env]
     host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs_dev]
@@ -257,6 +286,8 @@ def run_gpu(args, rank, world):
         pipe.vnrm.copy_(host_in["vnrm"], non_blocking=True)
         pipe.tris.copy_(host_in["tris"], non_blocking=True)
         pipe.env.copy_(host_in["env"], non_blocking=True)
+        pipe.tex_kd.copy_(host_in["tex_kd"], non_blocking=True)
+        pipe.tex_korm.copy_(host_in["tex_korm"], non_blocking=True)
         ref.copy_(host_ref, non_blocking=True)
         pipe.replay()
         for h, d in zip(host_out, outs_dev):
@@ -275,37 +306,43 @@ def run_gpu(args, rank, world):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     e2e_value = total_samples / (e2e_ms * 1e-3) / 1e6
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / event time)
+    # rooflines: algorithmic bytes (or FLOPs) per launch / CUDA-event time
     avg = {st: float(np.mean(v)) for st, v in stage_ms.items()}
     P = N * H * W
-    words = (sc.spp + 31) // 32
-    bvh_bytes = sum(mcdi.bvh_sizes(sc.tris.shape[0])[:2])
-    probe_bytes = sc.env.nbytes + pipe.probe.cond.numel() * 4 + pipe.probe.marg.numel() * 4
-    algo = {
-        # G-buffer planes in (4 x 16 B), c_d / kd_out / c_s out (3 x 16 B), mask out; BVH, probe, tables once
-        "shade_fwd": P * (64 + 48 + 4 * words) + bvh_bytes + probe_bytes,
-        # G-buffer + upstream (3 x 16 B) + mask in, three gradient planes out; probe in, probe gradient in+out
-        "shade_bwd": P * (64 + 48 + 4 * words + 48) + probe_bytes + 2 * sc.env.nbytes,
-    }
+    algo = algorithmic_bytes(P, sc.spp, tracer_structure_bytes(sc.tris.shape[0]), pipe.probe, sc.env)
     # denoiser: algorithmic tensor FLOPs (2 * 9 * c_in * c_out per output pixel and conv, unpadded)
     conv_flops = 0
     for name, ci, co in scenes.UNET_SHAPES:
         lvl = {"enc1": 0, "enc2": 1, "enc3": 2, "bot_": 3, "dec3": 2, "dec2": 1, "dec1": 0, "out": 0}[name[:4]]
         conv_flops += 2 * 9 * ci * co * (2 * N) * (H >> lvl) * (W >> lvl)
     flops = {"denoise_fwd": conv_flops, "denoise_bwd": conv_flops}  # input-gradient convs: same shapes
-    dom = max(("shade_fwd", "shade_bwd", "denoise_fwd", "denoise_bwd"), key=lambda s: avg[s])
     peak, peak_kind = peaks()
-    if dom in flops:
+    rays = shadow_ray_figures(pipe, flush, stream, args.steps, samples_per_step)
+    # the dominant kernel of the step (largest share of the launch list): the shadow-ray tracer, timed
+    # alone with CUDA events on its launching stream (L2 flushed before each launch)
+    t_trace = rays["ms"]
+    achieved = algo["wave_trace"] / (t_trace * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "wave_trace_kernel", "achieved": round(achieved, 2), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 5), "traffic": MEASURED_TRAFFIC.get("wave_trace_kernel"),
+            "peak_source": peak_kind, "algorithmic_bytes": int(algo["wave_trace"]), "ms": round(t_trace, 4),
+            "note": "algorithmic bytes: the traversal structure read once (nodes + triangle records) and the "
+                    "visibility bits written; the kernel is bound by L1 wavefronts of incoherent node fetches, "
+                    "see shadow_rays"}
+    stage_roof = {}
+    for st in ("shade_fwd", "shade_bwd"):
+        a = algo[st] / (avg[st] * 1e-3) / 1e9
+        stage_roof[st] = {"achieved": round(a, 2), "peak": peak, "unit": "GB/s", "frac": round(a / peak, 5),
+                          "algorithmic_bytes": int(algo[st]), "ms": round(avg[st], 4),
+                          "traffic": MEASURED_TRAFFIC.get(st)}
+    for st in ("denoise_fwd", "denoise_bwd"):
         tpeak, tkind = tensor_peak()
-        achieved = flops[dom] / (avg[dom] * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": dom, "achieved": round(achieved, 2), "peak": tpeak, "unit": "TFLOP/s",
-                "frac": round(achieved / tpeak, 5), "traffic": None, "peak_source": tkind,
-                "algorithmic_flops": int(flops[dom])}
-    else:
-        achieved = algo[dom] / (avg[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": MEASURED_TRAFFIC.get(dom), "peak_source": peak_kind,
-                "algorithmic_bytes": int(algo[dom])}
+        a = flops[st] / (avg[st] * 1e-3) / 1e12
+        stage_roof[st] = {"achieved": round(a, 2), "peak": tpeak, "unit": "TFLOP/s", "frac": round(a / tpeak, 5),
+                          "algorithmic_flops": int(flops[st]), "ms": round(avg[st], 4), "peak_source": tkind}
+    whole = sum(algo[st] for st in ("shade_fwd", "shade_bwd"))
+    stage_roof["shading_fwd_bwd"] = {"algorithmic_bytes": int(whole),
+                                     "frac_of_step": round(whole / (dev_ms_max * 1e-3) / 1e9 / peak, 5),
+                                     "note": "forward + backward shading bytes over the whole graph-replayed step"}
     den_tf = {k: round(flops[k] / (avg[k] * 1e-3) / 1e12, 2) for k in flops}
     clocks = clk.summary()
     launches = args.steps * sum(n_launch.values())
@@ -324,8 +361,7 @@ def run_gpu(args, rank, world):
         "stage_ms": {k: round(v, 4) for k, v in avg.items()},  # eager launches (events between stages)
         "wall_s": round(wall, 3),
         "roofline": roof,
-        "shade_fwd_hbm": {"achieved": round(algo["shade_fwd"] / (avg["shade_fwd"] * 1e-3) / 1e9, 2), "peak": peak,
-                          "unit": "GB/s", "frac": round(algo["shade_fwd"] / (avg["shade_fwd"] * 1e-3) / 1e9 / peak, 5)},
+        "stage_roofline": stage_roof,
         "denoiser_tflops": den_tf,
         "clocks": clocks,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -337,7 +373,7 @@ def run_gpu(args, rank, world):
     }
     result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
     result["denoiser_bilateral"] = time_bilateral(pipe, flush, stream, args.steps)
-    result["shadow_rays"] = shadow_ray_figures(pipe, flush, stream, args.steps, samples_per_step)
+    result["shadow_rays"] = rays
     result["bvh"] = time_bvh_refit(pipe, flush, stream, args.steps)
     result["shadow_edge_grad"] = time_shadow_edge_grad(pipe, flush, stream, args.steps)
     if world == 1 and not args.no_cpu_baseline:

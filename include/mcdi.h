@@ -373,6 +373,20 @@ MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_
                                       size_t act_bytes, const float* gy, float* gx, void* grad_ws,
                                       size_t grad_bytes, unsigned* err, void* stream);
 
+/* mcdi_denoise_record_plan (host; a measurement and test aid, not on the
+ * hot path): while rec is non-NULL, each convolution that mcdi_denoise_fwd /
+ * mcdi_denoise_bwd launch from the calling host thread appends one record of
+ * 8 ints to rec (host memory, room for cap records; later ones are dropped):
+ *   {pass (0 forward, 1 input gradient), convolution index 0..14 (the order of
+ *    mcdi_denoise_pack_weights), level (0 = full resolution), row-tile form
+ *    (1) or one CTA per 128-pixel tile (0), output rows per row tile R (0 in
+ *    the tile form), ReLU-mask prefetching variant (0/1), 2x2 max-pool written
+ *    from the epilogue (0/1), E4M3 operands (0/1)};
+ * *count (host) is reset to 0 by this call and counts the records written.
+ * mcdi_denoise_record_plan(NULL, 0, NULL) stops recording.  The records say
+ * which kernel variants a launch configuration runs. */
+MCDI_API mcdi_status mcdi_denoise_record_plan(int* rec, int cap, int* count);
+
 /* Final colour (Sec. 4.2): c = kd_out * D(c_d) + D(c_s), n pixels of float4
  * planes (w of c = 0). */
 MCDI_API mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float* den_cs, long long n,

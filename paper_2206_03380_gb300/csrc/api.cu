@@ -517,6 +517,16 @@ mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_img, int 
     return launched(e, "denoise_bwd");
 }
 
+mcdi_status mcdi_denoise_record_plan(int* rec, int cap, int* count) {
+    if (rec == nullptr) {
+        mcdi::set_plan_recorder(nullptr, 0, nullptr);
+        return MCDI_OK;
+    }
+    REQUIRE(cap >= 1 && count != nullptr, "cap must be >= 1 and count non-NULL when recording");
+    mcdi::set_plan_recorder(rec, cap, count);
+    return MCDI_OK;
+}
+
 mcdi_status mcdi_composite(const float* kd_out, const float* den_cd, const float* den_cs, long long n, float* c,
                            void* stream) {
     REQUIRE(n >= 1, "n must be >= 1");

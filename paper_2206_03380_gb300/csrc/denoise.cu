@@ -414,6 +414,22 @@ __global__ void pack_weights_e4m3_kernel(const float* __restrict__ W, int ci, in
 }  // namespace
 
 // ---------------------------------------------------------------- orchestration
+// Launch-plan recorder (mcdi_denoise_record_plan): per host thread, one record
+// of kPlanRecordInts ints per convolution launched while it is set.
+struct PlanRecorder {
+    int* rec = nullptr;
+    int cap = 0;
+    int* count = nullptr;
+};
+static thread_local PlanRecorder t_plan;
+
+void set_plan_recorder(int* rec, int cap, int* count) {
+    t_plan.rec = rec;
+    t_plan.cap = cap;
+    t_plan.count = count;
+    if (count) *count = 0;
+}
+
 struct Unet {
     const char* wbase;
     UnetWeightLayout L;
@@ -518,6 +534,17 @@ static cudaError_t run_conv(Unet& u, int level, const bf16* x, int x_slot, int c
         d.p.pool_ctotal = pool.ctotal;
         d.p.pool_amax = u.out(pool.slot);
         *pool.done = true;
+    }
+    if (t_plan.rec && t_plan.count && *t_plan.count < t_plan.cap) {
+        int* r = t_plan.rec + (size_t)kPlanRecordInts * (*t_plan.count)++;
+        r[0] = w.dgrad ? 1 : 0;
+        r[1] = w.i;
+        r[2] = level;
+        r[3] = d.rows_form ? 1 : 0;
+        r[4] = d.rows_form ? d.rp.rows : 0;
+        r[5] = conv_mask_prefetch(d) ? 1 : 0;
+        r[6] = d.p.pool_out != nullptr ? 1 : 0;
+        r[7] = d.p.fp8;
     }
     return conv_launch(d, s);
 }

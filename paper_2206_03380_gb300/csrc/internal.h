@@ -23,9 +23,9 @@ constexpr int kSortDigitBits = 10;  // 30-bit Morton keys: three passes
 constexpr int kSortPasses = 3;
 static_assert(kSortDigitBits * kSortPasses >= 30, "the passes must cover the 30 key bits");
 
-__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-inline BvhScratch bvh_scratch_layout(int n) {
+constexpr BvhScratch bvh_scratch_layout(int n) {
     BvhScratch s{};
     const size_t un = (size_t)(n > 0 ? n : 1);
     const size_t ni = un > 1 ? un - 1 : 1;
@@ -146,6 +146,8 @@ cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, in
 cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, int W, const void* acts,
                             const float* gy, float* gx_term, void* grad_ws, unsigned* err, cudaStream_t s,
                             const char** why);
+constexpr int kPlanRecordInts = 8;
+void set_plan_recorder(int* rec, int cap, int* count);  // nullptr rec: stop recording
 cudaError_t launch_conv3x3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* bias,
                            int cout_pad, int relu, void* y, unsigned* err, cudaStream_t s, const char** why);
 cudaError_t launch_conv3x3_e4m3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* x_amax,

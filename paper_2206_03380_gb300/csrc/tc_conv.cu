@@ -960,6 +960,8 @@ static void launch_rows(const ConvDesc& d, cudaStream_t stream) {
     else launch_k(conv_tc_rows_kernel<1, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
 }
 
+bool conv_mask_prefetch(const ConvDesc& d) { return d.rows_form && d.p.mode == kDgradMask && d.rp.nc <= 64; }
+
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -982,7 +984,7 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     if (attr_err != cudaSuccess) return attr_err;
     if (d.rows_form) {
         // masked input gradients whose mask words fit the prefetch registers take the prefetching variant
-        const bool mp = d.p.mode == kDgradMask && d.rp.nc <= 64;
+        const bool mp = conv_mask_prefetch(d);
         const bool pl = d.p.pool_out != nullptr;  // conv_make_desc keeps it only where the plan can pool
         if (d.p.fp8) {
             if (mp) launch_rows<true, true, false>(d, stream);

@@ -88,6 +88,10 @@ bool conv_make_desc(ConvDesc* d, const void* x, const void* w, const char** why)
 // Runs the persistent row-tile kernel when planned, else one CTA per tile.
 cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream);
 
+// Whether conv_launch runs the row-tile variant that prefetches the ReLU-mask
+// words of the next row (masked input gradients whose mask words fit its registers).
+bool conv_mask_prefetch(const ConvDesc& d);
+
 int conv_pick_tile_w(int W);
 
 }  // namespace mcdi

@@ -42,7 +42,7 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd",
            "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep", "mcdi_refit_bvh",
            "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad",
-           "mcdi_raster_workspace_size", "mcdi_raster_gbuffer"]
+           "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
     lib.mcdi_denoise_fwd.restype = st
     lib.mcdi_denoise_fwd.argtypes = [P, i, i, i, i, P, P, P, i, P, P, sz, P, P]
     lib.mcdi_denoise_bwd.restype = st
+    lib.mcdi_denoise_record_plan.restype = st
+    lib.mcdi_denoise_record_plan.argtypes = [P, i, P]
     lib.mcdi_denoise_bwd.argtypes = [P, i, i, i, i, P, sz, P, P, P, sz, P, P]
     lib.mcdi_composite.restype = st
     lib.mcdi_composite.argtypes = [P, P, P, C.c_longlong, P, P]
@@ -163,6 +165,13 @@ def bvh_sizes(n_tris: int):
     a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
     _check(load().mcdi_bvh_sizes(int(n_tris), C.byref(a), C.byref(b), C.byref(c)), "bvh_sizes")
     return a.value, b.value, c.value
+
+
+def tracer_structure_bytes(n_tris: int) -> int:
+    """Bytes of the structure a shadow ray walks: the depth-first nodes (2 n - 1 of 32 B) and the
+    triangle records (n of 48 B)."""
+    n = max(int(n_tris), 1)
+    return (2 * n - 1) * 32 + n * 48
 
 
 def build_bvh(verts, tris, nodes, tri_records, scratch, stream=None):
@@ -378,6 +387,30 @@ class Denoiser:
 
     def backward(self, gy, gx, stream=None):
         denoise_bwd(self.weights, self.acts, gy, gx, self.grad_ws, self.err, stream, self.precision)
+
+
+class denoise_plan_recorder:
+    """Context manager: records the launch plan of every convolution the denoiser
+    launches from this thread inside the block; ``records`` then holds one dict per
+    convolution (pass, conv, level, rows_form, rows, mask_prefetch, pool_fused, e4m3)."""
+
+    KEYS = ("pass", "conv", "level", "rows_form", "rows", "mask_prefetch", "pool_fused", "e4m3")
+
+    def __init__(self, cap: int = 256):
+        self.cap = cap
+        self.buf = (C.c_int * (8 * cap))()
+        self.count = C.c_int(0)
+        self.records = []
+
+    def __enter__(self):
+        _check(load().mcdi_denoise_record_plan(C.addressof(self.buf), self.cap, C.addressof(self.count)),
+               "denoise_record_plan")
+        return self
+
+    def __exit__(self, *exc):
+        load().mcdi_denoise_record_plan(None, 0, None)
+        n = self.count.value
+        self.records = [dict(zip(self.KEYS, self.buf[8 * k: 8 * k + 8])) for k in range(n)]
 
 
 class Denoise(torch.autograd.Function):

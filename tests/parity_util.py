@@ -45,3 +45,15 @@ def mask_bits(words, spp):
     words = np.asarray(words).astype(np.uint32).reshape(len(words), -1)
     j = np.arange(spp)
     return ((words[:, j // 32] >> (j % 32).astype(np.uint32)) & 1).astype(bool)
+
+
+def flipped_samples(gbits, obits, active, bad_pixels, margin):
+    """Samples whose discrete decisions the GPU and the oracle took differently:
+    (lower, upper) = (hit flips on active samples + one per pixel outside the
+    radiance tolerance, hit flips + every marginal sample of those pixels).  A
+    pixel outside the tolerance holds at least one flipped decision (texel, CDF
+    bin); flips that leave every pixel inside the tolerance (a sample grazing the
+    horizon contributes ~0 either way) are not counted."""
+    hits = int(((gbits != obits) & active).sum())
+    near = (margin < MARGIN) & ~((gbits != obits) & active)
+    return hits + int(bad_pixels.sum()), hits + int(near[bad_pixels].sum())

@@ -152,6 +152,82 @@ def test_denoise_autograd_function_matches_direct_calls(cuda_lib):
     assert kd_t.grad is None
 
 
+def _run_recorded(mcdi, den, term, kd, nrm, gy):
+    t = lambda a: torch.from_numpy(a).cuda().contiguous()
+    y = torch.zeros(term.shape, device="cuda")
+    gx = torch.zeros(term.shape, device="cuda")
+    with mcdi.denoise_plan_recorder() as rec:
+        den.forward(t(term), t(kd), t(nrm), y)
+        den.backward(t(gy), gx)
+    torch.cuda.synchronize()
+    assert den.err.item() == 0
+    return y.cpu().numpy()[..., :3], gx.cpu().numpy()[..., :3], rec.records
+
+
+def _compare_with_oracle(term, kd, nrm, gy, yg, gg, weights, storages):
+    x = oracle_input(term, kd, nrm)
+    gyo = torch.from_numpy(gy[..., :3]).permute(0, 3, 1, 2)
+    res = {}
+    for storage in storages:
+        yo, gxo, _ = D.unet_forward_backward(x, weights, gyo, storage=storage)
+        yo = yo.permute(0, 2, 3, 1).numpy()
+        go = gxo[:, 0:3].permute(0, 2, 3, 1).numpy()
+        res[storage] = (D.rel_l2(yg, yo), D.psnr(yg, yo), D.rel_l2(gg, go))
+    return res
+
+
+def test_unet_headline_launch_forward_and_input_gradient(cuda_lib):
+    """The benchmark's denoiser launch: the c_d and c_s terms of one 512 x 512 view
+    (2 images) with a random upstream gradient, forward and input gradient against the
+    oracle; the recorded launch plan must include the row-tile kernels that prefetch the
+    ReLU-mask words with 4 and with 2 output rows per tile (the instantiations the
+    benchmark times), and the pooling epilogue."""
+    mcdi = cuda_lib
+    rng = np.random.default_rng(5120)
+    term, kd, nrm = make_inputs(rng, 1, 512, 512)
+    weights = D.xavier_weights(6)
+    den = mcdi.Denoiser(mcdi.flatten_unet_params(weights), 2, 512, 512)
+    gy = rng.normal(size=term.shape).astype(np.float32)
+    gy[..., 3] = 0
+    yg, gg, plan = _run_recorded(mcdi, den, term, kd, nrm, gy)
+    assert np.isfinite(yg).all() and np.isfinite(gg).all()
+    assert len(plan) == 30 and sum(r["pass"] for r in plan) == 15
+    masked_rows = {r["rows"] for r in plan if r["pass"] == 1 and r["mask_prefetch"]}
+    assert {2, 4} <= masked_rows, plan
+    assert any(r["pool_fused"] for r in plan if r["pass"] == 0)
+    res = _compare_with_oracle(term, kd, nrm, gy, yg, gg, weights, ("bf16", None))
+    (bf_f, bf_p, bf_b), (f64_f, f64_p, f64_b) = res["bf16"], res[None]
+    print(f"denoiser 2 x 512^2 (plan rows fwd {[r['rows'] for r in plan if r['pass'] == 0]}, bwd "
+          f"{[r['rows'] for r in plan if r['pass'] == 1]}): vs BF16-storage oracle fwd rel-L2 {bf_f:.2e} "
+          f"({bf_p:.1f} dB), input-grad {bf_b:.2e}; vs float64 network fwd {f64_f:.2e} ({f64_p:.1f} dB), "
+          f"input-grad {f64_b:.2e}")
+    assert bf_f <= 1e-2 and bf_b <= 6e-2
+    assert f64_f <= 2e-2 and f64_b <= 0.2
+
+
+def test_unet_e4m3_forward_and_input_gradient_at_256(cuda_lib):
+    """E4M3 at 256 x 256 over two views (4 images): enough row tiles for the masked
+    input-gradient convolutions to run with 4 and 2 rows per tile."""
+    mcdi = cuda_lib
+    rng = np.random.default_rng(2560)
+    term, kd, nrm = make_inputs(rng, 2, 256, 256)
+    weights = D.xavier_weights(5)
+    den = mcdi.Denoiser(mcdi.flatten_unet_params(weights), term.shape[0], 256, 256, precision=mcdi.E4M3)
+    gy = rng.normal(size=term.shape).astype(np.float32)
+    gy[..., 3] = 0
+    yg, gg, plan = _run_recorded(mcdi, den, term, kd, nrm, gy)
+    assert np.isfinite(yg).all() and np.isfinite(gg).all()
+    assert all(r["e4m3"] for r in plan) and len(plan) == 30
+    masked_rows = {r["rows"] for r in plan if r["pass"] == 1 and r["mask_prefetch"]}
+    assert {2, 4} <= masked_rows, plan
+    res = _compare_with_oracle(term, kd, nrm, gy, yg, gg, weights, ("e4m3", None))
+    (q_f, q_p, q_b), (f_f, f_p, f_b) = res["e4m3"], res[None]
+    print(f"denoiser E4M3 4 x 256^2: vs E4M3-storage oracle fwd rel-L2 {q_f:.2e} ({q_p:.1f} dB), input-grad "
+          f"{q_b:.2e}; vs float64 network fwd {f_f:.2e} ({f_p:.1f} dB), input-grad {f_b:.2e}")
+    assert q_f <= 6e-2 and q_b <= 0.2
+    assert f_f <= 0.25 and f_b <= 0.6
+
+
 def test_unet_forward_at_headline_size(cuda_lib):
     """512 x 512, the two terms of one view (the benchmark's denoiser launch), forward only."""
     mcdi = cuda_lib

@@ -50,10 +50,12 @@ def test_fullsize_step_matches_oracle_on_sampled_pixels(cuda_lib, orc, headline)
     gout = gout[:, [0, 1, 2, 4, 5, 6, 8, 9, 10]]
     np.testing.assert_allclose(gout[:, 3:6], o_out[:, 3:6], rtol=1e-4, atol=1e-6)
     n_bad = 0
+    bad_px = np.zeros(len(pix), bool)
     for sl in (slice(0, 3), slice(6, 9)):
         bad, marginal, err = PU.compare_radiance(gout[:, sl], o_out[:, sl], recs)
         assert not (bad & ~marginal).any(), (err[bad & ~marginal], pix[bad & ~marginal])
         n_bad += bad.sum()
+        bad_px |= bad
     assert n_bad <= 3
     gbits = PU.mask_bits(to_np(pipe.mask).reshape(W * H, -1)[pix], sc.spp)
     obits = PU.mask_bits(o_vis, sc.spp)
@@ -62,6 +64,8 @@ def test_fullsize_step_matches_oracle_on_sampled_pixels(cuda_lib, orc, headline)
     assert mism.sum() <= max(1, 1e-4 * act.sum())
     assert np.all(recs["margin"][mism] < PU.MARGIN)
     assert recs["occluded"].sum() > 0.05 * act.sum()
+    lo, hi = PU.flipped_samples(gbits, obits, act, bad_px, recs["margin"])
+    print(f"headline flipped samples: {lo} (at most {hi}) of {int(act.sum())} active")
 
     # adjoint: upstream nonzero only on the sampled, non-marginal pixels
     marginal = (recs["margin"] < PU.MARGIN).any(1)
