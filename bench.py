@@ -152,12 +152,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ algorithmic bytes
-def tracer_structure_bytes(n_tris: int) -> int:
-    """Bytes of the traversal structure the shadow-ray tracer reads: the nodes it walks and the
-    48-byte triangle records."""
+def tracer_structure_bytes(bvh) -> int:
+    """Bytes of the traversal structure the shadow-ray tracer reads: the four-wide nodes of the
+    built tree (64 B each) and the 48-byte triangle records."""
     from paper_2206_03380_gb300 import mcdi
 
-    return mcdi.tracer_structure_bytes(n_tris)
+    return mcdi.tracer_structure_bytes(bvh)
 
 
 def algorithmic_bytes(P: int, spp: int, structure: int, probe, env) -> dict:
@@ -309,7 +309,7 @@ def run_gpu(args, rank, world):
     # rooflines: algorithmic bytes (or FLOPs) per launch / CUDA-event time
     avg = {st: float(np.mean(v)) for st, v in stage_ms.items()}
     P = N * H * W
-    algo = algorithmic_bytes(P, sc.spp, tracer_structure_bytes(sc.tris.shape[0]), pipe.probe, sc.env)
+    algo = algorithmic_bytes(P, sc.spp, tracer_structure_bytes(pipe.bvh), pipe.probe, sc.env)
     # denoiser: algorithmic tensor FLOPs (2 * 9 * c_in * c_out per output pixel and conv, unpadded)
     conv_flops = 0
     for name, ci, co in scenes.UNET_SHAPES:
@@ -458,13 +458,14 @@ def time_bilateral(pipe, flush, stream, steps, sigma=2.0):
     return {"sigma": sigma, "fwd_ms": round(float(np.mean(fwd)), 4), "bwd_ms": round(float(np.mean(bwd)), 4)}
 
 
-# per-test FP32 operations of the traversal, counted from the source: a slab
-# test is 6 subtracts + 6 multiplies + 11 min/max + 1 multiply + 1 compare; a
+# per-visit FP32 operations of the traversal, counted from the source: a visit of
+# a four-wide node is 3 subtracts + 6 multiplies of set-up and per child 6 adds
+# (byte to float) + 6 fused multiply-adds + 5 min/max + 1 compare (81 in all); a
 # two-sided Moller-Trumbore test that runs to the end is 2 cross products (9 ops
 # each), 4 dot products (5 each), 1 reciprocal, 3 subtracts, 3 multiplies,
 # 1 add and 6 compares (early outs make it shorter: an upper bound)
-SLAB_OPS, TRI_OPS = 25, 52
-NODE_BYTES, TRI_BYTES, RAY_BYTES = 32, 48, 32
+NODE_OPS, TRI_OPS = 81, 52
+NODE_BYTES, TRI_BYTES, RAY_BYTES = 64, 48, 32
 
 
 def alu_peak_gops():
@@ -528,8 +529,8 @@ def shadow_ray_figures(pipe, flush, stream, steps, samples):
             "requested_bytes": req, "requested_gbs": round(req_gbs, 1), "l2_read_peak_gbs": round(l2, 1),
             "l2_peak_source": "measured (read sweep over 8-32 MiB)",
             "frac_of_l2_read_peak": round(req_gbs / l2, 4) if l2 > 0 else None,
-            "traversal_fp32_ops_per_sample": round((visits * SLAB_OPS + tests * TRI_OPS) / max(samples, 1), 1),
-            "traversal_gops": round((visits * SLAB_OPS + tests * TRI_OPS) / (t * 1e-3) / 1e9, 1),
+            "traversal_fp32_ops_per_sample": round((visits * NODE_OPS + tests * TRI_OPS) / max(samples, 1), 1),
+            "traversal_gops": round((visits * NODE_OPS + tests * TRI_OPS) / (t * 1e-3) / 1e9, 1),
             "alu_peak_gops": round(alu_peak_gops(), 1),
             "alu_peak_source": "derived: SMs x 128 FP32 lanes x max SM clock (one operation per lane per cycle)"}
 

@@ -6,15 +6,19 @@
 // octrees, and k-d trees"):
 //   1. centroid bounds (block min/max + one atomic per block and axis);
 //   2. 30-bit Morton code of each centroid;
-//   3. stable LSD radix sort, 4 passes of 8 bits (histogram / per-digit scan
+//   3. stable LSD radix sort, 3 passes of 10 bits (histogram / per-digit scan
 //      across tiles / scatter with warp match_any ranking);
 //   4. one thread per internal node finds its key range and split from the
 //      common-prefix lengths of the sorted keys (ties broken by position);
 //   5. bottom-up bounds: each leaf walks to the root, the second thread to
-//      reach a node (atomic arrival counter) writes its two child boxes.
-// Output: 64-byte two-child nodes (root = node 0) and 48-byte triangle records
-// in leaf (Morton) order.
+//      reach a node (atomic arrival counter) writes its two child boxes;
+//   6. one thread per node: the depth-first copy with escape links and, for
+//      internal nodes at even depth, the four-wide node with 8-bit child boxes
+//      that shadow rays traverse.
+// Output: 64-byte two-child nodes (root = node 0), the depth-first copy, the
+// four-wide nodes and 48-byte triangle records in leaf (Morton) order.
 #include <float.h>
+#include <limits.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -380,22 +384,128 @@ __global__ void single_leaf_root_kernel(BvhNode* nodes, const float4* box_leaf) 
     nodes[0].d = make_int4(~0, ~0, 0, 0);
 }
 
+// ---- four-wide nodes for shadow rays
+// One axis of a four-wide node: step s = the smallest power of two with
+// extent / s <= 250 and s >= s_min, origin one step below the union's minimum
+// (rounded down); child boxes quantised outwards (differences rounded away
+// from the box, scaled exactly by 1 / s) and widened by one more step.  All in
+// FP32 with directed rounding: the decoded box o + q s always holds the child's
+// box with at least one step to spare on each side.
+struct WideAxis {
+    float o, s, inv_s;
+};
+
+// smallest power of two >= x (x a positive normal float)
+__device__ __forceinline__ float pow2_ceil(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    return __uint_as_float(((b & 0x7fffffu) ? e + 1u : e) << 23);
+}
+
+__device__ __forceinline__ WideAxis wide_axis(float lo, float hi, float s_min) {
+    float x = __fmul_ru(__fsub_ru(hi, lo), 1.0f / 250.0f) * 1.0000002f;
+    if (!(x >= s_min)) x = s_min;  // also catches a NaN extent
+    const float s = pow2_ceil(fminf(x, 1e30f));
+    return {__fsub_rd(lo, s), s, 1.0f / s};
+}
+
+__device__ __forceinline__ uint32_t wide_q(float v, const WideAxis& ax, bool upper) {
+    const float t = upper ? __fsub_ru(v, ax.o) * ax.inv_s : __fsub_rd(v, ax.o) * ax.inv_s;
+    float q = upper ? ceilf(t) + 1.0f : floorf(t) - 1.0f;
+    q = fminf(fmaxf(q, 0.0f), 255.0f);  // NaN -> 0 (fmaxf returns the non-NaN operand)
+    return (uint32_t)q;
+}
+
+__device__ __forceinline__ void write_wide_node(int k, const BvhNode* __restrict__ nodes,
+                                                const float4* __restrict__ box_int,
+                                                const float4* __restrict__ box_leaf, float s_min,
+                                                WideNode* __restrict__ out) {
+    int links[4];
+    int nl = 0;
+    const int4 d = nodes[k].d;
+    const int c2[2] = {d.x, d.y};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (c2[h] < 0) {
+            links[nl++] = c2[h];
+        } else {
+            const int4 e = nodes[c2[h]].d;
+            links[nl++] = e.x;
+            links[nl++] = e.y;
+        }
+    }
+    float4 lo[4], hi[4];
+    float ulo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, uhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int q = 0; q < nl; ++q) {
+        child_box(links[q], box_int, box_leaf, lo[q], hi[q]);
+        ulo[0] = fminf(ulo[0], lo[q].x), ulo[1] = fminf(ulo[1], lo[q].y), ulo[2] = fminf(ulo[2], lo[q].z);
+        uhi[0] = fmaxf(uhi[0], hi[q].x), uhi[1] = fmaxf(uhi[1], hi[q].y), uhi[2] = fmaxf(uhi[2], hi[q].z);
+    }
+    WideAxis ax[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ax[a] = wide_axis(ulo[a], uhi[a], s_min);
+    uint32_t qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
+    int lk[4];
+    for (int q = 0; q < 4; ++q) {
+        uint32_t l3[3], h3[3];
+        if (q < nl) {
+            const float cl[3] = {lo[q].x, lo[q].y, lo[q].z}, ch[3] = {hi[q].x, hi[q].y, hi[q].z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                l3[a] = wide_q(cl[a], ax[a], false);
+                h3[a] = wide_q(ch[a], ax[a], true);
+            }
+            lk[q] = links[q];
+        } else {  // empty slot: an inverted box on every axis
+            l3[0] = l3[1] = l3[2] = 255u;
+            h3[0] = h3[1] = h3[2] = 0u;
+            lk[q] = INT_MIN;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            qlo[a] |= l3[a] << (8 * q);
+            qhi[a] |= h3[a] << (8 * q);
+        }
+    }
+    WideNode w;
+    w.a = make_float4(ax[0].o, ax[1].o, ax[2].o, ax[0].s);
+    w.b = make_float4(ax[1].s, ax[2].s, __uint_as_float(qlo[0]), __uint_as_float(qlo[1]));
+    w.c = make_float4(__uint_as_float(qlo[2]), __uint_as_float(qhi[0]), __uint_as_float(qhi[1]),
+                      __uint_as_float(qhi[2]));
+    w.d = make_int4(lk[0], lk[1], lk[2], lk[3]);
+    out[k] = w;
+}
+
+// Smallest quantisation step: 2^-17 of the largest coordinate magnitude of the
+// root box, far above the FP32 rounding of slab distances for ray origins
+// inside the scene's bounds (about 4 u |o - origin| per axis).
+__device__ __forceinline__ float wide_min_step(const float4* box_int, const float4* box_leaf, int n) {
+    const float4 lo = n > 1 ? box_int[0] : box_leaf[0], hi = n > 1 ? box_int[1] : box_leaf[1];
+    const float m = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(lo.y)), fmaxf(fabsf(lo.z), fabsf(hi.x))),
+                          fmaxf(fabsf(hi.y), fabsf(hi.z)));
+    return fmaxf(m * 7.62939453125e-6f, 1e-30f);
+}
+
 // Depth-first (pre-order) copy of the tree with escape links.  For a node
 // whose subtree holds leaves [f, l], the nodes before it in pre-order are its
 // ancestors plus the subtrees hanging to the left of its root path, which
 // hold exactly the leaves [0, f): 2 f minus one per right turn of the path.
 // Hence dfs = 2 f + (left turns on the path from the root), and the subtree
 // of 2 (l - f) + 1 nodes ends just before skip = dfs + 2 (l - f) + 1.
+// The same walk gives each internal node's depth: nodes at even depth also
+// write their four-wide node, the others zero their slot.
 __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __restrict__ nodes,
                                                        const int* __restrict__ parent_int,
                                                        const int* __restrict__ parent_leaf,
                                                        const float4* __restrict__ box_int,
                                                        const float4* __restrict__ box_leaf, float4* gap,
-                                                       int gap_vec4, ThreadedNode* __restrict__ out) {
+                                                       int gap_vec4, ThreadedNode* __restrict__ out, float4* wgap,
+                                                       int wgap_vec4, WideNode* __restrict__ wide) {
     pdl_prologue();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    // zero the alignment gap before this array, so that equal meshes give equal bytes
+    // zero the alignment gaps before the arrays, so that equal meshes give equal bytes
     if (v < gap_vec4) gap[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v < wgap_vec4) wgap[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v >= 2 * n - 1) return;
     const bool leaf = v >= n - 1;
     const int k = leaf ? v - (n - 1) : v;  // leaf position or internal node index
@@ -413,11 +523,33 @@ __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __r
         hi = box_int[2 * (size_t)k + 1];
         par = parent_int[k];
     }
-    int lefts = 0;
+    int lefts = 0, depth = 0;
     for (int steps = 0; par >= 0 && steps < n; ++steps) {  // the path to the root is shorter than n
         if (nodes[par].d.x == link) ++lefts;
+        ++depth;
         link = par;
         par = parent_int[par];
+    }
+    if (n == 1) {  // the four-wide root of a single triangle: one leaf child
+        WideNode w;
+        const float s_min = wide_min_step(box_int, box_leaf, 1);
+        WideAxis ax[3] = {wide_axis(lo.x, hi.x, s_min), wide_axis(lo.y, hi.y, s_min), wide_axis(lo.z, hi.z, s_min)};
+        const float cl[3] = {lo.x, lo.y, lo.z}, ch[3] = {hi.x, hi.y, hi.z};
+        uint32_t ql[3], qh[3];
+        for (int a = 0; a < 3; ++a) {
+            ql[a] = 0xffffff00u | wide_q(cl[a], ax[a], false);
+            qh[a] = wide_q(ch[a], ax[a], true);
+        }
+        w.a = make_float4(ax[0].o, ax[1].o, ax[2].o, ax[0].s);
+        w.b = make_float4(ax[1].s, ax[2].s, __uint_as_float(ql[0]), __uint_as_float(ql[1]));
+        w.c = make_float4(__uint_as_float(ql[2]), __uint_as_float(qh[0]), __uint_as_float(qh[1]),
+                          __uint_as_float(qh[2]));
+        w.d = make_int4(~0, INT_MIN, INT_MIN, INT_MIN);
+        wide[0] = w;
+    } else if (!leaf) {
+        if ((depth & 1) == 0) write_wide_node(k, nodes, box_int, box_leaf, wide_min_step(box_int, box_leaf, n), wide);
+        else wide[k] = WideNode{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                                make_float4(0.f, 0.f, 0.f, 0.f), make_int4(0, 0, 0, 0)};
     }
     const int dfs = 2 * f + lefts;
     const int skip = dfs + 2 * (l - f) + 1;
@@ -427,6 +559,23 @@ __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __r
 }
 
 }  // namespace
+
+// depth-first copy and four-wide nodes (one launch; zeroes the alignment gaps)
+static cudaError_t launch_threaded(int n, void* nodes_v, const BvhNode* nodes, const int* parent_int,
+                                   const int* parent_leaf, const float4* box_int, const float4* box_leaf,
+                                   cudaStream_t stream) {
+    char* nb = static_cast<char*>(nodes_v);
+    ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
+    const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
+    const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
+    const size_t threaded_end = threaded_offset(n) + (size_t)(2 * n - 1) * sizeof(ThreadedNode);
+    const int wgap_vec4 = (int)((wide_offset(n) - threaded_end) / 16);
+    WideNode* wide = reinterpret_cast<WideNode*>(nb + wide_offset(n));
+    launch_k(threaded_kernel, (2 * n - 1 + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf, box_int,
+             box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn,
+             reinterpret_cast<float4*>(nb + threaded_end), wgap_vec4, wide);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, int n, void* nodes_v, void* recs_v,
                              void* scratch, const BvhScratch& L, cudaStream_t stream) {
@@ -464,13 +613,7 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
         launch_k(karras_kernel, (n - 1 + 255) / 256, 256, 0, stream, keys[cur], n, nodes, parent_int, parent_leaf);
         launch_k(refit_kernel, g256, 256, 0, stream, n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
     }
-    char* nb = static_cast<char*>(nodes_v);
-    ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
-    const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
-    const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
-    launch_k(threaded_kernel, (2 * n - 1 + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf, box_int,
-             box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
-    return cudaGetLastError();
+    return launch_threaded(n, nodes_v, nodes, parent_int, parent_leaf, box_int, box_leaf, stream);
 }
 
 // New vertex positions, same triangles: the leaf order (the final sort pass's
@@ -493,13 +636,7 @@ cudaError_t launch_refit_bvh(const float* verts, int n_verts, const int* tris, i
     launch_k(leaf_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, order, recs, box_leaf, flags);
     if (n == 1) launch_k(single_leaf_root_kernel, 1, 1, 0, stream, nodes, box_leaf);
     else launch_k(refit_kernel, g256, 256, 0, stream, n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
-    char* nb = static_cast<char*>(nodes_v);
-    ThreadedNode* tn = reinterpret_cast<ThreadedNode*>(nb + threaded_offset(n));
-    const size_t two_child = (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
-    const int gap_vec4 = (int)((threaded_offset(n) - two_child) / 16);
-    launch_k(threaded_kernel, (2 * n - 1 + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf, box_int,
-             box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn);
-    return cudaGetLastError();
+    return launch_threaded(n, nodes_v, nodes, parent_int, parent_leaf, box_int, box_leaf, stream);
 }
 
 }  // namespace mcdi

@@ -105,6 +105,34 @@ __host__ __device__ inline const ThreadedNode* threaded_nodes(const void* nodes,
     return reinterpret_cast<const ThreadedNode*>(static_cast<const char*>(nodes) + threaded_offset(n_tris));
 }
 
+// Four-wide node with compressed child boxes, 64 bytes, for shadow rays.  It
+// stands for a two-child node at even depth of the same tree together with its
+// children: its children are that node's grandchildren (or its children where
+// those are leaves), so one fetch tests up to four boxes.  Child k's box on
+// axis x is [o.x + qlo_x[k] s.x, o.x + qhi_x[k] s.x] with 8-bit q and a power
+// of two s, rounded outwards by at least one step s, which is what keeps the
+// slab test conservative in FP32 (the rounding of the slab distances stays
+// below one step for ray origins inside the scene's bounds).  An empty slot
+// has qlo = 255 and qhi = 0 on every axis, a box no ray hits.  Links: >= 0
+// index of a four-wide node (the node array is indexed like the two-child
+// nodes; odd-depth slots are unused and zero), < 0 leaf, ~link = index into
+// the triangle records.
+struct __align__(64) WideNode {
+    float4 a;  // o.x, o.y, o.z, s.x
+    float4 b;  // s.y, s.z, qlo_x[0..3] (bytes), qlo_y[0..3]
+    float4 c;  // qlo_z[0..3], qhi_x[0..3], qhi_y[0..3], qhi_z[0..3]
+    int4 d;    // links of children 0..3
+};
+
+__host__ __device__ inline size_t wide_offset(int n_tris) {
+    const size_t n = (size_t)(n_tris > 0 ? n_tris : 1);
+    return (threaded_offset(n_tris) + (2 * n - 1) * sizeof(ThreadedNode) + 255) & ~(size_t)255;
+}
+
+__host__ __device__ inline const WideNode* wide_nodes(const void* nodes, int n_tris) {
+    return reinterpret_cast<const WideNode*>(static_cast<const char*>(nodes) + wide_offset(n_tris));
+}
+
 constexpr int kTraversalStack = 64;  // >= depth of a tree over 62-bit unique keys
 
 }  // namespace mcdi

@@ -48,8 +48,9 @@ constexpr BvhScratch bvh_scratch_layout(int n) {
 }
 
 // two-child nodes (64 B each), then the depth-first copy with escape links
-// (2 n - 1 nodes of 32 B) at a 256-byte aligned offset
-inline size_t bvh_node_bytes(int n) { return threaded_offset(n) + (size_t)(2 * (n > 0 ? n : 1) - 1) * 32; }
+// (2 n - 1 nodes of 32 B) and the four-wide nodes (one 64-byte slot per
+// two-child node), each at a 256-byte aligned offset
+inline size_t bvh_node_bytes(int n) { return wide_offset(n) + (size_t)(n > 1 ? n - 1 : 1) * sizeof(WideNode); }
 inline size_t bvh_tri_bytes(int n) { return (size_t)(n > 0 ? n : 1) * 48; }
 
 // Record the reason returned by mcdi_last_error() on this thread ("" clears it).

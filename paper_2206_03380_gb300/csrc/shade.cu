@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a
         if (!draw_sample(Pr, px, a.n_light, a.n_cos, a.n_ggx, j, u, &wi, &t, &ci, &inv_denom)) continue;
         bool hit;
         if (vis_mask) hit = (word >> (j & 31)) & 1u;
-        else hit = any_hit(nodes, tris, a.n_tris, make_ray(px.p + px.n * a.ray_eps, wi));
+        else hit = any_hit_threaded(nodes, tris, a.n_tris, make_ray(px.p + px.n * a.ray_eps, wi));  // no stack
         const float A = (hit ? 1.0f - a.tau : 1.0f) * inv_denom;
         const float4 L4 = __ldg(Pr.env + t);
         const f3 L = xyz(L4);

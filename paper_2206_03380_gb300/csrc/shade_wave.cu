@@ -21,7 +21,10 @@ namespace {
 
 constexpr int kGenThreads = 128;
 constexpr int kTraceThreads = 128;
-constexpr int kTraceStepsPerRefill = 32;
+constexpr int kTraceBlocksPerSM = 8;
+constexpr int kTraceStepsPerRefill = 8;
+constexpr int kLeafQueue = 8;   // postponed triangle tests per lane
+constexpr int kLeafBatch = 16;  // lanes holding one that start a triangle round
 
 struct WaveBuffers {
     float4* ray_o;      // [rays] origin, w = slot index (int bits) of the sample
@@ -147,14 +150,19 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
     }
 }
 
-// Persistent any-hit tracer with per-lane refill.  A lane holds one ray and
-// its position in the depth-first node array (stackless traversal along
-// escape links: the whole traversal state is one index); every
-// kTraceStepsPerRefill node visits the warp refills the lanes that are idle
-// from the global slot counter.
-__global__ void __launch_bounds__(kTraceThreads, 16) wave_trace_kernel(const void* __restrict__ nodes,
-                                                                   const TriRecord* __restrict__ tris, int n_tris,
-                                                                   void* ws, long long slots) {
+// Persistent any-hit tracer with per-lane refill.  A lane holds one ray, the
+// four-wide node it visits next, a short stack of pending nodes and a queue of
+// leaf triangles whose boxes the ray hit (columns of shared-memory arrays);
+// every kTraceStepsPerRefill steps the warp refills the lanes that are idle
+// from the global slot counter.  A step visits one node per lane; triangle
+// tests are postponed and run as warp-wide rounds, one triangle per lane with
+// a non-empty queue, once kLeafBatch lanes hold one or a lane must drain its
+// queue (its nodes are done, or the queue cannot take another node's four
+// leaves), so most rounds run with many lanes converged instead of a few
+// lanes testing while the rest wait.  A ray whose pending nodes outgrow the
+// stack is decided by the stackless walk of the depth-first copy instead.
+__global__ void __launch_bounds__(kTraceThreads, kTraceBlocksPerSM) wave_trace_kernel(
+    const void* __restrict__ nodes, const TriRecord* __restrict__ tris, int n_tris, void* ws, long long slots) {
     pdl_prologue();
     WaveBuffers B = wave_buffers(ws, slots);
     const long long n_rays = (long long)*((volatile unsigned*)B.counter);
@@ -164,10 +172,15 @@ __global__ void __launch_bounds__(kTraceThreads, 16) wave_trace_kernel(const voi
     long long ray = -1;  // -1 idle, -2 no work left, >= 0 tracing
     int slot = 0;
     RayInv r;
-    int node = 0;
+    int node = 0, sp = 0, lq = 0;
+    bool overflow = false;
+    // one column per thread, so a warp's accesses fall in 32 different banks
+    __shared__ int s_stack[kWideStack * kTraceThreads];
+    __shared__ int s_leaf[kLeafQueue * kTraceThreads];
+    int* stack = s_stack + threadIdx.x;
+    int* leafq = s_leaf + threadIdx.x;
     if (n_tris <= 0) return;  // nothing can block a ray; gen already wrote misses
-    const ThreadedNode* tn = threaded_nodes(nodes, n_tris);
-    const int end = 2 * n_tris - 1;
+    const WideNode* wn = wide_nodes(nodes, n_tris);
     while (true) {
         const unsigned need = __ballot_sync(full, ray == -1);
         if (need) {
@@ -185,20 +198,36 @@ __global__ void __launch_bounds__(kTraceThreads, 16) wave_trace_kernel(const voi
                     r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
                     slot = __float_as_int(o.w);
                     node = 0;
+                    sp = 0;
+                    lq = 0;
+                    overflow = false;
                     ray = my;
                 }
             }
         }
         if (__all_sync(full, ray == -2)) break;
-        if (ray < 0) continue;
-        // up to kTraceStepsPerRefill node visits of this lane's ray; the node
-        // index strictly increases, so a ray ends within 2 n - 1 visits
+        // kTraceStepsPerRefill steps; every node is visited at most once, so a ray
+        // ends within n - 1 node visits and as many triangle rounds
         for (int step = 0; step < kTraceStepsPerRefill; ++step) {
-            node = threaded_step(tn, tris, r, node);
-            if (node < 0 || node >= end) {
-                if (node < 0) B.hit[slot] = 1;
+            const bool act = ray >= 0;
+            // a visit appends at most four leaves: a fuller queue waits for the rounds it forces
+            if (act && node >= 0 && lq <= kLeafQueue - 4)
+                node = wide_visit<kTraceThreads>(wn, r, node, stack, sp, overflow, leafq, lq);
+            const bool pend = act && lq > 0;
+            const bool must = pend && (node == kWideDone || lq > kLeafQueue - 4);
+            const unsigned vote = __ballot_sync(full, pend);
+            if (__popc(vote) >= kLeafBatch || __any_sync(full, must)) {
+                if (pend) {
+                    const int l = leafq[kTraceThreads * --lq];
+                    if (tri_hit(r, tris, ~l, nullptr, nullptr) < FLT_MAX) {
+                        B.hit[slot] = 1;
+                        ray = -1;
+                    }
+                }
+            }
+            if (ray >= 0 && node == kWideDone && lq == 0) {  // nodes done and no triangle left: a miss
+                if (overflow && any_hit_threaded(nodes, tris, n_tris, r)) B.hit[slot] = 1;
                 ray = -1;
-                break;
             }
         }
     }
@@ -244,8 +273,8 @@ __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, co
 }
 
 // Traversal statistics: the rays of the last forward pass re-traced one per
-// thread, with counters (stats[0] rays, [1] node visits = 32-byte node fetches
-// and slab tests, [2] triangle tests, [3] rays blocked, [4] rays whose result
+// thread, with counters (stats[0] rays, [1] node visits = 64-byte four-wide
+// node fetches, [2] triangle tests, [3] rays blocked, [4] rays whose result
 // differs from the forward's hit flag).  Warp sums, one 64-bit atomic each.
 __global__ void __launch_bounds__(kTraceThreads) wave_stats_kernel(const void* __restrict__ nodes,
                                                                    const TriRecord* __restrict__ tris, int n_tris,
@@ -255,23 +284,21 @@ __global__ void __launch_bounds__(kTraceThreads) wave_stats_kernel(const void* _
     WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
     const long long n_rays = (long long)B.counter[0];
     unsigned long long c[5] = {0, 0, 0, 0, 0};
-    const ThreadedNode* tn = threaded_nodes(nodes, n_tris > 0 ? n_tris : 1);
-    const int end = 2 * n_tris - 1;
+    const WideNode* wn = wide_nodes(nodes, n_tris > 0 ? n_tris : 1);
+    int stack[kWideStack];
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_rays;
          k += (long long)gridDim.x * blockDim.x) {
         const float4 o = B.ray_o[k], d = B.ray_d[k];
         const RayInv r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
         const int slot = __float_as_int(o.w);
-        bool blocked = false;
+        bool blocked = false, overflow = false;
         unsigned tests = 0;
-        for (int i = 0; i < end;) {
+        int node = 0, sp = 0;
+        for (int it = 0; it < 2 * n_tris && node >= 0; ++it) {
             ++c[1];
-            i = threaded_step<true>(tn, tris, r, i, &tests);
-            if (i < 0) {
-                blocked = true;
-                break;
-            }
+            node = wide_step<1, true>(wn, tris, r, node, stack, sp, overflow, &tests);
         }
+        blocked = node == kWideBlocked || (node >= 0 || overflow ? any_hit_threaded(nodes, tris, n_tris, r) : false);
         c[0] += 1;
         c[2] += tests;
         c[3] += blocked;

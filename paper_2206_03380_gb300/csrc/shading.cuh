@@ -101,8 +101,8 @@ __device__ __forceinline__ int threaded_step(const ThreadedNode* __restrict__ tn
 
 // any hit with t > 0 (shadow ray, no far limit): stackless traversal of the
 // depth-first layout, no ordering needed since any blocker ends the ray
-__device__ __forceinline__ bool any_hit(const void* nodes, const TriRecord* __restrict__ tris, int n_tris,
-                                        const RayInv& r) {
+__device__ __forceinline__ bool any_hit_threaded(const void* nodes, const TriRecord* __restrict__ tris, int n_tris,
+                                                 const RayInv& r) {
     if (n_tris <= 0) return false;
     const ThreadedNode* tn = threaded_nodes(nodes, n_tris);
     const int end = 2 * n_tris - 1;
@@ -111,6 +111,149 @@ __device__ __forceinline__ bool any_hit(const void* nodes, const TriRecord* __re
         if (i < 0) return true;
     }
     return false;
+}
+
+// ---------------------------------------------------------------- four-wide traversal
+constexpr int kWideStack = 24;          // pending nodes per ray; a deeper need falls back to the stackless walk
+constexpr int kWideBlocked = -1;        // wide_step: a triangle blocks the ray
+constexpr int kWideDone = -2;           // wide_step: nothing left to visit
+
+// byte k of w in the low mantissa bits of 2^23: the float 2^23 + q, exact
+__device__ __forceinline__ float qbyte(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + (uint32_t)k));
+}
+
+// Slab tests of the four child boxes of a four-wide node; bit k of the result
+// is set when the ray (t >= 0, no far limit) meets child k's box.  Per axis
+// the near plane is the low one for a non-negative direction, the high one
+// otherwise, so the plane at q needs no min / max:
+//   t = (o + q s - origin) / d = (2^23 + q) A + B',  A = s / d,  B' = (o - origin) / d - 2^23 A,
+// one fused multiply-add per plane (2^23 + q is the byte placed in a float's
+// mantissa).  Rounding B' costs at most half a step of t, the other roundings
+// far less for origins inside the scene's bounds; the boxes are widened by a
+// whole step on every side, so a ray that meets a child's box passes its test.
+__device__ __forceinline__ unsigned wide_child_hits(const RayInv& r, float4 a, float4 b, float4 c) {
+    const uint32_t lox = __float_as_uint(b.z), loy = __float_as_uint(b.w), loz = __float_as_uint(c.x);
+    const uint32_t hix = __float_as_uint(c.y), hiy = __float_as_uint(c.z), hiz = __float_as_uint(c.w);
+    const bool px = r.inv.x >= 0.0f, py = r.inv.y >= 0.0f, pz = r.inv.z >= 0.0f;
+    const uint32_t nx = px ? lox : hix, fx = px ? hix : lox;
+    const uint32_t ny = py ? loy : hiy, fy = py ? hiy : loy;
+    const uint32_t nz = pz ? loz : hiz, fz = pz ? hiz : loz;
+    const float ax = a.w * r.inv.x, ay = b.x * r.inv.y, az = b.y * r.inv.z;
+    const float bx = fmaf(-8388608.0f, ax, (a.x - r.o.x) * r.inv.x);
+    const float by = fmaf(-8388608.0f, ay, (a.y - r.o.y) * r.inv.y);
+    const float bz = fmaf(-8388608.0f, az, (a.z - r.o.z) * r.inv.z);
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float t0 = fmaxf(fmaxf(fmaf(qbyte(nx, k), ax, bx), fmaf(qbyte(ny, k), ay, by)),
+                               fmaxf(fmaf(qbyte(nz, k), az, bz), 0.0f));
+        const float t1 = fminf(fminf(fmaf(qbyte(fx, k), ax, bx), fmaf(qbyte(fy, k), ay, by)), fmaf(qbyte(fz, k), az, bz));
+        m |= (t0 <= t1 ? 1u : 0u) << k;
+    }
+    return m;
+}
+
+// One node of the four-wide any-hit traversal: tests the node's children,
+// tests the triangles of hit leaf children at once, continues with the first
+// hit inner child and pushes the others.  Returns the next node, kWideBlocked
+// or kWideDone.  Stack entry i lives at stack[i * kStride] (a thread's column
+// of a shared-memory array, or a local array); a push beyond kWideStack sets
+// *overflow instead (the caller then decides the ray by the stackless walk);
+// kCount adds the triangle tests made to *tri_tests.
+template <int kStride = 1, bool kCount = false>
+__device__ __forceinline__ int wide_step(const WideNode* __restrict__ wn, const TriRecord* __restrict__ tris,
+                                         const RayInv& r, int node, int* stack, int& sp, bool& overflow,
+                                         unsigned* tri_tests = nullptr) {
+    float4 a, b, c;
+    int4 d;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(wn + node));
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w), "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w)
+        : "l"(reinterpret_cast<const char*>(wn + node) + 32));
+    const unsigned m = wide_child_hits(r, a, b, c);
+    unsigned leaves = 0;
+    int next = kWideDone;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int l = k == 0 ? d.x : k == 1 ? d.y : k == 2 ? d.z : d.w;
+        if (!((m >> k) & 1u)) continue;
+        if (l < 0) {
+            leaves |= 1u << k;
+        } else if (next == kWideDone) {
+            next = l;
+        } else if (sp < kWideStack) {
+            stack[kStride * sp++] = l;
+        } else {
+            overflow = true;
+        }
+    }
+    while (leaves) {
+        const int k = __ffs(leaves) - 1;
+        leaves &= leaves - 1;
+        const int l = k == 0 ? d.x : k == 1 ? d.y : k == 2 ? d.z : d.w;
+        if (kCount) ++*tri_tests;
+        if (tri_hit(r, tris, ~l, nullptr, nullptr) < FLT_MAX) return kWideBlocked;
+    }
+    if (next == kWideDone && sp > 0) next = stack[kStride * --sp];
+    return next;
+}
+
+// The node part of wide_step for a traversal that postpones its triangle
+// tests: hit leaf children are appended to the lane's leaf queue
+// (leafq[i * kStride], lq entries; the caller keeps room for four) instead of
+// being tested.  Returns the next node or kWideDone.
+template <int kStride>
+__device__ __forceinline__ int wide_visit(const WideNode* __restrict__ wn, const RayInv& r, int node, int* stack,
+                                          int& sp, bool& overflow, int* leafq, int& lq) {
+    float4 a, b, c;
+    int4 d;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(wn + node));
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w), "=r"(d.x), "=r"(d.y), "=r"(d.z), "=r"(d.w)
+        : "l"(reinterpret_cast<const char*>(wn + node) + 32));
+    const unsigned m = wide_child_hits(r, a, b, c);
+    int next = kWideDone;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int l = k == 0 ? d.x : k == 1 ? d.y : k == 2 ? d.z : d.w;
+        if (!((m >> k) & 1u)) continue;
+        if (l < 0) {
+            leafq[kStride * lq++] = l;
+        } else if (next == kWideDone) {
+            next = l;
+        } else if (sp < kWideStack) {
+            stack[kStride * sp++] = l;
+        } else {
+            overflow = true;
+        }
+    }
+    if (next == kWideDone && sp > 0) next = stack[kStride * --sp];
+    return next;
+}
+
+// any hit with t > 0 (shadow ray, no far limit) over the four-wide nodes
+// (at most 2 n - 1 node visits: each node is pushed at most once)
+__device__ __forceinline__ bool any_hit(const void* nodes, const TriRecord* __restrict__ tris, int n_tris,
+                                        const RayInv& r) {
+    if (n_tris <= 0) return false;
+    const WideNode* wn = wide_nodes(nodes, n_tris);
+    int stack[kWideStack];
+    int sp = 0, node = 0;
+    bool overflow = false, done = false;
+    for (int it = 0; it < 2 * n_tris; ++it) {
+        node = wide_step(wn, tris, r, node, stack, sp, overflow);
+        if (node == kWideBlocked) return true;
+        if (node == kWideDone) {
+            done = true;
+            break;
+        }
+    }
+    return (overflow || !done) ? any_hit_threaded(nodes, tris, n_tris, r) : false;
 }
 
 // closest hit; returns the leaf (triangle record) index or -1

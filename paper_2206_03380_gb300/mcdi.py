@@ -167,11 +167,15 @@ def bvh_sizes(n_tris: int):
     return a.value, b.value, c.value
 
 
-def tracer_structure_bytes(n_tris: int) -> int:
-    """Bytes of the structure a shadow ray walks: the depth-first nodes (2 n - 1 of 32 B) and the
-    triangle records (n of 48 B)."""
-    n = max(int(n_tris), 1)
-    return (2 * n - 1) * 32 + n * 48
+def tracer_structure_bytes(bvh: "Bvh") -> int:
+    """Bytes of the structure a shadow ray walks in a built BVH: its four-wide nodes (64 B each;
+    the slots of odd-depth nodes are zero and unused) and the triangle records (48 B each).  A
+    measurement aid: reads the node array back to count the nodes in use."""
+    n = max(int(bvh.n_tris), 1)
+    r256 = lambda x: (x + 255) // 256 * 256
+    off = r256(r256(max(n - 1, 1) * 64) + (2 * n - 1) * 32)
+    scale_x = bvh.nodes[off: off + max(n - 1, 1) * 64].view(torch.float32).reshape(-1, 16)[:, 3]
+    return int((scale_x != 0).sum().item()) * 64 + n * 48
 
 
 def build_bvh(verts, tris, nodes, tri_records, scratch, stream=None):

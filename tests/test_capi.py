@@ -55,7 +55,9 @@ def test_argument_checks_without_gpu(lib):
     assert lib.mcdi_bvh_sizes(0, C.byref(a), C.byref(b), C.byref(s)) == mcdi.INVALID_ARG
     assert lib.mcdi_bvh_sizes(1000, C.byref(a), C.byref(b), C.byref(s)) == mcdi.OK
     # 999 two-child nodes of 64 B (256-aligned), then 1999 depth-first nodes of 32 B
-    assert a.value == (999 * 64 + 255) // 256 * 256 + 1999 * 32 and b.value == 1000 * 48 and s.value > 0
+    # two-child nodes, depth-first copy, four-wide nodes, each at a 256-byte aligned offset
+    r256 = lambda x: (x + 255) // 256 * 256
+    assert a.value == r256(r256(999 * 64) + 1999 * 32) + 999 * 64 and b.value == 1000 * 48 and s.value > 0
     # scratch smaller than the query -> rejected before any launch
     assert lib.mcdi_build_bvh(C.c_void_p(256), 3, C.c_void_p(256), 1000, C.c_void_p(256), C.c_void_p(256),
                               C.c_void_p(256), s.value - 1, None) == mcdi.INVALID_ARG

@@ -30,9 +30,9 @@ def _threaded(mcdi, bvh):
     nodes = bvh.nodes.cpu().numpy()
     recs = bvh.tri_records.cpu().numpy()[: n * 48].view(np.float32).reshape(n, 12)
     orig = recs[:, 3].copy().view(np.int32)
-    nb, _, _ = mcdi.bvh_sizes(n)
     m = 2 * n - 1
-    tn = nodes[nb - m * 32: nb].view(np.float32).reshape(m, 8)
+    off = (max(n - 1, 1) * 64 + 255) // 256 * 256  # after the two-child nodes
+    tn = nodes[off: off + m * 32].view(np.float32).reshape(m, 8)
     lo, hi = tn[:, 0:3], tn[:, 4:7]
     skip = tn[:, 3].copy().view(np.int32)
     rec = tn[:, 7].copy().view(np.int32)

@@ -156,6 +156,70 @@ def test_bvh_depth_first_escape_links(cuda_lib, scene):
     np.testing.assert_array_equal(np.sort(tri[tri >= 0]), np.arange(n))
 
 
+def decode_wide(raw, n):
+    """The four-wide nodes of a node buffer: {index: (o, s, qlo (4, 3), qhi (4, 3), links (4,))}."""
+    r256 = lambda x: (x + 255) // 256 * 256
+    off = r256(r256(max(n - 1, 1) * 64) + (2 * n - 1) * 32)
+    w = raw[off: off + max(n - 1, 1) * 64].reshape(-1, 64)
+    f = w.view(np.float32).reshape(-1, 16)
+    q = w[:, 24:48].reshape(-1, 6, 4)  # qlo x, y, z, qhi x, y, z; byte k = child k
+    links = w[:, 48:64].view(np.int32).reshape(-1, 4)
+    o = f[:, 0:3].astype(np.float64)
+    sc = np.stack([f[:, 3], f[:, 4], f[:, 5]], 1).astype(np.float64)
+    qlo = q[:, 0:3].transpose(0, 2, 1).astype(np.float64)
+    qhi = q[:, 3:6].transpose(0, 2, 1).astype(np.float64)
+    return o, sc, qlo, qhi, links
+
+
+@pytest.mark.parametrize("which", ["parity", "one_triangle"])
+def test_bvh_four_wide_nodes(cuda_lib, scene, which):
+    """The four-wide nodes shadow rays traverse: from the root every triangle is
+    reached exactly once, every decoded child box holds its subtree's triangles with
+    at least one quantisation step to spare on every side, empty slots are inverted
+    boxes, and slots of nodes at odd depth are zero."""
+    if which == "parity":
+        sc = scene
+    else:
+        sc = scenes.Scene(**{**scene.__dict__, "verts": np.array([[0, 0, 0], [1, 0.2, 0], [0.3, 1, 0.5]], np.float32),
+                             "vnrm": np.array([[0, 0, 1]] * 3, np.float32), "tris": np.array([[0, 1, 2]], np.int32)})
+    pipe = make_pipe(sc)
+    pipe.build_bvh()
+    n = sc.tris.shape[0]
+    raw = to_np(pipe.bvh.nodes)
+    recs = to_np(pipe.bvh.tri_records).view(np.float32)[: n * 12].reshape(-1, 12).astype(np.float64)
+    tri_lo = np.minimum(recs[:, 0:3], np.minimum(recs[:, 0:3] + recs[:, 4:7], recs[:, 0:3] + recs[:, 8:11]))
+    tri_hi = np.maximum(recs[:, 0:3], np.maximum(recs[:, 0:3] + recs[:, 4:7], recs[:, 0:3] + recs[:, 8:11]))
+    o, sc_, qlo, qhi, links = decode_wide(raw, n)
+    seen = np.zeros(n, int)
+    visited = set()
+
+    def subtree_box(link):
+        if link < 0:
+            seen[~link] += 1
+            return tri_lo[~link], tri_hi[~link]
+        assert link not in visited
+        visited.add(link)
+        lo, hi = np.full(3, np.inf), np.full(3, -np.inf)
+        for k in range(4):
+            c = int(links[link, k])
+            if c == np.iinfo(np.int32).min:
+                assert np.all(qlo[link, k] == 255) and np.all(qhi[link, k] == 0)
+                continue
+            blo, bhi = subtree_box(c)
+            dlo = o[link] + qlo[link, k] * sc_[link]
+            dhi = o[link] + qhi[link, k] * sc_[link]
+            assert np.all(dlo <= blo - sc_[link] * (1 - 1e-6)) and np.all(dhi >= bhi + sc_[link] * (1 - 1e-6))
+            lo, hi = np.minimum(lo, blo), np.maximum(hi, bhi)
+        return lo, hi
+
+    subtree_box(0)
+    np.testing.assert_array_equal(seen, np.ones(n, int))
+    unused = sorted(set(range(max(n - 1, 1))) - visited)
+    woff = ((max(n - 1, 1) * 64 + 255) // 256 * 256 + (2 * n - 1) * 32 + 255) // 256 * 256
+    assert np.all(raw[woff: woff + max(n - 1, 1) * 64].reshape(-1, 64)[unused] == 0)
+    assert np.all(np.log2(sc_[sorted(visited)]) == np.round(np.log2(sc_[sorted(visited)])))  # powers of two
+
+
 # ------------------------------------------------------------------ G-buffer
 @pytest.mark.parametrize("raster", [True, False])
 def test_primary_cast_matches_oracle(cuda_lib, orc, scene, oracle_gb, raster):

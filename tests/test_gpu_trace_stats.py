@@ -59,7 +59,7 @@ def test_stats_match_forward_and_oracle(cuda_lib, orc):
     assert abs(rays - n_act) <= max(2, n_marg), (rays, n_act, n_marg)
     n = sc.tris.shape[0]
     assert rays <= visits <= rays * (2 * n - 1)
-    assert blocked <= tests <= visits
+    assert blocked <= tests <= 4 * visits  # up to four leaf children per four-wide node
     # the tracer alone, again over the same rays: the flags it sets agree with the forward's
     c_d0 = pipe.c_d.clone()
     cuda_lib.shadow_ray_retrace(pipe.bvh, pipe.N, pipe.H, pipe.W, pipe.params, pipe.workspace)
