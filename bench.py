@@ -459,12 +459,13 @@ def time_bilateral(pipe, flush, stream, steps, sigma=2.0):
 
 
 # per-visit FP32 operations of the traversal, counted from the source: a visit of
-# a four-wide node is 3 subtracts + 6 multiplies of set-up and per child 6 adds
-# (byte to float) + 6 fused multiply-adds + 5 min/max + 1 compare (81 in all); a
+# a four-wide node is 3 subtracts + 6 multiplies + 3 fused multiply-adds of
+# set-up and per child 6 fused multiply-adds + 3 min/max (two of three operands)
+# + 1 compare (52 in all; the byte-to-float moves are integer permutes); a
 # two-sided Moller-Trumbore test that runs to the end is 2 cross products (9 ops
 # each), 4 dot products (5 each), 1 reciprocal, 3 subtracts, 3 multiplies,
 # 1 add and 6 compares (early outs make it shorter: an upper bound)
-NODE_OPS, TRI_OPS = 81, 52
+NODE_OPS, TRI_OPS = 52, 52
 NODE_BYTES, TRI_BYTES, RAY_BYTES = 64, 48, 32
 
 
@@ -708,7 +709,7 @@ def oracle_step(orc, sc, pix, tables=None):
     cam = np.tile(sc.cams[0, :3].astype(np.float64), (len(p), 1))
     ctr = np.stack([p, np.zeros(len(p))], 1).astype(np.uint32)
     out, vis, recs = orc.shade_fwd(sc.verts, sc.tris, sc.env, c32, m32, tot, rows, cam, ctr, n_light=sc.n_light,
-                                   n_cos=sc.n_cos, n_ggx=sc.n_ggx, seed=sc.seed)
+                                   n_cos=sc.n_cos, n_ggx=sc.n_ggx, seed=sc.seed, tau=1.0)
     g = np.ones((len(p), 9))
     orc.frozen_adjoint(recs, orc.param_rows(rows), cam, out[:, 9].astype(np.int32),
                        sc.env[..., :3].reshape(-1, 3).astype(np.float64), g)

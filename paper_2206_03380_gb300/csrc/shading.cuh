@@ -118,6 +118,18 @@ constexpr int kWideStack = 24;          // pending nodes per ray; a deeper need 
 constexpr int kWideBlocked = -1;        // wide_step: a triangle blocks the ray
 constexpr int kWideDone = -2;           // wide_step: nothing left to visit
 
+// three-operand minimum / maximum (one instruction on sm_100 and later)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // byte k of w in the low mantissa bits of 2^23: the float 2^23 + q, exact
 __device__ __forceinline__ float qbyte(uint32_t w, int k) {
     return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + (uint32_t)k));
@@ -146,9 +158,9 @@ __device__ __forceinline__ unsigned wide_child_hits(const RayInv& r, float4 a, f
     unsigned m = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float t0 = fmaxf(fmaxf(fmaf(qbyte(nx, k), ax, bx), fmaf(qbyte(ny, k), ay, by)),
+        const float t0 = fmax3(fmaf(qbyte(nx, k), ax, bx), fmaf(qbyte(ny, k), ay, by),
                                fmaxf(fmaf(qbyte(nz, k), az, bz), 0.0f));
-        const float t1 = fminf(fminf(fmaf(qbyte(fx, k), ax, bx), fmaf(qbyte(fy, k), ay, by)), fmaf(qbyte(fz, k), az, bz));
+        const float t1 = fmin3(fmaf(qbyte(fx, k), ax, bx), fmaf(qbyte(fy, k), ay, by), fmaf(qbyte(fz, k), az, bz));
         m |= (t0 <= t1 ? 1u : 0u) << k;
     }
     return m;

@@ -547,7 +547,8 @@ class GBuffer:
         return cls(*[torch.empty(N, H, W, 4, device=device) for _ in range(4)])
 
 
-def make_params(n_light, n_cos, n_ggx, seed, tau=0.0, ray_eps=1e-4, decorrelate_bwd=False) -> ShadeParams:
+def make_params(n_light, n_cos, n_ggx, seed, tau=1.0, ray_eps=1e-4, decorrelate_bwd=False) -> ShadeParams:
+    """Shading parameters; tau = 1 is binary visibility, where the paper's leakage ramp ends (App. A)."""
     return ShadeParams(int(n_light), int(n_cos), int(n_ggx), int(bool(decorrelate_bwd)), int(seed), float(tau),
                        float(ray_eps))
 

@@ -18,7 +18,7 @@ from .scenes import Scene
 
 
 class ShadingPipeline:
-    def __init__(self, scene: Scene, device="cuda", tau: float = 0.0, ray_eps: float = 1e-4,
+    def __init__(self, scene: Scene, device="cuda", tau: float = 1.0, ray_eps: float = 1e-4,
                  decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True,
                  denoiser_params=None, denoiser_precision=0, bilateral_sigma=None, raster: bool = True):
         mcdi.load()

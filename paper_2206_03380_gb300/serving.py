@@ -49,7 +49,7 @@ class _InFlight:
 
 class ServingEngine:
     def __init__(self, scene_list, probe_list, denoiser_params, n_slots: int = 4, hbm_budget: int = 8 << 30,
-                 device="cuda", tau: float = 0.0):
+                 device="cuda", tau: float = 1.0):
         mcdi.load()
         self.dev = torch.device(device)
         dev = self.dev

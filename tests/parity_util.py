@@ -24,7 +24,7 @@ def rel_err(g, o, floor):
     return np.abs(g - o) / np.maximum(np.abs(o), floor)
 
 
-def oracle_shade(orc, scene, gb_rows, pix, view, tau=0.0, ray_eps=1e-4, stream=0, margin=True):
+def oracle_shade(orc, scene, gb_rows, pix, view, tau=1.0, ray_eps=1e-4, stream=0, margin=True):
     c32, m32, tot = oracle_tables(orc, scene.env)
     cam = np.tile(scene.cams[view, :3].astype(np.float64), (len(pix), 1))
     ctr = np.stack([pix, np.full(len(pix), view)], axis=1).astype(np.uint32)

@@ -253,7 +253,7 @@ def run_fwd(pipe, gb_rows):
     return out.reshape(-1, 9), to_np(pipe.mask).reshape(pipe.N * pipe.H * pipe.W, -1)
 
 
-def check_forward(orc, scene, gpu_out, gpu_mask, gb_rows, pix, view, tau=0.0, flips=None):
+def check_forward(orc, scene, gpu_out, gpu_mask, gb_rows, pix, view, tau=1.0, flips=None):
     o_out, o_vis, recs = PU.oracle_shade(orc, scene, gb_rows, pix, view, tau=tau)
     cov = gb_rows[:, 3] > 0
     np.testing.assert_allclose(gpu_out[:, 3:6], o_out[:, 3:6], rtol=1e-6, atol=1e-7)
