@@ -509,9 +509,9 @@ def poisson_requests(n: int, rate: float, n_scenes: int, n_probes: int, seed: in
     return out
 
 
-def serving_scenes(n_scenes: int = 16, grids=(64, 128, 192, 256), seed: int = BASE_SEED + 5, tex: int = 512):
+def serving_scenes(n_scenes: int = 16, grids=(64, 128, 192, 300), seed: int = BASE_SEED + 5, tex: int = 512):
     """Resident scene set: meshes of the sphere-union family on several grid sizes
-    (about 50k to 780k triangles), each scene with its own textures and 200 orbit
+    (about 50k to 1M triangles), each scene with its own textures and 200 orbit
     cameras."""
     rng = np.random.default_rng(seed)
     meshes = [sdf_spheres_mesh(g, 32, np.random.default_rng(seed + g)) for g in grids]

@@ -1,7 +1,8 @@
 """The serving loop: requests of uneven resolution and spp against resident
 scenes, continuous batching over several streams vs one at a time; every
 request's image is bitwise the same alone and in the mix (per-request Philox
-seeds, deterministic kernels), and admission respects the HBM budget."""
+seeds, deterministic kernels, the same captured denoiser graph whichever slot
+runs it), and admission respects the HBM budget."""
 import numpy as np
 import pytest
 import torch
@@ -18,7 +19,7 @@ def engine(cuda_lib):
     sc = scenes.serving_scenes(n_scenes=4, grids=(32, 48), tex=64)
     pr = scenes.serving_probes(n_probes=3)
     den = cuda_lib.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3))
-    return ServingEngine(sc, pr, den, n_slots=3, hbm_budget=2 << 30)
+    return ServingEngine(sc, pr, den, n_slots=3, hbm_budget=2 << 30, sides=range(64, 193, 32), max_spp=16)
 
 
 def test_continuous_batching_matches_alone_and_serial(engine):
@@ -26,12 +27,14 @@ def test_continuous_batching_matches_alone_and_serial(engine):
                                    n_views=200)
     ids = [r.rid for r in reqs]
     mix = engine.run(reqs, mode="continuous", keep=ids)
+    lanes = engine.run(reqs, mode="continuous", keep=ids, lanes=(64 * 64 * 8,))
     ser = engine.run(reqs, mode="serial", keep=ids)
-    assert mix["n"] == ser["n"] == len(reqs)
+    assert mix["n"] == ser["n"] == lanes["n"] == len(reqs)
     for r in reqs:
         alone = engine.render_one(r)
         assert np.isfinite(alone).all()
         np.testing.assert_array_equal(mix["images"][r.rid], alone)
+        np.testing.assert_array_equal(lanes["images"][r.rid], alone)
         np.testing.assert_array_equal(ser["images"][r.rid], alone)
     assert mix["p99_ms"] >= mix["p50_ms"] > 0
     # images are not trivial: lit, covered pixels exist
