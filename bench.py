@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd MC shading Msamples/s & %HBM roofline at 512² 16spp"
 # DRAM bytes (read + write) per launch at the headline size, from one ncu capture of the kernel as it
 # stands (profiles/); an entry is removed when its kernels change.
-MEASURED_TRAFFIC = {"wave_trace_kernel": 62.79e6, "shade_fwd": 199.3e6, "shade_bwd": 24.9e6}
+MEASURED_TRAFFIC = {"wave_trace_kernel": 41.83e6, "shade_fwd": 157.3e6, "shade_bwd": 24.9e6}
 UNIT = "Msamples/s"
 L2_FLUSH_BYTES = 512 << 20
 # serving: requests of fewer than 2M samples in one lane, the rest in another (measured against 1M - 3M
@@ -486,10 +486,11 @@ def alu_peak_gops():
 
 def shadow_ray_figures(pipe, flush, stream, steps, samples):
     """The shadow-ray tracer of the forward pass timed alone (CUDA events, L2
-    flushed before each launch) and its counters: node visits and triangle
-    tests per ray, the bytes it requests from the memory system (32-byte ray
-    record, 32-byte nodes, 48-byte triangle records, one flag byte per blocked
-    ray) against a measured L2 read bandwidth, and FP32 operations per sample."""
+    flushed before each launch) and its counters: node visits (64-byte four-wide
+    nodes) and triangle tests per ray, the bytes it requests from the memory
+    system (16-byte ray record and its pixel's 16-byte origin, 64-byte nodes,
+    48-byte triangle records, one flag byte per blocked ray) against a measured
+    L2 read bandwidth, and FP32 operations per sample."""
     import torch
 
     from paper_2206_03380_gb300 import mcdi

@@ -27,26 +27,33 @@ constexpr int kLeafQueue = 8;   // postponed triangle tests per lane
 constexpr int kLeafBatch = 16;  // lanes holding one that start a triangle round
 
 struct WaveBuffers {
-    float4* ray_o;      // [rays] origin, w = slot index (int bits) of the sample
-    float4* ray_d;      // [rays] direction
+    float4* ray;        // [rays] direction, w = slot index (int bits) of the sample
+    float4* origin;     // [P] shadow-ray origin of each covered pixel (p + ray_eps n)
     float* contrib;     // [6][slots] c_d rgb, c_s rgb without visibility
     uint8_t* hit;       // [slots] 1 = shadow ray blocked
     unsigned* counter;  // [0] rays appended by gen, [1] trace work queue head
 };
 
-__device__ __forceinline__ WaveBuffers wave_buffers(void* ws, long long slots) {
+// byte offsets of the arrays (P pixels, slots = P spp), 256-byte aligned
+__host__ __device__ __forceinline__ size_t wave_origin_offset(long long slots) { return align256((size_t)slots * 16); }
+__host__ __device__ __forceinline__ size_t wave_contrib_offset(long long P, long long slots) {
+    return wave_origin_offset(slots) + align256((size_t)P * 16);
+}
+__host__ __device__ __forceinline__ size_t wave_hit_offset(long long P, long long slots) {
+    return wave_contrib_offset(P, slots) + align256((size_t)slots * 24);
+}
+__host__ __device__ __forceinline__ size_t wave_counter_offset(long long P, long long slots) {
+    return wave_hit_offset(P, slots) + align256((size_t)slots);
+}
+
+__device__ __forceinline__ WaveBuffers wave_buffers(void* ws, long long P, long long slots) {
     char* p = static_cast<char*>(ws);
     WaveBuffers b;
-    size_t o = 0;
-    b.ray_o = reinterpret_cast<float4*>(p + o);
-    o += align256((size_t)slots * 16);
-    b.ray_d = reinterpret_cast<float4*>(p + o);
-    o += align256((size_t)slots * 16);
-    b.contrib = reinterpret_cast<float*>(p + o);
-    o += align256((size_t)slots * 24);
-    b.hit = reinterpret_cast<uint8_t*>(p + o);
-    o += align256((size_t)slots);
-    b.counter = reinterpret_cast<unsigned*>(p + o);
+    b.ray = reinterpret_cast<float4*>(p);
+    b.origin = reinterpret_cast<float4*>(p + wave_origin_offset(slots));
+    b.contrib = reinterpret_cast<float*>(p + wave_contrib_offset(P, slots));
+    b.hit = reinterpret_cast<uint8_t*>(p + wave_hit_offset(P, slots));
+    b.counter = reinterpret_cast<unsigned*>(p + wave_counter_offset(P, slots));
     return b;
 }
 
@@ -61,9 +68,9 @@ __device__ __forceinline__ Probe wave_probe(const ShadeArgs& a) {
     return P;
 }
 
-__global__ void wave_reset_kernel(void* ws, long long slots) {
+__global__ void wave_reset_kernel(void* ws, long long P, long long slots) {
     pdl_prologue();
-    WaveBuffers B = wave_buffers(ws, slots);
+    WaveBuffers B = wave_buffers(ws, P, slots);
     B.counter[0] = 0u;
     B.counter[1] = 0u;
 }
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const long long slots = P * spp;
-    WaveBuffers B = wave_buffers(ws, slots);
+    WaveBuffers B = wave_buffers(ws, P, slots);
     const bool in_range = idx0 < P;
     const long long idx = in_range ? idx0 : P - 1;  // out-of-range lanes idle but join the warp votes
     const int view = (int)(idx / ((long long)a.H * a.W));
@@ -103,6 +110,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
     Probe Pr = wave_probe(a);
     stage_marginal(Pr, s_marg);
     const f3 origin = covered ? px.p + px.n * a.ray_eps : mk(0.f, 0.f, 0.f);
+    if (covered && quarter == 0) B.origin[idx] = make_float4(origin.x, origin.y, origin.z, 0.0f);
     for (int j = quarter; j < spp; j += kGenQuarters) {
         const long long s = (long long)j * P + idx;
         f3 wi = mk(0.f, 0.f, 0.f), cd = wi, cs = wi;
@@ -135,8 +143,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
             base = __shfl_sync(0xffffffffu, base, leader);
             if (active) {
                 const unsigned r = base + __popc(act & ((1u << lane) - 1u));
-                B.ray_o[r] = make_float4(origin.x, origin.y, origin.z, __int_as_float((int)s));
-                B.ray_d[r] = make_float4(wi.x, wi.y, wi.z, 0.0f);
+                B.ray[r] = make_float4(wi.x, wi.y, wi.z, __int_as_float((int)s));
             }
         }
         if (!covered) continue;  // the accumulation skips the slots of uncovered pixels
@@ -162,9 +169,10 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
 // lanes testing while the rest wait.  A ray whose pending nodes outgrow the
 // stack is decided by the stackless walk of the depth-first copy instead.
 __global__ void __launch_bounds__(kTraceThreads, kTraceBlocksPerSM) wave_trace_kernel(
-    const void* __restrict__ nodes, const TriRecord* __restrict__ tris, int n_tris, void* ws, long long slots) {
+    const void* __restrict__ nodes, const TriRecord* __restrict__ tris, int n_tris, void* ws, long long P,
+    long long slots) {
     pdl_prologue();
-    WaveBuffers B = wave_buffers(ws, slots);
+    WaveBuffers B = wave_buffers(ws, P, slots);
     const long long n_rays = (long long)*((volatile unsigned*)B.counter);
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -193,10 +201,10 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceBlocksPerSM) wave_trace_k
                 if (my >= n_rays) {
                     ray = -2;
                 } else {
-                    const float4 o = __ldg(B.ray_o + my);
-                    const float4 d = __ldg(B.ray_d + my);
+                    const float4 d = __ldg(B.ray + my);
+                    slot = __float_as_int(d.w);
+                    const float4 o = __ldg(B.origin + (uint32_t)slot % (uint32_t)P);  // slots < 2^31
                     r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
-                    slot = __float_as_int(o.w);
                     node = 0;
                     sp = 0;
                     lq = 0;
@@ -243,7 +251,7 @@ __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, co
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int nwords = (spp + 31) >> 5;
     const long long slots = P * spp;
-    WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
+    WaveBuffers B = wave_buffers(const_cast<void*>(ws), P, slots);
     // the same coverage test as the generator, which wrote no slots for uncovered pixels
     const float4 pos = a.gb_pos[idx], nrm = a.gb_nrm[idx];
     if (!(pos.w > 0.0f) || !(dot(xyz(nrm), xyz(nrm)) > 0.0f)) {
@@ -278,19 +286,20 @@ __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, co
 // differs from the forward's hit flag).  Warp sums, one 64-bit atomic each.
 __global__ void __launch_bounds__(kTraceThreads) wave_stats_kernel(const void* __restrict__ nodes,
                                                                    const TriRecord* __restrict__ tris, int n_tris,
-                                                                   const void* ws, long long slots,
+                                                                   const void* ws, long long P, long long slots,
                                                                    unsigned long long* __restrict__ stats) {
     pdl_prologue();
-    WaveBuffers B = wave_buffers(const_cast<void*>(ws), slots);
+    WaveBuffers B = wave_buffers(const_cast<void*>(ws), P, slots);
     const long long n_rays = (long long)B.counter[0];
     unsigned long long c[5] = {0, 0, 0, 0, 0};
     const WideNode* wn = wide_nodes(nodes, n_tris > 0 ? n_tris : 1);
     int stack[kWideStack];
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_rays;
          k += (long long)gridDim.x * blockDim.x) {
-        const float4 o = B.ray_o[k], d = B.ray_d[k];
+        const float4 d = B.ray[k];
+        const int slot = __float_as_int(d.w);
+        const float4 o = B.origin[(uint32_t)slot % (uint32_t)P];
         const RayInv r = make_ray(mk(o.x, o.y, o.z), mk(d.x, d.y, d.z));
-        const int slot = __float_as_int(o.w);
         bool blocked = false, overflow = false;
         unsigned tests = 0;
         int node = 0, sp = 0;
@@ -314,28 +323,23 @@ __global__ void __launch_bounds__(kTraceThreads) wave_stats_kernel(const void* _
 
 }  // namespace
 
-// byte offset of the ray counters in the forward workspace
-static size_t wave_counter_offset(long long slots) {
-    return align256((size_t)slots * 16) * 2 + align256((size_t)slots * 24) + align256((size_t)slots);
-}
-
 cudaError_t launch_shadow_ray_stats(const ShadeArgs& a, const void* ws, unsigned long long* stats,
                                     cudaStream_t stream) {
-    const long long slots = (long long)a.N * a.H * a.W * (a.n_light + a.n_cos + a.n_ggx);
+    const long long P = (long long)a.N * a.H * a.W, slots = P * (a.n_light + a.n_cos + a.n_ggx);
     cudaError_t e = cudaMemsetAsync(stats, 0, 5 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     launch_k(wave_stats_kernel, sms * 8, kTraceThreads, 0, stream, a.nodes, static_cast<const TriRecord*>(a.tris),
-             a.n_tris, ws, slots, stats);
+             a.n_tris, ws, P, slots, stats);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t stream) {
-    const long long slots = (long long)a.N * a.H * a.W * (a.n_light + a.n_cos + a.n_ggx);
+    const long long P = (long long)a.N * a.H * a.W, slots = P * (a.n_light + a.n_cos + a.n_ggx);
     // rewind the work queue head; the rays, and the hit flags they set again, stay as they are
-    cudaError_t e = cudaMemsetAsync(static_cast<char*>(ws) + wave_counter_offset(slots) + sizeof(unsigned), 0,
+    cudaError_t e = cudaMemsetAsync(static_cast<char*>(ws) + wave_counter_offset(P, slots) + sizeof(unsigned), 0,
                                     sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152, per_sm = 8;
@@ -344,12 +348,12 @@ cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
     if (per_sm < 1) per_sm = 1;
     launch_k(wave_trace_kernel, sms * per_sm, kTraceThreads, 0, stream, a.nodes, static_cast<const TriRecord*>(a.tris),
-             a.n_tris, ws, slots);
+             a.n_tris, ws, P, slots);
     return cudaGetLastError();
 }
 
 size_t shade_workspace_bytes(long long P, int spp) {
-    return wave_counter_offset(P * spp) + 256;
+    return wave_counter_offset(P, P * spp) + 256;
 }
 
 cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
@@ -357,7 +361,7 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
-    launch_k(wave_reset_kernel, 1, 1, 0, stream, ws, P * spp);
+    launch_k(wave_reset_kernel, 1, 1, 0, stream, ws, P, P * spp);
     launch_k(wave_gen_kernel, (int)((P + 31) / 32), kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream, a, ws,
              kd_out);
     int dev = 0, sms = 152, per_sm = 8;
@@ -366,7 +370,7 @@ cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_ou
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wave_trace_kernel, kTraceThreads, 0);
     if (per_sm < 1) per_sm = 1;
     launch_k(wave_trace_kernel, sms * per_sm, kTraceThreads, 0, stream, a.nodes, static_cast<const TriRecord*>(a.tris),
-             a.n_tris, ws, P * spp);
+             a.n_tris, ws, P, P * spp);
     launch_k(wave_accum_kernel, gblocks, kGenThreads, 0, stream, a, ws, c_d, c_s, vis_mask);
     return cudaGetLastError();
 }
