@@ -356,10 +356,26 @@ MCDI_API mcdi_status mcdi_read_sweep(const void* buf, size_t bytes, int passes, 
  * float4 (image i uses guide i % n_aux) -> y [n_img][H][W] float4 (rgb, w=0);
  * acts (act_bytes) receives the activations the backward needs.
  * mcdi_denoise_bwd: gy [n_img][H][W] float4 -> gx [n_img][H][W] float4, the
- * gradient with respect to the term channels (the weights are locked: no
- * weight gradient); acts from a forward of the same precision.  err: device
- * uint32 the kernels set to 1 if a pipeline wait timed out (zero it before
- * the call; outputs are then invalid).
+ * gradient with respect to the term channels; acts from a forward of the
+ * same precision.  grad_ws keeps every intermediate gradient for
+ * mcdi_denoise_wgrad.  err: device uint32 the kernels set to 1 if a pipeline
+ * wait timed out (zero it before the call; outputs are then invalid).
+ *
+ * Weight gradient (the live-trained denoiser of App. B; the main results of
+ * Sec. 4.2 lock the weights and need none):
+ * mcdi_denoise_wgrad_bytes (host): scratch bytes mcdi_denoise_wgrad needs for
+ * n_img images of H x W.
+ * mcdi_denoise_wgrad: after mcdi_denoise_fwd (acts) and mcdi_denoise_bwd
+ * (grad_ws) of the same images, precision and sizes, writes gw (device FP32,
+ * n_params values in the order of mcdi_denoise_pack_weights' params:
+ * dL/dW[co][ci][3][3] then dL/db[co] per convolution) for the loss whose
+ * gradient gy mcdi_denoise_bwd received.  Every entry is overwritten (no
+ * accumulation into gw).  Computed on the tensor cores from the BF16-stored
+ * activations and gradients with FP32 accumulation; with E4M3 operands the
+ * stored BF16 tensors are used (the quantisers pass gradients straight
+ * through).  Results are bitwise repeatable for a given GPU.  scratch:
+ * device, 256-byte aligned, scratch_bytes from mcdi_denoise_wgrad_bytes; acts
+ * and grad_ws are only read.  err as for mcdi_denoise_bwd.
  * ------------------------------------------------------------------------ */
 #define MCDI_DENOISE_BF16 0
 #define MCDI_DENOISE_E4M3 1
@@ -372,6 +388,11 @@ MCDI_API mcdi_status mcdi_denoise_fwd(const void* weights, int precision, int n_
 MCDI_API mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_img, int H, int W, const void* acts,
                                       size_t act_bytes, const float* gy, float* gx, void* grad_ws,
                                       size_t grad_bytes, unsigned* err, void* stream);
+
+MCDI_API mcdi_status mcdi_denoise_wgrad_bytes(int n_img, int H, int W, size_t* scratch_bytes);
+MCDI_API mcdi_status mcdi_denoise_wgrad(int precision, int n_img, int H, int W, const void* acts, size_t act_bytes,
+                                        const void* grad_ws, size_t grad_bytes, float* gw, void* scratch,
+                                        size_t scratch_bytes, unsigned* err, void* stream);
 
 /* mcdi_denoise_record_plan (host; a measurement and test aid, not on the
  * hot path): while rec is non-NULL, each convolution that mcdi_denoise_fwd /
@@ -452,6 +473,20 @@ MCDI_API mcdi_status mcdi_image_loss(const float* kd_out, const float* den_cd, c
 MCDI_API mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pad, const void* w,
                                        const float* bias, int cout_pad, int relu, void* y, unsigned* err,
                                        void* stream);
+
+/* Weight gradient of one such layer (the kernels of mcdi_denoise_wgrad):
+ * x: cin_pad channels, g: cout_pad channels (the gradient at the layer's
+ * pre-activation output), both BF16 8-channel planes as above; gw (device
+ * FP32) receives dW[co][ci][ky][kx] = sum over images and pixels p of
+ * g[co](p) x[ci](p + (ky - 1, kx - 1)) (x zero outside the image) for
+ * co < cout, ci < cin, then db[co] = sum over images and pixels of g[co]:
+ * cout * cin * 9 + cout floats, every one overwritten.  cin <= cin_pad (a
+ * multiple of 8, <= 1024), cout <= cout_pad (a multiple of 16, <= 96).
+ * scratch: device, 256-byte aligned, mcdi_conv3x3_wgrad_bytes bytes. */
+MCDI_API mcdi_status mcdi_conv3x3_wgrad_bytes(int n_img, int H, int W, int cin_pad, int cout_pad, size_t* bytes);
+MCDI_API mcdi_status mcdi_conv3x3_wgrad(const void* x, const void* g, int n_img, int H, int W, int cin_pad,
+                                        int cout_pad, int cin, int cout, float* gw, void* scratch,
+                                        size_t scratch_bytes, unsigned* err, void* stream);
 
 /* The same layer with E4M3 operands (the denoiser's FP8 path): x holds E4M3
  * codes in 16-channel planes (element (((i * C/16 + c/16) * H + y) * W + x)

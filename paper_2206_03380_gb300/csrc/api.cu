@@ -517,6 +517,36 @@ mcdi_status mcdi_denoise_bwd(const void* weights, int precision, int n_img, int 
     return launched(e, "denoise_bwd");
 }
 
+mcdi_status mcdi_denoise_wgrad_bytes(int n_img, int H, int W, size_t* scratch_bytes) {
+    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, MCDI_DENOISE_BF16, nullptr, nullptr, nullptr, nullptr);
+    if (s != MCDI_OK) return s;
+    REQUIRE(scratch_bytes != nullptr, "scratch_bytes must be non-NULL");
+    *scratch_bytes = mcdi::unet_wgrad_bytes(n_img, H, W);
+    return ok();
+}
+
+mcdi_status mcdi_denoise_wgrad(int precision, int n_img, int H, int W, const void* acts, size_t act_bytes,
+                               const void* grad_ws, size_t grad_bytes, float* gw, void* scratch, size_t scratch_bytes,
+                               unsigned* err, void* stream) {
+    size_t need_a = 0, need_g = 0;
+    mcdi_status s = mcdi_denoise_sizes(n_img, H, W, precision, nullptr, &need_a, &need_g, nullptr);
+    if (s != MCDI_OK) return s;
+    REQUIRE(acts != nullptr && ((uintptr_t)acts & 255u) == 0 && act_bytes >= need_a,
+            "acts must be 256-byte aligned and hold %zu bytes", need_a);
+    REQUIRE(grad_ws != nullptr && ((uintptr_t)grad_ws & 255u) == 0 && grad_bytes >= need_g,
+            "grad_ws must be 256-byte aligned and hold %zu bytes", need_g);
+    REQUIRE(gw != nullptr && ((uintptr_t)gw & 3u) == 0, "gw must be a non-NULL device float pointer");
+    const size_t need_s = mcdi::unet_wgrad_bytes(n_img, H, W);
+    REQUIRE(scratch != nullptr && ((uintptr_t)scratch & 255u) == 0, "scratch must be 256-byte aligned");
+    REQUIRE(scratch_bytes >= need_s, "scratch too small: %zu < %zu bytes", scratch_bytes, need_s);
+    REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
+    const char* why = "";
+    const cudaError_t e =
+        mcdi::launch_unet_wgrad(acts, grad_ws, n_img, H, W, gw, scratch, err, static_cast<cudaStream_t>(stream), &why);
+    if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "denoise_wgrad: %s", why);
+    return launched(e, "denoise_wgrad");
+}
+
 mcdi_status mcdi_denoise_record_plan(int* rec, int cap, int* count) {
     if (rec == nullptr) {
         mcdi::set_plan_recorder(nullptr, 0, nullptr);
@@ -617,6 +647,42 @@ mcdi_status mcdi_conv3x3_bf16(const void* x, int n_img, int H, int W, int cin_pa
                                          static_cast<cudaStream_t>(stream), &why);
     if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "conv3x3_bf16: %s", why);
     return launched(e, "conv3x3_bf16");
+}
+
+static mcdi_status wgrad_shape_ok(int n_img, int H, int W, int cin_pad, int cout_pad) {
+    REQUIRE(n_img >= 1 && H >= 1 && W >= 1 && (long long)n_img * H * W <= (1LL << 28), "bad image shape");
+    REQUIRE(cin_pad >= 8 && cin_pad % 8 == 0 && cin_pad <= 1024, "cin_pad must be a multiple of 8 in [8, 1024]");
+    REQUIRE(cout_pad >= 16 && cout_pad % 16 == 0 && cout_pad <= 96,
+            "cout_pad must be a multiple of 16 in [16, 96]");
+    return ok();
+}
+
+mcdi_status mcdi_conv3x3_wgrad_bytes(int n_img, int H, int W, int cin_pad, int cout_pad, size_t* bytes) {
+    mcdi_status s = wgrad_shape_ok(n_img, H, W, cin_pad, cout_pad);
+    if (s != MCDI_OK) return s;
+    REQUIRE(bytes != nullptr, "bytes must be non-NULL");
+    *bytes = mcdi::wgrad_scratch_bytes(cin_pad, cout_pad, n_img, H, W);
+    return ok();
+}
+
+mcdi_status mcdi_conv3x3_wgrad(const void* x, const void* g, int n_img, int H, int W, int cin_pad, int cout_pad,
+                               int cin, int cout, float* gw, void* scratch, size_t scratch_bytes, unsigned* err,
+                               void* stream) {
+    mcdi_status s = wgrad_shape_ok(n_img, H, W, cin_pad, cout_pad);
+    if (s != MCDI_OK) return s;
+    REQUIRE(cin >= 1 && cin <= cin_pad && cout >= 1 && cout <= cout_pad, "need 1 <= cin <= cin_pad, 1 <= cout <= cout_pad");
+    REQUIRE(x != nullptr && ((uintptr_t)x & 15u) == 0, "x must be 16-byte aligned");
+    REQUIRE(g != nullptr && ((uintptr_t)g & 15u) == 0, "g must be 16-byte aligned");
+    REQUIRE(gw != nullptr && ((uintptr_t)gw & 3u) == 0, "gw must be a device float pointer");
+    const size_t need = mcdi::wgrad_scratch_bytes(cin_pad, cout_pad, n_img, H, W);
+    REQUIRE(scratch != nullptr && ((uintptr_t)scratch & 255u) == 0, "scratch must be 256-byte aligned");
+    REQUIRE(scratch_bytes >= need, "scratch too small: %zu < %zu bytes", scratch_bytes, need);
+    REQUIRE(err != nullptr && ((uintptr_t)err & 3u) == 0, "err must be a device uint32");
+    const char* why = "";
+    const cudaError_t e = mcdi::launch_wgrad(x, cin_pad, g, cout_pad, n_img, H, W, cin, cout, scratch, gw, err,
+                                             static_cast<cudaStream_t>(stream), &why);
+    if (e == cudaErrorInvalidValue && why[0]) return fail(MCDI_DEVICE_ERROR, "conv3x3_wgrad: %s", why);
+    return launched(e, "conv3x3_wgrad");
 }
 
 mcdi_status mcdi_conv3x3_e4m3(const void* x, int n_img, int H, int W, int cin_pad, const void* w, const float* x_amax,

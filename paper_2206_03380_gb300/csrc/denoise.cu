@@ -720,6 +720,40 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- weight gradient
+// Per convolution, its forward input and the gradient at its pre-activation
+// output (ReLU-masked where the layer has one): both are left in place by the
+// forward (activations) and the input-gradient backward (gradient buffers).
+static const int kWgX[kUnetConvs] = {X0, A1, P1, A2, P2, A3, P3, B1, CAT3, D3A, CAT2, D2A, CAT1, D1A, D1B};
+static const int kWgG[kUnetConvs] = {GA1, GE1, GA2, GE2, GA3, GE3, GB1, GB2, GD3A, GD3B, GD2A, GD2B, GD1A, GD1B, GY};
+
+size_t unet_wgrad_bytes(int n, int H, int W) {
+    size_t m = 0;
+    for (int k = 0; k < kUnetConvs; ++k) {
+        const int l = kPlan[k].level;
+        m = std::max(m, wgrad_scratch_bytes(kActC[kWgX[k]], kGradC[kWgG[k]], n, H >> l, W >> l));
+    }
+    return m;
+}
+
+cudaError_t launch_unet_wgrad(const void* acts, const void* grad_ws, int n, int H, int W, float* gw, void* scratch,
+                              unsigned* err, cudaStream_t s, const char** why) {
+    size_t aoff[kActs], goff[kGrads], t;
+    layout_of<kActs>(kActC, kActLvl, n, H, W, aoff, &t);
+    layout_of<kGrads>(kGradC, kGradLvl, n, H, W, goff, &t);
+    size_t o = 0;  // parameter order: W[co][ci][3][3], then b[co], per convolution
+    for (int k = 0; k < kUnetConvs; ++k) {
+        const int l = kPlan[k].level;
+        const cudaError_t e =
+            launch_wgrad(static_cast<const char*>(acts) + aoff[kWgX[k]], kActC[kWgX[k]],
+                         static_cast<const char*>(grad_ws) + goff[kWgG[k]], kGradC[kWgG[k]], n, H >> l, W >> l,
+                         kPlan[k].ci, kPlan[k].co, scratch, gw + o, err, s, why);
+        if (e != cudaSuccess) return e;
+        o += (size_t)kPlan[k].co * kPlan[k].ci * 9 + kPlan[k].co;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv3x3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* bias,
                            int cout_pad, int relu, void* y, unsigned* err, cudaStream_t s, const char** why) {
     ConvDesc d = conv_desc(n, H, W, cin_pad, 2 * cin_pad, bias, cout_pad, cout_pad, kStore, relu, static_cast<bf16*>(y),

@@ -147,6 +147,14 @@ cudaError_t launch_unet_fwd(const void* weights, int precision, int n, int H, in
 cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, int W, const void* acts,
                             const float* gy, float* gx_term, void* grad_ws, unsigned* err, cudaStream_t s,
                             const char** why);
+size_t unet_wgrad_bytes(int n, int H, int W);
+cudaError_t launch_unet_wgrad(const void* acts, const void* grad_ws, int n, int H, int W, float* gw, void* scratch,
+                              unsigned* err, cudaStream_t s, const char** why);
+// one convolution's weight and bias gradient (wgrad.cu): x [n][x_ctot / 8][H][W][8] and g [n][g_ctot / 8][H][W][8]
+// BF16 planes -> gw = dW[co][ci][3][3] then db[co] (FP32)
+size_t wgrad_scratch_bytes(int x_ctot, int g_ctot, int n_img, int H, int W);
+cudaError_t launch_wgrad(const void* x, int x_ctot, const void* g, int g_ctot, int n_img, int H, int W, int ci,
+                         int co, void* scratch, float* gw, unsigned* err, cudaStream_t s, const char** why);
 constexpr int kPlanRecordInts = 8;
 void set_plan_recorder(int* rec, int cap, int* count);  // nullptr rec: stop recording
 cudaError_t launch_conv3x3(const void* x, int n, int H, int W, int cin_pad, const void* w, const float* bias,

@@ -24,51 +24,13 @@
 #include <cudaTypedefs.h>
 
 #include "tc_conv.cuh"
+#include "tcgen05.cuh"
 
 namespace mcdi {
 namespace {
 
 constexpr int kStages = 6;
 constexpr int kConvThreads = 128;
-constexpr uint64_t kWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait: false after kWaitNs without the phase completing
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t i = 1;; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 255u) == 0u && global_ns() - t0 > kWaitNs) return false;
-    }
-}
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
@@ -86,9 +48,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor of a K-major operand whose rows are 32 bytes
 // (16 BF16 channels) with the 32-byte swizzle: 8-row atoms of 256 bytes
@@ -148,21 +107,8 @@ __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t adesc, uint64_t b
 }
 #undef MCDI_MMA
 
-// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
-__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
-__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* v) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
     asm volatile(
@@ -436,9 +382,6 @@ constexpr int kRowMaxStages = 6;
 constexpr int kHaloW = 130;
 constexpr int kMaxRows = 4;
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 template <int R, bool FP8, bool MP, bool PL>
 __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
@@ -881,6 +824,26 @@ size_t conv_smem_bytes(int cout_pad) {
 }
 
 }  // namespace
+
+bool encode_plane_rows_map(CUtensorMap* map, const void* base, int W, int H, long long n_planes, int box_px,
+                           int box_rows, int box_planes, const char** why) {
+    auto enc = encode_fn(why);
+    if (!enc) return false;
+    // BF16 8-channel planes [plane][H][W][16 B] as rows of 8-byte elements (two per pixel), so that a box
+    // row of box_px pixels is one contiguous run for the copy engine
+    const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)n_planes};
+    const cuuint64_t str[2] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+    const cuuint32_t box[3] = {(cuuint32_t)box_px * 2, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+    const cuuint32_t ones[3] = {1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, str, box, ones,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "plane-row tensor map rejected by the driver";
+        return false;
+    }
+    return true;
+}
 
 // 128-pixel row tiles from 48 pixels up (narrower rows would leave most of each
 // tile's MMA rows empty); below that the smallest power of two covering W

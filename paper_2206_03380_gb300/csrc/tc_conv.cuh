@@ -92,6 +92,13 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream);
 // words of the next row (masked input gradients whose mask words fit its registers).
 bool conv_mask_prefetch(const ConvDesc& d);
 
+// Tensor map over BF16 8-channel planes [plane][H][W][16 B] (n_planes =
+// images x planes), rank 3 with 8-byte elements: coordinates (2 x, y, plane).
+// A box of box_planes x box_rows x box_px pixels (box_px <= 128) lands in
+// shared memory as [plane][row][px][16 B]; loads outside the tensor read
+// zeros.
+bool encode_plane_rows_map(CUtensorMap* map, const void* base, int W, int H, long long n_planes, int box_px,
+                           int box_rows, int box_planes, const char** why);
 int conv_pick_tile_w(int W);
 
 }  // namespace mcdi

@@ -42,7 +42,9 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_image_loss_workspace_size", "mcdi_image_loss", "mcdi_bilateral_fwd", "mcdi_bilateral_bwd",
            "mcdi_shadow_ray_stats", "mcdi_shadow_ray_retrace", "mcdi_read_sweep", "mcdi_refit_bvh",
            "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad",
-           "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan"]
+           "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan",
+           "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
+           "mcdi_conv3x3_wgrad"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -109,6 +111,14 @@ def load(path: str = LIB_PATH):
     lib.mcdi_denoise_record_plan.restype = st
     lib.mcdi_denoise_record_plan.argtypes = [P, i, P]
     lib.mcdi_denoise_bwd.argtypes = [P, i, i, i, i, P, sz, P, P, P, sz, P, P]
+    lib.mcdi_denoise_wgrad_bytes.restype = st
+    lib.mcdi_denoise_wgrad_bytes.argtypes = [i, i, i, C.POINTER(sz)]
+    lib.mcdi_denoise_wgrad.restype = st
+    lib.mcdi_denoise_wgrad.argtypes = [i, i, i, i, P, sz, P, sz, P, P, sz, P, P]
+    lib.mcdi_conv3x3_wgrad_bytes.restype = st
+    lib.mcdi_conv3x3_wgrad_bytes.argtypes = [i, i, i, i, i, C.POINTER(sz)]
+    lib.mcdi_conv3x3_wgrad.restype = st
+    lib.mcdi_conv3x3_wgrad.argtypes = [P, P, i, i, i, i, i, i, i, P, P, sz, P, P]
     lib.mcdi_composite.restype = st
     lib.mcdi_composite.argtypes = [P, P, P, C.c_longlong, P, P]
     lib.mcdi_conv3x3_bf16.restype = st
@@ -312,6 +322,22 @@ def conv3x3_bf16(x, w, bias, y, relu, err, stream=None):
                                     _ptr(err), _stream(stream)), "conv3x3_bf16")
 
 
+def conv3x3_wgrad_bytes(n: int, H: int, W: int, cin_pad: int, cout_pad: int) -> int:
+    b = C.c_size_t()
+    _check(load().mcdi_conv3x3_wgrad_bytes(int(n), int(H), int(W), int(cin_pad), int(cout_pad), C.byref(b)),
+           "conv3x3_wgrad_bytes")
+    return b.value
+
+
+def conv3x3_wgrad(x, g, cin: int, cout: int, gw, scratch, err, stream=None):
+    """x: BF16 [n][cin_pad/8][H][W][8], g: BF16 [n][cout_pad/8][H][W][8] -> gw (float32,
+    cout*cin*9 + cout): dW[co][ci][3][3] then db[co]."""
+    n, gx_, H, W, _ = x.shape
+    _check(load().mcdi_conv3x3_wgrad(_ptr(x), _ptr(g), n, H, W, 8 * gx_, 8 * g.shape[1], int(cin), int(cout), _ptr(gw),
+                                     _ptr(scratch), scratch.numel() * scratch.element_size(), _ptr(err),
+                                     _stream(stream)), "conv3x3_wgrad")
+
+
 def bilateral_fwd(gb_pos, gb_nrm, cams, c_in, sigma, c_out, wsum, radius=-1, stream=None):
     """Cross-bilateral filter of the [n_img][H][W] float4 batch c_in with the guides of
     N views (image i uses view i % N); wsum [N][H][W] float32 receives W(p)."""
@@ -350,6 +376,23 @@ def conv3x3_e4m3(x, w, x_amax, w_amax, bias, y, relu, err, stream=None):
     n, g, H, W, _ = x.shape
     _check(load().mcdi_conv3x3_e4m3(_ptr(x), n, H, W, 16 * g, _ptr(w), _ptr(x_amax), _ptr(w_amax), _ptr(bias),
                                     w.shape[0], int(bool(relu)), _ptr(y), _ptr(err), _stream(stream)), "conv3x3_e4m3")
+
+
+
+def denoise_wgrad_bytes(n_img: int, H: int, W: int) -> int:
+    b = C.c_size_t()
+    _check(load().mcdi_denoise_wgrad_bytes(int(n_img), int(H), int(W), C.byref(b)), "denoise_wgrad_bytes")
+    return b.value
+
+
+def denoise_wgrad(acts, grad_ws, gw, scratch, err, n_img: int, H: int, W: int, stream=None, precision: int = BF16):
+    """gw (device float32, n_params) = the weight and bias gradients of the 15 convolutions, after
+    denoise_fwd (acts) and denoise_bwd (grad_ws) of the same images."""
+    _check(load().mcdi_denoise_wgrad(int(precision), int(n_img), int(H), int(W), _ptr(acts),
+                                     acts.numel() * acts.element_size(), _ptr(grad_ws),
+                                     grad_ws.numel() * grad_ws.element_size(), _ptr(gw), _ptr(scratch),
+                                     scratch.numel() * scratch.element_size(), _ptr(err), _stream(stream)),
+           "denoise_wgrad")
 
 
 UNET_PLAN = [("enc1a", 9, 32), ("enc1b", 32, 32), ("enc2a", 32, 48), ("enc2b", 48, 48), ("enc3a", 48, 64),
@@ -391,6 +434,27 @@ class Denoiser:
 
     def backward(self, gy, gx, stream=None):
         denoise_bwd(self.weights, self.acts, gy, gx, self.grad_ws, self.err, stream, self.precision)
+
+    def weight_grad(self, gw=None, stream=None):
+        """The gradient of the parameters (float32, the order of flatten_unet_params) for the
+        last forward/backward pair; the scratch is allocated on first use."""
+        if getattr(self, "wgrad_ws", None) is None:
+            self.wgrad_ws = _empty_bytes(denoise_wgrad_bytes(self.n_img, self.H, self.W), self.weights.device)
+        if gw is None:
+            gw = torch.empty(self._params.numel(), dtype=torch.float32, device=self.weights.device)
+        denoise_wgrad(self.acts, self.grad_ws, gw, self.wgrad_ws, self.err, self.n_img, self.H, self.W, stream,
+                      self.precision)
+        return gw
+
+
+def unflatten_unet_params(flat):
+    """One vector in the library's order -> {name: (W (co, ci, 3, 3), b (co,))} (views for tensors)."""
+    out, o = {}, 0
+    for name, ci, co in UNET_PLAN:
+        n = co * ci * 9
+        out[name] = (flat[o:o + n].reshape(co, ci, 3, 3), flat[o + n:o + n + co])
+        o += n + co
+    return out
 
 
 class denoise_plan_recorder:
