@@ -374,6 +374,7 @@ def run_gpu(args, rank, world):
                   "unit": UNIT, "note": "the same step launched kernel by kernel from the host, with events between "
                                         "stages (the source of stage_ms)"},
     }
+    result["denoiser_wgrad"] = time_denoiser_wgrad(pipe.denoiser, conv_flops, flush, stream, args.steps)
     result["denoiser_e4m3"] = time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, args.steps)
     result["denoiser_bilateral"] = time_bilateral(pipe, flush, stream, args.steps)
     result["shadow_rays"] = rays
@@ -646,6 +647,63 @@ def time_denoiser_e4m3(pipe, den_params, conv_flops, flush, stream, steps):
     return out
 
 
+def time_denoiser_wgrad(den, conv_flops, flush, stream, steps):
+    """The denoiser's weight gradient (the live-trained variant, App. B; not part of the timed
+    step, whose denoiser weights are locked) after the step's forward and input gradient: 15
+    tcgen05 weight-gradient launches and 15 deterministic reductions, CUDA events, L2 flushed
+    before each pass.  FLOPs: the forward's (2 * 9 * c_in * c_out per pixel and convolution)."""
+    import torch
+
+    gw = den.weight_grad(stream=stream)
+    ts = []
+    for k in range(steps + 3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        flush.zero_()
+        ev[0].record(stream)
+        den.weight_grad(gw, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            ts.append(ev[0].elapsed_time(ev[1]))
+    if den.err.item() != 0:
+        raise RuntimeError("denoiser weight-gradient wait timed out")
+    t = float(np.mean(ts))
+    tpeak, tkind = tensor_peak()
+    tf = conv_flops / (t * 1e-3) / 1e12
+    return {"ms": round(t, 4), "tflops": round(tf, 2), "peak": tpeak, "frac": round(tf / tpeak, 4),
+            "peak_source": tkind, "launches": 30, "finite": bool(torch.isfinite(gw).all().item()),
+            "note": "dW and db of the 15 convolutions for the step's loss; off the timed step (locked weights)"}
+
+
+def run_wgrad_only(args):
+    """Only the denoiser weight gradient at the headline launch (2 images of 512^2, seeded
+    synthetic terms and guides): one forward and input gradient, then the timed weight
+    gradients.  A profiling entry that skips the rest of the benchmark."""
+    import torch
+
+    from paper_2206_03380_gb300 import mcdi, scenes
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(scenes.BASE_SEED + 11)
+    H = W = 512
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+    term = t(np.abs(rng.lognormal(0.0, 0.8, size=(2, H, W, 4))))
+    kd, nrm = t(rng.uniform(0, 1, size=(1, H, W, 4))), t(rng.normal(size=(1, H, W, 4)))
+    den = mcdi.Denoiser(mcdi.flatten_unet_params(scenes.unet_xavier_weights(scenes.BASE_SEED + 3)), 2, H, W,
+                        device=dev)
+    y, gx = torch.empty_like(term), torch.empty_like(term)
+    den.forward(term, kd, nrm, y)
+    den.backward(t(rng.normal(size=(2, H, W, 4))), gx)
+    conv_flops = 0
+    for name, ci, co in scenes.UNET_SHAPES:
+        lvl = {"enc1": 0, "enc2": 1, "enc3": 2, "bot_": 3, "dec3": 2, "dec2": 1, "dec1": 0, "out": 0}[name[:4]]
+        conv_flops += 2 * 9 * ci * co * 2 * (H >> lvl) * (W >> lvl)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    out = time_denoiser_wgrad(den, conv_flops, flush, torch.cuda.current_stream(), args.steps)
+    print(json.dumps({"denoiser_wgrad": out, "config": {"images": 2, "width": W, "height": H}}))
+
+
 def fp8_peak(stream, n=8192, reps=10):
     """Dense E4M3 peak measured with the vendor library (torch._scaled_mm, FP32 accumulation,
     per-tensor scales, BF16 output) on an n x n x n product, best of reps: the denominator of the
@@ -798,9 +856,14 @@ def main(argv=None):
                     help="graph replays of the 8-view 800^2 32-spp step on the ~1.3M-triangle mesh (0: skip)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the optimisation-step batch and print its figures (a profiling aid)")
+    ap.add_argument("--wgrad-only", action="store_true",
+                    help="run only the denoiser weight gradient at the headline launch (a profiling aid)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    if args.wgrad_only:
+        run_wgrad_only(args)
+        return
     if args.batch_only:
         import torch
 
