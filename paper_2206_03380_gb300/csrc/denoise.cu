@@ -1,9 +1,11 @@
 // The differentiable denoiser (Sec. 4.2 "Neural denoisers", App. B): a U-Net
 // of 3x3 convolutions applied to the demodulated diffuse term c_d and the
 // specular term c_s, each with the k_d and normal planes as guides.  Forward
-// and input-gradient backward (the paper's main results lock the denoiser
-// weights, so no weight gradient is formed; Sec. 4.2's gradient-sharing
-// identity dL/dX = dL/dO conv F^T is what the backward convolutions compute).
+// and input-gradient backward (Sec. 4.2's gradient-sharing identity
+// dL/dX = dL/dO conv F^T is what the backward convolutions compute); the
+// paper's main results lock the denoiser weights, and the weight gradient of
+// its live-trained variant (App. B) runs on request from the stored
+// activations and gradients (wgrad.cu).
 //
 // Precision: BF16 operands, or E4M3 operands with per-tensor scaling (every
 // convolution input and weight tensor quantised as round(v 448 / amax) just
