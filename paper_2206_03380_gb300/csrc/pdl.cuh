@@ -7,7 +7,8 @@
 // allowed to start before its predecessor completes — except while the
 // stream is being captured into a CUDA graph, whose replay already launches
 // back to back (measured: the mark saves about 80 us per headline step
-// launched kernel by kernel and costs about 30 us in the replayed graph).  For
+// launched kernel by kernel and costs about 30 us in the replayed graph; with
+// the convolutions' weight loads ahead of their wait it is a wash there).  For
 // a kernel launched without the mark the prologue's wait returns at once.
 #pragma once
 
@@ -21,6 +22,14 @@ __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+
+// The two halves of pdl_prologue, for kernels with setup that depends on nothing
+// the preceding kernel writes: let the next kernel launch, do that setup, then
+// wait (every thread, before its first access to data of earlier kernels).
+__device__ __forceinline__ void pdl_allow_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,

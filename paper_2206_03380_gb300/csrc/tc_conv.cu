@@ -386,7 +386,10 @@ constexpr int kMaxRows = 4;
 template <int R, bool FP8, bool MP, bool PL>
 __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
-    pdl_prologue();
+    // The setup that reads nothing the preceding kernel writes (barriers, bias, tensor memory and the
+    // weight load: the weights and biases are packed once) runs before the wait on that kernel, so it
+    // overlaps the preceding kernel's tail when the launch is programmatically dependent.
+    pdl_allow_dependents();
     extern __shared__ uint8_t smem_raw[];
     __shared__ float s_bias[256];
     __shared__ __align__(8) uint64_t full_bar[kRowMaxStages], empty_bar[kRowMaxStages], accf_bar[2], acce_bar[2],
@@ -440,15 +443,15 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
 
     int issued = 0;
     bool w_issued = false;
+    if (warp == 0 && has_work && lane == 0) {
+        const uint32_t wb = smem_u32(&w_bar);
+        mbar_expect_tx(wb, (uint32_t)n_chunks * w_chunk);
+        for (int c = 0; c < n_chunks; ++c) tma_load_4d(wbase + (uint32_t)c * w_chunk, &tmap_wh, 0, n0, 0, c, wb);
+        w_issued = true;
+    }
+    pdl_wait();  // activations, masks and outputs: after the preceding kernel has completed
     if (warp == 0) {
         if (has_work) {
-            if (lane == 0) {
-                const uint32_t wb = smem_u32(&w_bar);
-                mbar_expect_tx(wb, (uint32_t)n_chunks * w_chunk);
-                for (int c = 0; c < n_chunks; ++c)
-                    tma_load_4d(wbase + (uint32_t)c * w_chunk, &tmap_wh, 0, n0, 0, c, wb);
-                w_issued = true;
-            }
             // Halo rows by plain bulk copies: lane l < 2 (R + 2) owns row l % (R + 2)
             // of plane l / (R + 2); the part of the row outside the image is
             // zero-filled with shared-memory stores made visible to the async
