@@ -96,9 +96,7 @@ __global__ void __launch_bounds__(kShadeThreads) shade_fwd_kernel(ShadeArgs a, f
                     const float G2 = 1.0f / (1.0f + ggx_lambda(ci, px.a2) + ggx_lambda(px.co, px.a2));
                     const float q = schlick_weight(dot(px.wo, h));
                     const float ws = Hv * D * G2 / (4.0f * px.co) * inv_denom;
-                    cs = cs + mk(L.x * (px.F0.x + (1.0f - px.F0.x) * q), L.y * (px.F0.y + (1.0f - px.F0.y) * q),
-                                 L.z * (px.F0.z + (1.0f - px.F0.z) * q)) *
-                                  ws;
+                    cs = cs + spec_colour(L, px.F0, q, ws);
                 }
             }
         }

@@ -2,16 +2,20 @@
 // samples, weights and shadow rays as shade_fwd_kernel, split so that the
 // incoherent shadow-ray traversal runs in a lean kernel of its own.
 //
-//   gen    one thread per pixel: draws every sample, writes its unshadowed
-//          contribution (c_d and c_s parts) to slot j*P + pixel and appends its
-//          shadow ray, if any, to a dense ray list (a warp's rays for one sample
+//   gen    one thread per pixel: draws every sample; for a sample with a shadow
+//          ray it writes the scalars of its unshadowed contribution (probe texel,
+//          diffuse and specular weights, 16 bytes) to slot j*P + pixel and
+//          appends the ray to a dense ray list (a warp's rays for one sample
 //          index stay together: neighbouring pixels, same technique, nearby
-//          origins and similar directions);
+//          origins and similar directions); a sample without one (it
+//          contributes nothing) only marks its slot;
 //   trace  persistent warps pull rays from a global counter; a lane whose ray
 //          has finished takes the next ray at the next refill, so lanes do not
 //          wait for the warp's longest ray;
-//   accum  one thread per pixel: sums contribution_j x H_j in sample order
-//          j = 0..S-1 (bitwise repeatable) and packs the visibility mask.
+//   accum  one thread per pixel: rebuilds each marked-active sample's c_d and c_s
+//          parts from its scalars (the same arithmetic as gen), sums
+//          contribution_j x H_j in sample order j = 0..S-1 (bitwise repeatable)
+//          and packs the visibility mask.
 #include "common.cuh"
 #include "internal.h"
 #include "shading.cuh"
@@ -29,8 +33,9 @@ constexpr int kLeafBatch = 16;  // lanes holding one that start a triangle round
 struct WaveBuffers {
     float4* ray;        // [rays] direction, w = slot index (int bits) of the sample
     float4* origin;     // [P] shadow-ray origin of each covered pixel (p + ray_eps n)
-    float* contrib;     // [6][slots] c_d rgb, c_s rgb without visibility
-    uint8_t* hit;       // [slots] 1 = shadow ray blocked
+    float4* rec;        // [slots] active samples: probe texel (int bits), diffuse weight, Schlick weight,
+                        // specular weight (c_d = L sd, c_s = spec_colour(L, F0, q, ws), L the texel's radiance)
+    uint8_t* hit;       // [slots] 0 shadow ray clear, 1 blocked, 2 no shadow ray (the sample contributes nothing)
     unsigned* counter;  // [0] rays appended by gen, [1] trace work queue head
 };
 
@@ -40,7 +45,7 @@ __host__ __device__ __forceinline__ size_t wave_contrib_offset(long long P, long
     return wave_origin_offset(slots) + align256((size_t)P * 16);
 }
 __host__ __device__ __forceinline__ size_t wave_hit_offset(long long P, long long slots) {
-    return wave_contrib_offset(P, slots) + align256((size_t)slots * 24);
+    return wave_contrib_offset(P, slots) + align256((size_t)slots * 16);
 }
 __host__ __device__ __forceinline__ size_t wave_counter_offset(long long P, long long slots) {
     return wave_hit_offset(P, slots) + align256((size_t)slots);
@@ -51,7 +56,7 @@ __device__ __forceinline__ WaveBuffers wave_buffers(void* ws, long long P, long 
     WaveBuffers b;
     b.ray = reinterpret_cast<float4*>(p);
     b.origin = reinterpret_cast<float4*>(p + wave_origin_offset(slots));
-    b.contrib = reinterpret_cast<float*>(p + wave_contrib_offset(P, slots));
+    b.rec = reinterpret_cast<float4*>(p + wave_contrib_offset(P, slots));
     b.hit = reinterpret_cast<uint8_t*>(p + wave_hit_offset(P, slots));
     b.counter = reinterpret_cast<unsigned*>(p + wave_counter_offset(P, slots));
     return b;
@@ -113,7 +118,8 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
     if (covered && quarter == 0) B.origin[idx] = make_float4(origin.x, origin.y, origin.z, 0.0f);
     for (int j = quarter; j < spp; j += kGenQuarters) {
         const long long s = (long long)j * P + idx;
-        f3 wi = mk(0.f, 0.f, 0.f), cd = wi, cs = wi;
+        f3 wi = mk(0.f, 0.f, 0.f);
+        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
         bool active = false;
         if (covered) {
             int t;
@@ -121,17 +127,14 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
             const float2 u = sample_uniforms(a.seed, pix, (uint32_t)view, (uint32_t)j, a.stream_word);
             if (draw_sample(Pr, px, a.n_light, a.n_cos, a.n_ggx, j, u, &wi, &t, &ci, &inv_denom)) {
                 active = true;
-                const float4 L = __ldg(Pr.env + t);
-                cd = mk(L.x, L.y, L.z) * (ci * MCDI_INV_PI * inv_denom);
+                rec.x = __int_as_float(t);
+                rec.y = ci * MCDI_INV_PI * inv_denom;  // c_d = L rec.y
                 if (px.spec_on) {
                     const f3 h = normalize(wi + px.wo);
                     const float D = ggx_D(dot(px.n, h), sin2_between(px.n, h), px.a2);
                     const float G2 = 1.0f / (1.0f + ggx_lambda(ci, px.a2) + ggx_lambda(px.co, px.a2));
-                    const float q = schlick_weight(dot(px.wo, h));
-                    const float ws = D * G2 / (4.0f * px.co) * inv_denom;
-                    cs = mk(L.x * (px.F0.x + (1.0f - px.F0.x) * q), L.y * (px.F0.y + (1.0f - px.F0.y) * q),
-                            L.z * (px.F0.z + (1.0f - px.F0.z) * q)) *
-                         ws;
+                    rec.z = schlick_weight(dot(px.wo, h));
+                    rec.w = D * G2 / (4.0f * px.co) * inv_denom;  // c_s = spec_colour(L, F0, rec.z, rec.w)
                 }
             }
         }
@@ -146,14 +149,9 @@ __global__ void __launch_bounds__(kGenThreads) wave_gen_kernel(ShadeArgs a, void
                 B.ray[r] = make_float4(wi.x, wi.y, wi.z, __int_as_float((int)s));
             }
         }
-        if (!covered) continue;  // the accumulation skips the slots of uncovered pixels
-        B.hit[s] = 0;
-        B.contrib[0 * slots + s] = cd.x;
-        B.contrib[1 * slots + s] = cd.y;
-        B.contrib[2 * slots + s] = cd.z;
-        B.contrib[3 * slots + s] = cs.x;
-        B.contrib[4 * slots + s] = cs.y;
-        B.contrib[5 * slots + s] = cs.z;
+        if (!in_range) continue;
+        B.hit[s] = active ? 0 : 2;  // every slot, so that the accumulation needs no coverage test
+        if (active) B.rec[s] = rec;
     }
 }
 
@@ -252,25 +250,28 @@ __global__ void __launch_bounds__(kGenThreads) wave_accum_kernel(ShadeArgs a, co
     const int nwords = (spp + 31) >> 5;
     const long long slots = P * spp;
     WaveBuffers B = wave_buffers(const_cast<void*>(ws), P, slots);
-    // the same coverage test as the generator, which wrote no slots for uncovered pixels
-    const float4 pos = a.gb_pos[idx], nrm = a.gb_nrm[idx];
-    if (!(pos.w > 0.0f) || !(dot(xyz(nrm), xyz(nrm)) > 0.0f)) {
-        c_d[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-        c_s[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (vis_mask)
-            for (int w = 0; w < nwords; ++w) vis_mask[(size_t)idx * nwords + w] = 0u;
-        return;
-    }
+    // every slot is marked (uncovered pixels' slots as without a shadow ray), so an uncovered pixel
+    // sums nothing and its outputs come out zero
     const float hv = 1.0f - a.tau;
+    f3 F0 = mk(0.f, 0.f, 0.f);  // formed as load_pixel forms it in gen, at the first active sample
+    bool have_f0 = false;
     f3 cd = mk(0.f, 0.f, 0.f), cs = cd;
     uint32_t word = 0;
     for (int j = 0; j < spp; ++j) {
         const long long s = (long long)j * P + idx;
-        const bool hit = B.hit[s] != 0;
-        const float Hv = hit ? hv : 1.0f;
-        if (hit) word |= 1u << (j & 31);
-        cd = cd + mk(B.contrib[0 * slots + s], B.contrib[1 * slots + s], B.contrib[2 * slots + s]) * Hv;
-        cs = cs + mk(B.contrib[3 * slots + s], B.contrib[4 * slots + s], B.contrib[5 * slots + s]) * Hv;
+        const uint8_t h = B.hit[s];
+        if (h == 1) word |= 1u << (j & 31);
+        if (h != 2) {  // a sample without a shadow ray contributes nothing
+            if (!have_f0) {
+                F0 = fresnel0(xyz(a.gb_kd[idx]), a.gb_korm[idx].z);
+                have_f0 = true;
+            }
+            const float Hv = h ? hv : 1.0f;
+            const float4 rec = B.rec[s];
+            const float4 L = __ldg(a.env + __float_as_int(rec.x));
+            cd = cd + mk(L.x, L.y, L.z) * rec.y * Hv;
+            cs = cs + spec_colour(L, F0, rec.z, rec.w) * Hv;
+        }
         if (vis_mask && ((j & 31) == 31 || j == spp - 1)) {
             vis_mask[(size_t)idx * nwords + (j >> 5)] = word;
             word = 0;

@@ -531,6 +531,18 @@ __device__ __forceinline__ void gbuffer_hit(int k, float u, float v, const float
 }
 
 // ---------------------------------------------------------------- per pixel
+// Schlick's normal-incidence reflectance of the metallic blend (reading c1)
+__device__ __forceinline__ f3 fresnel0(f3 kd, float m) {
+    return mk(0.04f * (1.0f - m) + kd.x * m, 0.04f * (1.0f - m) + kd.y * m, 0.04f * (1.0f - m) + kd.z * m);
+}
+
+// the specular integrand's colour for probe radiance L: L (F0 + (1 - F0) q) ws, q the Schlick weight and ws
+// the scalar rest of the term (D G2 / (4 cos_o) over the MIS denominator)
+__device__ __forceinline__ f3 spec_colour(float4 L, f3 F0, float q, float ws) {
+    return mk(L.x * (F0.x + (1.0f - F0.x) * q), L.y * (F0.y + (1.0f - F0.y) * q), L.z * (F0.z + (1.0f - F0.z) * q)) *
+           ws;
+}
+
 struct Pixel {
     f3 p, n, wo, b1, b2;
     float lN, co, alpha, a2, g1o, r, m;
@@ -554,8 +566,7 @@ __device__ __forceinline__ bool load_pixel(float4 pos, float4 nrm, float4 kd, fl
     px->a2 = px->alpha * px->alpha;
     px->g1o = px->spec_on ? 1.0f / (1.0f + ggx_lambda(px->co, px->a2)) : 0.0f;
     px->kd = xyz(kd);
-    px->F0 = mk(0.04f * (1.0f - px->m) + px->kd.x * px->m, 0.04f * (1.0f - px->m) + px->kd.y * px->m,
-                0.04f * (1.0f - px->m) + px->kd.z * px->m);
+    px->F0 = fresnel0(px->kd, px->m);
     frame(px->n, &px->b1, &px->b2);
     return true;
 }
