@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd MC shading Msamples/s & %HBM roofline at 512² 16spp"
 # DRAM bytes (read + write) per launch at the headline size, from one ncu capture of the kernel as it
 # stands (profiles/); an entry is removed when its kernels change.
-MEASURED_TRAFFIC = {"wave_trace_kernel": 41.83e6, "shade_fwd": 157.3e6, "shade_bwd": 24.9e6}
+MEASURED_TRAFFIC = {"wave_trace_kernel": 41.83e6, "shade_fwd": 109.7e6, "shade_bwd": 24.9e6}
 UNIT = "Msamples/s"
 L2_FLUSH_BYTES = 512 << 20
 # serving: requests of fewer than 2M samples in one lane, the rest in another (measured against 1M - 3M
