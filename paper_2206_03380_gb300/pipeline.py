@@ -196,26 +196,117 @@ class ShadingPipeline:
         """Capture one `loss_step` against ``ref`` into a CUDA graph; see `_capture`."""
         return self._capture(lambda: self.loss_step(ref, lambda_light=lambda_light))
 
-    def _capture(self, fn):
+    def loss_step_io(self, ref, host_in: dict, host_ref, outputs, stream=None, lambda_light: float = 0.15):
+        """`loss_step` with its host I/O overlapped: this step's inputs are copied
+        from pinned host memory (``host_in``: verts, vnrm, tris, env, tex_kd,
+        tex_korm into the pipeline's buffers; ``host_ref`` into ``ref``) on
+        copy streams in the order the step first reads them (mesh, probe and
+        reference on one, each material texture on its own), and every
+        stage waits only for the inputs it reads: the BVH build for the mesh, the
+        probe tables for the probe, the rasterised G-buffer for the mesh and the
+        textures, the loss for the reference.  ``outputs`` lists (device tensor,
+        pinned host tensor) pairs read back as soon as their producer has run:
+        the loss and the composite while the denoiser input gradient and the
+        adjoint run, the rest at the end (over two streams).  Inside a captured
+        graph the waits become graph edges."""
+        dev = self.device
+        cur = stream if stream is not None else torch.cuda.current_stream(dev)
+        if getattr(self, "_io", None) is None:
+            self._io = [torch.cuda.Stream(dev) for _ in range(5)]
+        up, up_kd, up_korm, down, down2 = self._io
+        streams = (up, up_kd, up_korm, down, down2)
+        for st in streams:
+            st.wait_stream(cur)
+        ev = {k: torch.cuda.Event() for k in ("mesh", "env", "ref", "kd", "korm", "loss", "end")}
+        with torch.cuda.stream(up):
+            for k in ("verts", "tris", "vnrm"):
+                getattr(self, k).copy_(host_in[k], non_blocking=True)
+            ev["mesh"].record(up)
+            self.env.copy_(host_in["env"], non_blocking=True)
+            ev["env"].record(up)
+            ref.copy_(host_ref, non_blocking=True)
+            ev["ref"].record(up)
+        # the two material textures (most of the bytes) each on a stream of its own
+        with torch.cuda.stream(up_kd):
+            self.tex_kd.copy_(host_in["tex_kd"], non_blocking=True)
+            ev["kd"].record(up_kd)
+        with torch.cuda.stream(up_korm):
+            self.tex_korm.copy_(host_in["tex_korm"], non_blocking=True)
+            ev["korm"].record(up_korm)
+        if self._fork is None:
+            self._fork = torch.cuda.Stream(dev)
+        fork = self._fork
+        fork.wait_stream(cur)
+        fork.wait_event(ev["env"])
+        self.build_probe(fork)
+        if self.raster_ws is not None:
+            for k in ("mesh", "kd", "korm"):
+                fork.wait_event(ev[k])
+            self.primary(fork)
+        cur.wait_event(ev["mesh"])
+        self.build_bvh(cur)
+        if self.raster_ws is None:
+            for k in ("kd", "korm"):
+                cur.wait_event(ev[k])
+            self.primary(cur)
+        cur.wait_stream(fork)
+        self.forward(cur)
+        N = self.N
+        if self.denoiser is not None:
+            self.denoise(cur)
+        cur.wait_event(ev["ref"])
+        self.image_loss(ref, cur, lambda_light)
+        ev["loss"].record(cur)
+        early = [(d, h) for d, h in outputs if d is self.loss or d is self.color]
+        late = [(d, h) for d, h in outputs if not (d is self.loss or d is self.color)]
+        down.wait_event(ev["loss"])
+        with torch.cuda.stream(down):
+            for d, h in early:
+                h.copy_(d, non_blocking=True)
+        g_cd, g_cs = self.g_loss_terms[:N], self.g_loss_terms[N:]
+        if self.denoiser is not None:
+            self.denoise_backward(self.g_loss_terms, cur)
+            g_cd, g_cs = self.g_terms[:N], self.g_terms[N:]
+        self.backward(g_cd, self.g_loss_kdout, g_cs, cur)
+        ev["end"].record(cur)
+        for i, st in enumerate((down, down2)):  # the late read-backs split over two streams
+            st.wait_event(ev["end"])
+            with torch.cuda.stream(st):
+                for d, h in late[i::2]:
+                    h.copy_(d, non_blocking=True)
+        for st in streams:
+            cur.wait_stream(st)
+
+    def capture_loss_step_io(self, ref, host_in: dict, host_ref, outputs, lambda_light: float = 0.15):
+        """Capture one `loss_step_io` into a CUDA graph (its copies included); `replay_io()` reruns it."""
+        self._capture(lambda: self.loss_step_io(ref, host_in, host_ref, outputs, lambda_light=lambda_light),
+                      "graph_io")
+        return self.graph_io
+
+    def _capture(self, fn, attr: str = "graph"):
         """Capture one step into a CUDA graph (its launches, memsets and the
-        host-encoded tensor maps are baked in with these buffers); `replay()`
-        then reruns the whole step with one launch from the host.  A first step
-        runs uncaptured on a side stream so that one-time set-up (kernel
-        attributes, device queries, lazily allocated buffers) stays outside
-        the graph."""
+        host-encoded tensor maps are baked in with these buffers) kept as
+        ``self.<attr>``; `replay()` then reruns the whole step with one launch
+        from the host.  A first step runs uncaptured on a side stream so that
+        one-time set-up (kernel attributes, device queries, lazily allocated
+        buffers) stays outside the graph."""
         dev = self.device
         side = torch.cuda.Stream(dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
             fn()
         torch.cuda.current_stream(dev).wait_stream(side)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
             fn()
-        return self.graph
+        setattr(self, attr, graph)
+        return graph
 
     def replay(self):
         self.graph.replay()
+
+    def replay_io(self):
+        self.graph_io.replay()
 
     def covered_pixels(self) -> int:
         return int((self.gb.pos[..., 3] > 0).sum().item())
