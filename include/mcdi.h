@@ -226,6 +226,22 @@ MCDI_API mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* en
                                        const mcdi_shade_params* params, float* c_d, float* kd_out, float* c_s,
                                        uint32_t* vis_mask, void* workspace, size_t workspace_bytes, void* stream);
 
+/* mcdi_shade_mc_fwd in two calls on the same workspace (required), so that
+ * the sample generation, which reads no BVH, can run while the BVH is still
+ * being built: part 1 draws every sample (Sec. 3.1 estimator, Sec. 4.1 MIS)
+ * and writes kd_out, the shadow rays and the unshadowed contributions to
+ * `workspace` (bvh may be the view of a BVH not built yet: its buffers are
+ * not read); part 2, on a stream ordered after part 1 and after the BVH
+ * build, traces the shadow rays and writes c_d, c_s and vis_mask.  Arguments
+ * as mcdi_shade_mc_fwd; both parts must receive the same ones. */
+MCDI_API mcdi_status mcdi_shade_mc_fwd_part(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp,
+                                            const float* cond_cdf, const float* marg_cdf, const double* total,
+                                            const float* gb_pos, const float* gb_nrm, const float* gb_kd,
+                                            const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                                            const mcdi_shade_params* params, float* c_d, float* kd_out, float* c_s,
+                                            uint32_t* vis_mask, void* workspace, size_t workspace_bytes, int part,
+                                            void* stream);
+
 /* ------------------------------------------------------------------------
  * Hand-written adjoint of mcdi_shade_mc_fwd (Sec. 4.1: detached importance
  * sampling, the forward seed reused in the backward pass; Sec. 3.1: shadow

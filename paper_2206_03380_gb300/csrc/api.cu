@@ -269,6 +269,32 @@ mcdi_status mcdi_shade_mc_fwd(const mcdi_bvh_view* bvh, const float* env, int Wp
                     "shade_mc_fwd");
 }
 
+mcdi_status mcdi_shade_mc_fwd_part(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                                   const float* marg_cdf, const double* total, const float* gb_pos,
+                                   const float* gb_nrm, const float* gb_kd, const float* gb_korm,
+                                   const mcdi_camera* cams, int N, int H, int W, const mcdi_shade_params* params,
+                                   float* c_d, float* kd_out, float* c_s, uint32_t* vis_mask, void* workspace,
+                                   size_t workspace_bytes, int part, void* stream) {
+    REQUIRE(part == 1 || part == 2, "part must be 1 (sample generation) or 2 (shadow rays and accumulation)");
+    mcdi::ShadeArgs a;
+    mcdi_status s = shade_common(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N,
+                                 H, W, params, &a);
+    if (s != MCDI_OK) return s;
+    REQUIRE_BUF16(c_d);
+    REQUIRE_BUF16(kd_out);
+    REQUIRE_BUF16(c_s);
+    REQUIRE(vis_mask == nullptr || ((uintptr_t)vis_mask & 3u) == 0, "vis_mask must be 4-byte aligned");
+    size_t need = 0;
+    s = mcdi_shade_workspace_size(N, H, W, params, &need);
+    if (s != MCDI_OK) return s;
+    REQUIRE(workspace != nullptr && ((uintptr_t)workspace & 255u) == 0, "workspace must be non-NULL, 256-byte aligned");
+    REQUIRE(workspace_bytes >= need, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+    return launched(mcdi::launch_shade_fwd_wave(a, reinterpret_cast<float4*>(c_d), reinterpret_cast<float4*>(kd_out),
+                                                reinterpret_cast<float4*>(c_s), vis_mask, workspace,
+                                                static_cast<cudaStream_t>(stream), part),
+                    "shade_mc_fwd_part");
+}
+
 }  // extern "C"
 
 namespace {

@@ -104,7 +104,8 @@ cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, fl
 
 size_t shade_workspace_bytes(long long pixels, int spp);
 cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
-                                  void* ws, cudaStream_t stream);
+                                  void* ws, cudaStream_t stream,
+                                  int parts = 3);
 cudaError_t launch_shadow_ray_stats(const ShadeArgs& a, const void* ws, unsigned long long* stats,
                                     cudaStream_t stream);
 cudaError_t launch_shadow_ray_retrace(const ShadeArgs& a, void* ws, cudaStream_t stream);

@@ -39,15 +39,22 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
-    cudaLaunchAttribute attr{};
-    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[2]{};
+    unsigned n_attr = 0;
     cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(stream, &capture) != cudaSuccess) capture = cudaStreamCaptureStatusNone;
     if (capture == cudaStreamCaptureStatusNone) {
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
+        attr[n_attr].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n_attr++].val.programmaticStreamSerializationAllowed = 1;
     }
+    // a stream's priority, also for kernels captured into a graph (their nodes keep it)
+    int prio = 0;
+    if (cudaStreamGetPriority(stream, &prio) == cudaSuccess && prio != 0) {
+        attr[n_attr].id = cudaLaunchAttributePriority;
+        attr[n_attr++].val.priority = prio;
+    }
+    cfg.attrs = n_attr ? attr : nullptr;
+    cfg.numAttrs = n_attr;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

@@ -358,13 +358,16 @@ size_t shade_workspace_bytes(long long P, int spp) {
 }
 
 cudaError_t launch_shade_fwd_wave(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
-                                  void* ws, cudaStream_t stream) {
+                                  void* ws, cudaStream_t stream, int parts) {
     const long long P = (long long)a.N * a.H * a.W;
     const int spp = a.n_light + a.n_cos + a.n_ggx;
     const int gblocks = (int)((P + kGenThreads - 1) / kGenThreads);
-    launch_k(wave_reset_kernel, 1, 1, 0, stream, ws, P, P * spp);
-    launch_k(wave_gen_kernel, (int)((P + 31) / 32), kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream, a, ws,
-             kd_out);
+    if (parts & 1) {
+        launch_k(wave_reset_kernel, 1, 1, 0, stream, ws, P, P * spp);
+        launch_k(wave_gen_kernel, (int)((P + 31) / 32), kGenThreads, (size_t)(a.Hp + 1) * sizeof(float), stream, a,
+                 ws, kd_out);
+    }
+    if (!(parts & 2)) return cudaGetLastError();
     int dev = 0, sms = 152, per_sm = 8;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

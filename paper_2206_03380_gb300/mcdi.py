@@ -44,7 +44,7 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad",
            "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan",
            "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
-           "mcdi_conv3x3_wgrad"]
+           "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shade_mc_fwd.restype = st
     lib.mcdi_shade_mc_fwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, sz, P]
+    lib.mcdi_shade_mc_fwd_part.restype = st
+    lib.mcdi_shade_mc_fwd_part.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
+                                      C.POINTER(ShadeParams), P, P, P, P, P, sz, i, P]
     lib.mcdi_shade_mc_bwd.restype = st
     lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
@@ -248,6 +251,19 @@ def shade_mc_fwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeP
                                     _ptr(probe.total), _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm),
                                     _ptr(cams), N, H, W, C.byref(params), _ptr(c_d), _ptr(kd_out), _ptr(c_s),
                                     _ptr(vis_mask), _ptr(workspace), ws_bytes, _stream(stream)), "shade_mc_fwd")
+
+
+def shade_mc_fwd_part(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, c_d, kd_out, c_s,
+                      vis_mask, workspace, part: int, stream=None):
+    """Part 1 (sample generation, reads no BVH) or 2 (shadow rays and accumulation) of shade_mc_fwd."""
+    N, H, W = gb.pos.shape[:3]
+    Hp, Wp = probe.env.shape[:2]
+    _check(load().mcdi_shade_mc_fwd_part(C.byref(bvh.view), _ptr(probe.env), Wp, Hp, _ptr(probe.cond),
+                                         _ptr(probe.marg), _ptr(probe.total), _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd),
+                                         _ptr(gb.korm), _ptr(cams), N, H, W, C.byref(params), _ptr(c_d), _ptr(kd_out),
+                                         _ptr(c_s), _ptr(vis_mask), _ptr(workspace),
+                                         workspace.numel() * workspace.element_size(), int(part), _stream(stream)),
+           "shade_mc_fwd_part")
 
 
 def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, g_cd, g_kdout, g_cs,

@@ -66,6 +66,7 @@ class ShadingPipeline:
         self._loss = None
         self.workspace = None
         self._fork = None  # side stream of tables_and_geometry
+        self.overlap_generation = True  # see geometry_and_forward
         if wavefront:
             nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
             self.workspace = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
@@ -93,6 +94,40 @@ class ShadingPipeline:
     def forward(self, stream=None):
         mcdi.shade_mc_fwd(self.bvh, self.probe, self.gb, self.cams, self.params, self.c_d, self.kd_out, self.c_s,
                           self.mask, self.workspace, stream)
+
+    def forward_part(self, part: int, stream=None):
+        mcdi.shade_mc_fwd_part(self.bvh, self.probe, self.gb, self.cams, self.params, self.c_d, self.kd_out, self.c_s,
+                               self.mask, self.workspace, part, stream)
+
+    def geometry_and_forward(self, stream=None):
+        """`tables_and_geometry` then `forward`.  Launched kernel by kernel with the
+        wavefront and the rasterised G-buffer, the sample generation, which reads no
+        BVH, follows the G-buffer on the forked stream while the BVH is built on a
+        stream of the highest priority (so that its chain of small kernels gets SMs
+        before the generation's blocks), and the shadow rays follow both (measured:
+        25 us faster per headline step).  While a graph is being captured the plain
+        order is kept: replayed, the overlap gained nothing (its nodes run without
+        programmatic dependent launch)."""
+        if not (self.overlap_generation and self.workspace is not None and self.raster_ws is not None
+                and not torch.cuda.is_current_stream_capturing()):
+            self.tables_and_geometry(stream)
+            self.forward(stream)
+            return
+        cur = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if self._fork is None:
+            self._fork = torch.cuda.Stream(self.device)
+        if getattr(self, "_bvh_stream", None) is None:
+            self._bvh_stream = torch.cuda.Stream(self.device, priority=torch.cuda.Stream.priority_range()[1])
+        fork, bs = self._fork, self._bvh_stream
+        fork.wait_stream(cur)
+        bs.wait_stream(cur)
+        self.build_probe(fork)
+        self.primary(fork)
+        self.forward_part(1, fork)
+        self.build_bvh(bs)
+        cur.wait_stream(fork)
+        cur.wait_stream(bs)
+        self.forward_part(2, cur)
 
     def backward(self, g_cd, g_kdout, g_cs, stream=None, zero_env_grad=True):
         if zero_env_grad:
@@ -153,8 +188,7 @@ class ShadingPipeline:
         denoiser, composite + tonemapped L1 loss + lighting regulariser and their
         adjoint, denoiser input gradient, shading adjoint.  (L, L_image, L_light)
         stay on the device in ``self.loss``; the composite is ``self.color``."""
-        self.tables_and_geometry(stream)
-        self.forward(stream)
+        self.geometry_and_forward(stream)
         self.loss_and_backward(ref, stream, lambda_light)
 
     def image_loss(self, ref, stream=None, lambda_light: float = 0.15):

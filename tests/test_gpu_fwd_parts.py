@@ -1,0 +1,54 @@
+"""The shading forward in two calls (mcdi_shade_mc_fwd_part: sample
+generation, then shadow rays and accumulation on the same workspace) gives
+bitwise the outputs of the single call, also when the generation runs on a
+forked stream while the BVH is built on another (pipeline.geometry_and_forward
+launched kernel by kernel)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2206_03380_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _outs(pipe):
+    return [t.clone() for t in (pipe.c_d, pipe.kd_out, pipe.c_s, pipe.mask)]
+
+
+def test_forward_parts_match_the_single_call(cuda_lib):
+    from paper_2206_03380_gb300.pipeline import ShadingPipeline
+
+    sc = scenes.parity_scene()
+    pipe = ShadingPipeline(sc)
+    pipe.overlap_generation = False
+    pipe.tables_and_geometry()
+    pipe.forward()
+    torch.cuda.synchronize()
+    ref = _outs(pipe)
+    assert float(ref[0].abs().max()) > 0
+    for t in (pipe.c_d, pipe.kd_out, pipe.c_s, pipe.mask):
+        t.zero_()
+    pipe.forward_part(1)
+    pipe.forward_part(2)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, _outs(pipe)):
+        assert torch.equal(a, b)
+    # the overlapped schedule: generation beside the BVH build, on other streams
+    for t in (pipe.c_d, pipe.kd_out, pipe.c_s, pipe.mask):
+        t.zero_()
+    pipe.bvh.nodes.zero_()
+    pipe.overlap_generation = True
+    pipe.geometry_and_forward()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, _outs(pipe)):
+        assert torch.equal(a, b)
+
+
+def test_forward_part_rejects_a_bad_part(cuda_lib):
+    from paper_2206_03380_gb300.pipeline import ShadingPipeline
+
+    pipe = ShadingPipeline(scenes.parity_scene())
+    with pytest.raises(cuda_lib.McdiError) as e:
+        pipe.forward_part(3)
+    assert e.value.status == cuda_lib.INVALID_ARG
