@@ -179,6 +179,21 @@ MCDI_API mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, 
                                          float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
                                          size_t workspace_bytes, void* stream);
 
+/* mcdi_raster_gbuffer in two calls on the same workspace, so that the depth
+ * pass can run before the material textures are in device memory (for
+ * example while they are still being copied from the host): part 1 (depth)
+ * scan-converts the mesh into the workspace's depth buffer and reads only
+ * verts, tris and cams; part 2 (resolve), on a stream ordered after part 1,
+ * interpolates the winning triangle's attributes, looks up tex_kd / tex_korm
+ * and writes the four G-buffer planes.  Arguments as mcdi_raster_gbuffer; both
+ * parts must receive the same ones.  Any other part: MCDI_INVALID_ARG. */
+MCDI_API mcdi_status mcdi_raster_gbuffer_part(const float* verts, const float* vnrm, const int* tris, int n_verts,
+                                              int n_tris, const mcdi_camera* cams, int N, int H, int W,
+                                              const float* tex_kd, const float* tex_korm, int tex_size,
+                                              const float* uvmap, float* gb_pos, float* gb_nrm, float* gb_kd,
+                                              float* gb_korm, void* workspace, size_t workspace_bytes, int part,
+                                              void* stream);
+
 /* Sampling and shading parameters (host struct). */
 typedef struct {
     int n_light;              /* samples of the probe distribution            */

@@ -199,10 +199,11 @@ mcdi_status mcdi_raster_workspace_size(int N, int H, int W, size_t* bytes) {
     return ok();
 }
 
-mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
-                                const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
-                                const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos, float* gb_nrm,
-                                float* gb_kd, float* gb_korm, void* workspace, size_t workspace_bytes, void* stream) {
+static mcdi_status raster_gbuffer(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
+                                  const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                                  const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos,
+                                  float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
+                                  size_t workspace_bytes, void* stream, int parts) {
     REQUIRE(verts && vnrm && n_verts >= 1, "verts / vnrm must be non-NULL and n_verts >= 1");
     REQUIRE(n_tris >= 0 && (n_tris == 0 || tris != nullptr), "tris must be non-NULL when n_tris > 0");
     REQUIRE(((uintptr_t)verts & 3u) == 0 && ((uintptr_t)vnrm & 3u) == 0 && ((uintptr_t)tris & 3u) == 0,
@@ -224,8 +225,26 @@ mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, const int
     REQUIRE(workspace_bytes >= need, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
     return launched(mcdi::launch_raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm,
                                                 tex_size, uvmap[0], uvmap[1], uvmap[2], gb_pos, gb_nrm, gb_kd, gb_korm,
-                                                workspace, static_cast<cudaStream_t>(stream)),
+                                                workspace, static_cast<cudaStream_t>(stream), parts),
                     "raster_gbuffer");
+}
+
+mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
+                                const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                                const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos, float* gb_nrm,
+                                float* gb_kd, float* gb_korm, void* workspace, size_t workspace_bytes, void* stream) {
+    return raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size, uvmap,
+                          gb_pos, gb_nrm, gb_kd, gb_korm, workspace, workspace_bytes, stream, 3);
+}
+
+mcdi_status mcdi_raster_gbuffer_part(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
+                                     const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
+                                     const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos,
+                                     float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
+                                     size_t workspace_bytes, int part, void* stream) {
+    REQUIRE(part == 1 || part == 2, "part must be 1 (depth) or 2 (resolve), got %d", part);
+    return raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size, uvmap,
+                          gb_pos, gb_nrm, gb_kd, gb_korm, workspace, workspace_bytes, stream, part);
 }
 
 mcdi_status mcdi_shade_workspace_size(int N, int H, int W, const mcdi_shade_params* params, size_t* bytes) {

@@ -181,13 +181,16 @@ cudaError_t launch_raster_gbuffer(const float* verts, const float* vnrm, const i
                                   const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
                                   const float* tex_korm, int tex_size, float uv_ox, float uv_oz, float uv_s,
                                   float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, int parts) {
     const long long P = (long long)N * H * W;
     auto* z = static_cast<unsigned long long*>(workspace);
-    launch_k(zclear_kernel, blocks_for(P) < 4096 ? blocks_for(P) : 4096, kRasterThreads, 0, stream, z, P);
-    if (n_tris > 0)
-        launch_k(raster_kernel, blocks_for((long long)N * n_tris), kRasterThreads, 0, stream, verts, n_verts, tri_idx,
-                 n_tris, cams, N, H, W, z);
+    if (parts & 1) {  // depth pass: the mesh and the cameras only
+        launch_k(zclear_kernel, blocks_for(P) < 4096 ? blocks_for(P) : 4096, kRasterThreads, 0, stream, z, P);
+        if (n_tris > 0)
+            launch_k(raster_kernel, blocks_for((long long)N * n_tris), kRasterThreads, 0, stream, verts, n_verts,
+                     tri_idx, n_tris, cams, N, H, W, z);
+    }
+    if (!(parts & 2)) return cudaGetLastError();
     launch_k(resolve_kernel, blocks_for(P), kRasterThreads, 0, stream, (const unsigned long long*)z, verts, vnrm,
              tri_idx, n_verts, n_tris, cams, N, H, W, reinterpret_cast<const float4*>(tex_kd),
              reinterpret_cast<const float4*>(tex_korm), tex_size, uv_ox, uv_oz, uv_s,

@@ -44,7 +44,7 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad",
            "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan",
            "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
-           "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part"]
+           "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part", "mcdi_raster_gbuffer_part"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -80,6 +80,9 @@ def load(path: str = LIB_PATH):
     lib.mcdi_raster_gbuffer.restype = st
     lib.mcdi_raster_gbuffer.argtypes = [P, P, P, i, i, P, i, i, i, P, P, i, C.POINTER(C.c_float), P, P, P, P, P, sz,
                                         P]
+    lib.mcdi_raster_gbuffer_part.restype = st
+    lib.mcdi_raster_gbuffer_part.argtypes = [P, P, P, i, i, P, i, i, i, P, P, i, C.POINTER(C.c_float), P, P, P, P, P,
+                                             sz, i, P]
     lib.mcdi_shade_workspace_size.restype = st
     lib.mcdi_shade_workspace_size.argtypes = [i, i, i, C.POINTER(ShadeParams), C.POINTER(sz)]
     lib.mcdi_shade_mc_fwd.restype = st
@@ -233,6 +236,18 @@ def raster_gbuffer(verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, w
                                       _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd), _ptr(gb.korm), _ptr(workspace),
                                       workspace.numel() * workspace.element_size(), _stream(stream)),
            "raster_gbuffer")
+
+
+def raster_gbuffer_part(verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, workspace, part: int,
+                        stream=None):
+    """`raster_gbuffer` in two calls: part 1 (depth; reads the mesh and cameras only), then part 2
+    (resolve: attributes and texture lookups into the G-buffer) on a stream ordered after it."""
+    uv = (C.c_float * 3)(*[float(x) for x in uvmap])
+    _check(load().mcdi_raster_gbuffer_part(_ptr(verts), _ptr(vnrm), _ptr(tris), verts.shape[0], tris.shape[0],
+                                           _ptr(cams), cams.shape[0], int(H), int(W), _ptr(tex_kd), _ptr(tex_korm),
+                                           tex_kd.shape[0], uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd),
+                                           _ptr(gb.korm), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                           int(part), _stream(stream)), "raster_gbuffer_part")
 
 
 def shade_workspace_size(N: int, H: int, W: int, params: ShadeParams) -> int:

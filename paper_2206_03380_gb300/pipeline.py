@@ -91,6 +91,11 @@ class ShadingPipeline:
             mcdi.primary_cast(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
                               self.tex_korm, self.uvmap, self.gb, stream)
 
+    def primary_part(self, part: int, stream=None):
+        """The rasterised G-buffer in two parts: 1 = depth (mesh only), 2 = resolve (reads the textures)."""
+        mcdi.raster_gbuffer_part(self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
+                                 self.tex_korm, self.uvmap, self.gb, self.raster_ws, part, stream)
+
     def forward(self, stream=None):
         mcdi.shade_mc_fwd(self.bvh, self.probe, self.gb, self.cams, self.params, self.c_d, self.kd_out, self.c_s,
                           self.mask, self.workspace, stream)
@@ -233,55 +238,53 @@ class ShadingPipeline:
     def loss_step_io(self, ref, host_in: dict, host_ref, outputs, stream=None, lambda_light: float = 0.15):
         """`loss_step` with its host I/O overlapped: this step's inputs are copied
         from pinned host memory (``host_in``: verts, vnrm, tris, env, tex_kd,
-        tex_korm into the pipeline's buffers; ``host_ref`` into ``ref``) on
-        copy streams in the order the step first reads them (mesh, probe and
-        reference on one, each material texture on its own), and every
-        stage waits only for the inputs it reads: the BVH build for the mesh, the
-        probe tables for the probe, the rasterised G-buffer for the mesh and the
-        textures, the loss for the reference.  ``outputs`` lists (device tensor,
-        pinned host tensor) pairs read back as soon as their producer has run:
-        the loss and the composite while the denoiser input gradient and the
-        adjoint run, the rest at the end (over two streams).  Inside a captured
-        graph the waits become graph edges."""
+        tex_korm into the pipeline's buffers; ``host_ref`` into ``ref``) on one
+        copy stream in the order the step first needs them (mesh, probe, the two
+        material textures, reference: the host link is the bound, and copies on
+        several streams share it, so each input arrives earliest in sequence),
+        and every stage waits only for the inputs it reads: the BVH build and the
+        rasteriser's depth pass for the mesh, the probe tables for the probe, the
+        G-buffer's resolve for the textures, the loss for the reference.
+        ``outputs`` lists (device tensor, pinned host tensor) pairs read back as
+        soon as their producer has run: the loss and the composite while the
+        denoiser input gradient and the adjoint run, the rest at the end (over
+        two streams).  Inside a captured graph the waits become graph edges."""
         dev = self.device
         cur = stream if stream is not None else torch.cuda.current_stream(dev)
         if getattr(self, "_io", None) is None:
-            self._io = [torch.cuda.Stream(dev) for _ in range(5)]
-        up, up_kd, up_korm, down, down2 = self._io
-        streams = (up, up_kd, up_korm, down, down2)
+            self._io = [torch.cuda.Stream(dev) for _ in range(3)]
+        up, down, down2 = self._io
+        streams = (up, down, down2)
         for st in streams:
             st.wait_stream(cur)
-        ev = {k: torch.cuda.Event() for k in ("mesh", "env", "ref", "kd", "korm", "loss", "end")}
+        ev = {k: torch.cuda.Event() for k in ("mesh", "env", "tex", "ref", "loss", "end")}
         with torch.cuda.stream(up):
             for k in ("verts", "tris", "vnrm"):
                 getattr(self, k).copy_(host_in[k], non_blocking=True)
             ev["mesh"].record(up)
             self.env.copy_(host_in["env"], non_blocking=True)
             ev["env"].record(up)
+            self.tex_kd.copy_(host_in["tex_kd"], non_blocking=True)
+            self.tex_korm.copy_(host_in["tex_korm"], non_blocking=True)
+            ev["tex"].record(up)
             ref.copy_(host_ref, non_blocking=True)
             ev["ref"].record(up)
-        # the two material textures (most of the bytes) each on a stream of its own
-        with torch.cuda.stream(up_kd):
-            self.tex_kd.copy_(host_in["tex_kd"], non_blocking=True)
-            ev["kd"].record(up_kd)
-        with torch.cuda.stream(up_korm):
-            self.tex_korm.copy_(host_in["tex_korm"], non_blocking=True)
-            ev["korm"].record(up_korm)
         if self._fork is None:
             self._fork = torch.cuda.Stream(dev)
         fork = self._fork
         fork.wait_stream(cur)
+        fork.wait_event(ev["mesh"])
+        if self.raster_ws is not None:
+            self.primary_part(1, fork)
         fork.wait_event(ev["env"])
         self.build_probe(fork)
         if self.raster_ws is not None:
-            for k in ("mesh", "kd", "korm"):
-                fork.wait_event(ev[k])
-            self.primary(fork)
+            fork.wait_event(ev["tex"])
+            self.primary_part(2, fork)
         cur.wait_event(ev["mesh"])
         self.build_bvh(cur)
         if self.raster_ws is None:
-            for k in ("kd", "korm"):
-                cur.wait_event(ev[k])
+            cur.wait_event(ev["tex"])
             self.primary(cur)
         cur.wait_stream(fork)
         self.forward(cur)

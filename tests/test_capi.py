@@ -116,3 +116,7 @@ def test_raster_argument_checks_without_gpu(lib):
     bad[13] = C.c_void_p(4100)  # gb_pos not 16-byte aligned
     assert lib.mcdi_raster_gbuffer(*bad, n.value, None) == mcdi.INVALID_ARG
     assert b"gb_pos" in lib.mcdi_last_error()
+    assert lib.mcdi_raster_gbuffer_part(*args, n.value, 3, None) == mcdi.INVALID_ARG
+    assert b"part" in lib.mcdi_last_error()
+    assert lib.mcdi_raster_gbuffer_part(*args, n.value - 1, 1, None) == mcdi.INVALID_ARG
+    assert b"workspace" in lib.mcdi_last_error()

@@ -2,7 +2,9 @@
 generation, then shadow rays and accumulation on the same workspace) gives
 bitwise the outputs of the single call, also when the generation runs on a
 forked stream while the BVH is built on another (pipeline.geometry_and_forward
-launched kernel by kernel)."""
+launched kernel by kernel).  Likewise the rasterised G-buffer in two calls
+(mcdi_raster_gbuffer_part: depth from the mesh, then the resolve that reads
+the textures), also with the textures written only between the two."""
 import numpy as np
 import pytest
 import torch
@@ -51,4 +53,35 @@ def test_forward_part_rejects_a_bad_part(cuda_lib):
     pipe = ShadingPipeline(scenes.parity_scene())
     with pytest.raises(cuda_lib.McdiError) as e:
         pipe.forward_part(3)
+    assert e.value.status == cuda_lib.INVALID_ARG
+
+
+def _gb(pipe):
+    return [t.clone() for t in (pipe.gb.pos, pipe.gb.nrm, pipe.gb.kd, pipe.gb.korm)]
+
+
+def test_raster_parts_match_the_single_call(cuda_lib):
+    from paper_2206_03380_gb300.pipeline import ShadingPipeline
+
+    pipe = ShadingPipeline(scenes.parity_scene())
+    assert pipe.raster_ws is not None
+    pipe.primary()
+    torch.cuda.synchronize()
+    ref = _gb(pipe)
+    assert float(ref[0][..., 3].sum()) > 0 and float(ref[2].abs().max()) > 0
+    tex = pipe.tex_kd.clone(), pipe.tex_korm.clone()
+    for t in (pipe.gb.pos, pipe.gb.nrm, pipe.gb.kd, pipe.gb.korm, pipe.tex_kd, pipe.tex_korm):
+        t.zero_()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    pipe.primary_part(1, side)  # the depth pass reads no texture
+    torch.cuda.current_stream().wait_stream(side)
+    pipe.tex_kd.copy_(tex[0])
+    pipe.tex_korm.copy_(tex[1])
+    pipe.primary_part(2)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, _gb(pipe)):
+        assert torch.equal(a, b)
+    with pytest.raises(cuda_lib.McdiError) as e:
+        pipe.primary_part(0)
     assert e.value.status == cuda_lib.INVALID_ARG
