@@ -282,6 +282,24 @@ MCDI_API mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* en
                               const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm, float* g_env,
                               void* stream);
 
+/* mcdi_shade_mc_bwd restricted to the pixels [first, first + count) of the
+ * flattened [N][H][W] image (index (view H + y) W + x): writes g_kd, g_korm
+ * and g_nrm of those pixels only and accumulates their probe-texel gradients
+ * into g_env.  Every pixel's gradient is computed alone, so calls over
+ * disjoint spans that cover the image write the per-pixel outputs of one
+ * mcdi_shade_mc_bwd bit for bit (g_env: the same sum in another atomic
+ * order); a caller can then read back each span's outputs while the next span
+ * runs.  count = 0 launches nothing.  A span outside the image or count < 0:
+ * MCDI_INVALID_ARG.  Other arguments as mcdi_shade_mc_bwd. */
+MCDI_API mcdi_status mcdi_shade_mc_bwd_span(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp,
+                                            const float* cond_cdf, const float* marg_cdf, const double* total,
+                                            const float* gb_pos, const float* gb_nrm, const float* gb_kd,
+                                            const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                                            const mcdi_shade_params* params, const float* g_cd,
+                                            const float* g_kdout, const float* g_cs, const uint32_t* vis_mask,
+                                            float* g_kd, float* g_korm, float* g_nrm, float* g_env, long long first,
+                                            long long count, void* stream);
+
 /* ------------------------------------------------------------------------
  * Shadow-visibility gradients (the ablation of the paper's appendix
  * "Visibility gradients from shadows"; off in the paper's main results, where

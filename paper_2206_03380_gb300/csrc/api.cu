@@ -466,16 +466,20 @@ mcdi_status mcdi_read_sweep(const void* buf, size_t bytes, int passes, unsigned*
                     "read_sweep");
 }
 
-mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
-                              const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
-                              const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
-                              const mcdi_shade_params* params, const float* g_cd, const float* g_kdout,
-                              const float* g_cs, const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm,
-                              float* g_env, void* stream) {
+static mcdi_status shade_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                             const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
+                             const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                             const mcdi_shade_params* params, const float* g_cd, const float* g_kdout,
+                             const float* g_cs, const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm,
+                             float* g_env, long long first, long long count, void* stream) {
     mcdi::ShadeArgs a;
     mcdi_status s = shade_common(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N,
                                  H, W, params, &a);
     if (s != MCDI_OK) return s;
+    const long long P = (long long)N * H * W;
+    if (count < 0) count = P;
+    REQUIRE(first >= 0 && first <= P && count <= P - first,
+            "pixel span [%lld, %lld + %lld) outside the %lld pixels of [N][H][W]", first, first, count, P);
     REQUIRE_BUF16(g_cd);
     REQUIRE_BUF16(g_kdout);
     REQUIRE_BUF16(g_cs);
@@ -494,8 +498,30 @@ mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp
                                            reinterpret_cast<const float4*>(g_cs), mask,
                                            reinterpret_cast<float4*>(g_kd), reinterpret_cast<float4*>(g_korm),
                                            reinterpret_cast<float4*>(g_nrm), reinterpret_cast<float4*>(g_env),
-                                           static_cast<cudaStream_t>(stream)),
+                                           static_cast<cudaStream_t>(stream), first, count),
                     "shade_mc_bwd");
+}
+
+mcdi_status mcdi_shade_mc_bwd(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp, const float* cond_cdf,
+                              const float* marg_cdf, const double* total, const float* gb_pos, const float* gb_nrm,
+                              const float* gb_kd, const float* gb_korm, const mcdi_camera* cams, int N, int H, int W,
+                              const mcdi_shade_params* params, const float* g_cd, const float* g_kdout,
+                              const float* g_cs, const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm,
+                              float* g_env, void* stream) {
+    return shade_bwd(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N, H, W,
+                     params, g_cd, g_kdout, g_cs, vis_mask, g_kd, g_korm, g_nrm, g_env, 0, -1, stream);
+}
+
+mcdi_status mcdi_shade_mc_bwd_span(const mcdi_bvh_view* bvh, const float* env, int Wp, int Hp,
+                                   const float* cond_cdf, const float* marg_cdf, const double* total,
+                                   const float* gb_pos, const float* gb_nrm, const float* gb_kd, const float* gb_korm,
+                                   const mcdi_camera* cams, int N, int H, int W, const mcdi_shade_params* params,
+                                   const float* g_cd, const float* g_kdout, const float* g_cs,
+                                   const uint32_t* vis_mask, float* g_kd, float* g_korm, float* g_nrm, float* g_env,
+                                   long long first, long long count, void* stream) {
+    REQUIRE(count >= 0, "count must be >= 0, got %lld", count);
+    return shade_bwd(bvh, env, Wp, Hp, cond_cdf, marg_cdf, total, gb_pos, gb_nrm, gb_kd, gb_korm, cams, N, H, W,
+                     params, g_cd, g_kdout, g_cs, vis_mask, g_kd, g_korm, g_nrm, g_env, first, count, stream);
 }
 
 mcdi_status mcdi_denoise_sizes(int n_img, int H, int W, int precision, size_t* weight_bytes, size_t* act_bytes,

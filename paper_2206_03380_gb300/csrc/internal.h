@@ -128,7 +128,7 @@ cudaError_t launch_read_sweep(const void* buf, size_t bytes, int passes, unsigne
 
 cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float4* g_kdout, const float4* g_cs,
                              const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,
-                             cudaStream_t stream);
+                             cudaStream_t stream, long long first = 0, long long count = -1);
 
 // ---- denoiser (U-Net of 15 3x3 convolutions; denoise.cu)
 constexpr int kUnetConvs = 15;

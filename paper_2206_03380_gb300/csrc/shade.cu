@@ -126,16 +126,16 @@ __global__ void __launch_bounds__(kShadeThreads, 6) shade_bwd_kernel(ShadeArgs a
                                                                   float4* __restrict__ g_kd,
                                                                   float4* __restrict__ g_korm,
                                                                   float4* __restrict__ g_nrm,
-                                                                  float4* __restrict__ g_env) {
+                                                                  float4* __restrict__ g_env, long long first,
+                                                                  long long end) {
     pdl_prologue();
     extern __shared__ float s_marg[];  // marginal CDF, then [kBwdQuarters][kBwdPartials][32] partial sums
     Probe Pr = make_probe(a);
     stage_marginal(Pr, s_marg);
     float* s_part = s_marg + ((a.Hp + 1 + 3) & ~3);
     const int lane = threadIdx.x & 31, quarter = threadIdx.x >> 5;
-    const long long idx = (long long)blockIdx.x * 32 + lane;
-    const long long P = (long long)a.N * a.H * a.W;
-    const bool in_range = idx < P;
+    const long long idx = first + (long long)blockIdx.x * 32 + lane;  // pixels [first, end) of [N][H][W]
+    const bool in_range = idx < end;
     const int view = in_range ? (int)(idx / ((long long)a.H * a.W)) : 0;
     const uint32_t pix = (uint32_t)(idx - (long long)view * a.H * a.W);
     const int spp = a.n_light + a.n_cos + a.n_ggx;
@@ -282,11 +282,13 @@ cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, fl
 
 cudaError_t launch_shade_bwd(const ShadeArgs& a, const float4* g_cd, const float4* g_kdout, const float4* g_cs,
                              const uint32_t* vis_mask, float4* g_kd, float4* g_korm, float4* g_nrm, float4* g_env,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, long long first, long long count) {
     const long long P = (long long)a.N * a.H * a.W;
+    if (count < 0) count = P - first;
+    if (count <= 0) return cudaSuccess;
     const size_t smem = (size_t)(((a.Hp + 1 + 3) & ~3) + kBwdQuarters * kBwdPartials * 32) * sizeof(float);
-    launch_k(shade_bwd_kernel, grid_for(P, 32), kShadeThreads, smem, stream, a, g_cd, g_kdout, g_cs, vis_mask, g_kd,
-             g_korm, g_nrm, g_env);
+    launch_k(shade_bwd_kernel, grid_for(count, 32), kShadeThreads, smem, stream, a, g_cd, g_kdout, g_cs, vis_mask,
+             g_kd, g_korm, g_nrm, g_env, first, first + count);
     return cudaGetLastError();
 }
 

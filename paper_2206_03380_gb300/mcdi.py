@@ -44,7 +44,8 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_edge_table_workspace_size", "mcdi_build_edge_table", "mcdi_shadow_edge_grad",
            "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan",
            "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
-           "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part", "mcdi_raster_gbuffer_part"]
+           "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part", "mcdi_raster_gbuffer_part",
+           "mcdi_shade_mc_bwd_span"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -94,6 +95,10 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shade_mc_bwd.restype = st
     lib.mcdi_shade_mc_bwd.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
                                       C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, P]
+    lib.mcdi_shade_mc_bwd_span.restype = st
+    lib.mcdi_shade_mc_bwd_span.argtypes = [C.POINTER(BvhView), P, i, i, P, P, P, P, P, P, P, P, i, i, i,
+                                           C.POINTER(ShadeParams), P, P, P, P, P, P, P, P, C.c_longlong,
+                                           C.c_longlong, P]
     lib.mcdi_shadow_ray_stats.restype = st
     lib.mcdi_shadow_ray_stats.argtypes = [C.POINTER(BvhView), i, i, i, C.POINTER(ShadeParams), P, sz, P, P]
     lib.mcdi_shadow_ray_retrace.restype = st
@@ -290,6 +295,19 @@ def shade_mc_bwd(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeP
                                     _ptr(cams), N, H, W, C.byref(params), _ptr(g_cd), _ptr(g_kdout), _ptr(g_cs),
                                     _ptr(vis_mask), _ptr(g_kd), _ptr(g_korm), _ptr(g_nrm), _ptr(g_env),
                                     _stream(stream)), "shade_mc_bwd")
+
+
+def shade_mc_bwd_span(bvh: "Bvh", probe: "Probe", gb: "GBuffer", cams, params: ShadeParams, g_cd, g_kdout, g_cs,
+                      vis_mask, g_kd, g_korm, g_nrm, g_env, first: int, count: int, stream=None):
+    """`shade_mc_bwd` for the pixels [first, first + count) of the flattened [N][H][W] image only."""
+    N, H, W = gb.pos.shape[:3]
+    Hp, Wp = probe.env.shape[:2]
+    _check(load().mcdi_shade_mc_bwd_span(C.byref(bvh.view), _ptr(probe.env), Wp, Hp, _ptr(probe.cond),
+                                         _ptr(probe.marg), _ptr(probe.total), _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd),
+                                         _ptr(gb.korm), _ptr(cams), N, H, W, C.byref(params), _ptr(g_cd),
+                                         _ptr(g_kdout), _ptr(g_cs), _ptr(vis_mask), _ptr(g_kd), _ptr(g_korm),
+                                         _ptr(g_nrm), _ptr(g_env), int(first), int(count), _stream(stream)),
+           "shade_mc_bwd_span")
 
 
 def shadow_ray_stats(bvh: "Bvh", N: int, H: int, W: int, params: ShadeParams, workspace, stats, stream=None):

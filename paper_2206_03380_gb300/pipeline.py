@@ -67,6 +67,8 @@ class ShadingPipeline:
         self.workspace = None
         self._fork = None  # side stream of tables_and_geometry
         self.overlap_generation = True  # see geometry_and_forward
+        # pixel spans of the adjoint in loss_step_io (fractions of the image, None = the rest)
+        self.bwd_span_fractions = (0.5, 0.3, None)
         if wavefront:
             nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
             self.workspace = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
@@ -139,6 +141,11 @@ class ShadingPipeline:
             self.g_env.zero_()
         mcdi.shade_mc_bwd(self.bvh, self.probe, self.gb, self.cams, self.params, g_cd, g_kdout, g_cs, self.mask,
                           self.g_kd, self.g_korm, self.g_nrm, self.g_env, stream)
+
+    def backward_span(self, g_cd, g_kdout, g_cs, first: int, count: int, stream=None):
+        """`backward` for the pixels [first, first + count) only; g_env accumulates (zero it first)."""
+        mcdi.shade_mc_bwd_span(self.bvh, self.probe, self.gb, self.cams, self.params, g_cd, g_kdout, g_cs,
+                               self.mask, self.g_kd, self.g_korm, self.g_nrm, self.g_env, first, count, stream)
 
     def denoise(self, stream=None):
         """D(c_d), D(c_s): the U-Net with k_d,out and the normal as guides (Sec. 4.2), or
@@ -295,7 +302,8 @@ class ShadingPipeline:
         self.image_loss(ref, cur, lambda_light)
         ev["loss"].record(cur)
         early = [(d, h) for d, h in outputs if d is self.loss or d is self.color]
-        late = [(d, h) for d, h in outputs if not (d is self.loss or d is self.color)]
+        per_pixel = [(d, h) for d, h in outputs if any(d is t for t in (self.g_kd, self.g_korm, self.g_nrm))]
+        late = [(d, h) for d, h in outputs if not any(d is t for t, _ in early + per_pixel)]
         down.wait_event(ev["loss"])
         with torch.cuda.stream(down):
             for d, h in early:
@@ -304,13 +312,28 @@ class ShadingPipeline:
         if self.denoiser is not None:
             self.denoise_backward(self.g_loss_terms, cur)
             g_cd, g_cs = self.g_terms[:N], self.g_terms[N:]
-        self.backward(g_cd, self.g_loss_kdout, g_cs, cur)
+        # the adjoint in pixel spans, each span's per-pixel gradients read back while the next one
+        # runs; the spans shrink so that little is left to copy after the last (the probe gradient,
+        # summed over all pixels, follows it)
+        self.g_env.zero_()
+        P = self.N * self.H * self.W
+        first = 0
+        for frac in self.bwd_span_fractions:
+            count = P - first if frac is None else min(P - first, int(round(P * frac / 32.0)) * 32)
+            self.backward_span(g_cd, self.g_loss_kdout, g_cs, first, count, cur)
+            if per_pixel:
+                e = torch.cuda.Event()
+                e.record(cur)
+                down2.wait_event(e)
+                with torch.cuda.stream(down2):
+                    for d, h in per_pixel:
+                        h.view(-1, 4)[first:first + count].copy_(d.view(-1, 4)[first:first + count], non_blocking=True)
+            first += count
         ev["end"].record(cur)
-        for i, st in enumerate((down, down2)):  # the late read-backs split over two streams
-            st.wait_event(ev["end"])
-            with torch.cuda.stream(st):
-                for d, h in late[i::2]:
-                    h.copy_(d, non_blocking=True)
+        down.wait_event(ev["end"])
+        with torch.cuda.stream(down):
+            for d, h in late:
+                h.copy_(d, non_blocking=True)
         for st in streams:
             cur.wait_stream(st)
 

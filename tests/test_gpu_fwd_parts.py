@@ -4,7 +4,10 @@ bitwise the outputs of the single call, also when the generation runs on a
 forked stream while the BVH is built on another (pipeline.geometry_and_forward
 launched kernel by kernel).  Likewise the rasterised G-buffer in two calls
 (mcdi_raster_gbuffer_part: depth from the mesh, then the resolve that reads
-the textures), also with the textures written only between the two."""
+the textures), also with the textures written only between the two, and the
+adjoint over disjoint pixel spans (mcdi_shade_mc_bwd_span): per-pixel
+gradients bitwise those of one call, the probe gradient (summed by atomics in
+no fixed order) to 1e-5 of its largest entry."""
 import numpy as np
 import pytest
 import torch
@@ -85,3 +88,34 @@ def test_raster_parts_match_the_single_call(cuda_lib):
     with pytest.raises(cuda_lib.McdiError) as e:
         pipe.primary_part(0)
     assert e.value.status == cuda_lib.INVALID_ARG
+
+
+def test_adjoint_spans_match_the_single_call(cuda_lib):
+    from paper_2206_03380_gb300.pipeline import ShadingPipeline
+
+    sc = scenes.parity_scene()
+    pipe = ShadingPipeline(sc)
+    pipe.tables_and_geometry()
+    pipe.forward()
+    rng = np.random.default_rng(5)
+    g = [torch.from_numpy(rng.normal(size=pipe.c_d.shape).astype(np.float32)).cuda() for _ in range(3)]
+    pipe.backward(*g)
+    torch.cuda.synchronize()
+    outs = (pipe.g_kd, pipe.g_korm, pipe.g_nrm, pipe.g_env)
+    ref = [t.clone() for t in outs]
+    assert float(ref[0].abs().max()) > 0 and float(ref[3].abs().max()) > 0
+    for t in outs:
+        t.fill_(float("nan"))
+    pipe.g_env.zero_()
+    P = pipe.c_d.shape[0] * pipe.c_d.shape[1] * pipe.c_d.shape[2]
+    cuts = [0, 37, P // 3, P // 3, P - 1, P]  # ragged spans, an empty one, a single pixel
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        pipe.backward_span(*g, a, b - a)
+    torch.cuda.synchronize()
+    for a, b in zip(ref[:3], outs[:3]):
+        assert torch.equal(a, b)
+    torch.testing.assert_close(outs[3], ref[3], rtol=0, atol=1e-5 * float(ref[3].abs().max()))
+    for first, count in ((P, 1), (-1, 2), (0, -1), (P - 3, 4)):
+        with pytest.raises(cuda_lib.McdiError) as e:
+            pipe.backward_span(*g, first, count)
+        assert e.value.status == cuda_lib.INVALID_ARG
