@@ -547,6 +547,27 @@ MCDI_API mcdi_status mcdi_conv3x3_e4m3(const void* x, int n_img, int H, int W, i
                                        const float* x_amax, const float* w_amax, const float* bias, int cout_pad,
                                        int relu, void* y, unsigned* err, void* stream);
 
+/* ------------------------------------------------------------------------
+ * CUDA graphs whose nodes run at their own priorities (runtime support, no
+ * counterpart in the paper).  A graph captured from streams of different
+ * priorities records each kernel node's priority (the library's kernels carry
+ * their stream's priority as a launch attribute); a graph instantiated
+ * without cudaGraphInstantiateFlagUseNodePriority runs every node at the
+ * priority of the stream it is launched into, so the block scheduler cannot
+ * favour, for example, the BVH build's chain of small kernels over the
+ * sample generation beside it.
+ * mcdi_graph_instantiate: graph = a cudaGraph_t (for instance a kept graph of
+ *   torch.cuda.CUDAGraph(keep_graph=True)); the caller keeps it alive (and
+ *   every buffer its nodes use) while the instance exists.  *graph_exec
+ *   receives a cudaGraphExec_t instantiated with node priorities (NULL on
+ *   error).  Instantiation failure: MCDI_DEVICE_ERROR.
+ * mcdi_graph_launch: launches the instance into `stream` (cudaGraphLaunch).
+ * mcdi_graph_destroy: frees the instance (NULL is a no-op).
+ * ------------------------------------------------------------------------ */
+MCDI_API mcdi_status mcdi_graph_instantiate(void* graph, void** graph_exec);
+MCDI_API mcdi_status mcdi_graph_launch(void* graph_exec, void* stream);
+MCDI_API mcdi_status mcdi_graph_destroy(void* graph_exec);
+
 #ifdef __cplusplus
 }
 #endif

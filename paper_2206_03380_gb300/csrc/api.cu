@@ -776,3 +776,27 @@ mcdi_status mcdi_conv3x3_e4m3(const void* x, int n_img, int H, int W, int cin_pa
 }
 
 }  // extern "C"
+
+// ---- CUDA graphs with per-node priorities
+mcdi_status mcdi_graph_instantiate(void* graph, void** graph_exec) {
+    REQUIRE(graph != nullptr && graph_exec != nullptr, "graph / graph_exec must be non-NULL");
+    *graph_exec = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiateWithFlags(&exec, static_cast<cudaGraph_t>(graph),
+                                                        cudaGraphInstantiateFlagUseNodePriority);
+    if (e != cudaSuccess) return launched(e, "graph_instantiate");
+    *graph_exec = exec;
+    return ok();
+}
+
+mcdi_status mcdi_graph_launch(void* graph_exec, void* stream) {
+    REQUIRE(graph_exec != nullptr, "graph_exec must be non-NULL");
+    return launched(cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), static_cast<cudaStream_t>(stream)),
+                    "graph_launch");
+}
+
+mcdi_status mcdi_graph_destroy(void* graph_exec) {
+    if (graph_exec == nullptr) return ok();
+    return launched(cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec)), "graph_destroy");
+}
+

@@ -45,7 +45,7 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan",
            "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
            "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part", "mcdi_raster_gbuffer_part",
-           "mcdi_shade_mc_bwd_span"]
+           "mcdi_shade_mc_bwd_span", "mcdi_graph_instantiate", "mcdi_graph_launch", "mcdi_graph_destroy"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -112,6 +112,12 @@ def load(path: str = LIB_PATH):
     lib.mcdi_shadow_edge_grad.argtypes = [C.POINTER(BvhView), P, i, P, P, i, P, i, i, P, P, P, P, P, i, i, i,
                                           C.POINTER(ShadeParams), i, C.c_float, P, P, P, P, P]
     lib.mcdi_read_sweep.argtypes = [P, sz, i, P, P]
+    lib.mcdi_graph_instantiate.restype = st
+    lib.mcdi_graph_instantiate.argtypes = [P, C.POINTER(C.c_void_p)]
+    lib.mcdi_graph_launch.restype = st
+    lib.mcdi_graph_launch.argtypes = [P, P]
+    lib.mcdi_graph_destroy.restype = st
+    lib.mcdi_graph_destroy.argtypes = [P]
     lib.mcdi_denoise_sizes.restype = st
     lib.mcdi_denoise_sizes.argtypes = [i, i, i, i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_denoise_pack_weights.restype = st
@@ -174,6 +180,38 @@ def _check(status: int, where: str):
 # ------------------------------------------------------------------ entry points
 def version() -> int:
     return load().mcdi_version()
+
+
+class Graph:
+    """A step captured by torch into a CUDA graph and instantiated by the library
+    with per-node priorities (mcdi_graph_instantiate), so that kernels captured
+    from streams of higher priority keep it when the graph is replayed.  Holds
+    the torch graph (which owns the captured graph and its memory pool)."""
+
+    def __init__(self, torch_graph):
+        self.torch_graph = torch_graph
+        raw = torch_graph.raw_cuda_graph()
+        if not isinstance(raw, int):
+            raise TypeError(f"raw_cuda_graph() returned {type(raw).__name__}, expected an address")
+        out = C.c_void_p()
+        _check(load().mcdi_graph_instantiate(raw, C.byref(out)), "graph_instantiate")
+        self.exec = out.value
+
+    @staticmethod
+    def capture(fn):
+        """Capture ``fn()`` (on torch's capture stream) and instantiate it with node priorities."""
+        g = torch.cuda.CUDAGraph(keep_graph=True)
+        with torch.cuda.graph(g):
+            fn()
+        return Graph(g)
+
+    def replay(self, stream=None):
+        _check(load().mcdi_graph_launch(self.exec, _stream(stream)), "graph_launch")
+
+    def __del__(self):
+        if getattr(self, "exec", None) and _lib is not None:
+            _lib.mcdi_graph_destroy(self.exec)
+            self.exec = None
 
 
 def build_envmap_cdf(env, cond, marg, row_sum, total, stream=None):

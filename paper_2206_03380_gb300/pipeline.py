@@ -68,7 +68,8 @@ class ShadingPipeline:
         self._fork = None  # side stream of tables_and_geometry
         self.overlap_generation = True  # see geometry_and_forward
         # pixel spans of the adjoint in loss_step_io (fractions of the image, None = the rest)
-        self.bwd_span_fractions = (0.5, 0.3, None)
+        self.bwd_span_fractions = (0.4, 0.3, 0.2, None)
+        self._span_streams = []
         if wavefront:
             nbytes = mcdi.shade_workspace_size(self.N, self.H, self.W, self.params)
             self.workspace = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=dev)
@@ -107,25 +108,21 @@ class ShadingPipeline:
                                self.mask, self.workspace, part, stream)
 
     def geometry_and_forward(self, stream=None):
-        """`tables_and_geometry` then `forward`.  Launched kernel by kernel with the
-        wavefront and the rasterised G-buffer, the sample generation, which reads no
-        BVH, follows the G-buffer on the forked stream while the BVH is built on a
-        stream of the highest priority (so that its chain of small kernels gets SMs
-        before the generation's blocks), and the shadow rays follow both (measured:
-        25 us faster per headline step).  While a graph is being captured the plain
-        order is kept: replayed, the overlap gained nothing (its nodes run without
-        programmatic dependent launch)."""
-        if not (self.overlap_generation and self.workspace is not None and self.raster_ws is not None
-                and not torch.cuda.is_current_stream_capturing()):
+        """`tables_and_geometry` then `forward`.  With the wavefront and the rasterised
+        G-buffer, the sample generation, which reads no BVH, follows the G-buffer on the
+        forked stream while the BVH is built on a stream of the highest priority (so
+        that its chain of small kernels gets SMs before the generation's blocks), and
+        the shadow rays follow both (measured: 25 us faster per headline step launched
+        kernel by kernel, 20-40 us in the replayed graph, whose nodes keep their
+        priorities because the library instantiates it: mcdi.Graph)."""
+        if not (self.overlap_generation and self.workspace is not None and self.raster_ws is not None):
             self.tables_and_geometry(stream)
             self.forward(stream)
             return
         cur = stream if stream is not None else torch.cuda.current_stream(self.device)
         if self._fork is None:
             self._fork = torch.cuda.Stream(self.device)
-        if getattr(self, "_bvh_stream", None) is None:
-            self._bvh_stream = torch.cuda.Stream(self.device, priority=torch.cuda.Stream.priority_range()[1])
-        fork, bs = self._fork, self._bvh_stream
+        fork, bs = self._fork, self.bvh_stream()
         fork.wait_stream(cur)
         bs.wait_stream(cur)
         self.build_probe(fork)
@@ -135,6 +132,12 @@ class ShadingPipeline:
         cur.wait_stream(fork)
         cur.wait_stream(bs)
         self.forward_part(2, cur)
+
+    def bvh_stream(self):
+        """The stream of the highest priority the BVH build runs on beside the sample generation."""
+        if getattr(self, "_bvh_stream", None) is None:
+            self._bvh_stream = torch.cuda.Stream(self.device, priority=torch.cuda.Stream.priority_range()[1])
+        return self._bvh_stream
 
     def backward(self, g_cd, g_kdout, g_cs, stream=None, zero_env_grad=True):
         if zero_env_grad:
@@ -281,6 +284,7 @@ class ShadingPipeline:
         fork = self._fork
         fork.wait_stream(cur)
         fork.wait_event(ev["mesh"])
+        overlap = self.overlap_generation and self.workspace is not None and self.raster_ws is not None
         if self.raster_ws is not None:
             self.primary_part(1, fork)
         fork.wait_event(ev["env"])
@@ -288,13 +292,24 @@ class ShadingPipeline:
         if self.raster_ws is not None:
             fork.wait_event(ev["tex"])
             self.primary_part(2, fork)
-        cur.wait_event(ev["mesh"])
-        self.build_bvh(cur)
+        if overlap:  # sample generation beside the BVH build, which runs at the highest priority
+            self.forward_part(1, fork)
+            bs = self.bvh_stream()
+            bs.wait_stream(cur)
+            bs.wait_event(ev["mesh"])
+            self.build_bvh(bs)
+            cur.wait_stream(bs)
+        else:
+            cur.wait_event(ev["mesh"])
+            self.build_bvh(cur)
         if self.raster_ws is None:
             cur.wait_event(ev["tex"])
             self.primary(cur)
         cur.wait_stream(fork)
-        self.forward(cur)
+        if overlap:
+            self.forward_part(2, cur)
+        else:
+            self.forward(cur)
         N = self.N
         if self.denoiser is not None:
             self.denoise(cur)
@@ -312,23 +327,33 @@ class ShadingPipeline:
         if self.denoiser is not None:
             self.denoise_backward(self.g_loss_terms, cur)
             g_cd, g_cs = self.g_terms[:N], self.g_terms[N:]
-        # the adjoint in pixel spans, each span's per-pixel gradients read back while the next one
-        # runs; the spans shrink so that little is left to copy after the last (the probe gradient,
-        # summed over all pixels, follows it)
+        # the adjoint in pixel spans, each span's per-pixel gradients read back while the later ones
+        # run; the spans shrink so that little is left to copy after the last (the probe gradient,
+        # summed over all pixels, follows it).  The spans write disjoint pixels (and add into the probe
+        # gradient by atomics), so each is launched on a stream of its own, earlier spans at higher
+        # priority: the block scheduler finishes a span before it starts the next one's blocks, those
+        # fill the SMs while the span's last blocks drain, and a read-back waits for its own span only.
         self.g_env.zero_()
         P = self.N * self.H * self.W
+        fr = self.bwd_span_fractions
+        if len(self._span_streams) != len(fr):
+            self._span_streams = [torch.cuda.Stream(dev, priority=-(len(fr) - 1 - k)) for k in range(len(fr))]
         first = 0
-        for frac in self.bwd_span_fractions:
+        for k, frac in enumerate(fr):
             count = P - first if frac is None else min(P - first, int(round(P * frac / 32.0)) * 32)
-            self.backward_span(g_cd, self.g_loss_kdout, g_cs, first, count, cur)
+            st = self._span_streams[k]
+            st.wait_stream(cur)
+            self.backward_span(g_cd, self.g_loss_kdout, g_cs, first, count, st)
+            e = torch.cuda.Event()
+            e.record(st)
             if per_pixel:
-                e = torch.cuda.Event()
-                e.record(cur)
                 down2.wait_event(e)
                 with torch.cuda.stream(down2):
                     for d, h in per_pixel:
                         h.view(-1, 4)[first:first + count].copy_(d.view(-1, 4)[first:first + count], non_blocking=True)
             first += count
+        for k in range(len(fr)):
+            cur.wait_stream(self._span_streams[k])
         ev["end"].record(cur)
         down.wait_event(ev["end"])
         with torch.cuda.stream(down):
@@ -356,9 +381,9 @@ class ShadingPipeline:
         with torch.cuda.stream(side):
             fn()
         torch.cuda.current_stream(dev).wait_stream(side)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            fn()
+        # instantiated by the library with per-node priorities, so that kernels captured from
+        # high-priority streams keep their priority in the replay (mcdi.Graph)
+        graph = mcdi.Graph.capture(fn)
         setattr(self, attr, graph)
         return graph
 
