@@ -120,3 +120,14 @@ def test_raster_argument_checks_without_gpu(lib):
     assert b"part" in lib.mcdi_last_error()
     assert lib.mcdi_raster_gbuffer_part(*args, n.value - 1, 1, None) == mcdi.INVALID_ARG
     assert b"workspace" in lib.mcdi_last_error()
+
+
+def test_graph_entry_points_check_arguments_without_gpu(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    out = C.c_void_p(1234)
+    assert lib.mcdi_graph_instantiate(None, C.byref(out)) == mcdi.INVALID_ARG
+    assert lib.mcdi_graph_instantiate(C.c_void_p(4096), None) == mcdi.INVALID_ARG
+    assert lib.mcdi_graph_launch(None, None) == mcdi.INVALID_ARG
+    assert b"graph_exec" in lib.mcdi_last_error()
+    assert lib.mcdi_graph_destroy(None) == mcdi.OK
