@@ -7,9 +7,12 @@
 // allowed to start before its predecessor completes — except while the
 // stream is being captured into a CUDA graph, whose replay already launches
 // back to back (measured: the mark saves about 80 us per headline step
-// launched kernel by kernel and costs about 30 us in the replayed graph; with
-// the convolutions' weight loads ahead of their wait it is a wash there).  For
-// a kernel launched without the mark the prologue's wait returns at once.
+// launched kernel by kernel; on every node of the replayed graph it costs
+// about 40 us).  The convolutions, which allocate tensor memory and load their
+// weights before they wait, launch through launch_k_dependent, which keeps
+// the mark in the graph too (a programmatic edge from the preceding kernel
+// node): 40 us less per replayed headline step.  For a kernel launched without
+// the mark the prologue's wait returns at once.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,8 +35,8 @@ __device__ __forceinline__ void pdl_allow_dependents() {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
-                            Args&&... args) {
+inline cudaError_t launch_k_impl(bool dependent_in_graph, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                 size_t smem, cudaStream_t stream, Args&&... args) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -43,7 +46,7 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     unsigned n_attr = 0;
     cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(stream, &capture) != cudaSuccess) capture = cudaStreamCaptureStatusNone;
-    if (capture == cudaStreamCaptureStatusNone) {
+    if (capture == cudaStreamCaptureStatusNone || dependent_in_graph) {
         attr[n_attr].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[n_attr++].val.programmaticStreamSerializationAllowed = 1;
     }
@@ -56,6 +59,21 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     cfg.attrs = n_attr ? attr : nullptr;
     cfg.numAttrs = n_attr;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                            Args&&... args) {
+    return launch_k_impl(false, kernel, grid, block, smem, stream, std::forward<Args>(args)...);
+}
+
+// launch_k that keeps the programmatic dependence also inside a captured graph
+// (a programmatic edge from the preceding kernel node): for kernels whose
+// set-up before pdl_wait() is long enough to pay for it
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                      cudaStream_t stream, Args&&... args) {
+    return launch_k_impl(true, kernel, grid, block, smem, stream, std::forward<Args>(args)...);
 }
 
 }  // namespace mcdi

@@ -921,9 +921,11 @@ template <bool FP8, bool MP, bool PL>
 static void launch_rows(const ConvDesc& d, cudaStream_t stream) {
     const dim3 g(d.rp.grid), t(kRowThreads);
     const size_t sm = d.rp.smem_bytes;
-    if (d.rp.rows == 4) launch_k(conv_tc_rows_kernel<4, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
-    else if (d.rp.rows == 2) launch_k(conv_tc_rows_kernel<2, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
-    else launch_k(conv_tc_rows_kernel<1, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    if (d.rp.rows == 4)
+        launch_k_dependent(conv_tc_rows_kernel<4, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else if (d.rp.rows == 2)
+        launch_k_dependent(conv_tc_rows_kernel<2, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else launch_k_dependent(conv_tc_rows_kernel<1, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
 }
 
 bool conv_mask_prefetch(const ConvDesc& d) { return d.rows_form && d.p.mode == kDgradMask && d.rp.nc <= 64; }
