@@ -122,16 +122,23 @@ class ShadingPipeline:
         cur = stream if stream is not None else torch.cuda.current_stream(self.device)
         if self._fork is None:
             self._fork = torch.cuda.Stream(self.device)
-        fork, bs = self._fork, self.bvh_stream()
-        fork.wait_stream(cur)
-        bs.wait_stream(cur)
-        self.build_probe(fork)
+        fork, bs, ps = self._fork, self.bvh_stream(), self.probe_stream()
+        for st in (fork, bs, ps):
+            st.wait_stream(cur)
+        self.build_probe(ps)
         self.primary(fork)
+        fork.wait_stream(ps)
         self.forward_part(1, fork)
         self.build_bvh(bs)
         cur.wait_stream(fork)
         cur.wait_stream(bs)
         self.forward_part(2, cur)
+
+    def probe_stream(self):
+        """A third stream: the probe tables, beside the G-buffer and the BVH build."""
+        if getattr(self, "_probe_stream", None) is None:
+            self._probe_stream = torch.cuda.Stream(self.device)
+        return self._probe_stream
 
     def bvh_stream(self):
         """The stream of the highest priority the BVH build runs on beside the sample generation."""
@@ -287,11 +294,14 @@ class ShadingPipeline:
         overlap = self.overlap_generation and self.workspace is not None and self.raster_ws is not None
         if self.raster_ws is not None:
             self.primary_part(1, fork)
-        fork.wait_event(ev["env"])
-        self.build_probe(fork)
+        ps = self.probe_stream()
+        ps.wait_stream(cur)
+        ps.wait_event(ev["env"])
+        self.build_probe(ps)
         if self.raster_ws is not None:
             fork.wait_event(ev["tex"])
             self.primary_part(2, fork)
+        fork.wait_stream(ps)
         if overlap:  # sample generation beside the BVH build, which runs at the highest priority
             self.forward_part(1, fork)
             bs = self.bvh_stream()
