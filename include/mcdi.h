@@ -185,14 +185,19 @@ MCDI_API mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, 
  * scan-converts the mesh into the workspace's depth buffer and reads only
  * verts, tris and cams; part 2 (resolve), on a stream ordered after part 1,
  * interpolates the winning triangle's attributes, looks up tex_kd / tex_korm
- * and writes the four G-buffer planes.  Arguments as mcdi_raster_gbuffer; both
- * parts must receive the same ones.  Any other part: MCDI_INVALID_ARG. */
+ * and writes the four G-buffer planes.  tex_channels: 4 = [S][S] float4 (the
+ * 4th channel unused; 16-byte aligned), as mcdi_raster_gbuffer; 3 = packed
+ * [S][S][3] float (k_d RGB, k_orm = occlusion, roughness, metallic; 4-byte
+ * aligned), a quarter fewer bytes to copy from the host; both give the same
+ * G-buffer bit for bit.  Other arguments as mcdi_raster_gbuffer; both parts
+ * must receive the same ones.  Any other part or tex_channels:
+ * MCDI_INVALID_ARG. */
 MCDI_API mcdi_status mcdi_raster_gbuffer_part(const float* verts, const float* vnrm, const int* tris, int n_verts,
                                               int n_tris, const mcdi_camera* cams, int N, int H, int W,
                                               const float* tex_kd, const float* tex_korm, int tex_size,
-                                              const float* uvmap, float* gb_pos, float* gb_nrm, float* gb_kd,
-                                              float* gb_korm, void* workspace, size_t workspace_bytes, int part,
-                                              void* stream);
+                                              int tex_channels, const float* uvmap, float* gb_pos, float* gb_nrm,
+                                              float* gb_kd, float* gb_korm, void* workspace, size_t workspace_bytes,
+                                              int part, void* stream);
 
 /* Sampling and shading parameters (host struct). */
 typedef struct {

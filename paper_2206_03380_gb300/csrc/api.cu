@@ -201,8 +201,8 @@ mcdi_status mcdi_raster_workspace_size(int N, int H, int W, size_t* bytes) {
 
 static mcdi_status raster_gbuffer(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
                                   const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
-                                  const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos,
-                                  float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
+                                  const float* tex_korm, int tex_size, int tex_channels, const float* uvmap,
+                                  float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
                                   size_t workspace_bytes, void* stream, int parts) {
     REQUIRE(verts && vnrm && n_verts >= 1, "verts / vnrm must be non-NULL and n_verts >= 1");
     REQUIRE(n_tris >= 0 && (n_tris == 0 || tris != nullptr), "tris must be non-NULL when n_tris > 0");
@@ -212,8 +212,15 @@ static mcdi_status raster_gbuffer(const float* verts, const float* vnrm, const i
     REQUIRE(N >= 1 && H >= 1 && W >= 1 && (long long)N * H * W <= (1LL << 31) - 1, "bad image shape");
     REQUIRE((long long)N * n_tris <= (1LL << 31) - 1, "N*n_tris too large");
     REQUIRE(tex_size >= 1 && tex_size <= 16384, "tex_size out of range");
-    REQUIRE_BUF16(tex_kd);
-    REQUIRE_BUF16(tex_korm);
+    REQUIRE(tex_channels == 3 || tex_channels == 4, "tex_channels must be 3 or 4, got %d", tex_channels);
+    if (tex_channels == 4) {
+        REQUIRE_BUF16(tex_kd);
+        REQUIRE_BUF16(tex_korm);
+    } else {
+        REQUIRE(tex_kd != nullptr && tex_korm != nullptr && ((uintptr_t)tex_kd & 3u) == 0 &&
+                    ((uintptr_t)tex_korm & 3u) == 0,
+                "tex_kd / tex_korm must be non-NULL 4-byte aligned device pointers");
+    }
     REQUIRE(uvmap != nullptr, "uvmap (host, 3 floats) is NULL");
     REQUIRE_BUF16(gb_pos);
     REQUIRE_BUF16(gb_nrm);
@@ -225,7 +232,7 @@ static mcdi_status raster_gbuffer(const float* verts, const float* vnrm, const i
     REQUIRE(workspace_bytes >= need, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
     return launched(mcdi::launch_raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm,
                                                 tex_size, uvmap[0], uvmap[1], uvmap[2], gb_pos, gb_nrm, gb_kd, gb_korm,
-                                                workspace, static_cast<cudaStream_t>(stream), parts),
+                                                workspace, static_cast<cudaStream_t>(stream), parts, tex_channels),
                     "raster_gbuffer");
 }
 
@@ -233,18 +240,19 @@ mcdi_status mcdi_raster_gbuffer(const float* verts, const float* vnrm, const int
                                 const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
                                 const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos, float* gb_nrm,
                                 float* gb_kd, float* gb_korm, void* workspace, size_t workspace_bytes, void* stream) {
-    return raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size, uvmap,
+    return raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size, 4, uvmap,
                           gb_pos, gb_nrm, gb_kd, gb_korm, workspace, workspace_bytes, stream, 3);
 }
 
 mcdi_status mcdi_raster_gbuffer_part(const float* verts, const float* vnrm, const int* tris, int n_verts, int n_tris,
                                      const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
-                                     const float* tex_korm, int tex_size, const float* uvmap, float* gb_pos,
-                                     float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
+                                     const float* tex_korm, int tex_size, int tex_channels, const float* uvmap,
+                                     float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
                                      size_t workspace_bytes, int part, void* stream) {
     REQUIRE(part == 1 || part == 2, "part must be 1 (depth) or 2 (resolve), got %d", part);
-    return raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size, uvmap,
-                          gb_pos, gb_nrm, gb_kd, gb_korm, workspace, workspace_bytes, stream, part);
+    return raster_gbuffer(verts, vnrm, tris, n_verts, n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size,
+                          tex_channels, uvmap, gb_pos, gb_nrm, gb_kd, gb_korm, workspace, workspace_bytes, stream,
+                          part);
 }
 
 mcdi_status mcdi_shade_workspace_size(int N, int H, int W, const mcdi_shade_params* params, size_t* bytes) {

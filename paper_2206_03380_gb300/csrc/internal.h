@@ -97,7 +97,7 @@ cudaError_t launch_raster_gbuffer(const float* verts, const float* vnrm, const i
                                   const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
                                   const float* tex_korm, int tex_size, float uv_ox, float uv_oz, float uv_s,
                                   float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
-                                  cudaStream_t stream, int parts = 3);
+                                  cudaStream_t stream, int parts = 3, int tex_channels = 4);
 
 cudaError_t launch_shade_fwd(const ShadeArgs& a, float4* c_d, float4* kd_out, float4* c_s, uint32_t* vis_mask,
                              cudaStream_t stream);

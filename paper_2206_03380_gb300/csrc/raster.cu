@@ -138,10 +138,11 @@ __global__ void __launch_bounds__(kRasterThreads) raster_kernel(const float* __r
 }
 
 // the G-buffer entries of every pixel from its winning triangle
+template <int kCh>
 __global__ void __launch_bounds__(kRasterThreads) resolve_kernel(
     const unsigned long long* __restrict__ z, const float* __restrict__ verts, const float* __restrict__ vnrm,
     const int* __restrict__ tri_idx, int n_verts, int n_tris, const mcdi_camera* __restrict__ cams, int N, int H, int W,
-    const float4* __restrict__ tex_kd, const float4* __restrict__ tex_korm, int S, float uv_ox, float uv_oz,
+    const float* __restrict__ tex_kd, const float* __restrict__ tex_korm, int S, float uv_ox, float uv_oz,
     float uv_s, float4* __restrict__ gb_pos, float4* __restrict__ gb_nrm, float4* __restrict__ gb_kd,
     float4* __restrict__ gb_korm) {
     pdl_prologue();
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(kRasterThreads) resolve_kernel(
         const float t = tri_hit_v(make_ray(mk(C.origin[0], C.origin[1], C.origin[2]), camera_dir(C, pix % W, pix / W, W, H)),
                                   a, b - a, c - a, &u, &v);
         if (t < FLT_MAX)
-            gbuffer_hit(k, u, v, verts, vnrm, tri_idx, n_verts, tex_kd, tex_korm, S, uv_ox, uv_oz, uv_s, &P, &Nn, &KD,
-                        &KORM);
+            gbuffer_hit<kCh>(k, u, v, verts, vnrm, tri_idx, n_verts, tex_kd, tex_korm, S, uv_ox, uv_oz, uv_s, &P, &Nn,
+                             &KD, &KORM);
     }
     gb_pos[idx] = P;
     gb_nrm[idx] = Nn;
@@ -181,7 +182,7 @@ cudaError_t launch_raster_gbuffer(const float* verts, const float* vnrm, const i
                                   const mcdi_camera* cams, int N, int H, int W, const float* tex_kd,
                                   const float* tex_korm, int tex_size, float uv_ox, float uv_oz, float uv_s,
                                   float* gb_pos, float* gb_nrm, float* gb_kd, float* gb_korm, void* workspace,
-                                  cudaStream_t stream, int parts) {
+                                  cudaStream_t stream, int parts, int tex_channels) {
     const long long P = (long long)N * H * W;
     auto* z = static_cast<unsigned long long*>(workspace);
     if (parts & 1) {  // depth pass: the mesh and the cameras only
@@ -191,11 +192,10 @@ cudaError_t launch_raster_gbuffer(const float* verts, const float* vnrm, const i
                      tri_idx, n_tris, cams, N, H, W, z);
     }
     if (!(parts & 2)) return cudaGetLastError();
-    launch_k(resolve_kernel, blocks_for(P), kRasterThreads, 0, stream, (const unsigned long long*)z, verts, vnrm,
-             tri_idx, n_verts, n_tris, cams, N, H, W, reinterpret_cast<const float4*>(tex_kd),
-             reinterpret_cast<const float4*>(tex_korm), tex_size, uv_ox, uv_oz, uv_s,
-             reinterpret_cast<float4*>(gb_pos), reinterpret_cast<float4*>(gb_nrm), reinterpret_cast<float4*>(gb_kd),
-             reinterpret_cast<float4*>(gb_korm));
+    auto* rk = tex_channels == 3 ? resolve_kernel<3> : resolve_kernel<4>;
+    launch_k(rk, blocks_for(P), kRasterThreads, 0, stream, (const unsigned long long*)z, verts, vnrm, tri_idx, n_verts,
+             n_tris, cams, N, H, W, tex_kd, tex_korm, tex_size, uv_ox, uv_oz, uv_s, reinterpret_cast<float4*>(gb_pos),
+             reinterpret_cast<float4*>(gb_nrm), reinterpret_cast<float4*>(gb_kd), reinterpret_cast<float4*>(gb_korm));
     return cudaGetLastError();
 }
 

@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(kShadeThreads) primary_cast_kernel(
     const int leaf = closest_hit(nodes, tris, n_tris, make_ray(o, d), &t, &u, &v);
     float4 P = make_float4(0.f, 0.f, 0.f, 0.f), Nn = P, KD = P, KORM = P;
     if (leaf >= 0)
-        gbuffer_hit(__float_as_int(__ldg(&tris[leaf].v0.w)), u, v, verts, vnrm, tri_idx, n_verts, tex_kd, tex_korm, S,
-                    uv_ox, uv_oz, uv_s, &P, &Nn, &KD, &KORM);
+        gbuffer_hit(__float_as_int(__ldg(&tris[leaf].v0.w)), u, v, verts, vnrm, tri_idx, n_verts,
+                    reinterpret_cast<const float*>(tex_kd), reinterpret_cast<const float*>(tex_korm), S, uv_ox, uv_oz,
+                    uv_s, &P, &Nn, &KD, &KORM);
     gb_pos[idx] = P;
     gb_nrm[idx] = Nn;
     gb_kd[idx] = KD;

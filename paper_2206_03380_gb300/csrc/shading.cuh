@@ -487,14 +487,26 @@ __device__ __forceinline__ f3 camera_dir(const mcdi_camera& C, int x, int y, int
                         C.forward[2] + sx * C.right[2] + sy * C.up[2]));
 }
 
-__device__ __forceinline__ float4 bilinear(const float4* __restrict__ tex, int S, float u, float v) {
+// texel i of a texture stored with kCh floats per texel (4: float4, the 4th
+// channel unused; 3: packed RGB), as a float4 with w = 0 for kCh = 3
+template <int kCh>
+__device__ __forceinline__ float4 texel(const float* __restrict__ tex, size_t i) {
+    if constexpr (kCh == 4) {
+        return __ldg(reinterpret_cast<const float4*>(tex) + i);
+    } else {
+        return make_float4(__ldg(tex + 3 * i), __ldg(tex + 3 * i + 1), __ldg(tex + 3 * i + 2), 0.0f);
+    }
+}
+
+template <int kCh = 4>
+__device__ __forceinline__ float4 bilinear(const float* __restrict__ tex, int S, float u, float v) {
     const float x = u * (float)S - 0.5f, y = v * (float)S - 0.5f;
     const float x0 = floorf(x), y0 = floorf(y);
     const float fx = x - x0, fy = y - y0;
     const int xi0 = min(max((int)x0, 0), S - 1), xi1 = min(max((int)x0 + 1, 0), S - 1);
     const int yi0 = min(max((int)y0, 0), S - 1), yi1 = min(max((int)y0 + 1, 0), S - 1);
-    const float4 t00 = __ldg(tex + (size_t)yi0 * S + xi0), t10 = __ldg(tex + (size_t)yi0 * S + xi1);
-    const float4 t01 = __ldg(tex + (size_t)yi1 * S + xi0), t11 = __ldg(tex + (size_t)yi1 * S + xi1);
+    const float4 t00 = texel<kCh>(tex, (size_t)yi0 * S + xi0), t10 = texel<kCh>(tex, (size_t)yi0 * S + xi1);
+    const float4 t01 = texel<kCh>(tex, (size_t)yi1 * S + xi0), t11 = texel<kCh>(tex, (size_t)yi1 * S + xi1);
     auto lerp = [](float a, float b, float t) { return a + (b - a) * t; };
     return make_float4(lerp(lerp(t00.x, t10.x, fx), lerp(t01.x, t11.x, fx), fy),
                        lerp(lerp(t00.y, t10.y, fx), lerp(t01.y, t11.y, fx), fy),
@@ -504,11 +516,13 @@ __device__ __forceinline__ float4 bilinear(const float4* __restrict__ tex, int S
 
 // The G-buffer entries of a primary hit on triangle k (original index) at
 // barycentrics (u, v): interpolated position and normal, and the textures at
-// the planar coordinate of the position; left as they are for bad vertex indices.
+// the planar coordinate of the position (textures of kCh floats per texel);
+// left as they are for bad vertex indices.
+template <int kCh = 4>
 __device__ __forceinline__ void gbuffer_hit(int k, float u, float v, const float* __restrict__ verts,
                                             const float* __restrict__ vnrm,
                                             const int* __restrict__ tri_idx, int n_verts,
-                                            const float4* __restrict__ tex_kd, const float4* __restrict__ tex_korm,
+                                            const float* __restrict__ tex_kd, const float* __restrict__ tex_korm,
                                             int S, float uv_ox, float uv_oz, float uv_s, float4* P, float4* Nn,
                                             float4* KD, float4* KORM) {
     const int i0 = tri_idx[3 * (size_t)k], i1 = tri_idx[3 * (size_t)k + 1], i2 = tri_idx[3 * (size_t)k + 2];
@@ -524,8 +538,8 @@ __device__ __forceinline__ void gbuffer_hit(int k, float u, float v, const float
     *P = make_float4(pp[0], pp[1], pp[2], 1.0f);
     *Nn = make_float4(nn[0], nn[1], nn[2], 0.0f);
     const float tu = (pp[0] - uv_ox) * uv_s, tv = (pp[2] - uv_oz) * uv_s;
-    *KD = bilinear(tex_kd, S, tu, tv);
-    *KORM = bilinear(tex_korm, S, tu, tv);
+    *KD = bilinear<kCh>(tex_kd, S, tu, tv);
+    *KORM = bilinear<kCh>(tex_korm, S, tu, tv);
     KD->w = 0.f;
     KORM->w = 0.f;
 }

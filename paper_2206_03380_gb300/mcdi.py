@@ -82,8 +82,8 @@ def load(path: str = LIB_PATH):
     lib.mcdi_raster_gbuffer.argtypes = [P, P, P, i, i, P, i, i, i, P, P, i, C.POINTER(C.c_float), P, P, P, P, P, sz,
                                         P]
     lib.mcdi_raster_gbuffer_part.restype = st
-    lib.mcdi_raster_gbuffer_part.argtypes = [P, P, P, i, i, P, i, i, i, P, P, i, C.POINTER(C.c_float), P, P, P, P, P,
-                                             sz, i, P]
+    lib.mcdi_raster_gbuffer_part.argtypes = [P, P, P, i, i, P, i, i, i, P, P, i, i, C.POINTER(C.c_float), P, P, P,
+                                             P, P, sz, i, P]
     lib.mcdi_shade_workspace_size.restype = st
     lib.mcdi_shade_workspace_size.argtypes = [i, i, i, C.POINTER(ShadeParams), C.POINTER(sz)]
     lib.mcdi_shade_mc_fwd.restype = st
@@ -284,11 +284,15 @@ def raster_gbuffer(verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, w
 def raster_gbuffer_part(verts, vnrm, tris, cams, H, W, tex_kd, tex_korm, uvmap, gb, workspace, part: int,
                         stream=None):
     """`raster_gbuffer` in two calls: part 1 (depth; reads the mesh and cameras only), then part 2
-    (resolve: attributes and texture lookups into the G-buffer) on a stream ordered after it."""
+    (resolve: attributes and texture lookups into the G-buffer) on a stream ordered after it.  The
+    textures are (S, S, 4) or packed (S, S, 3) float32."""
     uv = (C.c_float * 3)(*[float(x) for x in uvmap])
+    ch = int(tex_kd.shape[-1])
+    if tex_korm.shape[-1] != ch:
+        raise ValueError("tex_kd and tex_korm must have the same number of channels")
     _check(load().mcdi_raster_gbuffer_part(_ptr(verts), _ptr(vnrm), _ptr(tris), verts.shape[0], tris.shape[0],
                                            _ptr(cams), cams.shape[0], int(H), int(W), _ptr(tex_kd), _ptr(tex_korm),
-                                           tex_kd.shape[0], uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd),
+                                           tex_kd.shape[0], ch, uv, _ptr(gb.pos), _ptr(gb.nrm), _ptr(gb.kd),
                                            _ptr(gb.korm), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                            int(part), _stream(stream)), "raster_gbuffer_part")
 

@@ -94,10 +94,12 @@ class ShadingPipeline:
             mcdi.primary_cast(self.bvh, self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
                               self.tex_korm, self.uvmap, self.gb, stream)
 
-    def primary_part(self, part: int, stream=None):
-        """The rasterised G-buffer in two parts: 1 = depth (mesh only), 2 = resolve (reads the textures)."""
-        mcdi.raster_gbuffer_part(self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, self.tex_kd,
-                                 self.tex_korm, self.uvmap, self.gb, self.raster_ws, part, stream)
+    def primary_part(self, part: int, stream=None, tex=None):
+        """The rasterised G-buffer in two parts: 1 = depth (mesh only), 2 = resolve (reads the textures:
+        ``tex`` = (k_d, k_orm) device textures, (S, S, 4) or packed (S, S, 3); default the pipeline's)."""
+        kd, korm = tex if tex is not None else (self.tex_kd, self.tex_korm)
+        mcdi.raster_gbuffer_part(self.verts, self.vnrm, self.tris, self.cams, self.H, self.W, kd, korm, self.uvmap,
+                                 self.gb, self.raster_ws, part, stream)
 
     def forward(self, stream=None):
         mcdi.shade_mc_fwd(self.bvh, self.probe, self.gb, self.cams, self.params, self.c_d, self.kd_out, self.c_s,
@@ -255,7 +257,9 @@ class ShadingPipeline:
     def loss_step_io(self, ref, host_in: dict, host_ref, outputs, stream=None, lambda_light: float = 0.15):
         """`loss_step` with its host I/O overlapped: this step's inputs are copied
         from pinned host memory (``host_in``: verts, vnrm, tris, env, tex_kd,
-        tex_korm into the pipeline's buffers; ``host_ref`` into ``ref``) on one
+        tex_korm into the pipeline's buffers — the textures either (S, S, 4) or
+        packed (S, S, 3), a quarter fewer bytes, which the rasteriser's resolve
+        reads as they are; ``host_ref`` into ``ref``) on one
         copy stream in the order the step first needs them (mesh, probe, the two
         material textures, reference: the host link is the bound, and copies on
         several streams share it, so each input arrives earliest in sequence),
@@ -275,14 +279,22 @@ class ShadingPipeline:
         for st in streams:
             st.wait_stream(cur)
         ev = {k: torch.cuda.Event() for k in ("mesh", "env", "tex", "ref", "loss", "end")}
+        tex = (self.tex_kd, self.tex_korm)
+        if host_in["tex_kd"].shape[-1] == 3:  # packed RGB: resolved from a packed device copy
+            if self.raster_ws is None:
+                raise ValueError("packed (S, S, 3) host textures need the rasterised G-buffer")
+            shape = tuple(host_in["tex_kd"].shape)
+            if getattr(self, "_tex3", None) is None or tuple(self._tex3[0].shape) != shape:
+                self._tex3 = tuple(torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(2))
+            tex = self._tex3
         with torch.cuda.stream(up):
             for k in ("verts", "tris", "vnrm"):
                 getattr(self, k).copy_(host_in[k], non_blocking=True)
             ev["mesh"].record(up)
             self.env.copy_(host_in["env"], non_blocking=True)
             ev["env"].record(up)
-            self.tex_kd.copy_(host_in["tex_kd"], non_blocking=True)
-            self.tex_korm.copy_(host_in["tex_korm"], non_blocking=True)
+            tex[0].copy_(host_in["tex_kd"], non_blocking=True)
+            tex[1].copy_(host_in["tex_korm"], non_blocking=True)
             ev["tex"].record(up)
             ref.copy_(host_ref, non_blocking=True)
             ev["ref"].record(up)
@@ -300,7 +312,7 @@ class ShadingPipeline:
         self.build_probe(ps)
         if self.raster_ws is not None:
             fork.wait_event(ev["tex"])
-            self.primary_part(2, fork)
+            self.primary_part(2, fork, tex)
         fork.wait_stream(ps)
         if overlap:  # sample generation beside the BVH build, which runs at the highest priority
             self.forward_part(1, fork)

@@ -116,10 +116,20 @@ def test_raster_argument_checks_without_gpu(lib):
     bad[13] = C.c_void_p(4100)  # gb_pos not 16-byte aligned
     assert lib.mcdi_raster_gbuffer(*bad, n.value, None) == mcdi.INVALID_ARG
     assert b"gb_pos" in lib.mcdi_last_error()
-    assert lib.mcdi_raster_gbuffer_part(*args, n.value, 3, None) == mcdi.INVALID_ARG
+    pargs = args[:12] + [4] + args[12:]  # tex_channels after tex_size
+    assert lib.mcdi_raster_gbuffer_part(*pargs, n.value, 3, None) == mcdi.INVALID_ARG
     assert b"part" in lib.mcdi_last_error()
-    assert lib.mcdi_raster_gbuffer_part(*args, n.value - 1, 1, None) == mcdi.INVALID_ARG
+    assert lib.mcdi_raster_gbuffer_part(*pargs, n.value - 1, 1, None) == mcdi.INVALID_ARG
     assert b"workspace" in lib.mcdi_last_error()
+    bad = list(pargs)
+    bad[12] = 2
+    assert lib.mcdi_raster_gbuffer_part(*bad, n.value, 2, None) == mcdi.INVALID_ARG
+    assert b"tex_channels" in lib.mcdi_last_error()
+    bad[12], bad[9] = 4, C.c_void_p(4100)  # float4 textures must be 16-byte aligned
+    assert lib.mcdi_raster_gbuffer_part(*bad, n.value, 2, None) == mcdi.INVALID_ARG
+    bad[12] = 3  # packed RGB: 4-byte alignment suffices
+    bad[9] = C.c_void_p(4098)
+    assert lib.mcdi_raster_gbuffer_part(*bad, n.value, 2, None) == mcdi.INVALID_ARG
 
 
 def test_graph_entry_points_check_arguments_without_gpu(lib):

@@ -4,7 +4,8 @@ bitwise the outputs of the single call, also when the generation runs on a
 forked stream while the BVH is built on another (pipeline.geometry_and_forward
 launched kernel by kernel).  Likewise the rasterised G-buffer in two calls
 (mcdi_raster_gbuffer_part: depth from the mesh, then the resolve that reads
-the textures), also with the textures written only between the two, and the
+the textures), also with the textures written only between the two and with
+packed RGB textures, and the
 adjoint over disjoint pixel spans (mcdi_shade_mc_bwd_span): per-pixel
 gradients bitwise those of one call, the probe gradient (summed by atomics in
 no fixed order) to 1e-5 of its largest entry."""
@@ -82,6 +83,17 @@ def test_raster_parts_match_the_single_call(cuda_lib):
     pipe.tex_kd.copy_(tex[0])
     pipe.tex_korm.copy_(tex[1])
     pipe.primary_part(2)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, _gb(pipe)):
+        assert torch.equal(a, b)
+    # packed RGB textures (the 4th channel dropped): the same G-buffer bit for bit
+    tex3 = [t[..., :3].contiguous() for t in tex]
+    for t in (pipe.gb.pos, pipe.gb.nrm, pipe.gb.kd, pipe.gb.korm):
+        t.zero_()
+    cuda_lib.raster_gbuffer_part(pipe.verts, pipe.vnrm, pipe.tris, pipe.cams, pipe.H, pipe.W, tex3[0], tex3[1],
+                                 pipe.uvmap, pipe.gb, pipe.raster_ws, 1)
+    cuda_lib.raster_gbuffer_part(pipe.verts, pipe.vnrm, pipe.tris, pipe.cams, pipe.H, pipe.W, tex3[0], tex3[1],
+                                 pipe.uvmap, pipe.gb, pipe.raster_ws, 2)
     torch.cuda.synchronize()
     for a, b in zip(ref, _gb(pipe)):
         assert torch.equal(a, b)

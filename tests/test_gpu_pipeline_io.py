@@ -14,7 +14,8 @@ from paper_2206_03380_gb300 import scenes
 pytestmark = pytest.mark.gpu
 
 
-def test_loss_step_io_graph_matches_the_plain_step(cuda_lib):
+@pytest.mark.parametrize("packed_textures", [False, True])
+def test_loss_step_io_graph_matches_the_plain_step(cuda_lib, packed_textures):
     from paper_2206_03380_gb300.pipeline import ShadingPipeline
 
     sc = scenes.parity_scene()
@@ -28,6 +29,9 @@ def test_loss_step_io_graph_matches_the_plain_step(cuda_lib):
     expect = [t.cpu().clone() for t in outs]
     names = ("verts", "vnrm", "tris", "env", "tex_kd", "tex_korm")
     host_in = {k: getattr(pipe, k).cpu().pin_memory() for k in names}
+    if packed_textures:  # (S, S, 3): the 4th channel is padding
+        for k in ("tex_kd", "tex_korm"):
+            host_in[k] = host_in[k][..., :3].contiguous().pin_memory()
     host_ref = ref.cpu().pin_memory()
     host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
     pipe.capture_loss_step_io(ref, host_in, host_ref, list(zip(outs, host_out)))
