@@ -205,7 +205,7 @@ def run_gpu(args, rank, world):
     # the library's kernels per step at this size (the level-0 and level-1 max-pools run inside the
     # convolutions' epilogues, the level-2 one as its own kernel; the G-buffer is rasterised: depth-buffer
     # clear, raster, resolve)
-    n_launch = {"probe_cdf": 2, "bvh_build": 3 + 9 + 2 + (2 if sc.tris.shape[0] > 1 else 1), "primary_cast": 3,
+    n_launch = {"probe_cdf": 2, "bvh_build": mcdi.bvh_build_launches(sc.tris.shape[0]), "primary_cast": 3,
                 "shade_fwd": 4, "denoise_fwd": 1 + 15 + 1, "loss": 2, "denoise_bwd": 1 + 15 + 3 + 3,
                 "shade_bwd": 1}
 

@@ -90,6 +90,11 @@ MCDI_API mcdi_status mcdi_bvh_sizes(int n_tris, size_t* node_bytes, size_t* tri_
 MCDI_API mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
                            void* tri_records, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Number of kernels mcdi_build_bvh launches for n_tris triangles (the Morton
+ * keys of a mesh of up to 262,144 triangles are sorted by one kernel per radix
+ * pass, of larger meshes by three).  For launch accounting; no device work. */
+MCDI_API mcdi_status mcdi_bvh_build_launches(int n_tris, int* launches);
+
 /* ------------------------------------------------------------------------
  * mcdi_refit_bvh: bounds-only update for a mesh whose vertices moved but
  * whose triangles (the tris array and n_tris) are those of the last
@@ -114,7 +119,7 @@ MCDI_API mcdi_status mcdi_refit_bvh(const float* verts, int n_verts, const int* 
  * host application that owns every device allocation, or a request loop
  * whose memory budget is fixed at start-up and may not grow (cudaMalloc can
  * also block on the device, which such loops cannot afford).
- * Scratch lives in one fixed device array inside the library (about 6 MB,
+ * Scratch lives in one fixed device array inside the library (7 MB,
  * held on every GPU that loads the library until the process exits); the
  * first call on a device looks up its address on that device, so make that
  * first call before any stream capture.  The call allocates and frees

@@ -149,6 +149,14 @@ mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int
                     "build_bvh");
 }
 
+mcdi_status mcdi_bvh_build_launches(int n_tris, int* launches) {
+    REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
+    REQUIRE(launches != nullptr, "launches is NULL");
+    // bounds (2), Morton codes, the sort, leaf records, hierarchy + boxes (1 or 2), depth-first copy
+    *launches = 3 + (mcdi::bvh_tile_sort(n_tris) ? 1 : 3) * mcdi::kSortPasses + 1 + (n_tris > 1 ? 2 : 1) + 1;
+    return ok();
+}
+
 mcdi_status mcdi_refit_bvh(const float* verts, int n_verts, const int* tris, int n_tris, void* nodes,
                            void* tri_records, void* scratch, size_t scratch_bytes, void* stream) {
     REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);

@@ -7,7 +7,9 @@
 //   1. centroid bounds (block min/max + one atomic per block and axis);
 //   2. 30-bit Morton code of each centroid;
 //   3. stable LSD radix sort, 3 passes of 10 bits (histogram / per-digit scan
-//      across tiles / scatter with warp match_any ranking);
+//      across tiles / scatter with warp match_any ranking; up to 262,144
+//      triangles one kernel per pass: each pass's digit counts per tile come
+//      from the kernel before it, the Morton kernel for the first);
 //   4. one thread per internal node finds its key range and split from the
 //      common-prefix lengths of the sorted keys (ties broken by position);
 //   5. bottom-up bounds: each leaf walks to the root, the second thread to
@@ -18,6 +20,7 @@
 // Output: 64-byte two-child nodes (root = node 0), the depth-first copy, the
 // four-wide nodes and 48-byte triangle records in leaf (Morton) order.
 #include <float.h>
+#include <algorithm>
 #include <limits.h>
 
 #include "common.cuh"
@@ -34,10 +37,13 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-__global__ void init_bounds_kernel(uint32_t* bounds) {
+// bounds to the empty box; the tile-sort digit counts (n_vec4 vectors) to zero
+__global__ void init_bounds_kernel(uint32_t* bounds, uint4* hist, int n_vec4) {
     pdl_prologue();
-    if (threadIdx.x < 3) bounds[threadIdx.x] = f2ord(FLT_MAX);
-    else if (threadIdx.x < 6) bounds[threadIdx.x] = f2ord(-FLT_MAX);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3) bounds[i] = f2ord(FLT_MAX);
+    else if (i < 6) bounds[i] = f2ord(-FLT_MAX);
+    for (int k = i; k < n_vec4; k += gridDim.x * blockDim.x) hist[k] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __global__ void __launch_bounds__(256) centroid_bounds_kernel(const float* __restrict__ verts, int n_verts,
@@ -80,6 +86,8 @@ __global__ void __launch_bounds__(256) centroid_bounds_kernel(const float* __res
     }
 }
 
+constexpr int kDigits = 1 << kSortDigitBits;
+
 // spread the low 10 bits of v so that bit i lands at bit 3i
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
     v &= 0x3ffu;
@@ -90,35 +98,44 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
     return v;
 }
 
+// (tile_hist non-null: also counts each key's first digit in its tile of kTileKeys keys,
+// one atomic per distinct (tile, digit) of a warp)
 __global__ void __launch_bounds__(256) morton_kernel(const float* __restrict__ verts, int n_verts,
                                                      const int* __restrict__ tris, int n,
                                                      const uint32_t* __restrict__ bounds, uint32_t* __restrict__ keys,
-                                                     uint32_t* __restrict__ vals) {
+                                                     uint32_t* __restrict__ vals, uint32_t* __restrict__ tile_hist) {
     pdl_prologue();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    f3 a, b, c;
-    load_tri(verts, n_verts, tris, k, a, b, c);
-    const f3 m = (a + b + c) * (1.0f / 3.0f);
-    const float lo[3] = {ord2f(bounds[0]), ord2f(bounds[1]), ord2f(bounds[2])};
-    const float hi[3] = {ord2f(bounds[3]), ord2f(bounds[4]), ord2f(bounds[5])};
-    const float p[3] = {m.x, m.y, m.z};
+    const bool valid = k < n;
     uint32_t code = 0;
+    if (valid) {
+        f3 a, b, c;
+        load_tri(verts, n_verts, tris, k, a, b, c);
+        const f3 m = (a + b + c) * (1.0f / 3.0f);
+        const float lo[3] = {ord2f(bounds[0]), ord2f(bounds[1]), ord2f(bounds[2])};
+        const float hi[3] = {ord2f(bounds[3]), ord2f(bounds[4]), ord2f(bounds[5])};
+        const float p[3] = {m.x, m.y, m.z};
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const float ext = hi[ax] - lo[ax];
-        float t = ext > 0.f ? (p[ax] - lo[ax]) / ext : 0.5f;
-        t = fminf(fmaxf(t, 0.f), 1.f);
-        const uint32_t q = min(1023u, (uint32_t)(t * 1024.f));
-        code |= spread3(q) << (2 - ax);
+        for (int ax = 0; ax < 3; ++ax) {
+            const float ext = hi[ax] - lo[ax];
+            float t = ext > 0.f ? (p[ax] - lo[ax]) / ext : 0.5f;
+            t = fminf(fmaxf(t, 0.f), 1.f);
+            const uint32_t q = min(1023u, (uint32_t)(t * 1024.f));
+            code |= spread3(q) << (2 - ax);
+        }
+        keys[k] = code;
+        vals[k] = (uint32_t)k;
     }
-    keys[k] = code;
-    vals[k] = (uint32_t)k;
+    if (tile_hist) {  // every lane of the warp takes part (blocks are whole warps)
+        const int lane = threadIdx.x & 31;
+        const uint32_t slot = valid ? (uint32_t)(k / kTileKeys) * kDigits + (code & (kDigits - 1)) : 0x80000000u | lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, slot);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(tile_hist + slot, (uint32_t)__popc(peers));
+    }
 }
 
 // ---- radix sort: 30-bit Morton keys in three passes of one 10-bit digit ----
 // (LSD and stable, so equal keys keep their triangle order)
-constexpr int kDigits = 1 << kSortDigitBits;
 constexpr int kDigitsPerThread = kDigits / kSortThreads;
 
 __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint32_t* __restrict__ keys, int n, int shift,
@@ -254,6 +271,125 @@ __global__ void __launch_bounds__(kSortThreads) digit_scatter_kernel(
             const uint32_t pos = dbase[d] + wc[warp][d] + rank[it];
             keys_out[pos] = key[it];
             vals_out[pos] = val[it];
+        }
+    }
+}
+
+// One radix pass over tiles of kTileKeys sorted positions, without a separate
+// count or scan launch: tile t's count of each digit in every tile comes from
+// `hist` (row t' = tile t'; made by the kernel before), so the tile finds its
+// start in each digit (the digit's keys in all tiles, digits before it, plus
+// those in tiles before it) itself; ranks within the tile as in
+// digit_scatter_kernel.  With hist_next it also counts, for the next pass, the
+// next digit of each key in the tile of its new position.
+constexpr int kTileValBits = 19;  // key index bits (n <= kTileSortMax); a warp-local rank above them
+static_assert(kTileSortMax <= (1 << kTileValBits), "key indices must fit below the rank bits");
+
+template <int kThreads, int kItems>
+__global__ void __launch_bounds__(kThreads, 1) tile_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int n, int shift, int n_tiles,
+    const uint32_t* __restrict__ hist, uint32_t* __restrict__ hist_next, int next_shift,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
+    constexpr int kWarps = kThreads / 32, kKeys = kThreads * kItems, kDp = kDigits / kThreads;
+    static_assert(32 * kItems <= (1 << (32 - kTileValBits)), "a warp-local rank must fit above the index bits");
+    static_assert(kDp == 2 || kDp == 4, "each thread owns two or four digits");
+    pdl_prologue();
+    __shared__ uint16_t wc[kWarps][kDigits];  // per-warp digit counters, then per-warp offsets
+    __shared__ uint32_t dbase[kDigits];       // this tile's first position in each digit
+    __shared__ uint32_t wsum[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int t = blockIdx.x;
+    const int base = t * kKeys;
+    const int cnt = min(kKeys, n - base);
+    const uint32_t vmask = (1u << kTileValBits) - 1u;
+    for (int i = tid; i < kWarps * kDigits / 2; i += kThreads) reinterpret_cast<uint32_t*>(&wc[0][0])[i] = 0u;
+    // element (warp, item, lane) is tile position warp * 32 kItems + item * 32 + lane
+    uint32_t key[kItems], v[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int lp = warp * (32 * kItems) + it * 32 + lane;
+        key[it] = lp < cnt ? keys_in[base + lp] : 0u;
+        v[it] = lp < cnt ? vals_in[base + lp] : 0u;
+    }
+    // digits kDp tid ... kDp tid + kDp - 1: their keys in the tiles before this one and in all tiles
+    const int d0 = kDp * tid;
+    uint32_t pre[kDp], tot[kDp];
+#pragma unroll
+    for (int q = 0; q < kDp; ++q) pre[q] = tot[q] = 0u;
+#pragma unroll 8
+    for (int r = 0; r < n_tiles; ++r) {
+        uint32_t h[kDp];
+        if constexpr (kDp == 2) {
+            const uint2 x = __ldcg(reinterpret_cast<const uint2*>(hist + (size_t)r * kDigits + d0));
+            h[0] = x.x, h[1] = x.y;
+        } else {
+            const uint4 x = __ldcg(reinterpret_cast<const uint4*>(hist + (size_t)r * kDigits + d0));
+            h[0] = x.x, h[1] = x.y, h[2] = x.z, h[3] = x.w;
+        }
+#pragma unroll
+        for (int q = 0; q < kDp; ++q) {
+            if (r < t) pre[q] += h[q];
+            tot[q] += h[q];
+        }
+    }
+    __syncthreads();
+    uint16_t* mywc = wc[warp];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const bool valid = warp * (32 * kItems) + it * 32 + lane < cnt;
+        const uint32_t d = valid ? ((key[it] >> shift) & (kDigits - 1)) : ((uint32_t)kDigits + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (valid) before = mywc[d];
+        __syncwarp();
+        if (valid && (peers & lt) == 0) mywc[d] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        v[it] = (v[it] & vmask) | ((before + __popc(peers & lt)) << kTileValBits);
+    }
+    // exclusive scan of the digit totals over the digits
+    uint32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kDp; ++q) sum += tot[q];
+    uint32_t inc = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += x;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();  // also: every warp's counters are complete
+    uint32_t g = inc - sum;
+    for (int w = 0; w < warp; ++w) g += wsum[w];
+#pragma unroll
+    for (int q = 0; q < kDp; ++q) {
+        dbase[d0 + q] = g + pre[q];
+        g += tot[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kDp; ++q) {  // per digit: exclusive scan over the warps (warp order = element order)
+        uint32_t run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = wc[w][d0 + q];
+            wc[w][d0 + q] = (uint16_t)run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const bool valid = warp * (32 * kItems) + it * 32 + lane < cnt;
+        uint32_t slot = 0x80000000u | lane;  // invalid lanes: a value no valid lane has
+        if (valid) {
+            const uint32_t d = (key[it] >> shift) & (kDigits - 1);
+            const uint32_t pos = dbase[d] + wc[warp][d] + (v[it] >> kTileValBits);  // < n
+            keys_out[pos] = key[it];
+            vals_out[pos] = v[it] & vmask;
+            slot = (pos / (uint32_t)kKeys) * kDigits + ((key[it] >> next_shift) & (kDigits - 1));
+        }
+        if (hist_next) {
+            const unsigned peers = __match_any_sync(0xffffffffu, slot);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(hist_next + slot, (uint32_t)__popc(peers));
         }
     }
 }
@@ -594,16 +730,28 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
     TriRecord* recs = static_cast<TriRecord*>(recs_v);
 
     const int g256 = (n + 255) / 256;
-    launch_k(init_bounds_kernel, 1, 32, 0, stream, bounds);
+    const bool tiled = bvh_tile_sort(n);
+    const int n_tiles = (n + kTileKeys - 1) / kTileKeys;
+    const int hist_vec4 = tiled ? kSortPasses * n_tiles * kDigits / 4 : 0;  // one row of counts per tile and pass
+    launch_k(init_bounds_kernel, tiled ? std::min(64, (hist_vec4 + 255) / 256) : 1, tiled ? 256 : 32, 0, stream,
+             bounds, reinterpret_cast<uint4*>(hist), hist_vec4);
     launch_k(centroid_bounds_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds);
-    launch_k(morton_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds, keys[0], vals[0]);
+    launch_k(morton_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, bounds, keys[0], vals[0],
+             tiled ? hist : nullptr);
     int cur = 0;
     for (int pass = 0; pass < kSortPasses; ++pass) {
         const int shift = pass * kSortDigitBits;
-        launch_k(digit_hist_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], n, shift, L.nblocks, hist);
-        launch_k(digit_scan_kernel, kDigits, 256, 0, stream, hist, L.nblocks, dtot);
-        launch_k(digit_scatter_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], vals[cur], n, shift, L.nblocks,
-                 hist, dtot, keys[cur ^ 1], vals[cur ^ 1]);
+        if (tiled) {
+            uint32_t* h = hist + (size_t)pass * n_tiles * kDigits;
+            uint32_t* h_next = pass + 1 < kSortPasses ? h + (size_t)n_tiles * kDigits : nullptr;
+            launch_k(tile_scatter_kernel<kTileThreads, kTileItems>, n_tiles, kTileThreads, 0, stream, keys[cur],
+                     vals[cur], n, shift, n_tiles, h, h_next, shift + kSortDigitBits, keys[cur ^ 1], vals[cur ^ 1]);
+        } else {
+            launch_k(digit_hist_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], n, shift, L.nblocks, hist);
+            launch_k(digit_scan_kernel, kDigits, 256, 0, stream, hist, L.nblocks, dtot);
+            launch_k(digit_scatter_kernel, L.nblocks, kSortThreads, 0, stream, keys[cur], vals[cur], n, shift,
+                     L.nblocks, hist, dtot, keys[cur ^ 1], vals[cur ^ 1]);
+        }
         cur ^= 1;
     }
     launch_k(leaf_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, vals[cur], recs, box_leaf, flags);

@@ -28,7 +28,7 @@ namespace {
 constexpr int kNoallocMaxTris = MCDI_NOALLOC_MAX_TRIS;
 constexpr int kMaxDevices = 64;
 
-constexpr size_t kNoallocScratchBytes = (size_t)6 << 20;
+constexpr size_t kNoallocScratchBytes = (size_t)7 << 20;
 static_assert(mcdi::bvh_scratch_layout(kNoallocMaxTris).total <= kNoallocScratchBytes,
               "the fixed scratch array must hold the build scratch of MCDI_NOALLOC_MAX_TRIS triangles");
 

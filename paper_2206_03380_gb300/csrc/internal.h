@@ -22,6 +22,14 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortDigitBits = 10;  // 30-bit Morton keys: three passes
 constexpr int kSortPasses = 3;
 static_assert(kSortDigitBits * kSortPasses >= 30, "the passes must cover the 30 key bits");
+// the same sort in one kernel per pass for meshes of up to kTileSortMax triangles: tiles of kTileKeys
+// sorted positions, each pass's digit counts per tile made by the kernel before it
+// (each tile reads every tile's counts: the cost grows with the square of the tile count)
+constexpr int kTileThreads = 256;
+constexpr int kTileItems = 8;
+constexpr int kTileKeys = kTileThreads * kTileItems;  // 2,048
+constexpr int kTileSortMax = 128 * kTileKeys;         // 262,144 triangles (at most 128 tiles)
+inline constexpr bool bvh_tile_sort(int n) { return n >= 1 && n <= kTileSortMax; }
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -36,7 +44,9 @@ constexpr BvhScratch bvh_scratch_layout(int n) {
     s.keys1 = o; o = align256(o + un * sizeof(uint32_t));
     s.vals0 = o; o = align256(o + un * sizeof(uint32_t));
     s.vals1 = o; o = align256(o + un * sizeof(uint32_t));
-    s.hist = o; o = align256(o + ((size_t)1 << kSortDigitBits) * s.nblocks * sizeof(uint32_t));
+    const size_t tiles = (un + kTileKeys - 1) / kTileKeys;
+    const size_t hist_rows = (size_t)s.nblocks > kSortPasses * tiles ? (size_t)s.nblocks : kSortPasses * tiles;
+    s.hist = o; o = align256(o + ((size_t)1 << kSortDigitBits) * hist_rows * sizeof(uint32_t));
     s.digit_tot = o; o = align256(o + ((size_t)1 << kSortDigitBits) * sizeof(uint32_t));
     s.parent_int = o; o = align256(o + ni * sizeof(int));
     s.parent_leaf = o; o = align256(o + un * sizeof(int));

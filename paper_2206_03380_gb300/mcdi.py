@@ -45,7 +45,8 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_raster_workspace_size", "mcdi_raster_gbuffer", "mcdi_denoise_record_plan",
            "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
            "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part", "mcdi_raster_gbuffer_part",
-           "mcdi_shade_mc_bwd_span", "mcdi_graph_instantiate", "mcdi_graph_launch", "mcdi_graph_destroy"]
+           "mcdi_shade_mc_bwd_span", "mcdi_graph_instantiate", "mcdi_graph_launch", "mcdi_graph_destroy",
+           "mcdi_bvh_build_launches"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -69,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.mcdi_bvh_sizes.argtypes = [i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_build_bvh.restype = st
     lib.mcdi_build_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
+    lib.mcdi_bvh_build_launches.restype = st
+    lib.mcdi_bvh_build_launches.argtypes = [i, C.POINTER(i)]
     lib.mcdi_refit_bvh.restype = st
     lib.mcdi_refit_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
     lib.mcdi_build_bvh_noalloc.restype = st
@@ -180,6 +183,13 @@ def _check(status: int, where: str):
 # ------------------------------------------------------------------ entry points
 def version() -> int:
     return load().mcdi_version()
+
+
+def bvh_build_launches(n_tris: int) -> int:
+    """Kernels mcdi_build_bvh launches for n_tris triangles on the current device."""
+    out = C.c_int()
+    _check(load().mcdi_bvh_build_launches(int(n_tris), C.byref(out)), "bvh_build_launches")
+    return out.value
 
 
 class Graph:
