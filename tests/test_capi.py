@@ -141,3 +141,18 @@ def test_graph_entry_points_check_arguments_without_gpu(lib):
     assert lib.mcdi_graph_launch(None, None) == mcdi.INVALID_ARG
     assert b"graph_exec" in lib.mcdi_last_error()
     assert lib.mcdi_graph_destroy(None) == mcdi.OK
+
+
+def test_bvh_build_launch_count_without_gpu(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    out = C.c_int()
+    counts = {}
+    for n in (1, 2, 198_164, 262_144, 262_145, 1_289_216):
+        assert lib.mcdi_bvh_build_launches(n, C.byref(out)) == mcdi.OK
+        counts[n] = out.value
+    # bounds (2) + Morton + 3 passes (one kernel each up to 262,144 triangles, else three) + leaf records
+    # + hierarchy and boxes (one launch for a single triangle) + depth-first copy
+    assert counts == {1: 9, 2: 10, 198_164: 10, 262_144: 10, 262_145: 16, 1_289_216: 16}
+    assert lib.mcdi_bvh_build_launches(0, C.byref(out)) == mcdi.INVALID_ARG
+    assert lib.mcdi_bvh_build_launches(5, None) == mcdi.INVALID_ARG
