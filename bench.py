@@ -206,7 +206,7 @@ def run_gpu(args, rank, world):
     # convolutions' epilogues, the level-2 one as its own kernel; the G-buffer is rasterised: depth-buffer
     # clear, raster, resolve)
     n_launch = {"probe_cdf": 2, "bvh_build": mcdi.bvh_build_launches(sc.tris.shape[0]), "primary_cast": 3,
-                "shade_fwd": 4, "denoise_fwd": 1 + 15 + 1, "loss": 2, "denoise_bwd": 1 + 15 + 3 + 3,
+                "shade_fwd": 4, "denoise_fwd": 1 + 15 + 1, "loss": 2, "denoise_bwd": 1 + 15 + 3,
                 "shade_bwd": 1}
 
     def one_step(ev=None):

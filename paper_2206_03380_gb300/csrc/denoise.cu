@@ -71,11 +71,12 @@ UnetWeightLayout unet_weight_layout() {
 enum Act { X0, A1, CAT1, P1, A2, CAT2, P2, A3, CAT3, P3, B1, D3A, D2A, D1A, D1B, kActs };
 static const int kActC[kActs] = {16, 32, 80, 32, 48, 112, 48, 64, 160, 64, 96, 64, 48, 32, 32};
 static const int kActLvl[kActs] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 2, 1, 0, 0};
-enum Grad { GY, GD1B, GD1A, GCAT1, GD2B, GD2A, GCAT2, GD3B, GD3A, GCAT3, GB2, GB1, GP3, GE3, GA3, GP2, GE2, GA2,
-            GP1, GE1, GA1, kGrads };
-static const int kGradC[kGrads] = {16, 32, 32, 80, 48, 48, 112, 64, 64, 160, 96, 96, 64, 64, 64, 48, 48, 48,
-                                   32, 32, 32};
-static const int kGradLvl[kGrads] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0};
+// (the gradient at each pool's output is never stored: the convolution that computes it routes it through
+// the pool into g_E directly, kDgradPoolBwd)
+enum Grad { GY, GD1B, GD1A, GCAT1, GD2B, GD2A, GCAT2, GD3B, GD3A, GCAT3, GB2, GB1, GE3, GA3, GE2, GA2, GE1, GA1,
+            kGrads };
+static const int kGradC[kGrads] = {16, 32, 32, 80, 48, 48, 112, 64, 64, 160, 96, 96, 64, 64, 48, 48, 32, 32};
+static const int kGradLvl[kGrads] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
 
 static size_t level_pixels(int n, int H, int W, int l) { return (size_t)n * (H >> l) * (W >> l); }
 
@@ -282,48 +283,6 @@ __global__ void up2_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __rest
     warp_amax(amax, m);
 }
 
-// gradient of an encoder output E (stored in cat at channel offset ecoff) that
-// feeds both the skip slice and the 2x2 max-pool: g_E = (g_cat skip slice +
-// pool gradient routed to the window's first maximum) * [E > 0].  One thread
-// per 2x2 window and 8-channel group reads the window once.
-__global__ void pool_bwd_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ cat, int Ctot, int ecoff,
-                                int C, const bf16* __restrict__ gpool, int n, int H, int W, bf16* __restrict__ gE,
-                                unsigned* amax) {
-    pdl_prologue();
-    const int Ho = H >> 1, Wo = W >> 1;
-    int img, g, yo, xo;
-    float m = 0.0f;
-    if (split_index((long long)blockIdx.x * blockDim.x + threadIdx.x, C >> 3, Ho, Wo, &img, &g, &yo, &xo, n)) {
-        const int G = Ctot >> 3, ge = (ecoff >> 3) + g;
-        const size_t w0 = poff(img, G, ge, H, W, 2 * yo, 2 * xo);
-        float win[4][8], gs[4][8], gp[8];
-        for (int k = 0; k < 4; ++k) {
-            const size_t o = w0 + ((size_t)(k >> 1) * W + (k & 1)) * 8;
-            ld8(cat + o, win[k]);
-            ld8(gcat + o, gs[k]);
-        }
-        ld8(gpool + poff(img, C >> 3, g, Ho, Wo, yo, xo), gp);
-        int arg[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            arg[c] = 0;
-            for (int k = 1; k < 4; ++k)
-                if (win[k][c] > win[arg[c]][c]) arg[c] = k;
-        }
-        const size_t e0 = poff(img, C >> 3, g, H, W, 2 * yo, 2 * xo);
-        for (int k = 0; k < 4; ++k) {
-            float out[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float v = gs[k][c] + (arg[c] == k ? gp[c] : 0.0f);
-                out[c] = win[k][c] > 0.0f ? v : 0.0f;
-            }
-            st8(gE + e0 + ((size_t)(k >> 1) * W + (k & 1)) * 8, out);
-            m = max8(m, out);
-        }
-    }
-    warp_amax(amax, m);
-}
 
 // fp32 [co][ci][3][3] + [co] (the plan's parameters, concatenated) -> packed
 // BF16 K-major forward weights [co_pad][tap][ci_pad], flipped transposed
@@ -505,10 +464,11 @@ struct PoolTo {  // a 2x2 max-pool of the convolution's output, into tensor `slo
 static cudaError_t run_conv(Unet& u, int level, const bf16* x, int x_slot, int cin_pad, Wsel w, const float* bias,
                             int cout_pad, int cout_valid, int mode, int relu, bf16* out, int out_slot, int out_ctotal,
                             int out_coff, float4* out_f32, const bf16* mask, int mask_ctotal, int mask_coff,
-                            cudaStream_t s, const char** why, PoolTo pool = PoolTo{}) {
+                            cudaStream_t s, const char** why, PoolTo pool = PoolTo{}, const bf16* gskip = nullptr) {
     const int Hl = u.H >> level, Wl = u.W >> level;
     ConvDesc d = conv_desc(u.n, Hl, Wl, cin_pad, 2 * cin_pad, bias, cout_pad, cout_valid, mode, relu, out, out_ctotal,
                            out_coff, out_f32, mask, mask_ctotal, mask_coff, u.err);
+    d.p.gskip = gskip;
     d.p.out_amax = u.out(out_slot);
     const void* xin = x;
     const void* win = w.dgrad ? (const void*)wf_of(u, w.i) : (const void*)wk_of(u, w.i);
@@ -673,14 +633,6 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
         launch_k(up2_bwd_kernel, blocks_for(work, 256), 256, 0, s, gcat, cat, Ctot, C, n, Hl, Wl, G(glow), u.out(glow));
         return cudaGetLastError();
     };
-    auto pool_bwd = [&](const bf16* gcat, const bf16* cat, int Ctot, int ecoff, int C, const bf16* gpool, int level,
-                        int gE) {
-        const int Hl = H >> level, Wl = W >> level;
-        const long long work = (long long)n * (Hl / 2) * (Wl / 2) * (C / 8);
-        launch_k(pool_bwd_kernel, blocks_for(work, 256), 256, 0, s, gcat, cat, Ctot, ecoff, C, gpool, n, Hl, Wl, G(gE),
-                 u.out(gE));
-        return cudaGetLastError();
-    };
     // out (32 -> 3): dgrad through the ReLU of dec1b
     CHECK(run_conv(u, 0, G(GY), GY, 16, Wsel{14, true}, nullptr, 32, 32, kDgradMask, 0, G(GD1B), GD1B, 32, 0, nullptr,
                    A(D1B), 32, 0, s, why));
@@ -701,19 +653,17 @@ cudaError_t launch_unet_bwd(const void* weights, int precision, int n, int H, in
     CHECK(up_bwd(G(GCAT3), A(CAT3), 160, 96, 3, GB2));
     CHECK(run_conv(u, 3, G(GB2), GB2, 96, Wsel{7, true}, nullptr, 96, 96, kDgradMask, 0, G(GB1), GB1, 96, 0, nullptr,
                    A(B1), 96, 0, s, why));
-    CHECK(run_conv(u, 3, G(GB1), GB1, 96, Wsel{6, true}, nullptr, 64, 64, kDgradPlain, 0, G(GP3), -1, 64, 0, nullptr,
-                   nullptr, 0, 0, s, why));
-    CHECK(pool_bwd(G(GCAT3), A(CAT3), 160, 96, 64, G(GP3), 2, GE3));
+    // the input gradient of the level-2 pool, routed through the pool into g_E3 by the epilogue
+    CHECK(run_conv(u, 3, G(GB1), GB1, 96, Wsel{6, true}, nullptr, 64, 64, kDgradPoolBwd, 0, G(GE3), GE3, 64, 0, nullptr,
+                   A(CAT3), 160, 96, s, why, PoolTo{}, G(GCAT3)));
     CHECK(run_conv(u, 2, G(GE3), GE3, 64, Wsel{5, true}, nullptr, 64, 64, kDgradMask, 0, G(GA3), GA3, 64, 0, nullptr,
                    A(A3), 64, 0, s, why));
-    CHECK(run_conv(u, 2, G(GA3), GA3, 64, Wsel{4, true}, nullptr, 48, 48, kDgradPlain, 0, G(GP2), -1, 48, 0, nullptr,
-                   nullptr, 0, 0, s, why));
-    CHECK(pool_bwd(G(GCAT2), A(CAT2), 112, 64, 48, G(GP2), 1, GE2));
+    CHECK(run_conv(u, 2, G(GA3), GA3, 64, Wsel{4, true}, nullptr, 48, 48, kDgradPoolBwd, 0, G(GE2), GE2, 48, 0, nullptr,
+                   A(CAT2), 112, 64, s, why, PoolTo{}, G(GCAT2)));
     CHECK(run_conv(u, 1, G(GE2), GE2, 48, Wsel{3, true}, nullptr, 48, 48, kDgradMask, 0, G(GA2), GA2, 48, 0, nullptr,
                    A(A2), 48, 0, s, why));
-    CHECK(run_conv(u, 1, G(GA2), GA2, 48, Wsel{2, true}, nullptr, 32, 32, kDgradPlain, 0, G(GP1), -1, 32, 0, nullptr,
-                   nullptr, 0, 0, s, why));
-    CHECK(pool_bwd(G(GCAT1), A(CAT1), 80, 48, 32, G(GP1), 0, GE1));
+    CHECK(run_conv(u, 1, G(GA2), GA2, 48, Wsel{2, true}, nullptr, 32, 32, kDgradPoolBwd, 0, G(GE1), GE1, 32, 0, nullptr,
+                   A(CAT1), 80, 48, s, why, PoolTo{}, G(GCAT1)));
     CHECK(run_conv(u, 0, G(GE1), GE1, 32, Wsel{1, true}, nullptr, 32, 32, kDgradMask, 0, G(GA1), GA1, 32, 0, nullptr,
                    A(A1), 32, 0, s, why));
     // the input gradient of the term channels (0..2) straight out of the last convolution's epilogue, as float4

@@ -145,6 +145,7 @@ __device__ __forceinline__ void load_mask16(const ConvParams& p, int c0, int img
 
 // bias / activation / mask and store of 16 output channels (two 8-channel
 // groups) of one pixel; pre: the pixel's mask words are already in (ma, mb)
+template <bool kPoolBwd>
 __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* v, int c0, int img, int x, int y,
                                            const float* bias16, float dq, float* amax, bool pre = false,
                                            uint4 ma = uint4{}, uint4 mb = uint4{}, uint32_t* keep = nullptr) {
@@ -152,6 +153,52 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]) * dq;
     const size_t hw = (size_t)p.H * p.W;
+    if constexpr (kPoolBwd) {  // the instantiation for kDgradPoolBwd (its loads would crowd the others' registers)
+        // (y, x) is a pooled pixel: its window is (2y + dy, 2x + dx) at twice the size
+        const int H2 = 2 * p.H, W2 = 2 * p.W;
+        auto bf = [](uint32_t w, int hi) {  // BF16 half of a packed pair as float
+            return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+        };
+#pragma unroll
+        for (int gg = 0; gg < 2; ++gg) {
+            const size_t e0 =
+                plane_off(img, p.mask_ctotal >> 3, ((p.mask_coff + c0) >> 3) + gg, H2, W2, 2 * y, 2 * x);
+            uint32_t we[4][4];  // the window's E values, packed BF16 pairs
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 t = __ldg(reinterpret_cast<const uint4*>(p.mask + e0 + ((size_t)(k >> 1) * W2 + (k & 1)) * 8));
+                we[k][0] = t.x, we[k][1] = t.y, we[k][2] = t.z, we[k][3] = t.w;
+            }
+            int arg[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {  // the window's first maximum, in window order
+                arg[c] = 0;
+                float best = bf(we[0][c >> 1], c & 1);
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    const float e = bf(we[k][c >> 1], c & 1);
+                    if (e > best) best = e, arg[c] = k;
+                }
+            }
+            const size_t o0 = plane_off(img, p.out_ctotal >> 3, ((p.out_coff + c0) >> 3) + gg, H2, W2, 2 * y, 2 * x);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const size_t off = ((size_t)(k >> 1) * W2 + (k & 1)) * 8;
+                const uint4 t = __ldg(reinterpret_cast<const uint4*>(p.gskip + e0 + off));
+                const uint32_t wg[4] = {t.x, t.y, t.z, t.w};
+                float o[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float gp = __bfloat162float(__float2bfloat16_rn(f[8 * gg + c]));  // as stored unfused
+                    const float v = bf(wg[c >> 1], c & 1) + (arg[c] == k ? gp : 0.0f);
+                    o[c] = bf(we[k][c >> 1], c & 1) > 0.0f ? v : 0.0f;
+                    *amax = fmaxf(*amax, fabsf(o[c]));
+                }
+                store8_bf16(p.out + o0 + off, o);
+            }
+        }
+        return;
+    } else {
     if (p.mode == kDgradMask || p.mode == kDgradPlain) {
         if (p.mode == kDgradMask) {
             uint4 mm[2] = {ma, mb};
@@ -204,6 +251,7 @@ __device__ __forceinline__ void epilogue16(const ConvParams& p, const uint32_t* 
         store8_bf16(o, f);
         store8_bf16(o + hw * 8, f + 8);
     }
+    }
 }
 
 // Publish a thread's running max |value| of the stored output: rounded to BF16
@@ -223,7 +271,7 @@ __device__ __forceinline__ float dequant_factor(const ConvParams& p) {
     return (__ldg(p.x_amax) * (1.0f / 448.0f)) * (__ldg(p.w_amax) * (1.0f / 448.0f));
 }
 
-template <bool FP8>
+template <bool FP8, bool PB>
 __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_x,
                                                                const __grid_constant__ CUtensorMap tmap_w,
                                                                const ConvParams p) {
@@ -332,7 +380,8 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(const __grid_cons
         uint32_t v[16];
         // collective load of 16 accumulator columns of this warp's 32 lanes
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (valid && c0 < p.cout_valid) epilogue16(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr, dq, &amax);
+        if (valid && c0 < p.cout_valid)
+            epilogue16<PB>(p, v, c0, img, x, y, p.bias ? p.bias + c0 : nullptr, dq, &amax);
         __syncwarp();
     }
     publish_amax(p.out_amax, amax, 0xffffffffu);
@@ -383,7 +432,9 @@ constexpr int kHaloW = 130;
 constexpr int kMaxRows = 4;
 
 
-template <int R, bool FP8, bool MP, bool PL>
+// EV: the epilogue variant, 0 plain, 1 also the 2x2 max-pool of the output (kStore), 2 the pool
+// gradient routed through the pool (kDgradPoolBwd)
+template <int R, bool FP8, bool MP, int EV>
 __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmap_wh,
                                                                    const ConvParams p, const RowPlan rp) {
     // The setup that reads nothing the preceding kernel writes (barriers, bias, tensor memory and the
@@ -603,8 +654,8 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
         // 2x2 max-pool of the stored values: the two pixels of a window are neighbouring
         // lanes, its two rows consecutive rows of this thread (R even, tiles start on even
         // rows and columns); the maxima are taken on the stored BF16 values
-        // (PL: the instantiation for the convolutions that feed a pooling layer)
-        const bool pool = PL && R % 2 == 0 && p.pool_out != nullptr && p.mode == kStore && Nc <= 2 * cstep;
+        // (EV 1: the instantiation for the convolutions that feed a pooling layer)
+        const bool pool = EV == 1 && R % 2 == 0 && p.pool_out != nullptr && p.mode == kStore && Nc <= 2 * cstep;
         float pool_amax = 0.0f;
         uint32_t ha[8], hb[8];  // the even row's stored values of chunks c0 / c1, packed BF16 pairs
         int i = 0;
@@ -622,7 +673,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
             }
             tc_fence_after();
             const float dq = dequant_factor(p);
-            constexpr int kRowUnroll = MP || PL ? 1 : R;  // prefetch / pool registers leave no room to unroll
+            constexpr int kRowUnroll = MP || EV != 0 ? 1 : R;  // prefetch / pool registers leave no room to unroll
 #pragma unroll kRowUnroll
             for (int r = 0; r < R; ++r) {
                 const int y = y0 + r;
@@ -639,8 +690,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) conv_tc_rows_kernel(const __gr
                     tmem_wait_ld();
                     uint32_t ka[8], kb[8];
                     const bool va = valid && n0 + c0 < p.cout_valid, vb = two && valid && n0 + c1 < p.cout_valid;
-                    if (va) epilogue16(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, pref, ca0, ca1, ka);
-                    if (vb) epilogue16(p, v + 16, n0 + c1, img, x, y, s_bias + c1, dq, &amax, pref, cb0, cb1, kb);
+                    if (va) epilogue16<EV == 2>(p, v, n0 + c0, img, x, y, s_bias + c0, dq, &amax, pref, ca0, ca1, ka);
+                    if (vb)
+                        epilogue16<EV == 2>(p, v + 16, n0 + c1, img, x, y, s_bias + c1, dq, &amax, pref, cb0, cb1, kb);
                     if (pool) {
                         if ((r & 1) == 0) {
 #pragma unroll
@@ -743,7 +795,7 @@ const DeviceLimits& device_limits() {
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false, false, false>) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv_tc_rows_kernel<4, false, false, 0>) != cudaSuccess ||
             optin <= (int)fa.sharedSizeBytes) {
             L.sms = 0;
             return;
@@ -907,25 +959,25 @@ bool conv_make_desc(ConvDesc* d, const void* x, const void* w, const char** why)
     return true;
 }
 
-template <bool FP8, bool MP, bool PL>
+template <bool FP8, bool MP, int EV>
 static void set_rows_smem(int bytes, cudaError_t* err) {
-    const void* fs[3] = {(const void*)conv_tc_rows_kernel<1, FP8, MP, PL>,
-                         (const void*)conv_tc_rows_kernel<2, FP8, MP, PL>,
-                         (const void*)conv_tc_rows_kernel<4, FP8, MP, PL>};
+    const void* fs[3] = {(const void*)conv_tc_rows_kernel<1, FP8, MP, EV>,
+                         (const void*)conv_tc_rows_kernel<2, FP8, MP, EV>,
+                         (const void*)conv_tc_rows_kernel<4, FP8, MP, EV>};
     for (const void* f : fs)
         if (*err == cudaSuccess && bytes > 0)
             *err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <bool FP8, bool MP, bool PL>
+template <bool FP8, bool MP, int EV>
 static void launch_rows(const ConvDesc& d, cudaStream_t stream) {
     const dim3 g(d.rp.grid), t(kRowThreads);
     const size_t sm = d.rp.smem_bytes;
     if (d.rp.rows == 4)
-        launch_k_dependent(conv_tc_rows_kernel<4, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+        launch_k_dependent(conv_tc_rows_kernel<4, FP8, MP, EV>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
     else if (d.rp.rows == 2)
-        launch_k_dependent(conv_tc_rows_kernel<2, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
-    else launch_k_dependent(conv_tc_rows_kernel<1, FP8, MP, PL>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+        launch_k_dependent(conv_tc_rows_kernel<2, FP8, MP, EV>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
+    else launch_k_dependent(conv_tc_rows_kernel<1, FP8, MP, EV>, g, t, sm, stream, d.tmap_wh, d.p, d.rp);
 }
 
 bool conv_mask_prefetch(const ConvDesc& d) { return d.rows_form && d.p.mode == kDgradMask && d.rp.nc <= 64; }
@@ -936,39 +988,49 @@ cudaError_t conv_launch(const ConvDesc& d, cudaStream_t stream) {
     std::call_once(once, [] {
         const int lim = (int)device_limits().rows_smem_max;
         const int tile = (int)conv_smem_bytes(256);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute((const void*)conv_tc_kernel<false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, tile);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute((const void*)conv_tc_kernel<true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, tile);
-        set_rows_smem<false, false, false>(lim, &attr_err);
-        set_rows_smem<true, false, false>(lim, &attr_err);
-        set_rows_smem<false, true, false>(lim, &attr_err);
-        set_rows_smem<true, true, false>(lim, &attr_err);
-        set_rows_smem<false, false, true>(lim, &attr_err);
-        set_rows_smem<true, false, true>(lim, &attr_err);
+        const void* generic[4] = {(const void*)conv_tc_kernel<false, false>, (const void*)conv_tc_kernel<true, false>,
+                                  (const void*)conv_tc_kernel<false, true>, (const void*)conv_tc_kernel<true, true>};
+        for (const void* f : generic)
+            if (attr_err == cudaSuccess)
+                attr_err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tile);
+        set_rows_smem<false, false, 0>(lim, &attr_err);
+        set_rows_smem<true, false, 0>(lim, &attr_err);
+        set_rows_smem<false, true, 0>(lim, &attr_err);
+        set_rows_smem<true, true, 0>(lim, &attr_err);
+        set_rows_smem<false, false, 1>(lim, &attr_err);
+        set_rows_smem<true, false, 1>(lim, &attr_err);
+        set_rows_smem<false, false, 2>(lim, &attr_err);
+        set_rows_smem<true, false, 2>(lim, &attr_err);
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (d.rows_form) {
         // masked input gradients whose mask words fit the prefetch registers take the prefetching variant
         const bool mp = conv_mask_prefetch(d);
         const bool pl = d.p.pool_out != nullptr;  // conv_make_desc keeps it only where the plan can pool
+        const bool pb = d.p.mode == kDgradPoolBwd;
         if (d.p.fp8) {
-            if (mp) launch_rows<true, true, false>(d, stream);
-            else if (pl) launch_rows<true, false, true>(d, stream);
-            else launch_rows<true, false, false>(d, stream);
+            if (mp) launch_rows<true, true, 0>(d, stream);
+            else if (pl) launch_rows<true, false, 1>(d, stream);
+            else if (pb) launch_rows<true, false, 2>(d, stream);
+            else launch_rows<true, false, 0>(d, stream);
         } else {
-            if (mp) launch_rows<false, true, false>(d, stream);
-            else if (pl) launch_rows<false, false, true>(d, stream);
-            else launch_rows<false, false, false>(d, stream);
+            if (mp) launch_rows<false, true, 0>(d, stream);
+            else if (pl) launch_rows<false, false, 1>(d, stream);
+            else if (pb) launch_rows<false, false, 2>(d, stream);
+            else launch_rows<false, false, 0>(d, stream);
         }
         return cudaGetLastError();
     }
     const int n_tiles = d.p.n_img * d.p.tiles_y * d.p.tiles_x;
     const size_t smem = conv_smem_bytes(d.p.cout_pad);
-    if (d.p.fp8) launch_k(conv_tc_kernel<true>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
-    else launch_k(conv_tc_kernel<false>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
+    const bool pb = d.p.mode == kDgradPoolBwd;
+    if (d.p.fp8) {
+        if (pb) launch_k(conv_tc_kernel<true, true>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
+        else launch_k(conv_tc_kernel<true, false>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
+    } else {
+        if (pb) launch_k(conv_tc_kernel<false, true>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
+        else launch_k(conv_tc_kernel<false, false>, n_tiles, kConvThreads, smem, stream, d.tmap_x, d.tmap_w, d.p);
+    }
     return cudaGetLastError();
 }
 

@@ -19,6 +19,10 @@ enum ConvEpilogue : int {
     kStoreF32 = 2,    // out float4 = (acc + bias) channels 0..2, w = 0 (final layer)
     kDgradMask = 3,   // out = bf16(acc * [mask > 0])  (input gradient through a ReLU)
     kDgradPlain = 4,  // out = bf16(acc)
+    // input gradient of a 2x2 max-pool's output, routed on: with gp = bf16(acc) and E (`mask`, twice the
+    // size) the pooled tensor, out (twice the size) = (skip gradient `gskip` + gp at the window's first
+    // maximum) * [E > 0] for the four pixels of the window
+    kDgradPoolBwd = 5,
 };
 
 struct ConvParams {
@@ -39,8 +43,9 @@ struct ConvParams {
     __nv_bfloat16* out;        // 8-channel planes, out_ctotal channels
     int out_ctotal, out_coff;
     float4* out_f32;           // [n_img][H][W] (kStoreF32)
-    const __nv_bfloat16* mask; // 8-channel planes, same spatial size as the output
+    const __nv_bfloat16* mask; // 8-channel planes, same spatial size as the output (kDgradPoolBwd: twice it)
     int mask_ctotal, mask_coff;
+    const __nv_bfloat16* gskip; // kDgradPoolBwd: the skip gradient, laid out as `mask`
     unsigned* err;             // device error word (set on a wait timeout)
     unsigned* out_amax;        // nullable: max |stored value| of the output (float bits), for E4M3 consumers
     // nullable (kStore in the row-tile form with an even number of rows per tile, at most 64 channels per
