@@ -152,8 +152,9 @@ mcdi_status mcdi_build_bvh(const float* verts, int n_verts, const int* tris, int
 mcdi_status mcdi_bvh_build_launches(int n_tris, int* launches) {
     REQUIRE(n_tris >= 1 && n_tris <= (1 << 27), "n_tris must be in [1, 2^27], got %d", n_tris);
     REQUIRE(launches != nullptr, "launches is NULL");
-    // bounds (2), Morton codes, the sort, leaf records, hierarchy + boxes (1 or 2), depth-first copy
-    *launches = 3 + (mcdi::bvh_tile_sort(n_tris) ? 1 : 3) * mcdi::kSortPasses + 1 + (n_tris > 1 ? 2 : 1) + 1;
+    // bounds (2), Morton codes, the sort, leaf records with the hierarchy, boxes, depth-first copy (a single
+    // triangle: leaf record, root)
+    *launches = 3 + (mcdi::bvh_tile_sort(n_tris) ? 1 : 3) * mcdi::kSortPasses + 2 + 1;
     return ok();
 }
 

@@ -402,12 +402,10 @@ __device__ __forceinline__ int common_prefix(const uint32_t* __restrict__ keys, 
     return __clz(a ^ b);
 }
 
-__global__ void __launch_bounds__(256) karras_kernel(const uint32_t* __restrict__ keys, int n,
-                                                     BvhNode* __restrict__ nodes, int* __restrict__ parent_int,
-                                                     int* __restrict__ parent_leaf) {
-    pdl_prologue();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+// internal node i (0 <= i < n - 1) of the hierarchy over the sorted keys
+__device__ __forceinline__ void karras_node(const uint32_t* __restrict__ keys, int n, int i,
+                                            BvhNode* __restrict__ nodes, int* __restrict__ parent_int,
+                                            int* __restrict__ parent_leaf) {
     const int d = (common_prefix(keys, n, i, i + 1) - common_prefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     const int dmin = common_prefix(keys, n, i, i - d);
     int lmax = 2;
@@ -434,14 +432,11 @@ __global__ void __launch_bounds__(256) karras_kernel(const uint32_t* __restrict_
     if (i == 0) parent_int[0] = -1;
 }
 
-// triangle records in leaf order + leaf boxes + cleared arrival counters
-__global__ void __launch_bounds__(256) leaf_kernel(const float* __restrict__ verts, int n_verts,
-                                                   const int* __restrict__ tris, int n,
-                                                   const uint32_t* __restrict__ order, TriRecord* __restrict__ recs,
-                                                   float4* __restrict__ box_leaf, uint32_t* __restrict__ flags) {
-    pdl_prologue();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+// triangle record, leaf box and cleared arrival counter of leaf position p (0 <= p < n)
+__device__ __forceinline__ void leaf_record(const float* __restrict__ verts, int n_verts,
+                                            const int* __restrict__ tris, int n, int p,
+                                            const uint32_t* __restrict__ order, TriRecord* __restrict__ recs,
+                                            float4* __restrict__ box_leaf, uint32_t* __restrict__ flags) {
     if (p < n - 1) flags[p] = 0u;
     const int k = (int)order[p];
     f3 a, b, c;
@@ -463,6 +458,30 @@ __global__ void __launch_bounds__(256) leaf_kernel(const float* __restrict__ ver
     }
     box_leaf[2 * (size_t)p] = make_float4(lo[0], lo[1], lo[2], 0.f);
     box_leaf[2 * (size_t)p + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+}
+
+// triangle records in leaf order + leaf boxes + cleared arrival counters
+__global__ void __launch_bounds__(256) leaf_kernel(const float* __restrict__ verts, int n_verts,
+                                                   const int* __restrict__ tris, int n,
+                                                   const uint32_t* __restrict__ order, TriRecord* __restrict__ recs,
+                                                   float4* __restrict__ box_leaf, uint32_t* __restrict__ flags) {
+    pdl_prologue();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) leaf_record(verts, n_verts, tris, n, p, order, recs, box_leaf, flags);
+}
+
+// the leaf records and the hierarchy in one launch (they read different outputs of the sort)
+__global__ void __launch_bounds__(256) leaf_karras_kernel(const float* __restrict__ verts, int n_verts,
+                                                          const int* __restrict__ tris, int n,
+                                                          const uint32_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ order,
+                                                          TriRecord* __restrict__ recs, float4* __restrict__ box_leaf,
+                                                          uint32_t* __restrict__ flags, BvhNode* __restrict__ nodes,
+                                                          int* __restrict__ parent_int, int* __restrict__ parent_leaf) {
+    pdl_prologue();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n - 1) karras_node(keys, n, p, nodes, parent_int, parent_leaf);
+    if (p < n) leaf_record(verts, n_verts, tris, n, p, order, recs, box_leaf, flags);
 }
 
 __device__ __forceinline__ void child_box(int link, const float4* box_int, const float4* box_leaf, float4& lo,
@@ -754,11 +773,12 @@ cudaError_t launch_build_bvh(const float* verts, int n_verts, const int* tris, i
         }
         cur ^= 1;
     }
-    launch_k(leaf_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, vals[cur], recs, box_leaf, flags);
     if (n == 1) {
+        launch_k(leaf_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, vals[cur], recs, box_leaf, flags);
         launch_k(single_leaf_root_kernel, 1, 1, 0, stream, nodes, box_leaf);
     } else {
-        launch_k(karras_kernel, (n - 1 + 255) / 256, 256, 0, stream, keys[cur], n, nodes, parent_int, parent_leaf);
+        launch_k(leaf_karras_kernel, g256, 256, 0, stream, verts, n_verts, tris, n, keys[cur], vals[cur], recs,
+                 box_leaf, flags, nodes, parent_int, parent_leaf);
         launch_k(refit_kernel, g256, 256, 0, stream, n, nodes, parent_int, parent_leaf, flags, box_int, box_leaf);
     }
     return launch_threaded(n, nodes_v, nodes, parent_int, parent_leaf, box_int, box_leaf, stream);

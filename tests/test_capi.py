@@ -151,8 +151,8 @@ def test_bvh_build_launch_count_without_gpu(lib):
     for n in (1, 2, 198_164, 262_144, 262_145, 1_289_216):
         assert lib.mcdi_bvh_build_launches(n, C.byref(out)) == mcdi.OK
         counts[n] = out.value
-    # bounds (2) + Morton + 3 passes (one kernel each up to 262,144 triangles, else three) + leaf records
-    # + hierarchy and boxes (one launch for a single triangle) + depth-first copy
-    assert counts == {1: 9, 2: 10, 198_164: 10, 262_144: 10, 262_145: 16, 1_289_216: 16}
+    # bounds (2) + Morton + 3 passes (one kernel each up to 262,144 triangles, else three) + leaf records with
+    # the hierarchy + boxes (a single triangle: leaf record + root) + depth-first copy
+    assert counts == {1: 9, 2: 9, 198_164: 9, 262_144: 9, 262_145: 15, 1_289_216: 15}
     assert lib.mcdi_bvh_build_launches(0, C.byref(out)) == mcdi.INVALID_ARG
     assert lib.mcdi_bvh_build_launches(5, None) == mcdi.INVALID_ARG

@@ -61,6 +61,6 @@ def test_leaf_order_is_the_stable_morton_sort(cuda_lib, n):
     np.testing.assert_array_equal(order, expect)
     launches = mcdi.bvh_build_launches(n)
     if n <= TILE_SORT_MAX:
-        assert launches == 3 + 3 + 1 + (2 if n > 1 else 1) + 1  # one kernel per pass
+        assert launches == 3 + 3 + 2 + 1  # one kernel per pass
     else:
-        assert launches == 3 + 9 + 1 + 2 + 1
+        assert launches == 3 + 9 + 2 + 1
