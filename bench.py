@@ -808,7 +808,7 @@ def omp_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-def cpu_baseline(sc, n_pix=1024):
+def cpu_baseline(sc, n_pix=8192):
     import oracle
 
     orc = oracle
@@ -861,7 +861,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mcdi", choices=["mcdi", "reference"])
-    ap.add_argument("--cpu-pixels", type=int, default=1024)
+    ap.add_argument("--cpu-pixels", type=int, default=8192)
     ap.add_argument("--ref-pixels", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
