@@ -17,17 +17,22 @@ namespace {
 constexpr int kLossThreads = 256;
 constexpr int kLossMaxBlocks = 1024;
 
-__device__ __forceinline__ float srgb(float y) {
-    return y <= 0.0031308f ? 12.92f * y : 1.055f * powf(y, 1.0f / 2.4f) - 0.055f;
-}
-
-// T(x) and dT/dx (0 below zero, where the clamp holds the value)
+// T(x) and dT/dx (0 below zero, where the clamp holds the value); one power serves both:
+// Gamma'(y) = (1.055 / 2.4) y^(1/2.4) / y on the power branch
 __device__ __forceinline__ float tonemap(float x, float* slope) {
     const float xc = fmaxf(x, 0.0f);
     const float y = log1pf(xc);
-    const float dg = y <= 0.0031308f ? 12.92f : (1.055f / 2.4f) * powf(y, 1.0f / 2.4f - 1.0f);
+    float t, dg;
+    if (y <= 0.0031308f) {
+        t = 12.92f * y;
+        dg = 12.92f;
+    } else {
+        const float p = powf(y, 1.0f / 2.4f);
+        t = 1.055f * p - 0.055f;
+        dg = (1.055f / 2.4f) * (p / y);
+    }
     *slope = x >= 0.0f ? dg / (xc + 1.0f) : 0.0f;
-    return srgb(y);
+    return t;
 }
 
 __device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
