@@ -648,7 +648,9 @@ __device__ __forceinline__ float wide_min_step(const float4* box_int, const floa
 // Hence dfs = 2 f + (left turns on the path from the root), and the subtree
 // of 2 (l - f) + 1 nodes ends just before skip = dfs + 2 (l - f) + 1.
 // The same walk gives each internal node's depth: nodes at even depth also
-// write their four-wide node, the others zero their slot.
+// write their four-wide node, the others zero their slot.  A leaf's path is
+// its parent's plus one step, so each internal node also writes the entries
+// of its leaf children (one walk per internal node, none per leaf).
 __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __restrict__ nodes,
                                                        const int* __restrict__ parent_int,
                                                        const int* __restrict__ parent_leaf,
@@ -661,31 +663,9 @@ __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __r
     // zero the alignment gaps before the arrays, so that equal meshes give equal bytes
     if (v < gap_vec4) gap[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v < wgap_vec4) wgap[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (v >= 2 * n - 1) return;
-    const bool leaf = v >= n - 1;
-    const int k = leaf ? v - (n - 1) : v;  // leaf position or internal node index
-    int f = k, l = k, link = leaf ? ~k : k, par = -1;
-    float4 lo, hi;
-    if (leaf) {
-        lo = box_leaf[2 * (size_t)k];
-        hi = box_leaf[2 * (size_t)k + 1];
-        if (n > 1) par = parent_leaf[k];
-    } else {
-        const int4 d = nodes[k].d;
-        f = d.z;
-        l = d.w;
-        lo = box_int[2 * (size_t)k];
-        hi = box_int[2 * (size_t)k + 1];
-        par = parent_int[k];
-    }
-    int lefts = 0, depth = 0;
-    for (int steps = 0; par >= 0 && steps < n; ++steps) {  // the path to the root is shorter than n
-        if (nodes[par].d.x == link) ++lefts;
-        ++depth;
-        link = par;
-        par = parent_int[par];
-    }
-    if (n == 1) {  // the four-wide root of a single triangle: one leaf child
+    if (n == 1) {  // one triangle: a single leaf, and a four-wide root with that one leaf child
+        if (v != 0) return;
+        const float4 lo = box_leaf[0], hi = box_leaf[1];
         WideNode w;
         const float s_min = wide_min_step(box_int, box_leaf, 1);
         WideAxis ax[3] = {wide_axis(lo.x, hi.x, s_min), wide_axis(lo.y, hi.y, s_min), wide_axis(lo.z, hi.z, s_min)};
@@ -701,16 +681,45 @@ __global__ void __launch_bounds__(256) threaded_kernel(int n, const BvhNode* __r
                           __uint_as_float(qh[2]));
         w.d = make_int4(~0, INT_MIN, INT_MIN, INT_MIN);
         wide[0] = w;
-    } else if (!leaf) {
-        if ((depth & 1) == 0) write_wide_node(k, nodes, box_int, box_leaf, wide_min_step(box_int, box_leaf, n), wide);
-        else wide[k] = WideNode{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                                make_float4(0.f, 0.f, 0.f, 0.f), make_int4(0, 0, 0, 0)};
+        out[0].lo = make_float4(lo.x, lo.y, lo.z, __int_as_float(1));
+        out[0].hi = make_float4(hi.x, hi.y, hi.z, __int_as_float(0));
+        return;
     }
+    // One thread per internal node: its path to the root gives its depth and left turns; a leaf child's
+    // path is the node's plus one step (a left turn for the first child), so the node writes those too.
+    if (v >= n - 1) return;
+    const int k = v;
+    const int4 d = nodes[k].d;
+    const int f = d.z, l = d.w;
+    int link = k, par = parent_int[k];
+    int lefts = 0, depth = 0;
+    for (int steps = 0; par >= 0 && steps < n; ++steps) {  // the path to the root is shorter than n
+        if (nodes[par].d.x == link) ++lefts;
+        ++depth;
+        link = par;
+        par = parent_int[par];
+    }
+    if ((depth & 1) == 0) write_wide_node(k, nodes, box_int, box_leaf, wide_min_step(box_int, box_leaf, n), wide);
+    else wide[k] = WideNode{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                            make_float4(0.f, 0.f, 0.f, 0.f), make_int4(0, 0, 0, 0)};
     const int dfs = 2 * f + lefts;
     const int skip = dfs + 2 * (l - f) + 1;
-    if (dfs < 0 || dfs >= 2 * n - 1) return;  // unreachable for a well-formed tree
-    out[dfs].lo = make_float4(lo.x, lo.y, lo.z, __int_as_float(skip));
-    out[dfs].hi = make_float4(hi.x, hi.y, hi.z, __int_as_float(leaf ? k : -1));
+    if (dfs >= 0 && dfs < 2 * n - 1) {  // always, for a well-formed tree
+        const float4 lo = box_int[2 * (size_t)k], hi = box_int[2 * (size_t)k + 1];
+        out[dfs].lo = make_float4(lo.x, lo.y, lo.z, __int_as_float(skip));
+        out[dfs].hi = make_float4(hi.x, hi.y, hi.z, __int_as_float(-1));
+    }
+    const int kids[2] = {d.x, d.y};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (kids[h] >= 0) continue;
+        const int q = ~kids[h];  // leaf position: range [q, q]
+        const int dl = 2 * q + lefts + (h == 0 ? 1 : 0);
+        if (dl < 0 || dl >= 2 * n - 1) continue;
+        const float4 lo = box_leaf[2 * (size_t)q], hi = box_leaf[2 * (size_t)q + 1];
+        out[dl].lo = make_float4(lo.x, lo.y, lo.z, __int_as_float(dl + 1));
+        out[dl].hi = make_float4(hi.x, hi.y, hi.z, __int_as_float(q));
+    }
 }
 
 }  // namespace
@@ -726,8 +735,9 @@ static cudaError_t launch_threaded(int n, void* nodes_v, const BvhNode* nodes, c
     const size_t threaded_end = threaded_offset(n) + (size_t)(2 * n - 1) * sizeof(ThreadedNode);
     const int wgap_vec4 = (int)((wide_offset(n) - threaded_end) / 16);
     WideNode* wide = reinterpret_cast<WideNode*>(nb + wide_offset(n));
-    launch_k(threaded_kernel, (2 * n - 1 + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf, box_int,
-             box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn,
+    // one thread per internal node (at least 32: the alignment gaps are zeroed by the first threads)
+    launch_k(threaded_kernel, (std::max(n - 1, 32) + 255) / 256, 256, 0, stream, n, nodes, parent_int, parent_leaf,
+             box_int, box_leaf, reinterpret_cast<float4*>(nb + two_child), gap_vec4, tn,
              reinterpret_cast<float4*>(nb + threaded_end), wgap_vec4, wide);
     return cudaGetLastError();
 }
