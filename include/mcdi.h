@@ -578,6 +578,17 @@ MCDI_API mcdi_status mcdi_graph_instantiate(void* graph, void** graph_exec);
 MCDI_API mcdi_status mcdi_graph_launch(void* graph_exec, void* stream);
 MCDI_API mcdi_status mcdi_graph_destroy(void* graph_exec);
 
+/* Whether the denoiser's convolutions launched by the calling thread into a
+ * stream that is being captured keep their programmatic dependence on the
+ * kernel before them (enable != 0, the default: their tensor-memory
+ * allocation and weight load then overlap that kernel's tail in the replay)
+ * or are captured like every other kernel (0).  Graphs replayed concurrently
+ * with other work (several requests on several streams) can run better
+ * without it, since a dependent launch's blocks hold SM slots while they wait.
+ * Applies to launches made after the call, on this thread only; launches
+ * outside capture are unaffected.  Always MCDI_OK. */
+MCDI_API mcdi_status mcdi_set_graph_dependent_launch(int enable);
+
 #ifdef __cplusplus
 }
 #endif

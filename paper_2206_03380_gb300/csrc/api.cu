@@ -794,6 +794,15 @@ mcdi_status mcdi_conv3x3_e4m3(const void* x, int n_img, int H, int W, int cin_pa
 
 }  // extern "C"
 
+namespace mcdi {
+thread_local bool t_graph_dependent_launch = true;
+}
+
+mcdi_status mcdi_set_graph_dependent_launch(int enable) {
+    mcdi::t_graph_dependent_launch = enable != 0;
+    return ok();
+}
+
 // ---- CUDA graphs with per-node priorities
 mcdi_status mcdi_graph_instantiate(void* graph, void** graph_exec) {
     REQUIRE(graph != nullptr && graph_exec != nullptr, "graph / graph_exec must be non-NULL");

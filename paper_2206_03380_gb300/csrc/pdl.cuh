@@ -21,6 +21,10 @@
 
 namespace mcdi {
 
+// whether launch_k_dependent keeps the programmatic dependence in graphs this thread captures (default on;
+// mcdi_set_graph_dependent_launch)
+extern thread_local bool t_graph_dependent_launch;
+
 __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -46,7 +50,7 @@ inline cudaError_t launch_k_impl(bool dependent_in_graph, void (*kernel)(KArgs..
     unsigned n_attr = 0;
     cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(stream, &capture) != cudaSuccess) capture = cudaStreamCaptureStatusNone;
-    if (capture == cudaStreamCaptureStatusNone || dependent_in_graph) {
+    if (capture == cudaStreamCaptureStatusNone || (dependent_in_graph && t_graph_dependent_launch)) {
         attr[n_attr].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[n_attr++].val.programmaticStreamSerializationAllowed = 1;
     }

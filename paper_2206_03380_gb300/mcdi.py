@@ -46,7 +46,7 @@ EXPORTS = ["mcdi_last_error", "mcdi_version", "mcdi_build_envmap_cdf", "mcdi_bvh
            "mcdi_denoise_wgrad_bytes", "mcdi_denoise_wgrad", "mcdi_conv3x3_wgrad_bytes",
            "mcdi_conv3x3_wgrad", "mcdi_shade_mc_fwd_part", "mcdi_raster_gbuffer_part",
            "mcdi_shade_mc_bwd_span", "mcdi_graph_instantiate", "mcdi_graph_launch", "mcdi_graph_destroy",
-           "mcdi_bvh_build_launches"]
+           "mcdi_bvh_build_launches", "mcdi_set_graph_dependent_launch"]
 BF16, E4M3 = 0, 1  # denoiser operand precisions (MCDI_DENOISE_BF16, MCDI_DENOISE_E4M3)
 NOALLOC_MAX_TRIS = 65536
 
@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.mcdi_bvh_sizes.argtypes = [i, C.POINTER(sz), C.POINTER(sz), C.POINTER(sz)]
     lib.mcdi_build_bvh.restype = st
     lib.mcdi_build_bvh.argtypes = [P, i, P, i, P, P, P, sz, P]
+    lib.mcdi_set_graph_dependent_launch.restype = st
+    lib.mcdi_set_graph_dependent_launch.argtypes = [i]
     lib.mcdi_bvh_build_launches.restype = st
     lib.mcdi_bvh_build_launches.argtypes = [i, C.POINTER(i)]
     lib.mcdi_refit_bvh.restype = st
@@ -183,6 +185,11 @@ def _check(status: int, where: str):
 # ------------------------------------------------------------------ entry points
 def version() -> int:
     return load().mcdi_version()
+
+
+def set_graph_dependent_launch(enable: bool):
+    """Whether this thread's captured convolutions keep their programmatic dependence (default True)."""
+    _check(load().mcdi_set_graph_dependent_launch(1 if enable else 0), "set_graph_dependent_launch")
 
 
 def bvh_build_launches(n_tris: int) -> int:

@@ -156,3 +156,10 @@ def test_bvh_build_launch_count_without_gpu(lib):
     assert counts == {1: 9, 2: 9, 198_164: 9, 262_144: 9, 262_145: 15, 1_289_216: 15}
     assert lib.mcdi_bvh_build_launches(0, C.byref(out)) == mcdi.INVALID_ARG
     assert lib.mcdi_bvh_build_launches(5, None) == mcdi.INVALID_ARG
+
+
+def test_graph_dependent_launch_switch_without_gpu(lib):
+    from paper_2206_03380_gb300 import mcdi
+
+    assert lib.mcdi_set_graph_dependent_launch(0) == mcdi.OK
+    assert lib.mcdi_set_graph_dependent_launch(1) == mcdi.OK
