@@ -17,6 +17,19 @@ from . import mcdi
 from .scenes import Scene
 
 
+def pixel_spans(P: int, fractions) -> list:
+    """Consecutive (first, count) spans of P pixels: each fraction of P rounded to a multiple of 32 pixels (one
+    adjoint block) and cut at what is left, the last entry (None) taking the rest; together they cover
+    [0, P) once, in order.  The adjoint runs span by span so that each span's gradients can be read back while
+    the later ones run."""
+    spans, first = [], 0
+    for frac in fractions:
+        count = P - first if frac is None else min(P - first, int(round(P * frac / 32.0)) * 32)
+        spans.append((first, count))
+        first += count
+    return spans
+
+
 class ShadingPipeline:
     def __init__(self, scene: Scene, device="cuda", tau: float = 1.0, ray_eps: float = 1e-4,
                  decorrelate_bwd: bool = False, keep_mask: bool = True, wavefront: bool = True,
@@ -356,13 +369,10 @@ class ShadingPipeline:
         # priority: the block scheduler finishes a span before it starts the next one's blocks, those
         # fill the SMs while the span's last blocks drain, and a read-back waits for its own span only.
         self.g_env.zero_()
-        P = self.N * self.H * self.W
-        fr = self.bwd_span_fractions
-        if len(self._span_streams) != len(fr):
-            self._span_streams = [torch.cuda.Stream(dev, priority=-(len(fr) - 1 - k)) for k in range(len(fr))]
-        first = 0
-        for k, frac in enumerate(fr):
-            count = P - first if frac is None else min(P - first, int(round(P * frac / 32.0)) * 32)
+        spans = pixel_spans(self.N * self.H * self.W, self.bwd_span_fractions)
+        if len(self._span_streams) != len(spans):
+            self._span_streams = [torch.cuda.Stream(dev, priority=-(len(spans) - 1 - k)) for k in range(len(spans))]
+        for k, (first, count) in enumerate(spans):
             st = self._span_streams[k]
             st.wait_stream(cur)
             self.backward_span(g_cd, self.g_loss_kdout, g_cs, first, count, st)
@@ -373,8 +383,7 @@ class ShadingPipeline:
                 with torch.cuda.stream(down2):
                     for d, h in per_pixel:
                         h.view(-1, 4)[first:first + count].copy_(d.view(-1, 4)[first:first + count], non_blocking=True)
-            first += count
-        for k in range(len(fr)):
+        for k in range(len(spans)):
             cur.wait_stream(self._span_streams[k])
         ev["end"].record(cur)
         down.wait_event(ev["end"])
